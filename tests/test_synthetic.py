@@ -1,0 +1,45 @@
+"""The seeded generators: structure of the synthetic Jacobians (sorted columns, diagonal
+present, symmetric pattern, wells after the cells) and the SPE10-shaped counts."""
+import numpy as np
+
+from synthetic import box_jacobian, grid_small, grid_spe10, perturb_values, random_rhs
+
+
+def _pattern_ok(a):
+    rp, ci = a.row_ptr, a.col_idx
+    assert rp[0] == 0 and rp[-1] == len(ci)
+    for i in range(a.nb):
+        row = ci[rp[i]:rp[i + 1]]
+        assert np.all(np.diff(row) > 0) and i in row
+
+
+def test_small_grid_shape():
+    a = grid_small()
+    assert (a.nb, a.b, a.nnzb) == (2048, 3, 13312)
+    _pattern_ok(a)
+    assert np.array_equal(grid_small().values, a.values)  # seeded
+
+
+def test_spe10_counts_formula():
+    # 60x220x85 cells + 4 wells: nnzb = cells + 2*faces + 2*4*85
+    nx, ny, nz = 60, 220, 85
+    faces = (nx - 1) * ny * nz + nx * (ny - 1) * nz + nx * ny * (nz - 1)
+    assert nx * ny * nz + 4 == 1122004
+    assert nx * ny * nz + 4 + 2 * faces + 2 * 4 * nz == 7780684
+    a = grid_spe10(nx=6, ny=7, nz=5)
+    faces = 5 * 7 * 5 + 6 * 6 * 5 + 6 * 7 * 4
+    assert a.nnzb == 6 * 7 * 5 + 4 + 2 * faces + 2 * 4 * 5
+    _pattern_ok(a)
+    rows = np.repeat(np.arange(a.nb), np.diff(a.row_ptr))
+    st = set(zip(rows.tolist(), a.col_idx.tolist()))
+    assert all((j, i) in st for i, j in st)
+
+
+def test_perturbation_and_rhs():
+    a = box_jacobian(5, 4, 3, 4, 3, n_wells=2)
+    v = perturb_values(a, 1)
+    r = v / a.values
+    ok = a.values != 0
+    assert np.all((r[ok] >= 0.95) & (r[ok] <= 1.05))
+    rhs = random_rhs(a, 2).reshape(a.nb, a.b)
+    assert np.all(rhs[a.n_cells:, 1:] == 0.0)
