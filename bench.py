@@ -1,0 +1,381 @@
+"""Benchmark: MSP-preconditioned FGMRES solves of the SPE10-shaped synthetic Jacobian.
+
+One step = one Newton-like linear solve through the C ABI: the step's Jacobian values
+(same pattern, every entry perturbed by U[0.95, 1.05]) are loaded with
+msp_update_values, then msp_solve runs the adaptive setup decision of Section 3.2
+(SETUP again iff the previous solve took more than mu iterations) and FGMRES(30) with
+the multi-stage preconditioner to relative residual 1e-6.
+
+Workload (default): 60x220x85 cells (1,122,000) + 4 wells, 4 unknowns per cell, FP64,
+seed 2209 -- the plain FP64 GPU path.  The matrix (about 1 GB of values) and every
+step's values and right-hand side are resident in HBM before the timed region (inputs
+larger than L2, no flush needed).  `e2e` repeats the measurement through the host-buffer
+entry points (values and right-hand side copied in from pinned host memory, the solution
+copied out, every step).
+
+`--impl reference` times the CPU oracle (single thread) on the same workload; each of
+its steps is one FGMRES iteration of the oracle on the full matrix, and its solves/s are
+extrapolated as 1 / (setup share + It * seconds per iteration) with the GPU solve's
+iteration count and setup frequency (stated in `cpu_baseline.sample`).
+
+Multi-GPU: the solve does not shard, so `--gpus N` (under torchrun) runs N independent
+replicas, one per GPU, and reports the total solves/s (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solves/s to 1e-6 rel. residual (1.1M cells x4)"
+TOL = 1e-6
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=6)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    p.add_argument("--mu", type=int, default=20)
+    p.add_argument("--nx", type=int, default=60)
+    p.add_argument("--ny", type=int, default=220)
+    p.add_argument("--nz", type=int, default=85)
+    p.add_argument("--value-sets", type=int, default=4)
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def workload_name(args):
+    return "spe10-shaped %dx%dx%d + 4 wells, 4x4 BSR, %s" % (
+        args.nx, args.ny, args.nz, "FP64" if args.precision == "fp64" else
+        "FP32 preconditioner / FP64 Krylov")
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.samples = []
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 6:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if not self.samples:
+            return None
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4)
+                          if s[2 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def traffic_for(site):
+    """DRAM bytes per launch of `site` from the committed ncu summary, if it was taken
+    on the current kernel sources (null otherwise)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        src = os.path.join(ROOT, "paper_2208_08594_gb300", "csrc", "solve_kernels.cu")
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        e = t.get(site)
+        if e and e.get("solve_kernels_sha") == sha:
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+def make_inputs(args, rank):
+    from synthetic import grid_spe10, perturb_values, random_rhs
+    a = grid_spe10(seed=2209 + rank, nx=args.nx, ny=args.ny, nz=args.nz)
+    sets = [perturb_values(a, 5000 + 17 * rank + k) for k in range(args.value_sets)]
+    rhs = [random_rhs(a, 7000 + 13 * rank + k) for k in range(args.value_sets)]
+    return a, sets, rhs
+
+
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2208_08594_gb300 as msp
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    a, sets, rhs = make_inputs(args, rank)
+    d_rp = torch.from_numpy(a.row_ptr).to(dev)
+    d_ci = torch.from_numpy(a.col_idx).to(dev)
+    d_v0 = torch.from_numpy(a.values.reshape(-1)).to(dev)
+    d_sets = [torch.from_numpy(v.reshape(-1)).to(dev) for v in sets]
+    d_rhs = [torch.from_numpy(r).to(dev) for r in rhs]
+    x = torch.zeros(a.n, dtype=torch.float64, device=dev)
+    prec = msp.MSP_PRECISION_FP32 if args.precision == "fp32" else msp.MSP_PRECISION_FP64
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    solver = msp.Solver(a.nb, a.b, d_rp, d_ci, d_v0, mu=args.mu, precision=prec)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    nsets = len(d_sets)
+
+    def step(k, infos):
+        solver.update_values(d_sets[k % nsets])
+        info = solver.solve(d_rhs[k % nsets], x, TOL)
+        if info["status"] != 0:
+            raise RuntimeError("solve failed: %s" % info)
+        infos.append(info)
+
+    warm = []
+    for k in range(args.warmup):
+        step(k, warm)
+
+    msp.msp_stats_reset()
+    msp.msp_stats_enable(2)
+    clocks = ClockSampler(torch.cuda.current_device())
+    infos = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        step(args.warmup + k, infos)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    launches = msp.msp_stats_launches()
+    stats = msp.msp_stats_get()
+    msp.msp_stats_enable(0)
+
+    # end to end through the host-buffer entry points
+    e2e = None
+    if not args.no_e2e:
+        pin_sets = [torch.from_numpy(v.reshape(-1)).pin_memory() for v in sets]
+        pin_rhs = [torch.from_numpy(r).pin_memory() for r in rhs]
+        pin_x = torch.zeros(a.n, dtype=torch.float64).pin_memory()
+        e2e_infos = []
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for k in range(args.steps):
+            kk = (args.warmup + k) % nsets
+            solver.update_values_host(pin_sets[kk].numpy())
+            info = solver.solve_host(pin_rhs[kk].numpy(), pin_x.numpy(), TOL)
+            e2e_infos.append(info)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = f0.elapsed_time(f1)
+        e2e = {"ms": e2e_ms, "h2d": (a.nnzb * a.b * a.b + a.n) * 8, "d2h": a.n * 8}
+
+    # max over ranks
+    if world > 1:
+        t = torch.tensor([ms, e2e["ms"] if e2e else 0.0], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_ms = float(t[0]), float(t[1])
+        if e2e:
+            e2e["ms"] = e2e_ms
+    solver_levels = solver.num_levels
+    solver.close()
+    if world > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
+
+    total_solves = args.steps * world
+    value = total_solves / (ms / 1000.0)
+    its = [i["iterations"] for i in infos]
+    setups = sum(i["setup_performed"] for i in infos)
+    peak, peak_kind = load_peaks()
+    # dominant timed call site
+    dom = max(stats.items(), key=lambda kv: kv[1][1]) if stats else None
+    roofline = None
+    if dom:
+        name, (n_l, tot_ms, tot_b) = dom
+        achieved = (tot_b / n_l) / ((tot_ms / n_l) / 1000.0) / 1e9
+        roofline = {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1),
+                    "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "traffic": traffic_for(name),
+                    "algorithmic_bytes_per_launch": tot_b / n_l,
+                    "avg_launch_ms": tot_ms / n_l, "launches": n_l,
+                    "share_of_step": round(tot_ms / ms, 4)}
+    breakdown = {k: {"launches": v[0], "ms": round(v[1], 3),
+                     "GBps": round(v[2] / (v[1] / 1000.0) / 1e9, 1) if v[1] > 0 else None}
+                 for k, v in sorted(stats.items(), key=lambda kv: -kv[1][1])}
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32-precond/f64-krylov",
+        "data": "synthetic (seeded SPE10-shaped Jacobian; SPE10 data not available)",
+        "config": {"workload": workload_name(args), "cells": args.nx * args.ny * args.nz,
+                   "block_rows": a.nb, "nnzb": a.nnzb, "mu": args.mu,
+                   "restart": 30, "tol": TOL, "levels": solver_levels,
+                   "iterations": its, "setups_in_timed_steps": setups,
+                   "setup_s_first": round(setup_s, 3),
+                   "l2": "inputs larger than L2 (1 GB of values), no flush",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "kernel_breakdown": breakdown,
+        "clocks": clk,
+    }
+    if e2e:
+        out["e2e"] = {"value": round(total_solves / (e2e["ms"] / 1000.0), 4), "unit": "solves/s",
+                      "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]}
+    out["_its_mean"] = float(np.mean(its))
+    out["_setup_frac"] = setups / max(1, args.steps)
+    return out
+
+
+def oracle_sample(args, its_mean, setup_frac, steps, warmup):
+    """Time the oracle on the full workload: setup once, then `warmup + steps` single
+    FGMRES iterations; returns (solves/s, seconds per iteration, setup seconds)."""
+    import oracle
+    from synthetic import grid_spe10, random_rhs
+    a = grid_spe10(seed=2209, nx=args.nx, ny=args.ny, nz=args.nz)
+    t0 = time.perf_counter()
+    o = oracle.Oracle(a, mu=args.mu, max_it=1)
+    setup_s = time.perf_counter() - t0
+    rhs = random_rhs(a, 7000)
+    per = []
+    for k in range(warmup + steps):
+        t = time.perf_counter()
+        o.solve(rhs, TOL)  # one preconditioned Arnoldi step (max_it = 1)
+        if k >= warmup:
+            per.append(time.perf_counter() - t)
+    t_it = float(np.median(per))
+    value = 1.0 / (setup_frac * setup_s + its_mean * t_it)
+    return value, t_it, setup_s
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    its_mean, setup_frac = 120.0, 1.0 if args.mu < 120 else 0.0
+    prev = os.path.join(ROOT, "profiles", "bench_last.json")
+    try:
+        with open(prev) as f:
+            last = json.load(f)
+        its_mean = float(last.get("_its_mean", its_mean))
+        setup_frac = float(last.get("_setup_frac", setup_frac))
+    except Exception:
+        pass
+    t0 = time.perf_counter()
+    value, t_it, setup_s = oracle_sample(args, its_mean, setup_frac, args.steps, args.warmup)
+    wall = time.perf_counter() - t0
+    sample = ("oracle on the full %dx%dx%d matrix: SETUP once (%.1f s) and %d timed single "
+              "FGMRES iterations (median %.3f s); solves/s = 1 / (%.2f * setup + %.1f "
+              "iterations), the GPU run's setup share and mean iteration count" % (
+                  args.nx, args.ny, args.nz, setup_s, args.steps, t_it, setup_frac, its_mean))
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "solves/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(t_it * 1000, 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": workload_name(args), "mu": args.mu},
+           "cpu_baseline": {"value": round(value, 6), "unit": "solves/s", "cores": 1,
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0},
+           "wall_s": round(wall, 1)}
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        out = run_reference(args)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    out = run_native(args)
+    if out is None:
+        return
+    # CPU baseline: the oracle, bounded sample (rank 0, N = 1 only)
+    if out["n_gpus"] == 1 and os.environ.get("MSP_BENCH_NO_CPU") != "1":
+        value, t_it, setup_s = oracle_sample(args, out["_its_mean"], out["_setup_frac"], 2, 1)
+        out["cpu_baseline"] = {
+            "value": round(value, 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": "oracle on the full matrix: SETUP once (%.1f s) + 2 timed single FGMRES "
+                      "iterations (median %.3f s), extrapolated to %.1f iterations and a setup "
+                      "share of %.2f" % (setup_s, t_it, out["_its_mean"], out["_setup_frac"])}
+    try:
+        os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+        with open(os.path.join(ROOT, "gpurun_out", "bench_last.json"), "w") as f:
+            json.dump(out, f)
+    except Exception:
+        pass
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * msp.h - C ABI of the GB300 (sm_103a) multi-stage preconditioned FGMRES solver.
+ *
+ * Operation (Zhao, Zhang, Feng, Shu, "An Improved Multi-Stage Preconditioner on GPUs
+ * for Compositional Reservoir Simulation", 2022):
+ *   solve A x = b for a fully implicit compositional Jacobian in block-sparse (BSR) form
+ *   (Eq. Jacobian-system, Section 2.2.4) with right-preconditioned flexible GMRES(m)
+ *   (Section 5: m = 30, MaxIt 1000) and the multi-stage preconditioner B of Eq. MSP,
+ *   applied by Algorithm 3.1:
+ *     stage N: block Gauss-Seidel on the concentration sub-system (Pi_N^T A Pi_N);
+ *     stage P: quasi-IMPES decoupled restriction to pressure, UA-AMG V-cycle with
+ *              pairwise aggregation, multi-colour Gauss-Seidel smoothing (PGS-MC,
+ *              Algorithm 4.3, colouring by Algorithms 4.1/4.2 on the adjacency matrix
+ *              of Eq. adjacency-matrix) and a dense direct coarsest solve;
+ *     stage R: block ILU(0) of the whole system in colour order;
+ *   with the adaptive SETUP of Section 3.2 (ASMSP): a later solve regenerates B only if
+ *   the previous solve took more than mu iterations.
+ *
+ * Conventions (all functions):
+ *   - BSR: row_ptr int32[nb+1], col_idx int32[nnzb] (ascending within a row, diagonal
+ *     block present), values float64[nnzb*b*b], each block row-major (row = equation,
+ *     column = unknown); unknown 0 of every block is pressure, 1..b-1 the
+ *     concentrations (Eq. Jacobian-system-reservoir).  Wells are ordinary block rows.
+ *   - Pointers named d_* are DEVICE pointers, h_* HOST pointers.  The library copies
+ *     what it needs; the caller keeps ownership of every buffer it passes and may
+ *     free it once the call returns (device work is ordered on `stream`).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All device work of a
+ *     call is enqueued on it; calls that return sizes or the solve info synchronise it.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ *   - Return value: MSP_OK (0), MSP_NOT_CONVERGED (1, x still valid) or a negative
+ *     MSP_ERR_* code; msp_status_string() describes it.  No C++ exception crosses
+ *     the ABI.  After an MSP_ERR_CUDA the handle should be freed.
+ */
+#ifndef MSP_GB300_H
+#define MSP_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MSP_OK 0
+#define MSP_NOT_CONVERGED 1
+#define MSP_ERR_ARG (-1)
+#define MSP_ERR_PATTERN (-2)
+#define MSP_ERR_SINGULAR_BLOCK (-3)
+#define MSP_ERR_NONFINITE (-4)
+#define MSP_ERR_BREAKDOWN (-5)
+#define MSP_ERR_NOMEM (-6)
+#define MSP_ERR_TIMEOUT (-7)
+#define MSP_ERR_CUDA (-8)
+
+/* Preconditioner selection (msp_config.precond).  MSP_PREC_MSP is Algorithm 3.1; the
+ * single-stage choices exist for testing the stages in isolation. */
+#define MSP_PREC_MSP 0
+#define MSP_PREC_NONE 1
+#define MSP_PREC_R_ONLY 2
+#define MSP_PREC_P_ONLY 3
+#define MSP_PREC_N_ONLY 4
+
+/* Arithmetic of the preconditioner (msp_config.precision).  FGMRES, its residuals,
+ * orthogonalisation and Hessenberg least squares, and the coarsest dense solve are
+ * always FP64. */
+#define MSP_PRECISION_FP64 0
+#define MSP_PRECISION_FP32 1 /* stage N/P/R values and arithmetic in FP32 */
+
+typedef struct msp_handle_s* msp_handle;
+
+typedef struct {
+  int mu;          /* adaptive-setup threshold mu >= 0 (Section 3.2); 0 = plain MSP */
+  int restart;     /* m of FGMRES(m), 1..64 (Section 5: 30) */
+  int max_it;      /* MaxIt (Section 5: 1000) */
+  int coarse_max;  /* coarsest AMG level size (Section 5: 10000) */
+  int npass;       /* pairwise matching passes per AMG level (2: aggregates <= 4) */
+  int pre_sweeps;  /* PGS-MC sweeps before the coarse correction (forward colours) */
+  int post_sweeps; /* PGS-MC sweeps after it (backward colours) */
+  int bgs_sweeps;  /* block GS sweeps of stage N */
+  int decoupling;  /* 1 = quasi-IMPES weights omega_i = D_i^-T e_0, 0 = none */
+  int bilu_order;  /* must be 0: ILU(0) in level-0 colour order */
+  int precond;     /* MSP_PREC_* */
+  int max_levels;  /* AMG level cap */
+  double beta;     /* strong-coupling threshold of the pairwise matching (0.25) */
+  unsigned long long agg_seed; /* seed of the matching visit order */
+  int coarse_hard_max;         /* refuse a coarsest level larger than this */
+  int precision;               /* MSP_PRECISION_* */
+} msp_config;
+
+typedef struct {
+  int status;           /* return code of the solve */
+  int iterations;       /* preconditioned Arnoldi steps over all restarts (It) */
+  int setup_performed;  /* 1 if this solve used a freshly generated B */
+  int setup_calls;      /* SETUP calls since msp_setup (Section 3.2's SetupCalls) */
+  int levels;           /* AMG levels */
+  int colours_l0;       /* colours g of the level-0 (block) graph */
+  double rel_residual;      /* true ||b - A x||_2 / ||b||_2 at exit */
+  double rel_residual_est;  /* Arnoldi estimate at exit */
+  double t_setup_ms;        /* host wall time of SETUP inside this call */
+  double t_solve_ms;        /* host wall time of the Krylov solve */
+} msp_solve_info;
+
+/* Fill *cfg with the defaults above (Section 5 parameters, mu = 20).  Never fails
+ * unless cfg is NULL (MSP_ERR_ARG). */
+int msp_config_default(msp_config* cfg);
+
+/* Build a solver for the BSR matrix (device arrays, see Conventions) and run SETUP:
+ * adjacency matrix (Eq. adjacency-matrix), VerticesGrouping (Algorithms 4.1/4.2) and
+ * the colour permutation (Algorithm 4.3 step 3) of the block graph, then the value
+ * setup (decoupling, AMG hierarchy, stage-N blocks, BILU(0)).  nb >= 1, 1 <= b <= 8,
+ * nnzb = row_ptr[nb].  Errors: MSP_ERR_ARG (sizes/config), MSP_ERR_PATTERN (unsorted
+ * or out-of-range columns, missing diagonal), MSP_ERR_NONFINITE, MSP_ERR_SINGULAR_BLOCK
+ * (a diagonal block, its concentration sub-block, a BILU pivot or the coarsest matrix
+ * is singular), MSP_ERR_NOMEM, MSP_ERR_CUDA.  On error *out is NULL. */
+int msp_setup(msp_handle* out, const msp_config* cfg, int32_t nb, int32_t b,
+              const int32_t* d_row_ptr, const int32_t* d_col_idx, const double* d_values,
+              int64_t nnzb, void* stream);
+
+/* New values for the same pattern (a later Newton step, Section 3.2).  Copies
+ * d_values (nnzb*b*b doubles).  Does not run SETUP: the next msp_solve decides. */
+int msp_update_values(msp_handle h, const double* d_values, void* stream);
+
+/* msp_update_values with a HOST array (pinned memory gives the fastest copy). */
+int msp_update_values_host(msp_handle h, const double* h_values, void* stream);
+
+/* Solve A x = b to ||b - A x|| / ||b|| <= rel_tol with x0 = 0.  d_b, d_x: device
+ * arrays of nb*b doubles (natural order; may not alias).  Runs SETUP first when the
+ * adaptive rule asks for it (previous It > mu).  info may be NULL.  Returns MSP_OK,
+ * MSP_NOT_CONVERGED (MaxIt reached; x holds the last iterate), MSP_ERR_NONFINITE,
+ * MSP_ERR_BREAKDOWN, or a setup error.  Synchronises the stream. */
+int msp_solve(msp_handle h, const double* d_b, double* d_x, double rel_tol,
+              msp_solve_info* info, void* stream);
+
+/* msp_solve with HOST arrays: copies h_b in and h_x out inside the call. */
+int msp_solve_host(msp_handle h, const double* h_b, double* h_x, double rel_tol,
+                   msp_solve_info* info, void* stream);
+
+/* Release every resource of the handle (NULL is accepted). */
+int msp_free(msp_handle h);
+
+/* Static description of a status code. */
+const char* msp_status_string(int status);
+
+/* Text of the last CUDA error seen by the calling host thread ("" if none); valid until
+ * the next call on that thread.  Diagnostics only. */
+const char* msp_last_error(void);
+
+/* ---- inspection (used by the parity tests; all are exact views of solver state) ---- */
+
+/* w = B g: one application of the configured preconditioner (Algorithm 3.1 for
+ * MSP_PREC_MSP) to g; device arrays of nb*b doubles, natural order. */
+int msp_apply_precond(msp_handle h, const double* d_g, double* d_w, void* stream);
+
+/* y = A x with the current values; device arrays of nb*b doubles, natural order. */
+int msp_spmv(msp_handle h, const double* d_x, double* d_y, void* stream);
+
+/* Number of AMG levels (level 0 = the pressure matrix of the block graph). */
+int msp_num_levels(msp_handle h);
+
+/* Size, stored nonzeros and colour count of level l (0 colours: level not coloured). */
+int msp_level_info(msp_handle h, int level, int32_t* n, int32_t* nnz, int32_t* ncolours);
+
+/* Copy level l to HOST arrays (any may be NULL): perm[n] (colour-ordered index ->
+ * index before colouring: the natural block row for l = 0, the aggregate number for
+ * l >= 1), cptr[ncolours+1], agg[n] (index of the next level, -1 on the coarsest),
+ * row_ptr[n+1], col_idx[nnz], values[nnz] of the colour-ordered level matrix. */
+int msp_level_get(msp_handle h, int level, int32_t* h_perm, int32_t* h_cptr,
+                  int32_t* h_agg, int32_t* h_row_ptr, int32_t* h_col_idx, double* h_values);
+
+/* Level-0 colour (1..g) of every block row in natural order (HOST array); returns g. */
+int msp_colour0(msp_handle h, int32_t* h_colour);
+
+/* ---- launch statistics (process-wide; instrumentation for benchmarks) ----
+ * mode 0: off; 1: count every kernel launch of this library; 2: also time each launch
+ * of the solve phase with CUDA events recorded on its stream and add up the
+ * algorithmic bytes it moves, per call site.  Timing adds two event records per launch. */
+int msp_stats_enable(int mode);
+/* Forget all counts and timings. */
+int msp_stats_reset(void);
+/* Kernel launches counted since the last reset (mode >= 1). */
+long long msp_stats_launches(void);
+/* Number of timed call sites (waits for pending timings). */
+int msp_stats_count(void);
+/* Call site `index`: its name (NUL-terminated, truncated to name_len), launches, summed
+ * CUDA-event milliseconds and summed algorithmic bytes.  Any output may be NULL. */
+int msp_stats_get(int index, char* name, int name_len, long long* launches, double* total_ms,
+                  double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSP_GB300_H */

@@ -1,0 +1,78 @@
+"""GB300-native multi-stage preconditioned FGMRES for fully implicit compositional
+Jacobians (block-sparse), after Zhao, Zhang, Feng and Shu (2022).
+
+The solver is the C-ABI library ``libmsp.so`` (declared in ``include/msp.h``); this
+package holds its CUDA sources (``csrc/``), the in-tree build (``build.py``) and a thin
+ctypes binding (``_native``) plus a small convenience wrapper (``Solver``).
+"""
+from __future__ import annotations
+
+from . import _native
+from ._native import (MSP_NOT_CONVERGED, MSP_OK, MSP_PREC_MSP, MSP_PREC_N_ONLY, MSP_PREC_NONE,
+                      MSP_PREC_P_ONLY, MSP_PREC_R_ONLY, MSP_PRECISION_FP32, MSP_PRECISION_FP64,
+                      MspError, msp_apply_precond, msp_colour0, msp_config_default, msp_free,
+                      msp_level_get, msp_level_info, msp_num_levels, msp_setup, msp_solve,
+                      msp_solve_host, msp_spmv, msp_status_string, msp_update_values,
+                      msp_update_values_host, msp_stats_enable, msp_stats_reset,
+                      msp_stats_launches, msp_stats_get)
+
+__all__ = ["Solver", "MspError", "msp_setup", "msp_update_values", "msp_update_values_host",
+           "msp_stats_enable", "msp_stats_reset", "msp_stats_launches", "msp_stats_get",
+           "msp_solve",
+           "msp_solve_host", "msp_free", "msp_apply_precond", "msp_spmv", "msp_num_levels",
+           "msp_level_info", "msp_level_get", "msp_colour0", "msp_config_default",
+           "msp_status_string", "MSP_OK", "MSP_NOT_CONVERGED", "MSP_PREC_MSP", "MSP_PREC_NONE",
+           "MSP_PREC_R_ONLY", "MSP_PREC_P_ONLY", "MSP_PREC_N_ONLY", "MSP_PRECISION_FP64",
+           "MSP_PRECISION_FP32"]
+
+
+class Solver:
+    """Owns one solver handle for a BSR matrix held in CUDA tensors.
+
+    ``row_ptr``/``col_idx`` int32 and ``values`` float64 (nnzb*b*b, row-major blocks) on
+    the current CUDA device; ``config`` keys are the fields of ``msp_config``.
+    """
+
+    def __init__(self, nb, b, row_ptr, col_idx, values, stream=None, **config):
+        self.nb, self.b = int(nb), int(b)
+        self.cfg = msp_config_default(**config)
+        self.h = msp_setup(self.cfg, self.nb, self.b, row_ptr, col_idx, values, stream)
+
+    def update_values(self, values, stream=None):
+        msp_update_values(self.h, values, stream)
+
+    def update_values_host(self, values, stream=None):
+        msp_update_values_host(self.h, values, stream)
+
+    def solve(self, rhs, x, rel_tol=1e-6, stream=None):
+        return msp_solve(self.h, rhs, x, rel_tol, stream)
+
+    def solve_host(self, rhs, x, rel_tol=1e-6, stream=None):
+        return msp_solve_host(self.h, rhs, x, rel_tol, stream)
+
+    def apply_precond(self, g, w, stream=None):
+        msp_apply_precond(self.h, g, w, stream)
+
+    def spmv(self, x, y, stream=None):
+        msp_spmv(self.h, x, y, stream)
+
+    @property
+    def num_levels(self):
+        return msp_num_levels(self.h)
+
+    def level(self, l):
+        return msp_level_get(self.h, l)
+
+    def colour0(self):
+        return msp_colour0(self.h, self.nb)
+
+    def close(self):
+        if self.h:
+            msp_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

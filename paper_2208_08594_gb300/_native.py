@@ -1,0 +1,277 @@
+"""ctypes binding of ``libmsp.so`` (include/msp.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Device arrays are passed
+as CUDA ``torch.Tensor`` objects (PyTorch provides the device memory and the stream);
+nothing here computes any part of the solve.  A missing library raises at import of
+the first call: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MSP_OK, MSP_NOT_CONVERGED = 0, 1
+MSP_ERR_ARG, MSP_ERR_PATTERN, MSP_ERR_SINGULAR_BLOCK = -1, -2, -3
+MSP_ERR_NONFINITE, MSP_ERR_BREAKDOWN, MSP_ERR_NOMEM = -4, -5, -6
+MSP_ERR_TIMEOUT, MSP_ERR_CUDA = -7, -8
+MSP_PREC_MSP, MSP_PREC_NONE, MSP_PREC_R_ONLY, MSP_PREC_P_ONLY, MSP_PREC_N_ONLY = 0, 1, 2, 3, 4
+MSP_PRECISION_FP64, MSP_PRECISION_FP32 = 0, 1
+
+# every entry point declared in include/msp.h
+EXPORTS = ("msp_config_default", "msp_setup", "msp_update_values", "msp_update_values_host",
+           "msp_solve",
+           "msp_solve_host", "msp_free", "msp_status_string", "msp_apply_precond", "msp_spmv",
+           "msp_num_levels", "msp_level_info", "msp_level_get", "msp_colour0",
+           "msp_last_error", "msp_stats_enable", "msp_stats_reset", "msp_stats_launches",
+           "msp_stats_count", "msp_stats_get")
+
+
+class MspConfig(C.Structure):
+    _fields_ = [("mu", C.c_int), ("restart", C.c_int), ("max_it", C.c_int),
+                ("coarse_max", C.c_int), ("npass", C.c_int), ("pre_sweeps", C.c_int),
+                ("post_sweeps", C.c_int), ("bgs_sweeps", C.c_int), ("decoupling", C.c_int),
+                ("bilu_order", C.c_int), ("precond", C.c_int), ("max_levels", C.c_int),
+                ("beta", C.c_double), ("agg_seed", C.c_ulonglong),
+                ("coarse_hard_max", C.c_int), ("precision", C.c_int)]
+
+
+class MspSolveInfo(C.Structure):
+    _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("setup_performed", C.c_int),
+                ("setup_calls", C.c_int), ("levels", C.c_int), ("colours_l0", C.c_int),
+                ("rel_residual", C.c_double), ("rel_residual_est", C.c_double),
+                ("t_setup_ms", C.c_double), ("t_solve_ms", C.c_double)]
+
+
+class MspError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s failed: %s (%d)%s" % (where, msp_status_string(status), status,
+                                                    _last_error_suffix()))
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libmsp.so (building it first if it is missing or stale and nvcc exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise ImportError("libmsp.so is not built: run paper_2208_08594_gb300.build.build()")
+    L = C.CDLL(path)
+    P, I, D = C.c_void_p, C.c_int, C.c_double
+    L.msp_config_default.argtypes = [C.POINTER(MspConfig)]
+    L.msp_setup.argtypes = [C.POINTER(P), C.POINTER(MspConfig), C.c_int32, C.c_int32, P, P, P,
+                            C.c_int64, P]
+    L.msp_update_values.argtypes = [P, P, P]
+    L.msp_update_values_host.argtypes = [P, P, P]
+    L.msp_solve.argtypes = [P, P, P, D, C.POINTER(MspSolveInfo), P]
+    L.msp_solve_host.argtypes = [P, P, P, D, C.POINTER(MspSolveInfo), P]
+    L.msp_free.argtypes = [P]
+    L.msp_status_string.argtypes = [I]
+    L.msp_status_string.restype = C.c_char_p
+    L.msp_apply_precond.argtypes = [P, P, P, P]
+    L.msp_spmv.argtypes = [P, P, P, P]
+    L.msp_num_levels.argtypes = [P]
+    L.msp_level_info.argtypes = [P, I, P, P, P]
+    L.msp_level_get.argtypes = [P, I, P, P, P, P, P, P]
+    L.msp_colour0.argtypes = [P, P]
+    L.msp_last_error.argtypes = []
+    L.msp_last_error.restype = C.c_char_p
+    L.msp_stats_enable.argtypes = [I]
+    L.msp_stats_reset.argtypes = []
+    L.msp_stats_launches.argtypes = []
+    L.msp_stats_launches.restype = C.c_longlong
+    L.msp_stats_count.argtypes = []
+    L.msp_stats_get.argtypes = [I, C.c_char_p, I, P, P, P]
+    for name in EXPORTS:
+        if name not in ("msp_status_string", "msp_last_error", "msp_stats_launches"):
+            getattr(L, name).restype = I
+    _lib = L
+    return L
+
+
+def _last_error_suffix():
+    try:
+        e = lib(False).msp_last_error()
+        return (": " + e.decode()) if e else ""
+    except Exception:
+        return ""
+
+
+def msp_status_string(status: int) -> str:
+    return lib().msp_status_string(int(status)).decode()
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _check_dev(t, dtype, numel, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError("%s must be a contiguous CUDA tensor of %s" % (name, dtype))
+    if numel is not None and t.numel() != numel:
+        raise ValueError("%s has %d elements, expected %d" % (name, t.numel(), numel))
+
+
+def msp_config_default(**overrides) -> MspConfig:
+    cfg = MspConfig()
+    lib().msp_config_default(C.byref(cfg))
+    for k, v in overrides.items():
+        if not hasattr(cfg, k):
+            raise KeyError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+def msp_setup(cfg: MspConfig, nb: int, b: int, row_ptr, col_idx, values, stream=None):
+    import torch
+    _check_dev(row_ptr, torch.int32, nb + 1, "row_ptr")
+    _check_dev(col_idx, torch.int32, None, "col_idx")
+    nnzb = col_idx.numel()
+    _check_dev(values, torch.float64, nnzb * b * b, "values")
+    h = C.c_void_p()
+    st = lib().msp_setup(C.byref(h), C.byref(cfg), nb, b, _ptr(row_ptr), _ptr(col_idx),
+                         _ptr(values), nnzb, _stream(stream))
+    if st != MSP_OK:
+        raise MspError(st, "msp_setup")
+    return h
+
+
+def msp_update_values(h, values, stream=None):
+    st = lib().msp_update_values(h, _ptr(values), _stream(stream))
+    if st != MSP_OK:
+        raise MspError(st, "msp_update_values")
+
+
+def msp_update_values_host(h, values: np.ndarray, stream=None):
+    assert values.dtype == np.float64 and values.flags.c_contiguous
+    st = lib().msp_update_values_host(h, _ptr(values), _stream(stream))
+    if st != MSP_OK:
+        raise MspError(st, "msp_update_values_host")
+
+
+def _info_dict(info):
+    return {f: getattr(info, f) for f, _ in MspSolveInfo._fields_}
+
+
+def msp_solve(h, b, x, rel_tol=1e-6, stream=None):
+    info = MspSolveInfo()
+    st = lib().msp_solve(h, _ptr(b), _ptr(x), float(rel_tol), C.byref(info), _stream(stream))
+    if st < 0 and st != MSP_ERR_BREAKDOWN:
+        raise MspError(st, "msp_solve")
+    return _info_dict(info)
+
+
+def msp_solve_host(h, b: np.ndarray, x: np.ndarray, rel_tol=1e-6, stream=None):
+    assert b.dtype == np.float64 and x.dtype == np.float64 and b.flags.c_contiguous
+    info = MspSolveInfo()
+    st = lib().msp_solve_host(h, _ptr(b), _ptr(x), float(rel_tol), C.byref(info),
+                              _stream(stream))
+    if st < 0 and st != MSP_ERR_BREAKDOWN:
+        raise MspError(st, "msp_solve_host")
+    return _info_dict(info)
+
+
+def msp_free(h):
+    if h:
+        lib().msp_free(h)
+
+
+def msp_apply_precond(h, g, w, stream=None):
+    st = lib().msp_apply_precond(h, _ptr(g), _ptr(w), _stream(stream))
+    if st != MSP_OK:
+        raise MspError(st, "msp_apply_precond")
+
+
+def msp_spmv(h, x, y, stream=None):
+    st = lib().msp_spmv(h, _ptr(x), _ptr(y), _stream(stream))
+    if st != MSP_OK:
+        raise MspError(st, "msp_spmv")
+
+
+def msp_num_levels(h) -> int:
+    return lib().msp_num_levels(h)
+
+
+def msp_level_info(h, level):
+    n, nnz, nc = C.c_int32(), C.c_int32(), C.c_int32()
+    st = lib().msp_level_info(h, level, C.byref(n), C.byref(nnz), C.byref(nc))
+    if st != MSP_OK:
+        raise MspError(st, "msp_level_info")
+    return n.value, nnz.value, nc.value
+
+
+def msp_level_get(h, level):
+    n, nnz, ncol = msp_level_info(h, level)
+    perm = np.zeros(n, np.int32)
+    cptr = np.zeros(max(ncol + 1, 1), np.int32)
+    agg = np.zeros(n, np.int32)
+    rp = np.zeros(n + 1, np.int32)
+    ci = np.zeros(nnz, np.int32)
+    v = np.zeros(nnz)
+    st = lib().msp_level_get(h, level, _ptr(perm), _ptr(cptr) if ncol else None, _ptr(agg),
+                             _ptr(rp), _ptr(ci), _ptr(v))
+    if st != MSP_OK:
+        raise MspError(st, "msp_level_get")
+    return dict(n=n, nnz=nnz, ncolours=ncol, perm=perm,
+                cptr=cptr[:ncol + 1] if ncol else np.zeros(0, np.int32), agg=agg,
+                row_ptr=rp, col_idx=ci, values=v)
+
+
+def msp_colour0(h, nb: int):
+    c = np.zeros(nb, np.int32)
+    g = lib().msp_colour0(h, _ptr(c))
+    if g < 0:
+        raise MspError(g, "msp_colour0")
+    return c, g
+
+
+def msp_stats_enable(mode: int):
+    st = lib().msp_stats_enable(int(mode))
+    if st != MSP_OK:
+        raise MspError(st, "msp_stats_enable")
+
+
+def msp_stats_reset():
+    lib().msp_stats_reset()
+
+
+def msp_stats_launches() -> int:
+    return int(lib().msp_stats_launches())
+
+
+def msp_stats_get():
+    """{site: (launches, total_ms, bytes)} of the timed call sites."""
+    L = lib()
+    out = {}
+    for k in range(L.msp_stats_count()):
+        name = C.create_string_buffer(64)
+        n, ms, by = C.c_longlong(), C.c_double(), C.c_double()
+        if L.msp_stats_get(k, name, 64, C.byref(n), C.byref(ms), C.byref(by)) == MSP_OK:
+            out[name.value.decode()] = (n.value, ms.value, by.value)
+    return out

@@ -1,0 +1,93 @@
+// Launchers of the CUDA kernels (host-callable).  All take a cudaStream_t and enqueue
+// asynchronously; they return MSP_OK or MSP_ERR_CUDA (launch failure).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace msp {
+
+// ---------------- solve phase: block rows of the colour-ordered BSR matrix --------------
+// y = A x (residual = false) or y = g - A x (residual = true); b = block size 1..8.
+template <typename T>
+int launch_bsr_spmv(int b, int nb, const int* rp, const int* ci, const T* v, const T* x,
+                    const T* g, T* y, bool residual, cudaStream_t s);
+// rP[i] = omega_i^T (g_i - (A w)_i)   (omega == nullptr: first unknown only)
+template <typename T>
+int launch_bsr_restrict_p(int b, int nb, const int* rp, const int* ci, const T* v,
+                          const T* w, const T* g, const T* omega, T* rP, cudaStream_t s);
+// stage N: one block-GS sweep over the rows [r0, r1) of one colour on the (b-1)x(b-1)
+// sub-blocks aN; reads/writes the concentration slots of w (stride b); lower_only for
+// the first sweep from zero (later colours still hold zero).
+template <typename T>
+int launch_bgs_colour(int b, int r0, int r1, const int* rp, const int* ci, const int* dpos,
+                      const T* aN, const T* dNinv, const T* g, T* w, bool lower_only,
+                      bool zero_pressure, cudaStream_t s);
+// stage R: forward y_i = r_i - sum_{j<i} L_ij y_j and backward x_i = U_ii^-1 (y_i -
+// sum_{j>i} U_ij x_j); the backward sweep also adds x_i into w.
+template <typename T>
+int launch_bilu_fwd(int b, int r0, int r1, const int* rp, const int* ci, const int* dpos,
+                    const T* lu, const T* r, T* y, cudaStream_t s);
+template <typename T>
+int launch_bilu_bwd(int b, int r0, int r1, const int* rp, const int* ci, const int* dpos,
+                    const T* lu, const T* uinv, const T* y, T* x, T* w, cudaStream_t s);
+// w[i*b] += e[i]
+template <typename T>
+int launch_prolong_p(int b, int nb, const T* e, T* w, cudaStream_t s);
+
+// ---------------- solve phase: scalar CSR AMG levels ----------------
+// PGS-MC on rows [r0, r1) of one colour: x_i = (b_i - sum_{j != i} a_ij x_j) / a_ii;
+// lower_only: entries right of the diagonal are skipped (x there is still zero).
+template <typename T>
+int launch_csr_gs_colour(int r0, int r1, const int* rp, const int* ci, const T* v,
+                         const int* dpos, const T* rdiag, const T* b, T* x, bool lower_only,
+                         cudaStream_t s);
+// bc[I] = sum over members i of aggregate I (ascending) of (b_i - (A x)_i)
+template <typename T>
+int launch_csr_residual_restrict(int nc, const int* mptr, const int* members, const int* rp,
+                                 const int* ci, const T* v, const T* b, const T* x, T* bc,
+                                 cudaStream_t s);
+// x_i += xc[agg[i]]
+template <typename T>
+int launch_prolong_add(int n, const int* agg, const T* xc, T* x, cudaStream_t s);
+// x = Ainv b (dense row-major n x n, FP64); b, x in the level's value type
+template <typename T>
+int launch_dense_gemv(int n, const double* Ainv, const T* b, T* x, cudaStream_t s);
+
+// ---------------- precision casts ----------------
+int launch_cast_d2f(size_t n, const double* in, float* out, cudaStream_t s);
+int launch_cast_f2d(size_t n, const float* in, double* out, cudaStream_t s);
+
+// ---------------- Krylov (FP64) ----------------
+// partial[blk * kmax + k] = sum over this block's rows of V[k][i] * w[i], k < K
+int launch_multi_dot(size_t n, const double* V, size_t ldv, int K, const double* w,
+                     double* partial, int nblocks, cudaStream_t s);
+// out[k] = sum_b partial[b * kmax + k] (fixed order), k < K;  accumulate: out[k] += ...
+int launch_reduce_partials(int K, int nblocks, const double* partial, double* out,
+                           bool accumulate, cudaStream_t s);
+// w -= sum_k h[k] V[k]; partial[blk] = sum of w_new^2 over the block
+int launch_multi_axpy_norm(size_t n, const double* V, size_t ldv, int K, const double* h,
+                           double* w, double* partial, int nblocks, cudaStream_t s);
+// v = w / sqrt(nrm2[0]) (nothing when the norm is zero); hn[0] = sqrt(nrm2[0])
+int launch_normalize(size_t n, const double* w, const double* nrm2, double* v, double* hn,
+                     cudaStream_t s);
+// x += sum_k y[k] Z[k]
+int launch_update_x(size_t n, const double* Z, size_t ldz, int K, const double* y, double* x,
+                    cudaStream_t s);
+// v = r / beta (beta a host scalar)
+int launch_scale(size_t n, const double* r, double alpha, double* v, cudaStream_t s);
+// partial[blk] = sum of x^2 over the block
+int launch_norm2_partial(size_t n, const double* x, double* partial, int nblocks,
+                         cudaStream_t s);
+// nonfinite check: flag[0] = 1 if any entry is not finite
+int launch_check_finite(size_t n, const double* x, int* flag, cudaStream_t s);
+// out[k*b + r] = in[perm[k]*b + r]  (gather, b-blocks)
+int launch_gather_blocks(int nb, int b, const int* perm, const double* in, double* out,
+                         cudaStream_t s);
+// out[perm[k]*b + r] = in[k*b + r]  (scatter, b-blocks)
+int launch_scatter_blocks(int nb, int b, const int* perm, const double* in, double* out,
+                          cudaStream_t s);
+
+int krylov_blocks();  // number of blocks the reduction kernels use
+
+}  // namespace msp

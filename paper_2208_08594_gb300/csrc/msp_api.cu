@@ -1,0 +1,1392 @@
+// Host orchestration and the C ABI of the solver (include/msp.h).
+//
+// SETUP (Section 3): block-graph adjacency (Eq. adjacency-matrix), VerticesGrouping
+// (Algorithms 4.1/4.2) and the colour permutation (Algorithm 4.3 step 3) once per
+// pattern; per value setup the quasi-IMPES decoupling, the UA-AMG hierarchy (pairwise
+// matching, Galerkin products, PGS-MC colourings, dense coarsest inverse), the stage-N
+// sub-blocks and BILU(0) in colour order.  SOLVE: right-preconditioned FGMRES(m) with
+// classical Gram-Schmidt and one re-orthogonalisation, the Hessenberg least squares in
+// FP64 on the host, and Algorithm 3.1 as the preconditioner.  ASMSP (Section 3.2): a
+// solve regenerates B iff the previous solve took more than mu iterations.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "setup_kernels.h"
+
+namespace msp {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+  g_last_error = buf;
+}
+
+// ---------------------------------------------------------------------------------
+// launch statistics (msp_stats_*): launch counting and per-site CUDA-event timing
+// ---------------------------------------------------------------------------------
+namespace {
+struct StatSite {
+  std::string name;
+  long long launches = 0;
+  double ms = 0.0, bytes = 0.0;
+};
+struct PendingTiming {
+  int site;
+  cudaEvent_t e0, e1;
+};
+std::mutex g_stats_mu;
+int g_stats_mode = 0;
+long long g_launches = 0;
+std::vector<StatSite> g_sites;
+std::vector<PendingTiming> g_pending;
+std::vector<cudaEvent_t> g_free_events;
+
+cudaEvent_t take_event() {
+  if (!g_free_events.empty()) {
+    cudaEvent_t e = g_free_events.back();
+    g_free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+int site_index(const char* name) {
+  for (size_t k = 0; k < g_sites.size(); ++k)
+    if (g_sites[k].name == name) return (int)k;
+  g_sites.push_back(StatSite{name});
+  return (int)g_sites.size() - 1;
+}
+
+// fold finished timings into the sites (waits for the recorded events)
+void resolve_pending() {
+  for (auto& p : g_pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.e1) == cudaSuccess && cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess)
+      g_sites[p.site].ms += ms;
+    g_free_events.push_back(p.e0);
+    g_free_events.push_back(p.e1);
+  }
+  g_pending.clear();
+}
+}  // namespace
+
+int launch_check(const char* file, int line) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, "kernel launch", file, line);
+    return MSP_ERR_CUDA;
+  }
+  if (g_stats_mode >= 1) {
+    std::lock_guard<std::mutex> lk(g_stats_mu);
+    ++g_launches;
+  }
+  return MSP_OK;
+}
+
+Probe::Probe(const char* site, double bytes, cudaStream_t s) : s_(s) {
+  if (g_stats_mode < 2) return;
+  std::lock_guard<std::mutex> lk(g_stats_mu);
+  e0_ = take_event();
+  e1_ = take_event();
+  if (!e0_ || !e1_) return;
+  site_ = site_index(site);
+  g_sites[site_].bytes += bytes;
+  g_sites[site_].launches++;
+  cudaEventRecord(e0_, s_);
+}
+
+Probe::~Probe() {
+  if (site_ < 0) return;
+  cudaEventRecord(e1_, s_);
+  std::lock_guard<std::mutex> lk(g_stats_mu);
+  g_pending.push_back(PendingTiming{site_, e0_, e1_});
+}
+
+int sm_count() {
+  static int cached = 0;
+  if (cached == 0) {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+      cached = n;
+    else
+      cached = 152;
+  }
+  return cached;
+}
+
+namespace {
+
+constexpr int kThreads = 256;
+using Clock = std::chrono::steady_clock;
+double ms_since(Clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+}
+
+inline int launch_status() { return launch_check(__FILE__, __LINE__); }
+
+// ---------------------------------------------------------------------------------
+// small host-orchestration kernels
+// ---------------------------------------------------------------------------------
+__global__ void rank_keys_kernel(int n, const int* __restrict__ srp, unsigned long long* keys) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const unsigned deg = (unsigned)(srp[v + 1] - srp[v]);
+    keys[v] = ((unsigned long long)(0x7fffffffu - deg) << 32) | (unsigned)v;
+  }
+}
+
+__global__ void colour_keys_kernel(int n, const int* __restrict__ colour, unsigned long long* keys) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    keys[v] = ((unsigned long long)(unsigned)colour[v] << 32) | (unsigned)v;
+}
+
+__global__ void perm_keys_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                 const int* __restrict__ rowmap, const int* __restrict__ colmap,
+                                 unsigned long long* __restrict__ keys, int* __restrict__ vals) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned long long r = (unsigned)rowmap[i];
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      keys[p] = (r << 32) | (unsigned)colmap[ci[p]];
+      vals[p] = p;
+    }
+  }
+}
+
+__global__ void seg_flags_kernel(size_t m, const unsigned long long* __restrict__ keys,
+                                 int* __restrict__ flags) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m;
+       k += (size_t)gridDim.x * blockDim.x)
+    flags[k] = (k == 0 || keys[k] != keys[k - 1]) ? 1 : 0;
+}
+
+__global__ void seg_compact_kernel(size_t m, const unsigned long long* __restrict__ keys,
+                                   const int* __restrict__ flags, const int* __restrict__ pos,
+                                   unsigned long long* __restrict__ ukeys,
+                                   int* __restrict__ seg_start, int nseg) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m;
+       k += (size_t)gridDim.x * blockDim.x)
+    if (flags[k]) {
+      ukeys[pos[k]] = keys[k];
+      seg_start[pos[k]] = (int)k;
+    }
+  if (blockIdx.x == 0 && threadIdx.x == 0) seg_start[nseg] = (int)m;
+}
+
+__global__ void gather_double_kernel(size_t m, const int* __restrict__ src,
+                                     const double* __restrict__ in, double* __restrict__ out) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m;
+       k += (size_t)gridDim.x * blockDim.x)
+    out[k] = in[src[k]];
+}
+
+__global__ void compose_kernel(int n, const int* __restrict__ a1, int* __restrict__ agg) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    agg[i] = a1[agg[i]];
+}
+
+__global__ void map_kernel(int n, const int* __restrict__ m, const int* __restrict__ in,
+                           int* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = m[in[i]];
+}
+
+__global__ void member_keys_kernel(int n, const int* __restrict__ agg, unsigned long long* keys) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    keys[i] = ((unsigned long long)(unsigned)agg[i] << 32) | (unsigned)i;
+}
+
+template <typename T>
+unsigned grid1(T n) {
+  return grid_for((size_t)n, kThreads);
+}
+
+// ---------------------------------------------------------------------------------
+// device CSR and levels
+// ---------------------------------------------------------------------------------
+struct DCsr {
+  int n = 0, nnz = 0;
+  DevBuf<int> rp, ci;
+  DevBuf<double> v;
+};
+
+// nonzeros left / right of the diagonal in the rows of every colour class (for the
+// algorithmic byte counts of the sweeps)
+struct ColourCounts {
+  std::vector<long long> lower, upper;
+};
+
+int colour_counts(const int* d_rp, const int* d_dpos, int n, const std::vector<int>& cptr,
+                  ColourCounts& cc, cudaStream_t s) {
+  std::vector<int> rp(n + 1), dp(n);
+  MSP_CUDA_TRY(cudaMemcpyAsync(rp.data(), d_rp, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+  MSP_CUDA_TRY(cudaMemcpyAsync(dp.data(), d_dpos, n * sizeof(int), cudaMemcpyDeviceToHost, s));
+  MSP_CUDA_TRY(cudaStreamSynchronize(s));
+  const int g = cptr.empty() ? 0 : (int)cptr.size() - 1;
+  cc.lower.assign(g, 0);
+  cc.upper.assign(g, 0);
+  for (int c = 0; c < g; ++c)
+    for (int i = cptr[c]; i < cptr[c + 1]; ++i) {
+      cc.lower[c] += dp[i] - rp[i];
+      cc.upper[c] += rp[i + 1] - dp[i] - 1;
+    }
+  return MSP_OK;
+}
+
+struct Level {
+  DCsr A;                   // colour-ordered level matrix
+  std::vector<int> cptr;    // colour classes (empty: not coloured)
+  ColourCounts cc;
+  DevBuf<int> perm;         // colour-ordered -> pre-colouring index
+  DevBuf<int> dpos;
+  DevBuf<double> rdiag;
+  DevBuf<int> agg;          // -> next level index
+  DevBuf<int> mptr, members;  // members of every next-level aggregate (ascending)
+  int nc = 0;
+  // FP32 copies (mixed precision)
+  DevBuf<float> v32, rdiag32;
+  // work vectors
+  DevBuf<double> b64, x64;
+  DevBuf<float> b32, x32;
+};
+
+}  // namespace
+}  // namespace msp
+
+struct msp_handle_s {
+  msp_config cfg{};
+  int nb = 0, b = 0;
+  int64_t nnzb = 0;
+  int device = 0;
+  msp::SortScratch* ss = nullptr;
+  msp::DevBuf<msp::DevFlags> flags;
+  msp::DevFlags* h_flags = nullptr;  // pinned
+  double* h_pin = nullptr;           // pinned host scratch (Hessenberg column, norms)
+  // pattern (level 0)
+  msp::DevBuf<int> perm0, iperm0, colour0;
+  std::vector<int> cptr0;
+  msp::ColourCounts cc0;
+  int g0 = 0;
+  msp::DevBuf<int> rp, ci, dpos, src;  // colour-ordered BSR pattern, source nonzero
+  msp::DevBuf<double> vals;            // colour-ordered current values
+  msp::DevBuf<double> staging;         // user values before the gather
+  // setup products
+  msp::DevBuf<double> omega, dNinv, aN, lu, uinv, cinv;
+  int ncoarse = 0;
+  std::vector<msp::Level> levels;
+  // FP32 copies
+  msp::DevBuf<float> vals32, omega32, dNinv32, aN32, lu32, uinv32;
+  // preconditioner work vectors
+  msp::DevBuf<double> pr, py, px;
+  msp::DevBuf<float> g32, w32, pr32, py32, px32;
+  // Krylov work
+  msp::DevBuf<double> V, Z, bperm, xperm, rvec, partial, hdev, nrm, ydev;
+  msp::DevBuf<int> ifl;
+  msp::DevBuf<double> e2e_b, e2e_x;  // staging of msp_solve_host
+  // adaptive setup
+  int setup_calls = 0;
+  int prev_it = -1;
+  bool first_solve = true;
+  bool setup_valid = false;
+};
+
+namespace msp {
+namespace {
+
+int sync_flags(msp_handle h, cudaStream_t s) {
+  MSP_CUDA_TRY(cudaMemcpyAsync(h->h_flags, h->flags.p, sizeof(DevFlags), cudaMemcpyDeviceToHost, s));
+  MSP_CUDA_TRY(cudaStreamSynchronize(s));
+  return h->h_flags->code;
+}
+
+int reset_flags(msp_handle h, cudaStream_t s) {
+  MSP_CUDA_TRY(cudaMemsetAsync(h->flags.p, 0, sizeof(DevFlags), s));
+  return MSP_OK;
+}
+
+// VerticesGrouping of the graph of a CSR/BSR pattern: colour[v] in 1..g, perm (colour
+// order -> index), cptr (host).
+int colour_graph(msp_handle h, int n, const int* rp, const int* ci, int nnz, DevBuf<int>& colour,
+                 DevBuf<int>& perm, std::vector<int>& cptr, int* g_out, cudaStream_t s) {
+  DevBuf<int> srp, sci;
+  int snnz = 0;
+  MSP_TRY(build_adjacency(h->ss, n, rp, ci, nnz, srp, sci, &snnz, s));
+  DevBuf<unsigned long long> keys;
+  DevBuf<int> vor, rank, wbar, meta;
+  DevBuf<unsigned char> state;
+  DevBuf<unsigned> bitmap;
+  MSP_TRY(keys.alloc(n));
+  MSP_TRY(vor.alloc(n));
+  MSP_TRY(rank.alloc(n));
+  rank_keys_kernel<<<grid1(n), kThreads, 0, s>>>(n, srp.p, keys.p);
+  MSP_TRY(launch_status());
+  MSP_TRY(sort_pairs_u64(h->ss, n, keys.p, nullptr, 64, s));
+  MSP_TRY(low32_of_keys(n, keys.p, vor.p, s));
+  MSP_TRY(launch_scatter_inverse(n, vor.p, rank.p, s));
+  const int n0 = (n + 31) / 32, n1 = (n0 + 31) / 32, n2 = (n1 + 31) / 32;
+  const size_t words = (size_t)n0 + n1 + n2;
+  MSP_TRY(state.alloc(n));
+  MSP_TRY(wbar.alloc(n));
+  MSP_TRY(bitmap.alloc(words));
+  MSP_TRY(meta.alloc(2));
+  MSP_TRY(colour.alloc(n));
+  MSP_CUDA_TRY(cudaMemsetAsync(meta.p, 0, 2 * sizeof(int), s));
+  MSP_TRY(launch_colouring(n, srp.p, sci.p, rank.p, vor.p, state.p, wbar.p, bitmap.p, words,
+                           colour.p, meta.p, s));
+  int hm[2] = {0, 0};
+  MSP_CUDA_TRY(cudaMemcpyAsync(hm, meta.p, sizeof(hm), cudaMemcpyDeviceToHost, s));
+  MSP_CUDA_TRY(cudaStreamSynchronize(s));
+  if (hm[1] != 0) return MSP_ERR_TIMEOUT;
+  const int g = hm[0];
+  // colour permutation: stable sort by (colour, index)
+  colour_keys_kernel<<<grid1(n), kThreads, 0, s>>>(n, colour.p, keys.p);
+  MSP_TRY(launch_status());
+  MSP_TRY(sort_pairs_u64(h->ss, n, keys.p, nullptr, 64, s));
+  MSP_TRY(perm.alloc(n));
+  MSP_TRY(low32_of_keys(n, keys.p, perm.p, s));
+  DevBuf<int> cp;
+  MSP_TRY(cp.alloc(g + 2));
+  MSP_TRY(rowptr_from_sorted_keys(n, g + 1, keys.p, cp.p, s));
+  std::vector<int> hcp(g + 2);
+  MSP_CUDA_TRY(cudaMemcpyAsync(hcp.data(), cp.p, (g + 2) * sizeof(int), cudaMemcpyDeviceToHost, s));
+  MSP_CUDA_TRY(cudaStreamSynchronize(s));
+  cptr.assign(hcp.begin() + 1, hcp.end());  // colour c (1-based) -> [hcp[c], hcp[c+1])
+  *g_out = g;
+  return MSP_OK;
+}
+
+// B = P A P^T for a scalar CSR matrix (rows/cols mapped by iperm), columns re-sorted;
+// src[q] = nonzero of A that lands at q.
+int permute_pattern(msp_handle h, int n, const int* rp, const int* ci, int nnz, const int* iperm,
+                    DevBuf<int>& brp, DevBuf<int>& bci, DevBuf<int>& src, cudaStream_t s) {
+  DevBuf<unsigned long long> keys;
+  MSP_TRY(keys.alloc(nnz > 0 ? nnz : 1));
+  MSP_TRY(src.alloc(nnz > 0 ? nnz : 1));
+  perm_keys_kernel<<<grid1(n), kThreads, 0, s>>>(n, rp, ci, iperm, iperm, keys.p, src.p);
+  MSP_TRY(launch_status());
+  MSP_TRY(sort_pairs_u64(h->ss, nnz, keys.p, src.p, 64, s));
+  MSP_TRY(brp.alloc(n + 1));
+  MSP_TRY(bci.alloc(nnz > 0 ? nnz : 1));
+  MSP_TRY(rowptr_from_sorted_keys(nnz, n, keys.p, brp.p, s));
+  MSP_TRY(low32_of_keys(nnz, keys.p, bci.p, s));
+  MSP_CUDA_TRY(cudaStreamSynchronize(s));
+  return MSP_OK;
+}
+
+// A_c = P^T A P for the aggregation agg (bit-exact sums in fine-nonzero order)
+int galerkin(msp_handle h, const DCsr& A, const int* agg, int nc, DCsr& C, cudaStream_t s) {
+  const size_t m = A.nnz;
+  DevBuf<unsigned long long> keys, ukeys;
+  DevBuf<int> src, flags, pos, seg;
+  MSP_TRY(keys.alloc(m));
+  MSP_TRY(src.alloc(m));
+  perm_keys_kernel<<<grid1(A.n), kThreads, 0, s>>>(A.n, A.rp.p, A.ci.p, agg, agg, keys.p, src.p);
+  MSP_TRY(launch_status());
+  MSP_TRY(sort_pairs_u64(h->ss, m, keys.p, src.p, 64, s));
+  MSP_TRY(flags.alloc(m));
+  MSP_TRY(pos.alloc(m));
+  seg_flags_kernel<<<grid1(m), kThreads, 0, s>>>(m, keys.p, flags.p);
+  MSP_TRY(launch_status());
+  MSP_TRY(exclusive_scan_int(h->ss, m, flags.p, pos.p, s));
+  int lp = 0, lf = 0;
+  MSP_CUDA_TRY(cudaMemcpyAsync(&lp, pos.p + m - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MSP_CUDA_TRY(cudaMemcpyAsync(&lf, flags.p + m - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MSP_CUDA_TRY(cudaStreamSynchronize(s));
+  const int nseg = lp + lf;
+  MSP_TRY(ukeys.alloc(nseg));
+  MSP_TRY(seg.alloc(nseg + 1));
+  seg_compact_kernel<<<grid1(m), kThreads, 0, s>>>(m, keys.p, flags.p, pos.p, ukeys.p, seg.p, nseg);
+  MSP_TRY(launch_status());
+  C.n = nc;
+  C.nnz = nseg;
+  MSP_TRY(C.rp.alloc(nc + 1));
+  MSP_TRY(C.ci.alloc(nseg));
+  MSP_TRY(C.v.alloc(nseg));
+  MSP_TRY(rowptr_from_sorted_keys(nseg, nc, ukeys.p, C.rp.p, s));
+  MSP_TRY(low32_of_keys(nseg, ukeys.p, C.ci.p, s));
+  MSP_TRY(launch_segment_sums(nseg, seg.p, src.p, A.v.p, C.v.p, s));
+  MSP_CUDA_TRY(cudaStreamSynchronize(s));
+  return MSP_OK;
+}
+
+// one pairwise matching pass (visit order splitmix64(i ^ seed)); agg in [0, *nagg)
+int pairwise_pass(msp_handle h, const DCsr& A, double beta, unsigned long long seed,
+                  DevBuf<int>& agg, int* nagg, cudaStream_t s) {
+  const int n = A.n;
+  DevBuf<int> srp, sci, tpos, partner, commit, rep, id;
+  int snnz = 0;
+  MSP_TRY(build_adjacency(h->ss, n, A.rp.p, A.ci.p, A.nnz, srp, sci, &snnz, s));
+  DevBuf<double> sval;
+  DevBuf<unsigned char> cand, state;
+  DevBuf<unsigned long long> hkey;
+  MSP_TRY(sval.alloc(snnz > 0 ? snnz : 1));
+  MSP_TRY(cand.alloc(snnz > 0 ? snnz : 1));
+  MSP_TRY(tpos.alloc(snnz > 0 ? snnz : 1));
+  MSP_TRY(hkey.alloc(n));
+  MSP_TRY(state.alloc(n));
+  MSP_TRY(partner.alloc(n));
+  MSP_TRY(commit.alloc(n));
+  MSP_TRY(launch_strength(n, A.rp.p, A.ci.p, A.v.p, srp.p, sci.p, beta, sval.p, cand.p, s));
+  MSP_TRY(launch_transpose_pos(n, srp.p, sci.p, tpos.p, s));
+  MSP_TRY(launch_visit_keys(n, seed, hkey.p, s));
+  MSP_CUDA_TRY(cudaMemsetAsync(state.p, 0, n, s));
+  MSP_TRY(launch_fill_int(n, -1, partner.p, s));
+  int rounds = 0;
+  while (true) {
+    MSP_CUDA_TRY(cudaMemsetAsync(&h->flags.p->count, 0, sizeof(int), s));
+    MSP_TRY(launch_match_round(n, srp.p, sci.p, tpos.p, sval.p, cand.p, hkey.p, state.p,
+                               commit.p, s));
+    MSP_TRY(launch_match_apply(n, commit.p, state.p, partner.p, h->flags.p, s));
+    MSP_CUDA_TRY(cudaMemcpyAsync(h->h_flags, h->flags.p, sizeof(DevFlags), cudaMemcpyDeviceToHost, s));
+    MSP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h->h_flags->count == 0) break;
+    if (++rounds > n + 8) return MSP_ERR_TIMEOUT;  // at least one node decides per round
+  }
+  MSP_TRY(rep.alloc(n));
+  MSP_TRY(id.alloc(n));
+  MSP_TRY(launch_match_reps(n, partner.p, rep.p, s));
+  MSP_TRY(exclusive_scan_int(h->ss, n, rep.p, id.p, s));
+  int lr = 0, li = 0;
+  MSP_CUDA_TRY(cudaMemcpyAsync(&lr, rep.p + n - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MSP_CUDA_TRY(cudaMemcpyAsync(&li, id.p + n - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MSP_TRY(agg.alloc(n));
+  MSP_TRY(launch_match_ids(n, partner.p, id.p, agg.p, s));
+  MSP_CUDA_TRY(cudaStreamSynchronize(s));
+  *nagg = lr + li;
+  return MSP_OK;
+}
+
+int level_extras(msp_handle h, Level& L, bool smoothed, cudaStream_t s) {
+  MSP_TRY(L.dpos.alloc(L.A.n));
+  MSP_TRY(L.rdiag.alloc(L.A.n));
+  MSP_TRY(launch_diag_pos(L.A.n, L.A.rp.p, L.A.ci.p, L.dpos.p, s));
+  if (smoothed) {
+    MSP_TRY(launch_rdiag(L.A.n, L.dpos.p, L.A.v.p, L.rdiag.p, h->flags.p, s));
+    MSP_TRY(colour_counts(L.A.rp.p, L.dpos.p, L.A.n, L.cptr, L.cc, s));
+  }
+  MSP_TRY(L.b64.alloc(L.A.n));
+  MSP_TRY(L.x64.alloc(L.A.n));
+  if (h->cfg.precision == MSP_PRECISION_FP32) {
+    MSP_TRY(L.v32.alloc(L.A.nnz));
+    MSP_TRY(L.rdiag32.alloc(L.A.n));
+    MSP_TRY(launch_cast_vals(L.A.nnz, L.A.v.p, L.v32.p, s));
+    MSP_TRY(launch_cast_vals(L.A.n, L.rdiag.p, L.rdiag32.p, s));
+    MSP_TRY(L.b32.alloc(L.A.n));
+    MSP_TRY(L.x32.alloc(L.A.n));
+  }
+  return MSP_OK;
+}
+
+// dense inverse of the coarsest matrix by in-place Gauss-Jordan (partial pivoting)
+int coarse_inverse(msp_handle h, const DCsr& C, cudaStream_t s) {
+  const int n = C.n;
+  DevBuf<double> A, col;
+  DevBuf<int> piv, cp;
+  MSP_TRY(A.alloc((size_t)n * n));
+  MSP_TRY(col.alloc(n));
+  MSP_TRY(piv.alloc(n));
+  MSP_TRY(cp.alloc(n));
+  MSP_TRY(h->cinv.alloc((size_t)n * n));
+  MSP_TRY(launch_csr_to_dense(n, C.rp.p, C.ci.p, C.v.p, A.p, s));
+  for (int k = 0; k < n; ++k) {
+    MSP_TRY(launch_gj_pivot(n, k, A.p, col.p, piv.p, h->flags.p, s));
+    MSP_TRY(launch_gj_update(n, k, A.p, col.p, s));
+  }
+  if (sync_flags(h, s) != MSP_OK) return h->h_flags->code;
+  std::vector<int> hp(n), cols(n);
+  MSP_CUDA_TRY(cudaMemcpyAsync(hp.data(), piv.p, n * sizeof(int), cudaMemcpyDeviceToHost, s));
+  MSP_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int c = 0; c < n; ++c) cols[c] = c;
+  for (int k = n - 1; k >= 0; --k)
+    if (hp[k] != k) std::swap(cols[k], cols[hp[k]]);
+  MSP_CUDA_TRY(cudaMemcpyAsync(cp.p, cols.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+  MSP_TRY(launch_gj_unscramble(n, cp.p, A.p, h->cinv.p, s));
+  MSP_CUDA_TRY(cudaStreamSynchronize(s));
+  h->ncoarse = n;
+  return MSP_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// value setup: decoupling, AMG hierarchy, stage N, BILU(0)
+// ---------------------------------------------------------------------------------
+int value_setup(msp_handle h, cudaStream_t s) {
+  const int nb = h->nb, b = h->b, bb = b * b, bn = b - 1;
+  const size_t nnzb = (size_t)h->nnzb;
+  const msp_config& cfg = h->cfg;
+  h->setup_valid = false;
+  MSP_TRY(reset_flags(h, s));
+  // quasi-IMPES weights omega_i = D_i^{-T} e_0
+  MSP_TRY(h->omega.alloc((size_t)nb * b));
+  MSP_TRY(launch_diag_inverse(b, nb, h->dpos.p, h->vals.p, nullptr, h->omega.p, h->flags.p, s));
+  if (sync_flags(h, s) != MSP_OK) return h->h_flags->code;
+  // level 0: the pressure matrix A_P on the block pattern
+  h->levels.clear();
+  h->levels.emplace_back();
+  {
+    Level& L0 = h->levels[0];
+    L0.A.n = nb;
+    L0.A.nnz = (int)nnzb;
+    MSP_TRY(L0.A.rp.alloc(nb + 1));
+    MSP_TRY(L0.A.ci.alloc(nnzb));
+    MSP_TRY(L0.A.v.alloc(nnzb));
+    MSP_CUDA_TRY(cudaMemcpyAsync(L0.A.rp.p, h->rp.p, (nb + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    MSP_CUDA_TRY(cudaMemcpyAsync(L0.A.ci.p, h->ci.p, nnzb * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    MSP_TRY(launch_pressure_matrix(b, nb, h->rp.p, h->vals.p, h->omega.p, cfg.decoupling != 0,
+                                   L0.A.v.p, s));
+    L0.cptr = h->cptr0;
+    MSP_TRY(L0.perm.alloc(nb));
+    MSP_CUDA_TRY(cudaMemcpyAsync(L0.perm.p, h->perm0.p, nb * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  }
+  // AMG hierarchy (Section 5: UA-AMG, pairwise matching, coarsest size coarse_max)
+  for (int l = 0;; ++l) {
+    const int nF = h->levels[l].A.n;
+    if (nF <= cfg.coarse_max || l + 1 >= cfg.max_levels) break;
+    DevBuf<int> agg;
+    MSP_TRY(agg.alloc(nF));
+    MSP_TRY(launch_iota(nF, agg.p, s));
+    int nc = nF;
+    DCsr cur;  // Galerkin matrix of the previous pass (pass >= 1)
+    for (int pass = 0; pass < cfg.npass; ++pass) {
+      const DCsr& A = (pass == 0) ? h->levels[l].A : cur;
+      DevBuf<int> a1;
+      int n1 = 0;
+      const unsigned long long seed = cfg.agg_seed + (unsigned long long)(2 * l + pass);
+      MSP_TRY(pairwise_pass(h, A, cfg.beta, seed, a1, &n1, s));
+      compose_kernel<<<grid1(nF), kThreads, 0, s>>>(nF, a1.p, agg.p);
+      MSP_TRY(launch_status());
+      nc = n1;
+      if (pass + 1 < cfg.npass) {
+        DCsr nxt;
+        MSP_TRY(galerkin(h, A, a1.p, n1, nxt, s));
+        cur = std::move(nxt);
+      }
+    }
+    if ((double)nc > 0.9 * (double)nF) break;  // coarsening stalled
+    DCsr Ac;
+    MSP_TRY(galerkin(h, h->levels[l].A, agg.p, nc, Ac, s));
+    Level C;
+    DevBuf<int> ipc;
+    MSP_TRY(ipc.alloc(nc));
+    if (nc > cfg.coarse_max && l + 2 < cfg.max_levels) {
+      DevBuf<int> colour;
+      int g = 0;
+      MSP_TRY(colour_graph(h, nc, Ac.rp.p, Ac.ci.p, Ac.nnz, colour, C.perm, C.cptr, &g, s));
+      MSP_TRY(launch_scatter_inverse(nc, C.perm.p, ipc.p, s));
+      DevBuf<int> srcmap;
+      C.A.n = nc;
+      C.A.nnz = Ac.nnz;
+      MSP_TRY(permute_pattern(h, nc, Ac.rp.p, Ac.ci.p, Ac.nnz, ipc.p, C.A.rp, C.A.ci, srcmap, s));
+      MSP_TRY(C.A.v.alloc(Ac.nnz));
+      gather_double_kernel<<<grid1(Ac.nnz), kThreads, 0, s>>>(Ac.nnz, srcmap.p, Ac.v.p, C.A.v.p);
+      MSP_TRY(launch_status());
+      MSP_CUDA_TRY(cudaStreamSynchronize(s));
+    } else {
+      MSP_TRY(C.perm.alloc(nc));
+      MSP_TRY(launch_iota(nc, C.perm.p, s));
+      MSP_TRY(launch_iota(nc, ipc.p, s));
+      C.A = std::move(Ac);
+    }
+    Level& F = h->levels[l];
+    MSP_TRY(F.agg.alloc(nF));
+    map_kernel<<<grid1(nF), kThreads, 0, s>>>(nF, ipc.p, agg.p, F.agg.p);
+    MSP_TRY(launch_status());
+    F.nc = nc;
+    // members of every coarse aggregate, ascending (restriction order)
+    {
+      DevBuf<unsigned long long> keys;
+      MSP_TRY(keys.alloc(nF));
+      member_keys_kernel<<<grid1(nF), kThreads, 0, s>>>(nF, F.agg.p, keys.p);
+      MSP_TRY(launch_status());
+      MSP_TRY(sort_pairs_u64(h->ss, nF, keys.p, nullptr, 64, s));
+      MSP_TRY(F.members.alloc(nF));
+      MSP_TRY(F.mptr.alloc(nc + 1));
+      MSP_TRY(low32_of_keys(nF, keys.p, F.members.p, s));
+      MSP_TRY(rowptr_from_sorted_keys(nF, nc, keys.p, F.mptr.p, s));
+      MSP_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    h->levels.push_back(std::move(C));
+  }
+  if (h->levels.back().A.n > cfg.coarse_hard_max) return MSP_ERR_ARG;
+  for (size_t l = 0; l < h->levels.size(); ++l)
+    MSP_TRY(level_extras(h, h->levels[l], l + 1 < h->levels.size(), s));
+  if (sync_flags(h, s) != MSP_OK) return h->h_flags->code;
+  MSP_TRY(coarse_inverse(h, h->levels.back().A, s));
+  // stage N: concentration sub-blocks and the inverses of their diagonal blocks
+  if (bn > 0) {
+    MSP_TRY(h->aN.alloc(nnzb * bn * bn));
+    MSP_TRY(h->dNinv.alloc((size_t)nb * bn * bn));
+    MSP_TRY(launch_extract_N(b, nnzb, h->vals.p, h->aN.p, s));
+    MSP_TRY(launch_diagN_inverse(b, nb, h->dpos.p, h->vals.p, h->dNinv.p, h->flags.p, s));
+  }
+  // stage R: BILU(0) in colour order
+  MSP_TRY(h->lu.alloc(nnzb * bb));
+  MSP_TRY(h->uinv.alloc((size_t)nb * bb));
+  MSP_CUDA_TRY(cudaMemcpyAsync(h->lu.p, h->vals.p, nnzb * bb * sizeof(double),
+                               cudaMemcpyDeviceToDevice, s));
+  for (int c = 0; c < h->g0; ++c)
+    MSP_TRY(launch_bilu_factor(b, h->cptr0[c], h->cptr0[c + 1], h->rp.p, h->ci.p, h->dpos.p,
+                               h->lu.p, h->uinv.p, h->flags.p, s));
+  if (sync_flags(h, s) != MSP_OK) return h->h_flags->code;
+  if (cfg.precision == MSP_PRECISION_FP32) {
+    MSP_TRY(h->omega32.alloc((size_t)nb * b));
+    MSP_TRY(launch_cast_vals((size_t)nb * b, h->omega.p, h->omega32.p, s));
+    if (bn > 0) {
+      MSP_TRY(h->aN32.alloc(nnzb * bn * bn));
+      MSP_TRY(h->dNinv32.alloc((size_t)nb * bn * bn));
+      MSP_TRY(launch_cast_vals(nnzb * bn * bn, h->aN.p, h->aN32.p, s));
+      MSP_TRY(launch_cast_vals((size_t)nb * bn * bn, h->dNinv.p, h->dNinv32.p, s));
+    }
+    MSP_TRY(h->lu32.alloc(nnzb * bb));
+    MSP_TRY(h->uinv32.alloc((size_t)nb * bb));
+    MSP_TRY(launch_cast_vals(nnzb * bb, h->lu.p, h->lu32.p, s));
+    MSP_TRY(launch_cast_vals((size_t)nb * bb, h->uinv.p, h->uinv32.p, s));
+  }
+  MSP_CUDA_TRY(cudaStreamSynchronize(s));
+  h->setup_calls++;
+  h->setup_valid = true;
+  return MSP_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// preconditioner application (Algorithm 3.1), value type T
+// ---------------------------------------------------------------------------------
+template <typename T>
+struct PView {
+  const T *vals, *omega, *aN, *dNinv, *lu, *uinv;
+  std::vector<const T*> lv, lrd;
+  std::vector<T*> lb, lx;
+  T *r, *y, *x;
+};
+
+PView<double> view64(msp_handle h) {
+  PView<double> p;
+  p.vals = h->vals.p;
+  p.omega = h->cfg.decoupling ? h->omega.p : nullptr;
+  p.aN = h->aN.p;
+  p.dNinv = h->dNinv.p;
+  p.lu = h->lu.p;
+  p.uinv = h->uinv.p;
+  for (auto& L : h->levels) {
+    p.lv.push_back(L.A.v.p);
+    p.lrd.push_back(L.rdiag.p);
+    p.lb.push_back(L.b64.p);
+    p.lx.push_back(L.x64.p);
+  }
+  p.r = h->pr.p;
+  p.y = h->py.p;
+  p.x = h->px.p;
+  return p;
+}
+
+PView<float> view32(msp_handle h) {
+  PView<float> p;
+  p.vals = h->vals32.p;
+  p.omega = h->cfg.decoupling ? h->omega32.p : nullptr;
+  p.aN = h->aN32.p;
+  p.dNinv = h->dNinv32.p;
+  p.lu = h->lu32.p;
+  p.uinv = h->uinv32.p;
+  for (auto& L : h->levels) {
+    p.lv.push_back(L.v32.p);
+    p.lrd.push_back(L.rdiag32.p);
+    p.lb.push_back(L.b32.p);
+    p.lx.push_back(L.x32.p);
+  }
+  p.r = h->pr32.p;
+  p.y = h->py32.p;
+  p.x = h->px32.p;
+  return p;
+}
+
+// algorithmic bytes of one colour sweep launch over rows [r0, r1) reading `entries`
+// nonzeros of `eb` bytes each (value + column index) plus `rowb` bytes per row
+inline double sweep_bytes(int r0, int r1, long long entries, double eb, double rowb) {
+  return (double)entries * eb + (double)(r1 - r0) * rowb;
+}
+
+template <typename T>
+int vcycle(msp_handle h, const PView<T>& P, int l, cudaStream_t s) {
+  Level& L = h->levels[l];
+  const int n = L.A.n;
+  const double sT = sizeof(T);
+  if (l + 1 == (int)h->levels.size()) {
+    Probe pr("coarse_gemv", (double)n * n * 8.0 + 2.0 * n * sT, s);
+    return launch_dense_gemv<T>(n, h->cinv.p, P.lb[l], P.lx[l], s);
+  }
+  const int g = (int)L.cptr.size() - 1;
+  if (h->cfg.pre_sweeps <= 0) MSP_CUDA_TRY(cudaMemsetAsync(P.lx[l], 0, n * sizeof(T), s));
+  for (int sw = 0; sw < h->cfg.pre_sweeps; ++sw)
+    for (int c = 0; c < g; ++c) {
+      const long long e = L.cc.lower[c] + (sw == 0 ? 0 : L.cc.upper[c]);
+      Probe pr("amg_gs_sweep", sweep_bytes(L.cptr[c], L.cptr[c + 1], e, sT + 4, 3 * sT + 12), s);
+      MSP_TRY(launch_csr_gs_colour<T>(L.cptr[c], L.cptr[c + 1], L.A.rp.p, L.A.ci.p, P.lv[l],
+                                      L.dpos.p, P.lrd[l], P.lb[l], P.lx[l], sw == 0, s));
+    }
+  {
+    Probe pr("amg_residual_restrict",
+             (double)L.A.nnz * (sT + 4) + (double)n * (3 * sT + 12) + (double)L.nc * (sT + 4), s);
+    MSP_TRY(launch_csr_residual_restrict<T>(L.nc, L.mptr.p, L.members.p, L.A.rp.p, L.A.ci.p,
+                                            P.lv[l], P.lb[l], P.lx[l], P.lb[l + 1], s));
+  }
+  MSP_TRY(vcycle<T>(h, P, l + 1, s));
+  {
+    Probe pr("amg_prolong", (double)n * (3 * sT + 4), s);
+    MSP_TRY(launch_prolong_add<T>(n, L.agg.p, P.lx[l + 1], P.lx[l], s));
+  }
+  for (int sw = 0; sw < h->cfg.post_sweeps; ++sw)
+    for (int c = g - 1; c >= 0; --c) {
+      const long long e = L.cc.lower[c] + L.cc.upper[c];
+      Probe pr("amg_gs_sweep", sweep_bytes(L.cptr[c], L.cptr[c + 1], e, sT + 4, 3 * sT + 12), s);
+      MSP_TRY(launch_csr_gs_colour<T>(L.cptr[c], L.cptr[c + 1], L.A.rp.p, L.A.ci.p, P.lv[l],
+                                      L.dpos.p, P.lrd[l], P.lb[l], P.lx[l], false, s));
+    }
+  return MSP_OK;
+}
+
+template <typename T>
+int stage_N(msp_handle h, const PView<T>& P, const T* g, T* w, cudaStream_t s) {
+  const int b = h->b;
+  if (h->cfg.bgs_sweeps <= 0) {
+    MSP_CUDA_TRY(cudaMemsetAsync(w, 0, (size_t)h->nb * b * sizeof(T), s));
+    return MSP_OK;
+  }
+  const double sT = sizeof(T), bn = b - 1;
+  for (int sw = 0; sw < h->cfg.bgs_sweeps; ++sw)
+    for (int c = 0; c < h->g0; ++c) {
+      const long long e = h->cc0.lower[c] + (sw == 0 ? 0 : h->cc0.upper[c]);
+      Probe pr("stageN_bgs_sweep",
+               sweep_bytes(h->cptr0[c], h->cptr0[c + 1], e, bn * bn * sT + 4,
+                           (2 * bn + 1 + bn * bn) * sT + 12), s);
+      MSP_TRY(launch_bgs_colour<T>(b, h->cptr0[c], h->cptr0[c + 1], h->rp.p, h->ci.p, h->dpos.p,
+                                   P.aN, P.dNinv, g, w, sw == 0, sw == 0, s));
+    }
+  return MSP_OK;
+}
+
+// algorithmic bytes of a BSR row sweep over all block rows (values, columns, row
+// pointers, the input vector once, `vecs` further vectors of nb*b values)
+inline double bsr_bytes(msp_handle h, double sT, double vecs) {
+  const double b = h->b;
+  return (double)h->nnzb * (b * b * sT + 4) + (double)(h->nb + 1) * 4 +
+         (double)h->nb * b * sT * (1 + vecs);
+}
+
+template <typename T>
+int stage_P(msp_handle h, const PView<T>& P, const T* g, T* w, cudaStream_t s) {
+  const double sT = sizeof(T);
+  {
+    Probe pr("stageP_residual_restrict", bsr_bytes(h, sT, 2) + (double)h->nb * sT, s);
+    MSP_TRY(launch_bsr_restrict_p<T>(h->b, h->nb, h->rp.p, h->ci.p, P.vals, w, g, P.omega,
+                                     P.lb[0], s));
+  }
+  MSP_TRY(vcycle<T>(h, P, 0, s));
+  Probe pr("stageP_prolong", (double)h->nb * 3 * sT, s);
+  return launch_prolong_p<T>(h->b, h->nb, P.lx[0], w, s);
+}
+
+template <typename T>
+int stage_R(msp_handle h, const PView<T>& P, const T* r, T* w, cudaStream_t s) {
+  const int b = h->b;
+  const double sT = sizeof(T), bb = (double)b * b;
+  for (int c = 0; c < h->g0; ++c) {
+    Probe pr("stageR_bilu_fwd",
+             sweep_bytes(h->cptr0[c], h->cptr0[c + 1], h->cc0.lower[c], bb * sT + 4,
+                         3.0 * b * sT + 12), s);
+    MSP_TRY(launch_bilu_fwd<T>(b, h->cptr0[c], h->cptr0[c + 1], h->rp.p, h->ci.p, h->dpos.p, P.lu,
+                               r, P.y, s));
+  }
+  for (int c = h->g0 - 1; c >= 0; --c) {
+    Probe pr("stageR_bilu_bwd",
+             sweep_bytes(h->cptr0[c], h->cptr0[c + 1], h->cc0.upper[c], bb * sT + 4,
+                         (5.0 * b + bb) * sT + 12), s);
+    MSP_TRY(launch_bilu_bwd<T>(b, h->cptr0[c], h->cptr0[c + 1], h->rp.p, h->ci.p, h->dpos.p, P.lu,
+                               P.uinv, P.y, P.x, w, s));
+  }
+  return MSP_OK;
+}
+
+// w = B g (colour-ordered vectors of nb*b values of type T)
+template <typename T>
+int apply_precond_t(msp_handle h, const PView<T>& P, const T* g, T* w, cudaStream_t s) {
+  const size_t n = (size_t)h->nb * h->b;
+  switch (h->cfg.precond) {
+    case MSP_PREC_NONE:
+      MSP_CUDA_TRY(cudaMemcpyAsync(w, g, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+      return MSP_OK;
+    case MSP_PREC_N_ONLY:
+      if (h->b < 2) {
+        MSP_CUDA_TRY(cudaMemsetAsync(w, 0, n * sizeof(T), s));
+        return MSP_OK;
+      }
+      return stage_N<T>(h, P, g, w, s);
+    case MSP_PREC_P_ONLY:
+      MSP_CUDA_TRY(cudaMemsetAsync(w, 0, n * sizeof(T), s));
+      return stage_P<T>(h, P, g, w, s);
+    case MSP_PREC_R_ONLY:
+      MSP_CUDA_TRY(cudaMemsetAsync(w, 0, n * sizeof(T), s));
+      return stage_R<T>(h, P, g, w, s);
+    default:
+      break;
+  }
+  // Algorithm 3.1 with w = 0: r = g; w += Pi_N B_N Pi_N^T r
+  if (h->b >= 2)
+    MSP_TRY(stage_N<T>(h, P, g, w, s));
+  else
+    MSP_CUDA_TRY(cudaMemsetAsync(w, 0, n * sizeof(T), s));
+  // r = g - A w; w += Pi_P B_P Pi_P^T r  (residual fused into the restriction)
+  MSP_TRY(stage_P<T>(h, P, g, w, s));
+  // r = g - A w; w += R r
+  {
+    Probe pr("msp_residual_spmv", bsr_bytes(h, sizeof(T), 2), s);
+    MSP_TRY(launch_bsr_spmv<T>(h->b, h->nb, h->rp.p, h->ci.p, P.vals, w, g, P.r, true, s));
+  }
+  return stage_R<T>(h, P, P.r, w, s);
+}
+
+// w = B g on FP64 colour-ordered vectors, in the configured precision
+int apply_precond(msp_handle h, const double* g, double* w, cudaStream_t s) {
+  if (h->cfg.precision == MSP_PRECISION_FP32) {
+    const size_t n = (size_t)h->nb * h->b;
+    MSP_TRY(launch_cast_d2f(n, g, h->g32.p, s));
+    MSP_TRY(apply_precond_t<float>(h, view32(h), h->g32.p, h->w32.p, s));
+    return launch_cast_f2d(n, h->w32.p, w, s);
+  }
+  return apply_precond_t<double>(h, view64(h), g, w, s);
+}
+
+int alloc_work(msp_handle h) {
+  const size_t n = (size_t)h->nb * h->b;
+  const int m = h->cfg.restart;
+  MSP_TRY(h->pr.alloc(n));
+  MSP_TRY(h->py.alloc(n));
+  MSP_TRY(h->px.alloc(n));
+  if (h->cfg.precision == MSP_PRECISION_FP32) {
+    MSP_TRY(h->g32.alloc(n));
+    MSP_TRY(h->w32.alloc(n));
+    MSP_TRY(h->pr32.alloc(n));
+    MSP_TRY(h->py32.alloc(n));
+    MSP_TRY(h->px32.alloc(n));
+    MSP_TRY(h->vals32.alloc((size_t)h->nnzb * h->b * h->b));
+  }
+  MSP_TRY(h->V.alloc((size_t)(m + 1) * n));
+  MSP_TRY(h->Z.alloc((size_t)m * n));
+  MSP_TRY(h->bperm.alloc(n));
+  MSP_TRY(h->xperm.alloc(n));
+  MSP_TRY(h->rvec.alloc(n));
+  MSP_TRY(h->partial.alloc((size_t)krylov_blocks() * 72));
+  MSP_TRY(h->hdev.alloc(72));
+  MSP_TRY(h->nrm.alloc(72));
+  MSP_TRY(h->ydev.alloc(72));
+  MSP_TRY(h->ifl.alloc(4));
+  return MSP_OK;
+}
+
+// ||x||_2 of a device vector (deterministic reduction), synchronous
+int norm2(msp_handle h, const double* x, size_t n, double* out, cudaStream_t s) {
+  const int nbk = krylov_blocks();
+  MSP_TRY(launch_norm2_partial(n, x, h->partial.p, nbk, s));
+  MSP_TRY(launch_reduce_partials(1, nbk, h->partial.p, h->nrm.p, false, s));
+  MSP_CUDA_TRY(cudaMemcpyAsync(h->h_pin, h->nrm.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  MSP_CUDA_TRY(cudaStreamSynchronize(s));
+  *out = std::sqrt(h->h_pin[0]);
+  return MSP_OK;
+}
+
+int refresh_values(msp_handle h, const double* d_user_values, cudaStream_t s) {
+  const int bb = h->b * h->b;
+  MSP_TRY(launch_gather_values((size_t)h->nnzb, bb, h->src.p, d_user_values, h->vals.p, s));
+  if (h->cfg.precision == MSP_PRECISION_FP32)
+    MSP_TRY(launch_cast_vals((size_t)h->nnzb * bb, h->vals.p, h->vals32.p, s));
+  return MSP_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// FGMRES(m) on colour-ordered vectors (x0 = 0)
+// ---------------------------------------------------------------------------------
+int fgmres(msp_handle h, double tol, int* iters, double* relres, double* relres_est,
+           cudaStream_t s) {
+  const size_t n = (size_t)h->nb * h->b;
+  const int m = h->cfg.restart;
+  const int nbk = krylov_blocks();
+  const double* bvec = h->bperm.p;
+  double* x = h->xperm.p;
+  double* V = h->V.p;
+  double* Z = h->Z.p;
+  *iters = 0;
+  *relres = 0.0;
+  *relres_est = 0.0;
+  double bnorm = 0.0;
+  MSP_TRY(norm2(h, bvec, n, &bnorm, s));
+  if (!std::isfinite(bnorm)) return MSP_ERR_NONFINITE;
+  MSP_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  if (bnorm == 0.0) return MSP_OK;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), sv(m + 1), y(m);
+  int it = 0, status = MSP_NOT_CONVERGED;
+  double est = 1.0;
+  while (true) {
+    MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, x, bvec, h->rvec.p,
+                                    true, s));
+    double beta = 0.0;
+    MSP_TRY(norm2(h, h->rvec.p, n, &beta, s));
+    if (!std::isfinite(beta)) return MSP_ERR_NONFINITE;
+    if (beta / bnorm <= tol) {
+      est = beta / bnorm;
+      status = MSP_OK;
+      break;
+    }
+    if (it >= h->cfg.max_it) break;
+    MSP_TRY(launch_scale(n, h->rvec.p, 1.0 / beta, V, s));
+    std::fill(sv.begin(), sv.end(), 0.0);
+    sv[0] = beta;
+    int j_used = 0;
+    bool breakdown = false;
+    for (int j = 0; j < m; ++j) {
+      double* vj = V + (size_t)j * n;
+      double* zj = Z + (size_t)j * n;
+      double* w = V + (size_t)(j + 1) * n;
+      MSP_TRY(apply_precond(h, vj, zj, s));
+      {
+        Probe pr("krylov_spmv", bsr_bytes(h, 8.0, 1), s);
+        MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, zj, nullptr, w,
+                                        false, s));
+      }
+      ++it;
+      // classical Gram-Schmidt, twice
+      const int K = j + 1;
+      for (int pass = 0; pass < 2; ++pass) {
+        double* hc = pass == 0 ? h->hdev.p : h->ydev.p;
+        {
+          Probe pr("krylov_multi_dot", (double)(K + 1) * n * 8.0, s);
+          MSP_TRY(launch_multi_dot(n, V, n, K, w, h->partial.p, nbk, s));
+        }
+        MSP_TRY(launch_reduce_partials(K, nbk, h->partial.p, hc, false, s));
+        Probe pr("krylov_multi_axpy", (double)(K + 2) * n * 8.0, s);
+        MSP_TRY(launch_multi_axpy_norm(n, V, n, K, hc, w, h->partial.p, nbk, s));
+      }
+      MSP_TRY(launch_reduce_partials(K, 1, h->ydev.p, h->hdev.p, true, s));  // h = h1 + h2
+      MSP_TRY(launch_reduce_partials(1, nbk, h->partial.p, h->nrm.p, false, s));
+      MSP_TRY(launch_normalize(n, w, h->nrm.p, w, h->nrm.p + 1, s));
+      MSP_CUDA_TRY(cudaMemcpyAsync(h->h_pin, h->hdev.p, K * sizeof(double), cudaMemcpyDeviceToHost, s));
+      MSP_CUDA_TRY(cudaMemcpyAsync(h->h_pin + 64, h->nrm.p + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+      MSP_CUDA_TRY(cudaStreamSynchronize(s));
+      for (int i = 0; i < K; ++i) H[(size_t)i * m + j] = h->h_pin[i];
+      const double hn = h->h_pin[64];
+      H[(size_t)(j + 1) * m + j] = hn;
+      for (int i = 0; i < j; ++i) {
+        const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+      }
+      const double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+      const double rho = std::sqrt(a * a + c * c);
+      if (rho == 0.0) {
+        cs[j] = 1.0;
+        sn[j] = 0.0;
+      } else {
+        cs[j] = a / rho;
+        sn[j] = c / rho;
+      }
+      H[(size_t)j * m + j] = rho;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      sv[j + 1] = -sn[j] * sv[j];
+      sv[j] = cs[j] * sv[j];
+      j_used = j + 1;
+      est = std::fabs(sv[j + 1]) / bnorm;
+      if (!std::isfinite(est)) return MSP_ERR_NONFINITE;
+      if (hn == 0.0) breakdown = true;
+      if (est <= tol || it >= h->cfg.max_it || breakdown) break;
+    }
+    for (int i = j_used - 1; i >= 0; --i) {
+      double t = sv[i];
+      for (int k = i + 1; k < j_used; ++k) t -= H[(size_t)i * m + k] * y[k];
+      y[i] = H[(size_t)i * m + i] != 0.0 ? t / H[(size_t)i * m + i] : 0.0;
+    }
+    MSP_CUDA_TRY(cudaMemcpyAsync(h->ydev.p, y.data(), j_used * sizeof(double), cudaMemcpyHostToDevice, s));
+    MSP_TRY(launch_update_x(n, Z, n, j_used, h->ydev.p, x, s));
+    MSP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (breakdown) {
+      MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, x, bvec,
+                                      h->rvec.p, true, s));
+      double rr = 0.0;
+      MSP_TRY(norm2(h, h->rvec.p, n, &rr, s));
+      rr /= bnorm;
+      if (!(rr <= tol)) {
+        *iters = it;
+        *relres = rr;
+        *relres_est = est;
+        return MSP_ERR_BREAKDOWN;
+      }
+    }
+  }
+  MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, x, bvec, h->rvec.p,
+                                  true, s));
+  double rr = 0.0;
+  MSP_TRY(norm2(h, h->rvec.p, n, &rr, s));
+  *relres = rr / bnorm;
+  *relres_est = est;
+  *iters = it;
+  return status;
+}
+
+int pattern_setup(msp_handle h, const int32_t* d_rp, const int32_t* d_ci, cudaStream_t s) {
+  const int nb = h->nb;
+  const size_t nnzb = (size_t)h->nnzb;
+  DevBuf<int> urp, uci, udpos;
+  MSP_TRY(urp.alloc(nb + 1));
+  MSP_TRY(uci.alloc(nnzb));
+  MSP_TRY(udpos.alloc(nb));
+  MSP_CUDA_TRY(cudaMemcpyAsync(urp.p, d_rp, (nb + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  MSP_CUDA_TRY(cudaMemcpyAsync(uci.p, d_ci, nnzb * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  int hr[2] = {0, 0};
+  MSP_CUDA_TRY(cudaMemcpyAsync(&hr[0], urp.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MSP_CUDA_TRY(cudaMemcpyAsync(&hr[1], urp.p + nb, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MSP_CUDA_TRY(cudaStreamSynchronize(s));
+  if (hr[0] != 0 || (int64_t)hr[1] != h->nnzb) return MSP_ERR_PATTERN;
+  MSP_TRY(reset_flags(h, s));
+  MSP_TRY(launch_check_pattern(nb, urp.p, uci.p, udpos.p, h->flags.p, s));
+  if (sync_flags(h, s) != MSP_OK) return h->h_flags->code;
+  // colouring of the block graph (Algorithms 4.1/4.2) and the colour permutation
+  MSP_TRY(colour_graph(h, nb, urp.p, uci.p, (int)nnzb, h->colour0, h->perm0, h->cptr0, &h->g0, s));
+  MSP_TRY(h->iperm0.alloc(nb));
+  MSP_TRY(launch_scatter_inverse(nb, h->perm0.p, h->iperm0.p, s));
+  MSP_TRY(permute_pattern(h, nb, urp.p, uci.p, (int)nnzb, h->iperm0.p, h->rp, h->ci, h->src, s));
+  MSP_TRY(h->dpos.alloc(nb));
+  MSP_TRY(launch_diag_pos(nb, h->rp.p, h->ci.p, h->dpos.p, s));
+  MSP_TRY(colour_counts(h->rp.p, h->dpos.p, nb, h->cptr0, h->cc0, s));
+  MSP_CUDA_TRY(cudaStreamSynchronize(s));
+  return MSP_OK;
+}
+
+void destroy(msp_handle h) {
+  if (!h) return;
+  if (h->h_flags) cudaFreeHost(h->h_flags);
+  if (h->h_pin) cudaFreeHost(h->h_pin);
+  if (h->ss) sort_scratch_destroy(h->ss);
+  delete h;
+}
+
+bool config_ok(const msp_config& c, int b) {
+  return c.mu >= 0 && c.restart >= 1 && c.restart <= 64 && c.max_it >= 0 && c.coarse_max >= 1 &&
+         c.npass >= 1 && c.npass <= 4 && c.pre_sweeps >= 0 && c.post_sweeps >= 0 &&
+         c.bgs_sweeps >= 0 && c.bilu_order == 0 && c.precond >= 0 && c.precond <= 4 &&
+         c.max_levels >= 1 && c.beta >= 0.0 && c.coarse_hard_max >= 1 &&
+         (c.precision == MSP_PRECISION_FP64 || c.precision == MSP_PRECISION_FP32) && b >= 1 &&
+         b <= 8;
+}
+
+}  // namespace
+}  // namespace msp
+
+using namespace msp;
+
+extern "C" {
+
+int msp_config_default(msp_config* c) {
+  if (!c) return MSP_ERR_ARG;
+  c->mu = 20;
+  c->restart = 30;
+  c->max_it = 1000;
+  c->coarse_max = 10000;
+  c->npass = 2;
+  c->pre_sweeps = 1;
+  c->post_sweeps = 1;
+  c->bgs_sweeps = 1;
+  c->decoupling = 1;
+  c->bilu_order = 0;
+  c->precond = MSP_PREC_MSP;
+  c->max_levels = 20;
+  c->beta = 0.25;
+  c->agg_seed = 0x2208085940ULL;
+  c->coarse_hard_max = 20000;
+  c->precision = MSP_PRECISION_FP64;
+  return MSP_OK;
+}
+
+const char* msp_status_string(int st) {
+  switch (st) {
+    case MSP_OK: return "ok";
+    case MSP_NOT_CONVERGED: return "not converged (MaxIt reached)";
+    case MSP_ERR_ARG: return "invalid argument";
+    case MSP_ERR_PATTERN: return "invalid BSR pattern (unsorted/out-of-range columns or missing diagonal)";
+    case MSP_ERR_SINGULAR_BLOCK: return "singular diagonal block, pivot or coarsest matrix";
+    case MSP_ERR_NONFINITE: return "non-finite value";
+    case MSP_ERR_BREAKDOWN: return "Krylov breakdown";
+    case MSP_ERR_NOMEM: return "out of device memory";
+    case MSP_ERR_TIMEOUT: return "a bounded device loop exceeded its limit";
+    case MSP_ERR_CUDA: return "CUDA error";
+    default: return "unknown status";
+  }
+}
+
+// Last CUDA error text of this thread (diagnostics; not part of the stable ABI).
+const char* msp_last_error(void) { return g_last_error.c_str(); }
+
+int msp_setup(msp_handle* out, const msp_config* cfg, int32_t nb, int32_t b,
+              const int32_t* d_row_ptr, const int32_t* d_col_idx, const double* d_values,
+              int64_t nnzb, void* stream) {
+  if (!out) return MSP_ERR_ARG;
+  *out = nullptr;
+  if (!cfg || nb <= 0 || b < 1 || b > 8 || nnzb < nb || nnzb > 0x7fffffffLL || !d_row_ptr ||
+      !d_col_idx || !d_values || !config_ok(*cfg, b))
+    return MSP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  msp_handle h = nullptr;
+  try {
+    h = new msp_handle_s();
+    h->cfg = *cfg;
+    h->nb = nb;
+    h->b = b;
+    h->nnzb = nnzb;
+    cudaGetDevice(&h->device);
+    h->ss = sort_scratch_create();
+    int st = h->flags.alloc(1);
+    if (st == MSP_OK && cudaMallocHost(&h->h_flags, sizeof(DevFlags)) != cudaSuccess) st = MSP_ERR_NOMEM;
+    if (st == MSP_OK && cudaMallocHost(&h->h_pin, 128 * sizeof(double)) != cudaSuccess) st = MSP_ERR_NOMEM;
+    if (st == MSP_OK) {
+      auto t0 = Clock::now();
+      st = pattern_setup(h, d_row_ptr, d_col_idx, s);
+      if (st == MSP_OK) st = h->vals.alloc((size_t)nnzb * b * b);
+      if (st == MSP_OK) st = alloc_work(h);
+      if (st == MSP_OK) st = reset_flags(h, s);
+      if (st == MSP_OK) st = launch_check_finite_vals((size_t)nnzb * b * b, d_values, h->flags.p, s);
+      if (st == MSP_OK && sync_flags(h, s) != MSP_OK) st = h->h_flags->code;
+      if (st == MSP_OK) st = refresh_values(h, d_values, s);
+      if (st == MSP_OK) st = value_setup(h, s);
+      (void)t0;
+    }
+    if (st != MSP_OK) {
+      destroy(h);
+      return st;
+    }
+  } catch (const std::bad_alloc&) {
+    destroy(h);
+    return MSP_ERR_NOMEM;
+  } catch (...) {
+    destroy(h);
+    return MSP_ERR_CUDA;
+  }
+  *out = h;
+  return MSP_OK;
+}
+
+int msp_update_values(msp_handle h, const double* d_values, void* stream) {
+  if (!h || !d_values) return MSP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    MSP_TRY(reset_flags(h, s));
+    MSP_TRY(launch_check_finite_vals((size_t)h->nnzb * h->b * h->b, d_values, h->flags.p, s));
+    if (sync_flags(h, s) != MSP_OK) return h->h_flags->code;
+    return refresh_values(h, d_values, s);
+  } catch (...) {
+    return MSP_ERR_NOMEM;
+  }
+}
+
+int msp_update_values_host(msp_handle h, const double* h_values, void* stream) {
+  if (!h || !h_values) return MSP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t cnt = (size_t)h->nnzb * h->b * h->b;
+  if (!h->staging.p) MSP_TRY(h->staging.alloc(cnt));
+  MSP_CUDA_TRY(cudaMemcpyAsync(h->staging.p, h_values, cnt * sizeof(double),
+                               cudaMemcpyHostToDevice, s));
+  return msp_update_values(h, h->staging.p, stream);
+}
+
+int msp_solve(msp_handle h, const double* d_b, double* d_x, double rel_tol,
+              msp_solve_info* info, void* stream) {
+  if (!h || !d_b || !d_x || !(rel_tol > 0.0)) return MSP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  msp_solve_info local{};
+  msp_solve_info* inf = info ? info : &local;
+  std::memset(inf, 0, sizeof(*inf));
+  try {
+    const size_t n = (size_t)h->nb * h->b;
+    MSP_CUDA_TRY(cudaMemsetAsync(h->ifl.p, 0, sizeof(int), s));
+    MSP_TRY(launch_check_finite(n, d_b, h->ifl.p, s));
+    int bad = 0;
+    MSP_CUDA_TRY(cudaMemcpyAsync(&bad, h->ifl.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MSP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (bad) {
+      inf->status = MSP_ERR_NONFINITE;
+      return MSP_ERR_NONFINITE;
+    }
+    // adaptive setup (Section 3.2)
+    auto ts = Clock::now();
+    if (!h->first_solve && (h->prev_it > h->cfg.mu || !h->setup_valid)) {
+      const int st = value_setup(h, s);
+      if (st != MSP_OK) {
+        inf->status = st;
+        return st;
+      }
+      inf->setup_performed = 1;
+    } else if (h->first_solve) {
+      inf->setup_performed = 1;  // generated by msp_setup (iota = 1)
+    }
+    inf->t_setup_ms = ms_since(ts);
+    h->first_solve = false;
+    auto t0 = Clock::now();
+    MSP_TRY(launch_gather_blocks(h->nb, h->b, h->perm0.p, d_b, h->bperm.p, s));
+    int it = 0;
+    double rr = 0.0, est = 0.0;
+    const int st = fgmres(h, rel_tol, &it, &rr, &est, s);
+    if (st >= 0 || st == MSP_ERR_BREAKDOWN)
+      MSP_TRY(launch_scatter_blocks(h->nb, h->b, h->perm0.p, h->xperm.p, d_x, s));
+    MSP_CUDA_TRY(cudaStreamSynchronize(s));
+    h->prev_it = it;
+    inf->status = st;
+    inf->iterations = it;
+    inf->setup_calls = h->setup_calls;
+    inf->levels = (int)h->levels.size();
+    inf->colours_l0 = h->g0;
+    inf->rel_residual = rr;
+    inf->rel_residual_est = est;
+    inf->t_solve_ms = ms_since(t0);
+    return st;
+  } catch (...) {
+    inf->status = MSP_ERR_NOMEM;
+    return MSP_ERR_NOMEM;
+  }
+}
+
+int msp_solve_host(msp_handle h, const double* h_b, double* h_x, double rel_tol,
+                   msp_solve_info* info, void* stream) {
+  if (!h || !h_b || !h_x) return MSP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)h->nb * h->b, bytes = n * sizeof(double);
+  if (!h->e2e_b.p) MSP_TRY(h->e2e_b.alloc(n));
+  if (!h->e2e_x.p) MSP_TRY(h->e2e_x.alloc(n));
+  MSP_CUDA_TRY(cudaMemcpyAsync(h->e2e_b.p, h_b, bytes, cudaMemcpyHostToDevice, s));
+  const int st = msp_solve(h, h->e2e_b.p, h->e2e_x.p, rel_tol, info, stream);
+  if (st < 0 && st != MSP_ERR_BREAKDOWN) return st;
+  MSP_CUDA_TRY(cudaMemcpyAsync(h_x, h->e2e_x.p, bytes, cudaMemcpyDeviceToHost, s));
+  MSP_CUDA_TRY(cudaStreamSynchronize(s));
+  return st;
+}
+
+int msp_free(msp_handle h) {
+  destroy(h);
+  return MSP_OK;
+}
+
+int msp_apply_precond(msp_handle h, const double* d_g, double* d_w, void* stream) {
+  if (!h || !d_g || !d_w) return MSP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    MSP_TRY(launch_gather_blocks(h->nb, h->b, h->perm0.p, d_g, h->bperm.p, s));
+    MSP_TRY(apply_precond(h, h->bperm.p, h->xperm.p, s));
+    MSP_TRY(launch_scatter_blocks(h->nb, h->b, h->perm0.p, h->xperm.p, d_w, s));
+    MSP_CUDA_TRY(cudaStreamSynchronize(s));
+    return MSP_OK;
+  } catch (...) {
+    return MSP_ERR_NOMEM;
+  }
+}
+
+int msp_spmv(msp_handle h, const double* d_x, double* d_y, void* stream) {
+  if (!h || !d_x || !d_y) return MSP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  MSP_TRY(launch_gather_blocks(h->nb, h->b, h->perm0.p, d_x, h->bperm.p, s));
+  MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, h->bperm.p, nullptr,
+                                  h->xperm.p, false, s));
+  MSP_TRY(launch_scatter_blocks(h->nb, h->b, h->perm0.p, h->xperm.p, d_y, s));
+  MSP_CUDA_TRY(cudaStreamSynchronize(s));
+  return MSP_OK;
+}
+
+int msp_stats_enable(int mode) {
+  if (mode < 0 || mode > 2) return MSP_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_stats_mu);
+  g_stats_mode = mode;
+  return MSP_OK;
+}
+
+int msp_stats_reset(void) {
+  std::lock_guard<std::mutex> lk(g_stats_mu);
+  resolve_pending();
+  g_sites.clear();
+  g_launches = 0;
+  return MSP_OK;
+}
+
+long long msp_stats_launches(void) {
+  std::lock_guard<std::mutex> lk(g_stats_mu);
+  return g_launches;
+}
+
+int msp_stats_count(void) {
+  std::lock_guard<std::mutex> lk(g_stats_mu);
+  resolve_pending();
+  return (int)g_sites.size();
+}
+
+int msp_stats_get(int index, char* name, int name_len, long long* launches, double* total_ms,
+                  double* bytes) {
+  std::lock_guard<std::mutex> lk(g_stats_mu);
+  resolve_pending();
+  if (index < 0 || index >= (int)g_sites.size()) return MSP_ERR_ARG;
+  const StatSite& st = g_sites[index];
+  if (name && name_len > 0) {
+    std::strncpy(name, st.name.c_str(), name_len - 1);
+    name[name_len - 1] = 0;
+  }
+  if (launches) *launches = st.launches;
+  if (total_ms) *total_ms = st.ms;
+  if (bytes) *bytes = st.bytes;
+  return MSP_OK;
+}
+
+int msp_num_levels(msp_handle h) { return h ? (int)h->levels.size() : MSP_ERR_ARG; }
+
+int msp_level_info(msp_handle h, int level, int32_t* n, int32_t* nnz, int32_t* ncolours) {
+  if (!h || level < 0 || level >= (int)h->levels.size()) return MSP_ERR_ARG;
+  const Level& L = h->levels[level];
+  if (n) *n = L.A.n;
+  if (nnz) *nnz = L.A.nnz;
+  if (ncolours) *ncolours = L.cptr.empty() ? 0 : (int)L.cptr.size() - 1;
+  return MSP_OK;
+}
+
+int msp_level_get(msp_handle h, int level, int32_t* h_perm, int32_t* h_cptr, int32_t* h_agg,
+                  int32_t* h_row_ptr, int32_t* h_col_idx, double* h_values) {
+  if (!h || level < 0 || level >= (int)h->levels.size()) return MSP_ERR_ARG;
+  const Level& L = h->levels[level];
+  const int n = L.A.n;
+  if (h_perm) MSP_CUDA_TRY(cudaMemcpy(h_perm, L.perm.p, n * sizeof(int), cudaMemcpyDeviceToHost));
+  if (h_cptr && !L.cptr.empty()) std::copy(L.cptr.begin(), L.cptr.end(), h_cptr);
+  if (h_agg) {
+    if (L.agg.p)
+      MSP_CUDA_TRY(cudaMemcpy(h_agg, L.agg.p, n * sizeof(int), cudaMemcpyDeviceToHost));
+    else
+      std::fill(h_agg, h_agg + n, -1);
+  }
+  if (h_row_ptr)
+    MSP_CUDA_TRY(cudaMemcpy(h_row_ptr, L.A.rp.p, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+  if (h_col_idx)
+    MSP_CUDA_TRY(cudaMemcpy(h_col_idx, L.A.ci.p, L.A.nnz * sizeof(int), cudaMemcpyDeviceToHost));
+  if (h_values)
+    MSP_CUDA_TRY(cudaMemcpy(h_values, L.A.v.p, L.A.nnz * sizeof(double), cudaMemcpyDeviceToHost));
+  return MSP_OK;
+}
+
+int msp_colour0(msp_handle h, int32_t* h_colour) {
+  if (!h || !h_colour) return MSP_ERR_ARG;
+  MSP_CUDA_TRY(cudaMemcpy(h_colour, h->colour0.p, h->nb * sizeof(int), cudaMemcpyDeviceToHost));
+  return h->g0;
+}
+
+}  // extern "C"

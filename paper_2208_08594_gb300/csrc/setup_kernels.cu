@@ -1,0 +1,425 @@
+// Setup kernels without bit-exactness requirements: pattern validation, value
+// gathers, stage-N sub-blocks, BILU(0) factorisation by colour, the dense inverse of
+// the coarsest AMG matrix (in-place Gauss-Jordan with partial pivoting), casts.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "setup_kernels.h"
+
+namespace msp {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int launch_status() { return launch_check(__FILE__, __LINE__); }
+
+__device__ void raise_flag(DevFlags* f, int code, int index) {
+  if (atomicCAS(&f->code, MSP_OK, code) == MSP_OK) f->index = index;
+}
+
+__global__ void check_pattern_kernel(int nb, const int* __restrict__ rp, const int* __restrict__ ci,
+                                     int* __restrict__ dpos, DevFlags* flags) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
+    const int p0 = rp[i], p1 = rp[i + 1];
+    if (p1 < p0) {
+      raise_flag(flags, MSP_ERR_PATTERN, i);
+      continue;
+    }
+    int d = -1;
+    for (int p = p0; p < p1; ++p) {
+      const int j = ci[p];
+      if (j < 0 || j >= nb || (p > p0 && j <= ci[p - 1])) {
+        raise_flag(flags, MSP_ERR_PATTERN, i);
+        d = -2;
+        break;
+      }
+      if (j == i) d = p;
+    }
+    if (d == -1) raise_flag(flags, MSP_ERR_PATTERN, i);
+    dpos[i] = d;
+  }
+}
+
+__global__ void check_finite_vals_kernel(size_t n, const double* __restrict__ v, DevFlags* flags) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+       k += (size_t)gridDim.x * blockDim.x)
+    if (!isfinite(v[k])) {
+      raise_flag(flags, MSP_ERR_NONFINITE, (int)(k < 0x7fffffff ? k : 0x7fffffff));
+      return;
+    }
+}
+
+__global__ void gather_values_kernel(size_t nnz, int bb, const int* __restrict__ src,
+                                     const double* __restrict__ in, double* __restrict__ out) {
+  const size_t total = nnz * bb;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const size_t q = t / bb, k = t % bb;
+    out[t] = in[(size_t)src[q] * bb + k];
+  }
+}
+
+__global__ void extract_N_kernel(int b, size_t nnzb, const double* __restrict__ v,
+                                 double* __restrict__ aN) {
+  const int bn = b - 1;
+  const size_t total = nnzb * bn * bn;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const size_t p = t / (bn * bn);
+    const int rc = (int)(t % (bn * bn)), r = rc / bn, c = rc % bn;
+    aN[t] = v[p * b * b + (size_t)(r + 1) * b + c + 1];
+  }
+}
+
+__global__ void diag_pos_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                int* __restrict__ dpos) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int d = -1;
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+      if (ci[p] == i) {
+        d = p;
+        break;
+      }
+    dpos[i] = d;
+  }
+}
+
+__global__ void rdiag_kernel(int n, const int* __restrict__ dpos, const double* __restrict__ v,
+                             double* __restrict__ rdiag, DevFlags* flags) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int d = dpos[i];
+    const double a = d >= 0 ? v[d] : 0.0;
+    if (!(a != 0.0)) {
+      raise_flag(flags, MSP_ERR_SINGULAR_BLOCK, i);
+      rdiag[i] = 0.0;
+    } else {
+      rdiag[i] = 1.0 / a;
+    }
+  }
+}
+
+template <int N>
+__device__ bool small_inverse(const double* __restrict__ D, double* X) {
+  double a[N][N], x[N][N];
+#pragma unroll
+  for (int r = 0; r < N; ++r)
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+      a[r][c] = D[r * N + c];
+      x[r][c] = (r == c) ? 1.0 : 0.0;
+    }
+  for (int c = 0; c < N; ++c) {
+    int p = c;
+    for (int r = c + 1; r < N; ++r)
+      if (fabs(a[r][c]) > fabs(a[p][c])) p = r;
+    if (!(a[p][c] != 0.0) || !isfinite(a[p][c])) return false;
+    if (p != c) {
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        double t = a[p][k];
+        a[p][k] = a[c][k];
+        a[c][k] = t;
+        t = x[p][k];
+        x[p][k] = x[c][k];
+        x[c][k] = t;
+      }
+    }
+    const double inv = 1.0 / a[c][c];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      a[c][k] *= inv;
+      x[c][k] *= inv;
+    }
+    for (int r = 0; r < N; ++r) {
+      if (r == c) continue;
+      const double f = a[r][c];
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        a[r][k] -= f * a[c][k];
+        x[r][k] -= f * x[c][k];
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < N; ++r)
+#pragma unroll
+    for (int c = 0; c < N; ++c) X[r * N + c] = x[r][c];
+  return true;
+}
+
+// Block ILU(0) (IKJ form) of the rows of one colour: for every k < i in the pattern,
+// L_ik = A_ik U_kk^-1 and A_ij -= L_ik A_kj for the later j of row i present in row k.
+template <int B>
+__global__ void bilu_factor_kernel(int r0, int r1, const int* __restrict__ rp,
+                                   const int* __restrict__ ci, const int* __restrict__ dpos,
+                                   double* __restrict__ lu, double* __restrict__ uinv,
+                                   DevFlags* flags) {
+  constexpr int BB = B * B;
+  for (int i = r0 + blockIdx.x * blockDim.x + threadIdx.x; i < r1; i += gridDim.x * blockDim.x) {
+    const int p0 = rp[i], pd = dpos[i], p1 = rp[i + 1];
+    for (int p = p0; p < pd; ++p) {
+      const int k = ci[p];
+      double L[BB];
+      const double* Ap = lu + (size_t)p * BB;
+      const double* Uk = uinv + (size_t)k * BB;
+#pragma unroll
+      for (int r = 0; r < B; ++r)
+#pragma unroll
+        for (int c = 0; c < B; ++c) {
+          double s = 0.0;
+#pragma unroll
+          for (int m = 0; m < B; ++m) s = fma(Ap[r * B + m], Uk[m * B + c], s);
+          L[r * B + c] = s;
+        }
+#pragma unroll
+      for (int t = 0; t < BB; ++t) lu[(size_t)p * BB + t] = L[t];
+      const int k0 = rp[k], k1 = rp[k + 1];
+      int kr = k0;
+      for (int q = p + 1; q < p1; ++q) {
+        const int j = ci[q];
+        while (kr < k1 && ci[kr] < j) ++kr;  // both rows ascending
+        if (kr >= k1) break;
+        if (ci[kr] != j) continue;
+        const double* Ukj = lu + (size_t)kr * BB;
+        double* Aq = lu + (size_t)q * BB;
+#pragma unroll
+        for (int r = 0; r < B; ++r)
+#pragma unroll
+          for (int c = 0; c < B; ++c) {
+            double s = 0.0;
+#pragma unroll
+            for (int m = 0; m < B; ++m) s = fma(L[r * B + m], Ukj[m * B + c], s);
+            Aq[r * B + c] -= s;
+          }
+      }
+    }
+    double X[BB];
+    if (!small_inverse<B>(lu + (size_t)pd * BB, X)) {
+      raise_flag(flags, MSP_ERR_SINGULAR_BLOCK, i);
+      continue;
+    }
+#pragma unroll
+    for (int t = 0; t < BB; ++t) uinv[(size_t)i * BB + t] = X[t];
+  }
+}
+
+__global__ void csr_to_dense_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                    const double* __restrict__ v, double* __restrict__ A) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double* row = A + (size_t)i * n;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) row[ci[p]] = v[p];
+  }
+}
+
+// pivot search in column k (rows k..n-1, first maximum), row swap, pivot row scaling,
+// and a copy of column k (after the swap) for the rank-1 update
+__global__ void gj_pivot_kernel(int n, int k, double* __restrict__ A, double* __restrict__ col,
+                                int* __restrict__ piv, DevFlags* flags) {
+  __shared__ double sv[1024];
+  __shared__ int si[1024];
+  double best = -1.0;
+  int bi = n;
+  for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+    const double a = fabs(A[(size_t)i * n + k]);
+    if (a > best) {
+      best = a;
+      bi = i;
+    }
+  }
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const double a = sv[threadIdx.x + o];
+      const int ia = si[threadIdx.x + o];
+      if (a > sv[threadIdx.x] || (a == sv[threadIdx.x] && ia < si[threadIdx.x])) {
+        sv[threadIdx.x] = a;
+        si[threadIdx.x] = ia;
+      }
+    }
+    __syncthreads();
+  }
+  const int p = si[0];
+  if (!(sv[0] > 0.0) || p >= n) {
+    if (threadIdx.x == 0) raise_flag(flags, MSP_ERR_SINGULAR_BLOCK, k);
+    return;
+  }
+  if (threadIdx.x == 0) piv[k] = p;
+  if (p != k)
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const double t = A[(size_t)p * n + j];
+      A[(size_t)p * n + j] = A[(size_t)k * n + j];
+      A[(size_t)k * n + j] = t;
+    }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = A[(size_t)i * n + k];
+  __syncthreads();
+  const double inv = 1.0 / col[k];
+  for (int j = threadIdx.x; j < n; j += blockDim.x)
+    A[(size_t)k * n + j] = (j == k) ? inv : A[(size_t)k * n + j] * inv;
+}
+
+__global__ void gj_update_kernel(int n, int k, double* __restrict__ A,
+                                 const double* __restrict__ col) {
+  const double* rowk = A + (size_t)k * n;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < (size_t)n * n;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / n), j = (int)(t % n);
+    if (i == k) continue;
+    const double f = col[i];
+    if (j == k)
+      A[t] = -f * rowk[k];
+    else
+      A[t] -= f * rowk[j];
+  }
+}
+
+__global__ void gj_unscramble_kernel(int n, const int* __restrict__ colperm,
+                                     const double* __restrict__ A, double* __restrict__ out) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < (size_t)n * n;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / n), c = (int)(t % n);
+    out[t] = A[(size_t)i * n + colperm[c]];
+  }
+}
+
+__global__ void cast_vals_kernel(size_t n, const double* __restrict__ in, float* __restrict__ out) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
+       t += (size_t)gridDim.x * blockDim.x)
+    out[t] = (float)in[t];
+}
+
+__global__ void iota_kernel(int n, int* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = i;
+}
+
+__global__ void fill_int_kernel(size_t n, int value, int* out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = value;
+}
+
+__global__ void scatter_inverse_kernel(int n, const int* __restrict__ perm, int* __restrict__ iperm) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    iperm[perm[k]] = k;
+}
+
+}  // namespace
+
+int launch_check_pattern(int nb, const int* rp, const int* ci, int* dpos, DevFlags* flags,
+                         cudaStream_t s) {
+  check_pattern_kernel<<<grid_for(nb, kThreads), kThreads, 0, s>>>(nb, rp, ci, dpos, flags);
+  return launch_status();
+}
+
+int launch_check_finite_vals(size_t n, const double* v, DevFlags* flags, cudaStream_t s) {
+  if (!n) return MSP_OK;
+  check_finite_vals_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, v, flags);
+  return launch_status();
+}
+
+int launch_gather_values(size_t nnz, int bb, const int* src, const double* in, double* out,
+                         cudaStream_t s) {
+  if (!nnz) return MSP_OK;
+  gather_values_kernel<<<grid_for(nnz * bb, kThreads), kThreads, 0, s>>>(nnz, bb, src, in, out);
+  return launch_status();
+}
+
+int launch_extract_N(int b, size_t nnzb, const double* v, double* aN, cudaStream_t s) {
+  if (b < 2 || !nnzb) return MSP_OK;
+  extract_N_kernel<<<grid_for(nnzb * (b - 1) * (b - 1), kThreads), kThreads, 0, s>>>(b, nnzb, v,
+                                                                                     aN);
+  return launch_status();
+}
+
+int launch_diag_pos(int n, const int* rp, const int* ci, int* dpos, cudaStream_t s) {
+  if (n <= 0) return MSP_OK;
+  diag_pos_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, rp, ci, dpos);
+  return launch_status();
+}
+
+int launch_rdiag(int n, const int* dpos, const double* v, double* rdiag, DevFlags* flags,
+                 cudaStream_t s) {
+  if (n <= 0) return MSP_OK;
+  rdiag_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, dpos, v, rdiag, flags);
+  return launch_status();
+}
+
+int launch_bilu_factor(int b, int r0, int r1, const int* rp, const int* ci, const int* dpos,
+                       double* lu, double* uinv, DevFlags* flags, cudaStream_t s) {
+  if (r1 <= r0) return MSP_OK;
+  const unsigned grid = grid_for(r1 - r0, 128);
+  switch (b) {
+#define MSP_BF_CASE(BB)                                                                   \
+  case BB:                                                                                \
+    bilu_factor_kernel<BB><<<grid, 128, 0, s>>>(r0, r1, rp, ci, dpos, lu, uinv, flags);   \
+    break;
+    MSP_BF_CASE(1)
+    MSP_BF_CASE(2)
+    MSP_BF_CASE(3)
+    MSP_BF_CASE(4)
+    MSP_BF_CASE(5)
+    MSP_BF_CASE(6)
+    MSP_BF_CASE(7)
+    MSP_BF_CASE(8)
+#undef MSP_BF_CASE
+    default:
+      return MSP_ERR_ARG;
+  }
+  return launch_status();
+}
+
+int launch_csr_to_dense(int n, const int* rp, const int* ci, const double* v, double* A,
+                        cudaStream_t s) {
+  if (n <= 0) return MSP_OK;
+  MSP_CUDA_TRY(cudaMemsetAsync(A, 0, (size_t)n * n * sizeof(double), s));
+  csr_to_dense_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, rp, ci, v, A);
+  return launch_status();
+}
+
+int launch_gj_pivot(int n, int k, double* A, double* col, int* piv, DevFlags* flags,
+                    cudaStream_t s) {
+  gj_pivot_kernel<<<1, 1024, 0, s>>>(n, k, A, col, piv, flags);
+  return launch_status();
+}
+
+int launch_gj_update(int n, int k, double* A, const double* col, cudaStream_t s) {
+  gj_update_kernel<<<grid_for((size_t)n * n, kThreads), kThreads, 0, s>>>(n, k, A, col);
+  return launch_status();
+}
+
+int launch_gj_unscramble(int n, const int* colperm, const double* A, double* out,
+                         cudaStream_t s) {
+  gj_unscramble_kernel<<<grid_for((size_t)n * n, kThreads), kThreads, 0, s>>>(n, colperm, A,
+                                                                             out);
+  return launch_status();
+}
+
+int launch_cast_vals(size_t n, const double* in, float* out, cudaStream_t s) {
+  if (!n) return MSP_OK;
+  cast_vals_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, in, out);
+  return launch_status();
+}
+
+int launch_iota(int n, int* out, cudaStream_t s) {
+  if (n <= 0) return MSP_OK;
+  iota_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, out);
+  return launch_status();
+}
+
+int launch_fill_int(size_t n, int value, int* out, cudaStream_t s) {
+  if (!n) return MSP_OK;
+  fill_int_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, value, out);
+  return launch_status();
+}
+
+int launch_scatter_inverse(int n, const int* perm, int* iperm, cudaStream_t s) {
+  if (n <= 0) return MSP_OK;
+  scatter_inverse_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, perm, iperm);
+  return launch_status();
+}
+
+}  // namespace msp

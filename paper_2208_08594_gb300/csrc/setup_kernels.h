@@ -1,0 +1,105 @@
+// Launchers of the setup kernels (host-callable, asynchronous on the given stream).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace msp {
+
+// ---- bit-exact kernels (setup_exact.cu, compiled without FMA contraction) ----
+// Inverse of every diagonal block (Gauss-Jordan, partial pivoting) and the quasi-IMPES
+// weights omega_i = first row of D_i^-1.  flags->code = MSP_ERR_SINGULAR_BLOCK on a zero
+// pivot (flags->index = block row).
+int launch_diag_inverse(int b, int nb, const int* dpos, const double* v, double* dinv,
+                        double* omega, DevFlags* flags, cudaStream_t s);
+// Inverses of the (b-1)x(b-1) concentration sub-blocks of the diagonal blocks.
+int launch_diagN_inverse(int b, int nb, const int* dpos, const double* v, double* dNinv,
+                         DevFlags* flags, cudaStream_t s);
+// A_P[p] = sum_k omega_i[k] * A_p[k][0] (decoupling) or A_p[0][0]
+int launch_pressure_matrix(int b, int nb, const int* rp, const double* v, const double* omega,
+                           bool decoupling, double* ap, cudaStream_t s);
+// strength s_q = -(a_ij + a_ji)/2 on the adjacency entries q = (i, j) and the candidate
+// flags s_q >= beta * max_k s_ik (max > 0)
+int launch_strength(int n, const int* arp, const int* aci, const double* av, const int* srp,
+                    const int* sci, double beta, double* sval, unsigned char* cand,
+                    cudaStream_t s);
+// tpos[q] = position of (j, i) in row j of the symmetric pattern S, for q = (i, j)
+int launch_transpose_pos(int n, const int* srp, const int* sci, int* tpos, cudaStream_t s);
+// SplitMix64 visit keys hkey[i] = splitmix64(i ^ seed)
+int launch_visit_keys(int n, unsigned long long seed, unsigned long long* hkey, cudaStream_t s);
+// one round of the parallel pairwise matching; commit[i] = j+2 (pair), 1 (single), 0 (wait)
+int launch_match_round(int n, const int* srp, const int* sci, const int* tpos,
+                       const double* sval, const unsigned char* cand,
+                       const unsigned long long* hkey, const unsigned char* state, int* commit,
+                       cudaStream_t s);
+// apply the commits of a round; flags->count += undecided nodes left
+int launch_match_apply(int n, const int* commit, unsigned char* state, int* partner,
+                       DevFlags* flags, cudaStream_t s);
+// rep[i] = 1 if i is the smallest member of its pair (or single)
+int launch_match_reps(int n, const int* partner, int* rep, cudaStream_t s);
+// agg[i] = id[min(i, partner[i])]
+int launch_match_ids(int n, const int* partner, const int* id, int* agg, cudaStream_t s);
+// Galerkin sums over sorted segments: out[k] = 0 + v[src[seg_start[k]]] + ... in order
+int launch_segment_sums(int nseg, const int* seg_start, const int* src, const double* v,
+                        double* out, cudaStream_t s);
+// Sequential VerticesGrouping (Algorithms 4.1/4.2) by one warp.  rank/vor: order by
+// (degree desc, index asc).  scratch: n bytes state, n ints wbar list, bitmap words.
+// On return colour[v] in 1..g and meta[0] = g; meta[1] = error flag.
+int launch_colouring(int n, const int* srp, const int* sci, const int* rank, const int* vor,
+                     unsigned char* state, int* wbar, unsigned* bitmap, size_t bitmap_words,
+                     int* colour, int* meta, cudaStream_t s);
+
+// ---- other setup kernels (setup_kernels.cu) ----
+// errors in the BSR pattern: unsorted / out of range columns, missing diagonal
+int launch_check_pattern(int nb, const int* rp, const int* ci, int* dpos, DevFlags* flags,
+                         cudaStream_t s);
+int launch_check_finite_vals(size_t n, const double* v, DevFlags* flags, cudaStream_t s);
+int launch_gather_values(size_t nnz, int bb, const int* src, const double* in, double* out,
+                         cudaStream_t s);
+int launch_extract_N(int b, size_t nnzb, const double* v, double* aN, cudaStream_t s);
+int launch_diag_pos(int n, const int* rp, const int* ci, int* dpos, cudaStream_t s);
+int launch_rdiag(int n, const int* dpos, const double* v, double* rdiag, DevFlags* flags,
+                 cudaStream_t s);
+// BILU(0) factorisation of the rows [r0, r1) of one colour (rows of earlier colours done)
+int launch_bilu_factor(int b, int r0, int r1, const int* rp, const int* ci, const int* dpos,
+                       double* lu, double* uinv, DevFlags* flags, cudaStream_t s);
+// dense copy of a CSR matrix (n x n row-major)
+int launch_csr_to_dense(int n, const int* rp, const int* ci, const double* v, double* A,
+                        cudaStream_t s);
+// one Gauss-Jordan step of the in-place dense inversion
+int launch_gj_pivot(int n, int k, double* A, double* col, int* piv, DevFlags* flags,
+                    cudaStream_t s);
+int launch_gj_update(int n, int k, double* A, const double* col, cudaStream_t s);
+int launch_gj_unscramble(int n, const int* colperm, const double* A, double* out,
+                         cudaStream_t s);
+int launch_cast_vals(size_t n, const double* in, float* out, cudaStream_t s);
+int launch_iota(int n, int* out, cudaStream_t s);
+int launch_fill_int(size_t n, int value, int* out, cudaStream_t s);
+int launch_scatter_inverse(int n, const int* perm, int* iperm, cudaStream_t s);
+
+// ---- CUB-based primitives (setup_sort.cu) ----
+struct SortScratch;  // reusable temporary storage
+SortScratch* sort_scratch_create();
+void sort_scratch_destroy(SortScratch*);
+// sort 64-bit keys ascending (stable), optional int32 payload; results in place
+int sort_pairs_u64(SortScratch*, size_t n, unsigned long long* keys, int* vals, int end_bit,
+                   cudaStream_t s);
+int exclusive_scan_int(SortScratch*, size_t n, const int* in, int* out, cudaStream_t s);
+
+// Symmetrised off-diagonal adjacency of a CSR/BSR pattern (Eq. adjacency-matrix).
+// Allocates srp (n+1) and sci (nnz); returns nnz in *snnz.
+int build_adjacency(SortScratch*, int n, const int* rp, const int* ci, int nnz,
+                    DevBuf<int>& srp, DevBuf<int>& sci, int* snnz, cudaStream_t s);
+
+}  // namespace msp
+
+namespace msp {
+// more CUB-based helpers (setup_sort.cu)
+int unique_sorted_keys(SortScratch*, size_t m, unsigned long long* keys, size_t* m_out,
+                       DevBuf<unsigned long long>& out, cudaStream_t s);
+int rowptr_from_sorted_keys(size_t m, int n, const unsigned long long* keys, int* row_ptr,
+                            cudaStream_t s);
+int low32_of_keys(size_t m, const unsigned long long* keys, int* out, cudaStream_t s);
+}  // namespace msp

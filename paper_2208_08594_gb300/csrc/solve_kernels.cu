@@ -1,0 +1,731 @@
+// Solve-phase kernels: BSR block-row kernels (SpMV / residual, decoupled pressure
+// restriction, stage-N block GS, BILU(0) sweeps), scalar CSR level kernels (PGS-MC
+// sweeps, residual + aggregate restriction, prolongation, dense coarsest GEMV) and the
+// FP64 Krylov reductions.  All are memory-bound streaming kernels: one thread group of
+// GP(b) lanes owns a block row, lane r owns equation r of the block and reads that row
+// of every b x b block (b contiguous values), so a group reads whole blocks with
+// 8/16-byte vector loads and consecutive groups read consecutive block rows.
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace msp {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <int B>
+struct Gp {
+  static constexpr int v = B <= 1 ? 1 : (B <= 2 ? 2 : (B <= 4 ? 4 : 8));
+};
+
+// Load B consecutive values with the widest aligned vector loads (rows start at
+// multiples of B*sizeof(T) bytes from a 256-byte aligned allocation).
+template <int B, typename T>
+__device__ __forceinline__ void load_row(const T* __restrict__ p, T (&r)[B]) {
+  constexpr int bytes = B * (int)sizeof(T);
+  if constexpr (bytes % 16 == 0) {
+#pragma unroll
+    for (int k = 0; k < bytes / 16; ++k) {
+      float4 t = __ldg(reinterpret_cast<const float4*>(p) + k);
+      memcpy(reinterpret_cast<char*>(r) + 16 * k, &t, 16);
+    }
+  } else if constexpr (bytes % 8 == 0) {
+#pragma unroll
+    for (int k = 0; k < bytes / 8; ++k) {
+      float2 t = __ldg(reinterpret_cast<const float2*>(p) + k);
+      memcpy(reinterpret_cast<char*>(r) + 8 * k, &t, 8);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < B; ++c) r[c] = __ldg(p + c);
+  }
+}
+
+template <int B, typename T>
+__device__ __forceinline__ T row_dot(const T (&a)[B], const T (&x)[B]) {
+  T s = a[0] * x[0];
+#pragma unroll
+  for (int c = 1; c < B; ++c) s = fma(a[c], x[c], s);
+  return s;
+}
+
+// sum over the GP lanes of a group (all lanes of the group participate)
+template <int GP, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int o = GP / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, GP);
+  return v;
+}
+
+// ----------------------------------------------------------------------------------
+// y = A x  or  y = g - A x
+// ----------------------------------------------------------------------------------
+template <int B, typename T, bool RES>
+__global__ void __launch_bounds__(kThreads) bsr_spmv_kernel(int nb, const int* __restrict__ rp,
+                                                           const int* __restrict__ ci,
+                                                           const T* __restrict__ v,
+                                                           const T* __restrict__ x,
+                                                           const T* __restrict__ g,
+                                                           T* __restrict__ y) {
+  constexpr int GP = Gp<B>::v;
+  const int lane = threadIdx.x % GP;
+  const int gpb = blockDim.x / GP;
+  const int stride = gridDim.x * gpb;
+  for (int i = blockIdx.x * gpb + threadIdx.x / GP; i < nb; i += stride) {
+    if (lane >= B) continue;
+    const int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
+    T acc = T(0);
+    int p = p0;
+    for (; p + 1 < p1; p += 2) {  // two blocks in flight
+      const int j0 = __ldg(ci + p), j1 = __ldg(ci + p + 1);
+      T a0[B], a1[B], x0[B], x1[B];
+      load_row<B>(v + ((size_t)p * B + lane) * B, a0);
+      load_row<B>(v + ((size_t)(p + 1) * B + lane) * B, a1);
+      load_row<B>(x + (size_t)j0 * B, x0);
+      load_row<B>(x + (size_t)j1 * B, x1);
+      acc += row_dot<B>(a0, x0);
+      acc += row_dot<B>(a1, x1);
+    }
+    if (p < p1) {
+      const int j0 = __ldg(ci + p);
+      T a0[B], x0[B];
+      load_row<B>(v + ((size_t)p * B + lane) * B, a0);
+      load_row<B>(x + (size_t)j0 * B, x0);
+      acc += row_dot<B>(a0, x0);
+    }
+    y[(size_t)i * B + lane] = RES ? g[(size_t)i * B + lane] - acc : acc;
+  }
+}
+
+// ----------------------------------------------------------------------------------
+// rP[i] = omega_i^T (g_i - (A w)_i)
+// ----------------------------------------------------------------------------------
+template <int B, typename T>
+__global__ void __launch_bounds__(kThreads) bsr_restrict_p_kernel(
+    int nb, const int* __restrict__ rp, const int* __restrict__ ci, const T* __restrict__ v,
+    const T* __restrict__ w, const T* __restrict__ g, const T* __restrict__ omega,
+    T* __restrict__ rP) {
+  constexpr int GP = Gp<B>::v;
+  const int lane = threadIdx.x % GP;
+  const int gpb = blockDim.x / GP;
+  // the loop bound depends on the block only, so every lane reaches the group shuffle
+  for (int base = blockIdx.x * gpb; base < nb; base += gridDim.x * gpb) {
+    const int i = base + threadIdx.x / GP;
+    T res = T(0);
+    const bool active = (i < nb) && (lane < B);
+    if (active) {
+      const int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
+      T acc = T(0);
+      for (int p = p0; p < p1; ++p) {
+        const int j = __ldg(ci + p);
+        T a[B], xx[B];
+        load_row<B>(v + ((size_t)p * B + lane) * B, a);
+        load_row<B>(w + (size_t)j * B, xx);
+        acc += row_dot<B>(a, xx);
+      }
+      res = g[(size_t)i * B + lane] - acc;
+      res = omega ? res * omega[(size_t)i * B + lane] : (lane == 0 ? res : T(0));
+    }
+    res = group_sum<GP>(res);
+    if (i < nb && lane == 0) rP[i] = res;
+  }
+}
+
+// ----------------------------------------------------------------------------------
+// stage N block GS sweep over one colour (BN = b - 1 concentration unknowns)
+// ----------------------------------------------------------------------------------
+template <int B, typename T>
+__global__ void __launch_bounds__(kThreads) bgs_colour_kernel(
+    int r0, int r1, const int* __restrict__ rp, const int* __restrict__ ci,
+    const int* __restrict__ dpos, const T* __restrict__ aN, const T* __restrict__ dNinv,
+    const T* __restrict__ g, T* __restrict__ w, bool lower_only, bool zero_pressure) {
+  constexpr int BN = B - 1;
+  constexpr int GP = Gp<BN>::v;
+  const int lane = threadIdx.x % GP;
+  const int gpb = blockDim.x / GP;
+  const int grp = threadIdx.x / GP;
+  for (int base = r0 + blockIdx.x * gpb; base < r1; base += gridDim.x * gpb) {
+    const int i = base + grp;
+    T acc = T(0);
+    const bool active = (i < r1) && (lane < BN);
+    if (active) {
+      acc = g[(size_t)i * B + 1 + lane];
+      const int p0 = __ldg(rp + i), pd = __ldg(dpos + i), p1 = __ldg(rp + i + 1);
+      const int pend = lower_only ? pd : p1;
+      for (int p = p0; p < pend; ++p) {
+        if (p == pd) continue;
+        const int j = __ldg(ci + p);
+        const T* xr = w + (size_t)j * B + 1;
+        const T* ar = aN + ((size_t)p * BN + lane) * BN;
+#pragma unroll
+        for (int c = 0; c < BN; ++c) acc = fma(-__ldg(ar + c), xr[c], acc);
+      }
+    }
+    // x_i = D_N,i^{-1} acc : gather the BN partial results of the group
+    T out = T(0);
+    const T* di = dNinv + ((size_t)(active ? i : 0) * BN + (lane < BN ? lane : 0)) * BN;
+#pragma unroll
+    for (int c = 0; c < BN; ++c) {
+      T ac = __shfl_sync(0xffffffffu, acc, c, GP);
+      if (active) out = fma(__ldg(di + c), ac, out);
+    }
+    if (active) {
+      w[(size_t)i * B + 1 + lane] = out;
+      if (zero_pressure && lane == 0) w[(size_t)i * B] = T(0);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------------
+// BILU(0) forward (unit lower) over one colour
+// ----------------------------------------------------------------------------------
+template <int B, typename T>
+__global__ void __launch_bounds__(kThreads) bilu_fwd_kernel(
+    int r0, int r1, const int* __restrict__ rp, const int* __restrict__ ci,
+    const int* __restrict__ dpos, const T* __restrict__ lu, const T* __restrict__ r,
+    T* __restrict__ y) {
+  constexpr int GP = Gp<B>::v;
+  const int lane = threadIdx.x % GP;
+  const int gpb = blockDim.x / GP;
+  for (int i = r0 + blockIdx.x * gpb + threadIdx.x / GP; i < r1; i += gridDim.x * gpb) {
+    if (lane >= B) continue;
+    T acc = r[(size_t)i * B + lane];
+    const int p0 = __ldg(rp + i), pd = __ldg(dpos + i);
+    for (int p = p0; p < pd; ++p) {
+      const int j = __ldg(ci + p);
+      T a[B], yy[B];
+      load_row<B>(lu + ((size_t)p * B + lane) * B, a);
+#pragma unroll
+      for (int c = 0; c < B; ++c) yy[c] = y[(size_t)j * B + c];
+      acc -= row_dot<B>(a, yy);
+    }
+    y[(size_t)i * B + lane] = acc;
+  }
+}
+
+// BILU(0) backward over one colour: x_i = U_ii^{-1} (y_i - sum_{j>i} U_ij x_j); w_i += x_i
+template <int B, typename T>
+__global__ void __launch_bounds__(kThreads) bilu_bwd_kernel(
+    int r0, int r1, const int* __restrict__ rp, const int* __restrict__ ci,
+    const int* __restrict__ dpos, const T* __restrict__ lu, const T* __restrict__ uinv,
+    const T* __restrict__ y, T* __restrict__ x, T* __restrict__ w) {
+  constexpr int GP = Gp<B>::v;
+  const int lane = threadIdx.x % GP;
+  const int gpb = blockDim.x / GP;
+  const int grp = threadIdx.x / GP;
+  for (int base = r0 + blockIdx.x * gpb; base < r1; base += gridDim.x * gpb) {
+    const int i = base + grp;
+    const bool active = (i < r1) && (lane < B);
+    T acc = T(0);
+    if (active) {
+      acc = y[(size_t)i * B + lane];
+      const int pd = __ldg(dpos + i), p1 = __ldg(rp + i + 1);
+      for (int p = pd + 1; p < p1; ++p) {
+        const int j = __ldg(ci + p);
+        T a[B], xx[B];
+        load_row<B>(lu + ((size_t)p * B + lane) * B, a);
+#pragma unroll
+        for (int c = 0; c < B; ++c) xx[c] = x[(size_t)j * B + c];
+        acc -= row_dot<B>(a, xx);
+      }
+    }
+    T out = T(0);
+    const T* ui = uinv + ((size_t)(active ? i : 0) * B + (lane < B ? lane : 0)) * B;
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+      T ac = __shfl_sync(0xffffffffu, acc, c, GP);
+      if (active) out = fma(__ldg(ui + c), ac, out);
+    }
+    if (active) {
+      x[(size_t)i * B + lane] = out;
+      w[(size_t)i * B + lane] += out;
+    }
+  }
+}
+
+template <typename T>
+__global__ void prolong_p_kernel(int b, int nb, const T* __restrict__ e, T* __restrict__ w) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x)
+    w[(size_t)i * b] += e[i];
+}
+
+// ----------------------------------------------------------------------------------
+// scalar CSR level kernels: TPR lanes per row
+// ----------------------------------------------------------------------------------
+constexpr int kTpr = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) csr_gs_colour_kernel(
+    int r0, int r1, const int* __restrict__ rp, const int* __restrict__ ci,
+    const T* __restrict__ v, const int* __restrict__ dpos, const T* __restrict__ rdiag,
+    const T* __restrict__ b, T* __restrict__ x, bool lower_only) {
+  const int lane = threadIdx.x % kTpr;
+  const int rpb = blockDim.x / kTpr;
+  for (int base = r0 + blockIdx.x * rpb; base < r1; base += gridDim.x * rpb) {
+    const int i = base + threadIdx.x / kTpr;
+    T s = T(0);
+    if (i < r1) {
+      const int p0 = __ldg(rp + i), pd = __ldg(dpos + i);
+      const int p1 = lower_only ? pd : __ldg(rp + i + 1);
+      for (int p = p0 + lane; p < p1; p += kTpr) {
+        if (p == pd) continue;
+        s = fma(__ldg(v + p), x[__ldg(ci + p)], s);
+      }
+    }
+    s = group_sum<kTpr>(s);
+    if (i < r1 && lane == 0) x[i] = (b[i] - s) * rdiag[i];
+  }
+}
+
+// one group of kTpr lanes per coarse row I; members of I processed in ascending order
+template <typename T>
+__global__ void __launch_bounds__(kThreads) csr_residual_restrict_kernel(
+    int nc, const int* __restrict__ mptr, const int* __restrict__ members,
+    const int* __restrict__ rp, const int* __restrict__ ci, const T* __restrict__ v,
+    const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ bc) {
+  const int lane = threadIdx.x % kTpr;
+  const int rpb = blockDim.x / kTpr;
+  for (int base = blockIdx.x * rpb; base < nc; base += gridDim.x * rpb) {
+    const int I = base + threadIdx.x / kTpr;
+    T total = T(0);
+    if (I < nc) {
+      const int m0 = __ldg(mptr + I), m1 = __ldg(mptr + I + 1);
+      for (int m = m0; m < m1; ++m) {
+        const int i = __ldg(members + m);
+        T s = T(0);
+        const int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
+        for (int p = p0 + lane; p < p1; p += kTpr) s = fma(__ldg(v + p), __ldg(x + __ldg(ci + p)), s);
+        total += (lane == 0 ? b[i] : T(0)) - s;
+      }
+    }
+    total = group_sum<kTpr>(total);
+    if (I < nc && lane == 0) bc[I] = total;
+  }
+}
+
+template <typename T>
+__global__ void prolong_add_kernel(int n, const int* __restrict__ agg, const T* __restrict__ xc,
+                                   T* __restrict__ x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    x[i] += xc[agg[i]];
+}
+
+// x = Ainv b, one warp per row
+template <typename T>
+__global__ void __launch_bounds__(kThreads) dense_gemv_kernel(int n, const double* __restrict__ A,
+                                                             const T* __restrict__ b,
+                                                             T* __restrict__ x) {
+  const int lane = threadIdx.x % kWarp;
+  const int wpb = blockDim.x / kWarp;
+  for (int r = blockIdx.x * wpb + threadIdx.x / kWarp; r < n; r += gridDim.x * wpb) {
+    const double* row = A + (size_t)r * n;
+    double s = 0.0;
+    for (int c = lane; c < n; c += kWarp) s = fma(__ldg(row + c), (double)b[c], s);
+    s = group_sum<kWarp>(s);
+    if (lane == 0) x[r] = (T)s;
+  }
+}
+
+__global__ void cast_d2f_kernel(size_t n, const double* __restrict__ in, float* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+__global__ void cast_f2d_kernel(size_t n, const float* __restrict__ in, double* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (double)in[i];
+}
+
+// ----------------------------------------------------------------------------------
+// Krylov reductions (deterministic: per-block partials, then a fixed-order sum)
+// ----------------------------------------------------------------------------------
+constexpr int kDotChunk = 8;
+constexpr int kMaxK = 72;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = group_sum<kWarp>(v);
+  const int w = threadIdx.x / kWarp, l = threadIdx.x % kWarp;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < blockDim.x / kWarp) t = sh[threadIdx.x];
+  if (w == 0) t = group_sum<kWarp>(t);
+  return t;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kThreads) multi_dot_kernel(size_t n, const double* __restrict__ V,
+                                                            size_t ldv, int K,
+                                                            const double* __restrict__ w,
+                                                            double* __restrict__ partial) {
+  __shared__ double sh[kThreads / kWarp];
+  for (int k0 = 0; k0 < K; k0 += kDotChunk) {
+    const int kc = min(kDotChunk, K - k0);
+    double acc[kDotChunk];
+#pragma unroll
+    for (int k = 0; k < kDotChunk; ++k) acc[k] = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+      const double wi = w[i];
+#pragma unroll
+      for (int k = 0; k < kDotChunk; ++k)
+        if (k < kc) acc[k] = fma(__ldg(V + (size_t)(k0 + k) * ldv + i), wi, acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < kDotChunk; ++k) {
+      if (k >= kc) break;
+      double t = block_sum(acc[k], sh);
+      if (threadIdx.x == 0) partial[(size_t)blockIdx.x * kMaxK + k0 + k] = t;
+    }
+  }
+}
+
+__global__ void reduce_partials_kernel(int K, int nblocks, const double* __restrict__ partial,
+                                       double* __restrict__ out, bool accumulate) {
+  const int k = threadIdx.x;
+  if (k >= K) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * kMaxK + k];
+  out[k] = accumulate ? out[k] + s : s;
+}
+
+__global__ void __launch_bounds__(kThreads) multi_axpy_norm_kernel(
+    size_t n, const double* __restrict__ V, size_t ldv, int K, const double* __restrict__ h,
+    double* __restrict__ w, double* __restrict__ partial) {
+  __shared__ double sh[kThreads / kWarp];
+  __shared__ double hs[kMaxK];
+  for (int k = threadIdx.x; k < K; k += blockDim.x) hs[k] = h[k];
+  __syncthreads();
+  double nrm = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    double wi = w[i];
+    for (int k = 0; k < K; ++k) wi = fma(-hs[k], __ldg(V + (size_t)k * ldv + i), wi);
+    w[i] = wi;
+    nrm = fma(wi, wi, nrm);
+  }
+  double t = block_sum(nrm, sh);
+  if (threadIdx.x == 0) partial[(size_t)blockIdx.x * kMaxK] = t;
+}
+
+__global__ void __launch_bounds__(kThreads) norm2_partial_kernel(size_t n, const double* __restrict__ x,
+                                                                double* __restrict__ partial) {
+  __shared__ double sh[kThreads / kWarp];
+  double nrm = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    nrm = fma(x[i], x[i], nrm);
+  double t = block_sum(nrm, sh);
+  if (threadIdx.x == 0) partial[(size_t)blockIdx.x * kMaxK] = t;
+}
+
+// in place allowed (v == w)
+__global__ void normalize_kernel(size_t n, const double* w, const double* __restrict__ nrm2,
+                                 double* v, double* __restrict__ hn) {
+  const double h = sqrt(nrm2[0]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) hn[0] = h;
+  if (h == 0.0) return;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    v[i] = w[i] / h;
+}
+
+__global__ void update_x_kernel(size_t n, const double* __restrict__ Z, size_t ldz, int K,
+                                const double* __restrict__ y, double* __restrict__ x) {
+  __shared__ double ys[kMaxK];
+  for (int k = threadIdx.x; k < K; k += blockDim.x) ys[k] = y[k];
+  __syncthreads();
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    double xi = x[i];
+    for (int k = 0; k < K; ++k) xi = fma(ys[k], __ldg(Z + (size_t)k * ldz + i), xi);
+    x[i] = xi;
+  }
+}
+
+__global__ void scale_kernel(size_t n, const double* __restrict__ r, double alpha,
+                             double* __restrict__ v) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    v[i] = r[i] * alpha;
+}
+
+__global__ void check_finite_kernel(size_t n, const double* __restrict__ x, int* flag) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    if (!isfinite(x[i])) {
+      atomicExch(flag, 1);
+      return;
+    }
+}
+
+__global__ void gather_blocks_kernel(int nb, int b, const int* __restrict__ perm,
+                                     const double* __restrict__ in, double* __restrict__ out) {
+  const size_t n = (size_t)nb * b;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const size_t k = t / b, r = t % b;
+    out[t] = in[(size_t)perm[k] * b + r];
+  }
+}
+
+__global__ void scatter_blocks_kernel(int nb, int b, const int* __restrict__ perm,
+                                      const double* __restrict__ in, double* __restrict__ out) {
+  const size_t n = (size_t)nb * b;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const size_t k = t / b, r = t % b;
+    out[(size_t)perm[k] * b + r] = in[t];
+  }
+}
+
+inline int launch_status() { return launch_check(__FILE__, __LINE__); }
+
+// grid covering `groups` thread groups of GP lanes, capped at 8 blocks per SM
+inline unsigned grid_groups(size_t groups, int gp) {
+  return grid_for(groups * (size_t)gp, kThreads, 8);
+}
+
+}  // namespace
+
+#define MSP_B_SWITCH(b, ...)  \
+  switch (b) {                 \
+    case 1: { constexpr int B_ = 1; __VA_ARGS__; } break; \
+    case 2: { constexpr int B_ = 2; __VA_ARGS__; } break; \
+    case 3: { constexpr int B_ = 3; __VA_ARGS__; } break; \
+    case 4: { constexpr int B_ = 4; __VA_ARGS__; } break; \
+    case 5: { constexpr int B_ = 5; __VA_ARGS__; } break; \
+    case 6: { constexpr int B_ = 6; __VA_ARGS__; } break; \
+    case 7: { constexpr int B_ = 7; __VA_ARGS__; } break; \
+    case 8: { constexpr int B_ = 8; __VA_ARGS__; } break; \
+    default: return MSP_ERR_ARG; \
+  }
+
+template <typename T>
+int launch_bsr_spmv(int b, int nb, const int* rp, const int* ci, const T* v, const T* x,
+                    const T* g, T* y, bool residual, cudaStream_t s) {
+  if (nb <= 0) return MSP_OK;
+  MSP_B_SWITCH(b, {
+    const unsigned grid = grid_groups(nb, Gp<B_>::v);
+    if (residual)
+      bsr_spmv_kernel<B_, T, true><<<grid, kThreads, 0, s>>>(nb, rp, ci, v, x, g, y);
+    else
+      bsr_spmv_kernel<B_, T, false><<<grid, kThreads, 0, s>>>(nb, rp, ci, v, x, g, y);
+  });
+  return launch_status();
+}
+
+template <typename T>
+int launch_bsr_restrict_p(int b, int nb, const int* rp, const int* ci, const T* v, const T* w,
+                          const T* g, const T* omega, T* rP, cudaStream_t s) {
+  if (nb <= 0) return MSP_OK;
+  MSP_B_SWITCH(b, {
+    const unsigned grid = grid_groups(nb, Gp<B_>::v);
+    bsr_restrict_p_kernel<B_, T><<<grid, kThreads, 0, s>>>(nb, rp, ci, v, w, g, omega, rP);
+  });
+  return launch_status();
+}
+
+template <typename T>
+int launch_bgs_colour(int b, int r0, int r1, const int* rp, const int* ci, const int* dpos,
+                      const T* aN, const T* dNinv, const T* g, T* w, bool lower_only,
+                      bool zero_pressure, cudaStream_t s) {
+  if (r1 <= r0 || b < 2) return MSP_OK;
+  switch (b) {
+#define MSP_BGS_CASE(BB)                                                                   \
+  case BB: {                                                                               \
+    const unsigned grid = grid_groups(r1 - r0, Gp<BB - 1>::v);                             \
+    bgs_colour_kernel<BB, T><<<grid, kThreads, 0, s>>>(r0, r1, rp, ci, dpos, aN, dNinv, g, \
+                                                       w, lower_only, zero_pressure);      \
+  } break;
+    MSP_BGS_CASE(2)
+    MSP_BGS_CASE(3)
+    MSP_BGS_CASE(4)
+    MSP_BGS_CASE(5)
+    MSP_BGS_CASE(6)
+    MSP_BGS_CASE(7)
+    MSP_BGS_CASE(8)
+#undef MSP_BGS_CASE
+    default:
+      return MSP_ERR_ARG;
+  }
+  return launch_status();
+}
+
+template <typename T>
+int launch_bilu_fwd(int b, int r0, int r1, const int* rp, const int* ci, const int* dpos,
+                    const T* lu, const T* r, T* y, cudaStream_t s) {
+  if (r1 <= r0) return MSP_OK;
+  MSP_B_SWITCH(b, {
+    const unsigned grid = grid_groups(r1 - r0, Gp<B_>::v);
+    bilu_fwd_kernel<B_, T><<<grid, kThreads, 0, s>>>(r0, r1, rp, ci, dpos, lu, r, y);
+  });
+  return launch_status();
+}
+
+template <typename T>
+int launch_bilu_bwd(int b, int r0, int r1, const int* rp, const int* ci, const int* dpos,
+                    const T* lu, const T* uinv, const T* y, T* x, T* w, cudaStream_t s) {
+  if (r1 <= r0) return MSP_OK;
+  MSP_B_SWITCH(b, {
+    const unsigned grid = grid_groups(r1 - r0, Gp<B_>::v);
+    bilu_bwd_kernel<B_, T><<<grid, kThreads, 0, s>>>(r0, r1, rp, ci, dpos, lu, uinv, y, x, w);
+  });
+  return launch_status();
+}
+
+template <typename T>
+int launch_prolong_p(int b, int nb, const T* e, T* w, cudaStream_t s) {
+  if (nb <= 0) return MSP_OK;
+  prolong_p_kernel<T><<<grid_for(nb, kThreads), kThreads, 0, s>>>(b, nb, e, w);
+  return launch_status();
+}
+
+template <typename T>
+int launch_csr_gs_colour(int r0, int r1, const int* rp, const int* ci, const T* v,
+                         const int* dpos, const T* rdiag, const T* b, T* x, bool lower_only,
+                         cudaStream_t s) {
+  if (r1 <= r0) return MSP_OK;
+  const unsigned grid = grid_groups(r1 - r0, kTpr);
+  csr_gs_colour_kernel<T><<<grid, kThreads, 0, s>>>(r0, r1, rp, ci, v, dpos, rdiag, b, x,
+                                                    lower_only);
+  return launch_status();
+}
+
+template <typename T>
+int launch_csr_residual_restrict(int nc, const int* mptr, const int* members, const int* rp,
+                                 const int* ci, const T* v, const T* b, const T* x, T* bc,
+                                 cudaStream_t s) {
+  if (nc <= 0) return MSP_OK;
+  const unsigned grid = grid_groups(nc, kTpr);
+  csr_residual_restrict_kernel<T><<<grid, kThreads, 0, s>>>(nc, mptr, members, rp, ci, v, b,
+                                                            x, bc);
+  return launch_status();
+}
+
+template <typename T>
+int launch_prolong_add(int n, const int* agg, const T* xc, T* x, cudaStream_t s) {
+  if (n <= 0) return MSP_OK;
+  prolong_add_kernel<T><<<grid_for(n, kThreads), kThreads, 0, s>>>(n, agg, xc, x);
+  return launch_status();
+}
+
+template <typename T>
+int launch_dense_gemv(int n, const double* Ainv, const T* b, T* x, cudaStream_t s) {
+  if (n <= 0) return MSP_OK;
+  dense_gemv_kernel<T><<<grid_groups(n, kWarp), kThreads, 0, s>>>(n, Ainv, b, x);
+  return launch_status();
+}
+
+int launch_cast_d2f(size_t n, const double* in, float* out, cudaStream_t s) {
+  if (!n) return MSP_OK;
+  cast_d2f_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, in, out);
+  return launch_status();
+}
+int launch_cast_f2d(size_t n, const float* in, double* out, cudaStream_t s) {
+  if (!n) return MSP_OK;
+  cast_f2d_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, in, out);
+  return launch_status();
+}
+
+int krylov_blocks() { return sm_count() * 4; }
+
+int launch_multi_dot(size_t n, const double* V, size_t ldv, int K, const double* w,
+                     double* partial, int nblocks, cudaStream_t s) {
+  if (K > kMaxK) return MSP_ERR_ARG;
+  multi_dot_kernel<<<nblocks, kThreads, 0, s>>>(n, V, ldv, K, w, partial);
+  return launch_status();
+}
+
+int launch_reduce_partials(int K, int nblocks, const double* partial, double* out,
+                           bool accumulate, cudaStream_t s) {
+  if (K > kMaxK) return MSP_ERR_ARG;
+  reduce_partials_kernel<<<1, kMaxK, 0, s>>>(K, nblocks, partial, out, accumulate);
+  return launch_status();
+}
+
+int launch_multi_axpy_norm(size_t n, const double* V, size_t ldv, int K, const double* h,
+                           double* w, double* partial, int nblocks, cudaStream_t s) {
+  if (K > kMaxK) return MSP_ERR_ARG;
+  multi_axpy_norm_kernel<<<nblocks, kThreads, 0, s>>>(n, V, ldv, K, h, w, partial);
+  return launch_status();
+}
+
+int launch_norm2_partial(size_t n, const double* x, double* partial, int nblocks,
+                         cudaStream_t s) {
+  norm2_partial_kernel<<<nblocks, kThreads, 0, s>>>(n, x, partial);
+  return launch_status();
+}
+
+int launch_normalize(size_t n, const double* w, const double* nrm2, double* v, double* hn,
+                     cudaStream_t s) {
+  normalize_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, w, nrm2, v, hn);
+  return launch_status();
+}
+
+int launch_update_x(size_t n, const double* Z, size_t ldz, int K, const double* y, double* x,
+                    cudaStream_t s) {
+  if (K > kMaxK) return MSP_ERR_ARG;
+  if (K <= 0) return MSP_OK;
+  update_x_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, Z, ldz, K, y, x);
+  return launch_status();
+}
+
+int launch_scale(size_t n, const double* r, double alpha, double* v, cudaStream_t s) {
+  scale_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, r, alpha, v);
+  return launch_status();
+}
+
+int launch_check_finite(size_t n, const double* x, int* flag, cudaStream_t s) {
+  if (!n) return MSP_OK;
+  check_finite_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, x, flag);
+  return launch_status();
+}
+
+int launch_gather_blocks(int nb, int b, const int* perm, const double* in, double* out,
+                         cudaStream_t s) {
+  gather_blocks_kernel<<<grid_for((size_t)nb * b, kThreads), kThreads, 0, s>>>(nb, b, perm,
+                                                                               in, out);
+  return launch_status();
+}
+
+int launch_scatter_blocks(int nb, int b, const int* perm, const double* in, double* out,
+                          cudaStream_t s) {
+  scatter_blocks_kernel<<<grid_for((size_t)nb * b, kThreads), kThreads, 0, s>>>(nb, b, perm,
+                                                                                in, out);
+  return launch_status();
+}
+
+// explicit instantiations for the two value types of the preconditioner
+#define MSP_INST(T)                                                                         \
+  template int launch_bsr_spmv<T>(int, int, const int*, const int*, const T*, const T*,     \
+                                  const T*, T*, bool, cudaStream_t);                        \
+  template int launch_bsr_restrict_p<T>(int, int, const int*, const int*, const T*,         \
+                                        const T*, const T*, const T*, T*, cudaStream_t);    \
+  template int launch_bgs_colour<T>(int, int, int, const int*, const int*, const int*,      \
+                                    const T*, const T*, const T*, T*, bool, bool,           \
+                                    cudaStream_t);                                          \
+  template int launch_bilu_fwd<T>(int, int, int, const int*, const int*, const int*,        \
+                                  const T*, const T*, T*, cudaStream_t);                    \
+  template int launch_bilu_bwd<T>(int, int, int, const int*, const int*, const int*,        \
+                                  const T*, const T*, const T*, T*, T*, cudaStream_t);      \
+  template int launch_prolong_p<T>(int, int, const T*, T*, cudaStream_t);                   \
+  template int launch_csr_gs_colour<T>(int, int, const int*, const int*, const T*,          \
+                                       const int*, const T*, const T*, T*, bool,            \
+                                       cudaStream_t);                                       \
+  template int launch_csr_residual_restrict<T>(int, const int*, const int*, const int*,     \
+                                               const int*, const T*, const T*, const T*,    \
+                                               T*, cudaStream_t);                           \
+  template int launch_prolong_add<T>(int, const int*, const T*, T*, cudaStream_t);          \
+  template int launch_dense_gemv<T>(int, const double*, const T*, T*, cudaStream_t);
+MSP_INST(double)
+MSP_INST(float)
+#undef MSP_INST
+
+}  // namespace msp

@@ -1,0 +1,241 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle.
+
+* integer setup outputs bit-exact: level-0 colouring (Algorithms 4.1/4.2), colour
+  permutations, aggregates, coarse patterns; the level matrices too (their arithmetic is
+  rounded identically on both sides);
+* one preconditioner application (Algorithm 3.1) within 1e-10 relative in FP64, and
+  each stage on its own;
+* the FGMRES(30) solve to 1e-6: iteration count within +-1, true residual <= tol;
+* SpMV elementwise; edge cases (block size 1, single level, wells, zero and non-finite
+  right-hand sides, invalid patterns).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synthetic import (box_jacobian, grid_small, grid_spe10, perturb_values, poisson3d_bsr,
+                       random_rhs)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2208_08594_gb300 as msp  # noqa: E402
+
+DEV = torch.device("cuda:0")
+TOL_APPLY = 1e-10
+
+
+def _dev(a):
+    return (torch.from_numpy(np.ascontiguousarray(a.row_ptr)).to(DEV),
+            torch.from_numpy(np.ascontiguousarray(a.col_idx)).to(DEV),
+            torch.from_numpy(np.ascontiguousarray(a.values.reshape(-1))).to(DEV))
+
+
+def _pair(a, **cfg):
+    rp, ci, v = _dev(a)
+    g = msp.Solver(a.nb, a.b, rp, ci, v, **cfg)
+    o = oracle.Oracle(a, **cfg)
+    return g, o
+
+
+def _vec(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+
+
+CASES = {
+    "small_b3": lambda: (grid_small(), dict(coarse_max=100)),
+    "spe10_like_b4": lambda: (grid_spe10(nx=23, ny=17, nz=9), dict(coarse_max=120)),
+    "wells_b2": lambda: (box_jacobian(13, 11, 7, 2, 5, layered=True, kz_ratio=0.1, n_wells=3),
+                         dict(coarse_max=60)),
+    "b6_ragged": lambda: (box_jacobian(9, 7, 5, 6, 8, n_wells=1), dict(coarse_max=40)),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request):
+    a, cfg = CASES[request.param]()
+    g, o = _pair(a, **cfg)
+    yield a, g, o, cfg
+    g.close()
+    o.close()
+
+
+def test_level0_colouring_bit_exact(case):
+    a, g, o, _ = case
+    cg, ng = g.colour0()
+    co, no = o.colour0()
+    assert ng == no
+    assert np.array_equal(cg, co)
+
+
+def test_hierarchy_bit_exact(case):
+    a, g, o, _ = case
+    assert g.num_levels == o.num_levels
+    for l in range(o.num_levels):
+        lg, lo = g.level(l), o.level(l)
+        for key in ("n", "nnz", "ncolours"):
+            assert lg[key] == lo[key], (l, key)
+        for key in ("perm", "cptr", "agg", "row_ptr", "col_idx"):
+            assert np.array_equal(lg[key], lo[key]), (l, key)
+        assert np.array_equal(lg["values"], lo["values"]), l
+
+
+def test_spmv(case):
+    a, g, o, _ = case
+    x = np.random.default_rng(0).normal(size=a.n)
+    y = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+    g.spmv(_vec(x), y)
+    ref = o.spmv(x)
+    assert np.allclose(y.cpu().numpy(), ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+
+
+def test_msp_application(case):
+    a, g, o, _ = case
+    for seed in (1, 2):
+        x = random_rhs(a, seed)
+        w = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+        g.apply_precond(_vec(x), w)
+        ref = o.apply_precond(x)
+        err = np.abs(w.cpu().numpy() - ref).max() / np.abs(ref).max()
+        assert err <= TOL_APPLY, err
+
+
+def test_solve_iterations(case):
+    a, g, o, _ = case
+    rhs = random_rhs(a, 11)
+    x = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+    info = g.solve(_vec(rhs), x, 1e-6)
+    xo, io = o.solve(rhs, 1e-6)
+    assert info["status"] == 0 and io["status"] == 0
+    assert abs(info["iterations"] - io["iterations"]) <= 1, (info["iterations"], io["iterations"])
+    A = a.to_scipy()
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(rhs - A @ xg) / np.linalg.norm(rhs) <= 1e-6 * 1.001
+    assert info["rel_residual"] <= 1e-6
+
+
+@pytest.mark.parametrize("precond", [msp.MSP_PREC_N_ONLY, msp.MSP_PREC_P_ONLY,
+                                     msp.MSP_PREC_R_ONLY, msp.MSP_PREC_NONE])
+def test_single_stages(precond):
+    a = grid_spe10(nx=11, ny=9, nz=5)
+    g, o = _pair(a, precond=precond, coarse_max=40)
+    x = random_rhs(a, 3)
+    w = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+    g.apply_precond(_vec(x), w)
+    ref = o.apply_precond(x)
+    err = np.abs(w.cpu().numpy() - ref).max() / max(np.abs(ref).max(), 1e-300)
+    assert err <= TOL_APPLY, err
+    g.close()
+
+
+def test_block_size_one_poisson_exact_coarse():
+    a = poisson3d_bsr(9, 8, 7)
+    g, o = _pair(a, coarse_max=10000)
+    assert g.num_levels == 1
+    rhs = np.random.default_rng(4).normal(size=a.n)
+    x = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+    info = g.solve(_vec(rhs), x, 1e-8)
+    assert info["iterations"] == 1 and info["status"] == 0
+    g.close()
+
+
+def test_poisson_multilevel():
+    a = poisson3d_bsr(24, 24, 24)
+    g, o = _pair(a, coarse_max=200)
+    for l in range(o.num_levels):
+        lg, lo = g.level(l), o.level(l)
+        assert np.array_equal(lg["agg"], lo["agg"]) and np.array_equal(lg["perm"], lo["perm"])
+    rhs = np.random.default_rng(5).normal(size=a.n)
+    x = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+    info = g.solve(_vec(rhs), x, 1e-6)
+    xo, io = o.solve(rhs, 1e-6)
+    assert abs(info["iterations"] - io["iterations"]) <= 1
+    g.close()
+
+
+def test_zero_and_nonfinite_rhs():
+    a = grid_spe10(nx=6, ny=5, nz=4)
+    g, _ = _pair(a, coarse_max=20)
+    x = torch.ones(a.n, dtype=torch.float64, device=DEV)
+    info = g.solve(torch.zeros(a.n, dtype=torch.float64, device=DEV), x, 1e-6)
+    assert info["iterations"] == 0 and float(x.abs().max()) == 0.0
+    bad = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+    bad[5] = float("nan")
+    with pytest.raises(msp.MspError) as e:
+        g.solve(bad, x, 1e-6)
+    assert e.value.status == -4
+    g.close()
+
+
+def test_invalid_pattern_rejected():
+    a = grid_spe10(nx=4, ny=4, nz=3)
+    rp, ci, v = _dev(a)
+    ci2 = ci.clone()
+    ci2[[3, 4]] = ci2[[4, 3]]  # unsorted row
+    with pytest.raises(msp.MspError) as e:
+        msp.Solver(a.nb, a.b, rp, ci2, v)
+    assert e.value.status == -2
+    v2 = v.clone()
+    v2[17] = float("inf")
+    with pytest.raises(msp.MspError) as e:
+        msp.Solver(a.nb, a.b, rp, ci, v2)
+    assert e.value.status == -4
+
+
+def test_singular_diagonal_block_rejected():
+    a = grid_spe10(nx=4, ny=4, nz=3)
+    vals = a.values.copy()
+    d = [p for p in range(a.row_ptr[5], a.row_ptr[6]) if a.col_idx[p] == 5][0]
+    vals[d] = 0.0
+    rp, ci, _ = _dev(a)
+    with pytest.raises(msp.MspError) as e:
+        msp.Solver(a.nb, a.b, rp, ci, _vec(vals.reshape(-1)))
+    assert e.value.status == -3
+
+
+def test_adaptive_setup_sequence_matches_oracle():
+    a = grid_spe10(nx=10, ny=12, nz=5)
+    mu = 12
+    g, o = _pair(a, mu=mu, coarse_max=100)
+    its_g, setups_g, its_o, setups_o = [], [], [], []
+    for k in range(5):
+        if k > 0:
+            vals = perturb_values(a, 300 + k)
+            g.update_values(_vec(vals.reshape(-1)))
+            o.update_values(vals)
+        rhs = random_rhs(a, 400 + k)
+        x = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+        ig = g.solve(_vec(rhs), x, 1e-6)
+        _, io = o.solve(rhs, 1e-6)
+        its_g.append(ig["iterations"])
+        setups_g.append(ig["setup_performed"])
+        its_o.append(io["iterations"])
+        setups_o.append(io["setup_performed"])
+    # the GPU follows the rule on its own iteration counts ...
+    assert setups_g == [1] + [int(its_g[k - 1] > mu) for k in range(1, 5)]
+    # ... and matches the oracle's counts within one iteration
+    assert all(abs(x - y) <= 1 for x, y in zip(its_g, its_o)), (its_g, its_o)
+    g.close()
+
+
+def test_fp32_preconditioner_converges_to_fp64_accuracy():
+    a = grid_spe10(nx=23, ny=17, nz=9)
+    rp, ci, v = _dev(a)
+    g = msp.Solver(a.nb, a.b, rp, ci, v, coarse_max=120, precision=msp.MSP_PRECISION_FP32)
+    o = oracle.Oracle(a, coarse_max=120)
+    rhs = random_rhs(a, 11)
+    x = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+    info = g.solve(_vec(rhs), x, 1e-6)
+    xo, io = o.solve(rhs, 1e-6)
+    A = a.to_scipy()
+    xg = x.cpu().numpy()
+    assert info["status"] == 0
+    assert np.linalg.norm(rhs - A @ xg) / np.linalg.norm(rhs) <= 1e-6 * 1.001
+    assert abs(info["iterations"] - io["iterations"]) <= max(2, io["iterations"] // 10)
+    # both iterates meet the same residual tolerance, so they agree to the
+    # conditioning of A times that tolerance; the measured gap is far smaller
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-3
+    g.close()
