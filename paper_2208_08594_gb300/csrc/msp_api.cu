@@ -51,6 +51,11 @@ struct PendingTiming {
 std::mutex g_stats_mu;
 int g_stats_mode = 0;
 long long g_launches = 0;
+// while a CUDA graph is being captured on this thread, launches and probe bytes are
+// tallied here instead of being counted / timed
+thread_local bool t_capturing = false;
+thread_local long long t_cap_launches = 0;
+thread_local double t_cap_bytes = 0.0;
 std::vector<StatSite> g_sites;
 std::vector<PendingTiming> g_pending;
 std::vector<cudaEvent_t> g_free_events;
@@ -92,6 +97,10 @@ int launch_check(const char* file, int line) {
     set_last_cuda_error(e, "kernel launch", file, line);
     return MSP_ERR_CUDA;
   }
+  if (t_capturing) {
+    ++t_cap_launches;
+    return MSP_OK;
+  }
   if (g_stats_mode >= 1) {
     std::lock_guard<std::mutex> lk(g_stats_mu);
     ++g_launches;
@@ -100,6 +109,10 @@ int launch_check(const char* file, int line) {
 }
 
 Probe::Probe(const char* site, double bytes, cudaStream_t s) : s_(s) {
+  if (t_capturing) {
+    t_cap_bytes += bytes;
+    return;
+  }
   if (g_stats_mode < 2) return;
   std::lock_guard<std::mutex> lk(g_stats_mu);
   e0_ = take_event();
@@ -298,6 +311,12 @@ struct msp_handle_s {
   msp::DevBuf<double> V, Z, bperm, xperm, rvec, partial, hdev, nrm, ydev;
   msp::DevBuf<int> ifl;
   msp::DevBuf<double> e2e_b, e2e_x;  // staging of msp_solve_host
+  // the preconditioner as a CUDA graph on fixed input/output buffers
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  long long graph_launches = 0;  // kernels in the graph
+  double graph_bytes = 0.0;      // algorithmic bytes of one replay
+  msp::DevBuf<double> pg64, pw64;
   // adaptive setup
   int setup_calls = 0;
   int prev_it = -1;
@@ -307,6 +326,10 @@ struct msp_handle_s {
 
 namespace msp {
 namespace {
+
+void drop_graph(msp_handle h);
+int permute_pattern(msp_handle h, int n, const int* rp, const int* ci, int nnz, const int* iperm,
+                    DevBuf<int>& brp, DevBuf<int>& bci, DevBuf<int>& src, cudaStream_t s);
 
 int sync_flags(msp_handle h, cudaStream_t s) {
   MSP_CUDA_TRY(cudaMemcpyAsync(h->h_flags, h->flags.p, sizeof(DevFlags), cudaMemcpyDeviceToHost, s));
@@ -327,9 +350,8 @@ int colour_graph(msp_handle h, int n, const int* rp, const int* ci, int nnz, Dev
   int snnz = 0;
   MSP_TRY(build_adjacency(h->ss, n, rp, ci, nnz, srp, sci, &snnz, s));
   DevBuf<unsigned long long> keys;
-  DevBuf<int> vor, rank, wbar, meta;
-  DevBuf<unsigned char> state;
-  DevBuf<unsigned> bitmap;
+  DevBuf<int> vor, rank, wbar, meta, rrp, rci, rsrc, colour_r;
+  DevBuf<unsigned> bitmap, inV;
   MSP_TRY(keys.alloc(n));
   MSP_TRY(vor.alloc(n));
   MSP_TRY(rank.alloc(n));
@@ -338,16 +360,21 @@ int colour_graph(msp_handle h, int n, const int* rp, const int* ci, int nnz, Dev
   MSP_TRY(sort_pairs_u64(h->ss, n, keys.p, nullptr, 64, s));
   MSP_TRY(low32_of_keys(n, keys.p, vor.p, s));
   MSP_TRY(launch_scatter_inverse(n, vor.p, rank.p, s));
+  // relabel S by priority rank: the greedy then picks the smallest label
+  MSP_TRY(permute_pattern(h, n, srp.p, sci.p, snnz, rank.p, rrp, rci, rsrc, s));
   const int n0 = (n + 31) / 32, n1 = (n0 + 31) / 32, n2 = (n1 + 31) / 32;
   const size_t words = (size_t)n0 + n1 + n2;
-  MSP_TRY(state.alloc(n));
+  MSP_TRY(inV.alloc(n0));
   MSP_TRY(wbar.alloc(n));
   MSP_TRY(bitmap.alloc(words));
   MSP_TRY(meta.alloc(2));
+  MSP_TRY(colour_r.alloc(n));
   MSP_TRY(colour.alloc(n));
   MSP_CUDA_TRY(cudaMemsetAsync(meta.p, 0, 2 * sizeof(int), s));
-  MSP_TRY(launch_colouring(n, srp.p, sci.p, rank.p, vor.p, state.p, wbar.p, bitmap.p, words,
-                           colour.p, meta.p, s));
+  MSP_TRY(launch_colouring(n, rrp.p, rci.p, inV.p, wbar.p, bitmap.p, words, colour_r.p, meta.p,
+                           s));
+  map_kernel<<<grid1(n), kThreads, 0, s>>>(n, colour_r.p, rank.p, colour.p);  // colour[v] = colour_r[rank[v]]
+  MSP_TRY(launch_status());
   int hm[2] = {0, 0};
   MSP_CUDA_TRY(cudaMemcpyAsync(hm, meta.p, sizeof(hm), cudaMemcpyDeviceToHost, s));
   MSP_CUDA_TRY(cudaStreamSynchronize(s));
@@ -529,9 +556,11 @@ int value_setup(msp_handle h, cudaStream_t s) {
   const size_t nnzb = (size_t)h->nnzb;
   const msp_config& cfg = h->cfg;
   h->setup_valid = false;
+  drop_graph(h);
   MSP_TRY(reset_flags(h, s));
   // quasi-IMPES weights omega_i = D_i^{-T} e_0
   MSP_TRY(h->omega.alloc((size_t)nb * b));
+  Probe pr_all("setup:value_total", 0.0, s);
   MSP_TRY(launch_diag_inverse(b, nb, h->dpos.p, h->vals.p, nullptr, h->omega.p, h->flags.p, s));
   if (sync_flags(h, s) != MSP_OK) return h->h_flags->code;
   // level 0: the pressure matrix A_P on the block pattern
@@ -566,26 +595,39 @@ int value_setup(msp_handle h, cudaStream_t s) {
       DevBuf<int> a1;
       int n1 = 0;
       const unsigned long long seed = cfg.agg_seed + (unsigned long long)(2 * l + pass);
-      MSP_TRY(pairwise_pass(h, A, cfg.beta, seed, a1, &n1, s));
+      {
+        Probe pr("setup:pairwise_matching", 0.0, s);
+        MSP_TRY(pairwise_pass(h, A, cfg.beta, seed, a1, &n1, s));
+      }
       compose_kernel<<<grid1(nF), kThreads, 0, s>>>(nF, a1.p, agg.p);
       MSP_TRY(launch_status());
       nc = n1;
       if (pass + 1 < cfg.npass) {
         DCsr nxt;
+        Probe pr("setup:galerkin", 0.0, s);
         MSP_TRY(galerkin(h, A, a1.p, n1, nxt, s));
         cur = std::move(nxt);
       }
     }
     if ((double)nc > 0.9 * (double)nF) break;  // coarsening stalled
     DCsr Ac;
-    MSP_TRY(galerkin(h, h->levels[l].A, agg.p, nc, Ac, s));
+    {
+      Probe pr("setup:galerkin", 0.0, s);
+      MSP_TRY(galerkin(h, h->levels[l].A, agg.p, nc, Ac, s));
+    }
     Level C;
     DevBuf<int> ipc;
     MSP_TRY(ipc.alloc(nc));
     if (nc > cfg.coarse_max && l + 2 < cfg.max_levels) {
       DevBuf<int> colour;
       int g = 0;
-      MSP_TRY(colour_graph(h, nc, Ac.rp.p, Ac.ci.p, Ac.nnz, colour, C.perm, C.cptr, &g, s));
+      {
+        static const char* names[] = {"setup:colouring_l1", "setup:colouring_l2",
+                                      "setup:colouring_l3", "setup:colouring_l4",
+                                      "setup:colouring_l5+"};
+        Probe pr(names[std::min(l, 4)], 0.0, s);
+        MSP_TRY(colour_graph(h, nc, Ac.rp.p, Ac.ci.p, Ac.nnz, colour, C.perm, C.cptr, &g, s));
+      }
       MSP_TRY(launch_scatter_inverse(nc, C.perm.p, ipc.p, s));
       DevBuf<int> srcmap;
       C.A.n = nc;
@@ -625,7 +667,10 @@ int value_setup(msp_handle h, cudaStream_t s) {
   for (size_t l = 0; l < h->levels.size(); ++l)
     MSP_TRY(level_extras(h, h->levels[l], l + 1 < h->levels.size(), s));
   if (sync_flags(h, s) != MSP_OK) return h->h_flags->code;
-  MSP_TRY(coarse_inverse(h, h->levels.back().A, s));
+  {
+    Probe pr("setup:coarse_inverse", 0.0, s);
+    MSP_TRY(coarse_inverse(h, h->levels.back().A, s));
+  }
   // stage N: concentration sub-blocks and the inverses of their diagonal blocks
   if (bn > 0) {
     MSP_TRY(h->aN.alloc(nnzb * bn * bn));
@@ -634,6 +679,7 @@ int value_setup(msp_handle h, cudaStream_t s) {
     MSP_TRY(launch_diagN_inverse(b, nb, h->dpos.p, h->vals.p, h->dNinv.p, h->flags.p, s));
   }
   // stage R: BILU(0) in colour order
+  Probe pr_bilu("setup:bilu_factor", 0.0, s);
   MSP_TRY(h->lu.alloc(nnzb * bb));
   MSP_TRY(h->uinv.alloc((size_t)nb * bb));
   MSP_CUDA_TRY(cudaMemcpyAsync(h->lu.p, h->vals.p, nnzb * bb * sizeof(double),
@@ -858,15 +904,72 @@ int apply_precond_t(msp_handle h, const PView<T>& P, const T* g, T* w, cudaStrea
   return stage_R<T>(h, P, P.r, w, s);
 }
 
-// w = B g on FP64 colour-ordered vectors, in the configured precision
-int apply_precond(msp_handle h, const double* g, double* w, cudaStream_t s) {
-  if (h->cfg.precision == MSP_PRECISION_FP32) {
-    const size_t n = (size_t)h->nb * h->b;
-    MSP_TRY(launch_cast_d2f(n, g, h->g32.p, s));
-    MSP_TRY(apply_precond_t<float>(h, view32(h), h->g32.p, h->w32.p, s));
-    return launch_cast_f2d(n, h->w32.p, w, s);
+void drop_graph(msp_handle h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->graph = nullptr;
+}
+
+// Capture Algorithm 3.1 on the fixed buffers (pg -> pw) into a CUDA graph; it stays
+// valid until the next value setup (update_values keeps every buffer in place).
+int capture_graph(msp_handle h) {
+  drop_graph(h);
+  if (!h->cap_stream) MSP_CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  const bool fp32 = h->cfg.precision == MSP_PRECISION_FP32;
+  cudaGraph_t g = nullptr;
+  MSP_CUDA_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  t_capturing = true;
+  t_cap_launches = 0;
+  t_cap_bytes = 0.0;
+  const int st = fp32 ? apply_precond_t<float>(h, view32(h), h->g32.p, h->w32.p, h->cap_stream)
+                      : apply_precond_t<double>(h, view64(h), h->pg64.p, h->pw64.p, h->cap_stream);
+  t_capturing = false;
+  const cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+  if (st != MSP_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
   }
-  return apply_precond_t<double>(h, view64(h), g, w, s);
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+    return MSP_ERR_CUDA;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    h->graph = nullptr;
+    set_last_cuda_error(ei, "cudaGraphInstantiate", __FILE__, __LINE__);
+    return MSP_ERR_CUDA;
+  }
+  h->graph_launches = t_cap_launches;
+  h->graph_bytes = t_cap_bytes;
+  return MSP_OK;
+}
+
+// w = B g on FP64 colour-ordered vectors, in the configured precision.  Replays the
+// captured graph, except while per-launch timing is on (stats mode 2).
+int apply_precond(msp_handle h, const double* g, double* w, cudaStream_t s) {
+  const size_t n = (size_t)h->nb * h->b;
+  const bool fp32 = h->cfg.precision == MSP_PRECISION_FP32;
+  if (g_stats_mode >= 2) {
+    if (fp32) {
+      MSP_TRY(launch_cast_d2f(n, g, h->g32.p, s));
+      MSP_TRY(apply_precond_t<float>(h, view32(h), h->g32.p, h->w32.p, s));
+      return launch_cast_f2d(n, h->w32.p, w, s);
+    }
+    return apply_precond_t<double>(h, view64(h), g, w, s);
+  }
+  if (!h->graph) MSP_TRY(capture_graph(h));
+  if (fp32)
+    MSP_TRY(launch_cast_d2f(n, g, h->g32.p, s));
+  else
+    MSP_CUDA_TRY(cudaMemcpyAsync(h->pg64.p, g, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  MSP_CUDA_TRY(cudaGraphLaunch(h->graph, s));
+  if (g_stats_mode >= 1) {
+    std::lock_guard<std::mutex> lk(g_stats_mu);
+    g_launches += h->graph_launches;
+  }
+  if (fp32) return launch_cast_f2d(n, h->w32.p, w, s);
+  MSP_CUDA_TRY(cudaMemcpyAsync(w, h->pw64.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return MSP_OK;
 }
 
 int alloc_work(msp_handle h) {
@@ -875,6 +978,8 @@ int alloc_work(msp_handle h) {
   MSP_TRY(h->pr.alloc(n));
   MSP_TRY(h->py.alloc(n));
   MSP_TRY(h->px.alloc(n));
+  MSP_TRY(h->pg64.alloc(n));
+  MSP_TRY(h->pw64.alloc(n));
   if (h->cfg.precision == MSP_PRECISION_FP32) {
     MSP_TRY(h->g32.alloc(n));
     MSP_TRY(h->w32.alloc(n));
@@ -966,7 +1071,8 @@ int fgmres(msp_handle h, double tol, int* iters, double* relres, double* relres_
                                         false, s));
       }
       ++it;
-      // classical Gram-Schmidt, twice
+      // classical Gram-Schmidt, twice (CGS2): h = V^T w, w -= V h, repeated; the norm of
+      // w comes with the second update
       const int K = j + 1;
       for (int pass = 0; pass < 2; ++pass) {
         double* hc = pass == 0 ? h->hdev.p : h->ydev.p;
@@ -1074,6 +1180,8 @@ int pattern_setup(msp_handle h, const int32_t* d_rp, const int32_t* d_ci, cudaSt
 
 void destroy(msp_handle h) {
   if (!h) return;
+  drop_graph(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->h_flags) cudaFreeHost(h->h_flags);
   if (h->h_pin) cudaFreeHost(h->h_pin);
   if (h->ss) sort_scratch_destroy(h->ss);

@@ -300,13 +300,18 @@ __global__ void segment_sums_kernel(int nseg, const int* __restrict__ seg_start,
 }
 
 // ----------------------------------------------------------------------------------
-// Sequential VerticesGrouping by one warp.  state: 0 = in V of the current pass,
-// 1 = moved to Wbar in this pass, 2 = coloured.  The frontier hat W is a three-level
-// bitmap over the priority rank (degree desc, index asc), so its first set bit is the
-// vertex Algorithm 4.1 picks (D1).  Stale frontier entries (vertices that left V as
-// neighbours of W) are dropped when popped: that is the else branch of Algorithm 4.1,
-// which only moves such a vertex to Wbar where it already is.  When the frontier is
-// empty the pick is the first rank still in V (a cursor that only moves forward).
+// Sequential VerticesGrouping by one warp on the graph relabelled by priority rank
+// (degree desc, index asc), so that "the vertex Algorithm 4.1 picks" (D1) is simply
+// the smallest label.  inV is a bitmap of the vertices in V of the current pass
+// (test-and-clear with atomics, so the lanes can remove neighbours concurrently); a
+// vertex leaves V when it is coloured or moved to Wbar, and the Wbar list of a pass is
+// V of the next one.  The frontier hat W is a three-level bitmap, so its first set bit
+// is the next pick.  Stale frontier entries (vertices that left V as neighbours of W)
+// are dropped when popped: that is the else branch of Algorithm 4.1, which only moves
+// such a vertex to Wbar where it already is.  With an empty frontier the pick is the
+// smallest label still in V (a cursor that only moves forward).  Both bitmaps live in
+// shared memory when they fit; the second circle is gathered with every lane issuing
+// its loads back to back (owner rows looked up in shared memory).
 // ----------------------------------------------------------------------------------
 struct Bitmap3 {
   unsigned* l0;
@@ -351,23 +356,36 @@ __device__ void bm_set(const Bitmap3& bm, int r) {
   }
 }
 
-__global__ void __launch_bounds__(32) colouring_kernel(
-    int n, const int* __restrict__ srp, const int* __restrict__ sci, const int* __restrict__ rank,
-    const int* __restrict__ vor, unsigned char* state, int* wbar, unsigned* gbitmap,
-    int use_smem, int* colour, int* meta) {
+__device__ __forceinline__ bool in_v(const unsigned* inV, int v) {
+  return (inV[v >> 5] >> (v & 31)) & 1u;
+}
+
+constexpr int kSecondU = 8;  // second-circle entries gathered per lane per round
+
+// layout flags: bit 0 = frontier bitmap in shared memory, bit 1 = inV in shared memory
+__global__ void __launch_bounds__(32) colouring_kernel(int n, const int* __restrict__ srp,
+                                                       const int* __restrict__ sci,
+                                                       unsigned* ginV, int* wbar,
+                                                       unsigned* gbitmap, int layout,
+                                                       int* colour, int* meta) {
   extern __shared__ unsigned smem_bits[];
+  __shared__ int s_kb[32], s_off[33];
   const int lane = threadIdx.x;
   Bitmap3 bm;
   bm.n0 = (n + 31) / 32;
   bm.n1 = (bm.n0 + 31) / 32;
   bm.n2 = (bm.n1 + 31) / 32;
-  unsigned* base = use_smem ? smem_bits : gbitmap;
-  bm.l0 = base;
-  bm.l1 = base + bm.n0;
-  bm.l2 = base + bm.n0 + bm.n1;
-  const int nwords = bm.n0 + bm.n1 + bm.n2;
-  for (int k = lane; k < nwords; k += 32) base[k] = 0u;
-  for (int v = lane; v < n; v += 32) state[v] = 0;
+  const int fw = bm.n0 + bm.n1 + bm.n2;
+  unsigned* fbase = (layout & 1) ? smem_bits : gbitmap;
+  unsigned* inV = (layout & 2) ? smem_bits + ((layout & 1) ? fw : 0) : ginV;
+  bm.l0 = fbase;
+  bm.l1 = fbase + bm.n0;
+  bm.l2 = fbase + bm.n0 + bm.n1;
+  for (int k = lane; k < fw; k += 32) fbase[k] = 0u;
+  for (int k = lane; k < bm.n0; k += 32) {
+    const int rem = n - 32 * k;
+    inV[k] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+  }
   __syncwarp();
   int coloured = 0, g = 0;
   while (coloured < n) {
@@ -378,13 +396,13 @@ __global__ void __launch_bounds__(32) colouring_kernel(
     }
     int cursor = 0, nwbar = 0;
     // every frontier entry of this pass is a distinct vertex of V, popped once
-    const long long max_picks = (long long)(n - coloured) + 2;
+    const long long max_picks = 2LL * (n - coloured) + 2;
     long long picks = 0;
     while (true) {
       int v = -1;
       // frontier first (hat W), dropping stale entries
       while (true) {
-        if (++picks > max_picks + (long long)(n - coloured)) {
+        if (++picks > max_picks) {
           if (lane == 0) meta[1] = 1;
           return;
         }
@@ -393,21 +411,20 @@ __global__ void __launch_bounds__(32) colouring_kernel(
         __syncwarp();
         if (lane == 0) bm_clear(bm, r);
         __syncwarp();
-        const int u = vor[r];
-        if (state[u] == 0) {
-          v = u;
+        if (in_v(inV, r)) {
+          v = r;
           break;
         }
       }
       if (v < 0) {
-        // V in rank order
+        // V by label
         while (cursor < n) {
           const int r = cursor + lane;
-          const bool inv = (r < n) && state[vor[r]] == 0;
+          const bool inv = (r < n) && in_v(inV, r);
           const unsigned m = __ballot_sync(0xffffffffu, inv);
           if (m) {
             cursor += __ffs(m) - 1;
-            v = vor[cursor];
+            v = cursor;
             break;
           }
           cursor += 32;
@@ -416,37 +433,45 @@ __global__ void __launch_bounds__(32) colouring_kernel(
       }
       // W = W u {v}
       if (lane == 0) {
-        state[v] = 2;
+        atomicAnd(inV + (v >> 5), ~(1u << (v & 31)));
         colour[v] = g;
       }
       ++coloured;
-      __syncwarp();
-      // Wbar = Wbar u (S_v n V), V = V / S_v
-      const int q0 = srp[v], q1 = srp[v + 1];
+      const int q0 = __ldg(srp + v), q1 = __ldg(srp + v + 1);
+      // Wbar = Wbar u (S_v n V), V = V / S_v  (all chunks first)
+      int kb0 = 0, kl0 = 0;  // row of this lane's neighbour in the first chunk
       for (int q = q0; q < q1; q += 32) {
         const int qq = q + lane;
         bool take = false;
         int j = -1;
         if (qq < q1) {
-          j = sci[qq];
-          take = state[j] == 0;
+          j = __ldg(sci + qq);
+          if (q == q0) {
+            kb0 = __ldg(srp + j);
+            kl0 = __ldg(srp + j + 1) - kb0;
+          }
+          const unsigned bit = 1u << (j & 31);
+          take = (atomicAnd(inV + (j >> 5), ~bit) & bit) != 0u;
         }
         const unsigned m = __ballot_sync(0xffffffffu, take);
-        if (take) {
-          state[j] = 1;
-          wbar[nwbar + __popc(m & ((1u << lane) - 1u))] = j;
-        }
+        if (take) wbar[nwbar + __popc(m & ((1u << lane) - 1u))] = j;
         nwbar += __popc(m);
       }
       __syncwarp();
       // hat W = hat W u hat S_v: undetermined vertices of the second circle
       for (int q = q0; q < q1; q += 32) {
         const int qq = q + lane;
-        int kb = 0, kl = 0;
-        if (qq < q1) {
-          const int k = sci[qq];
-          kb = srp[k];
-          kl = srp[k + 1] - kb;
+        int kb = kb0, kl = kl0;
+        if (q != q0) {
+          kb = 0;
+          kl = 0;
+          if (qq < q1) {
+            const int k = __ldg(sci + qq);
+            kb = __ldg(srp + k);
+            kl = __ldg(srp + k + 1) - kb;
+          }
+        } else if (qq >= q1) {
+          kl = 0;
         }
         // exclusive prefix of the row lengths across the lanes of this chunk
         int off = kl;
@@ -456,25 +481,35 @@ __global__ void __launch_bounds__(32) colouring_kernel(
         }
         const int total = __shfl_sync(0xffffffffu, off, 31);
         off -= kl;
+        s_kb[lane] = kb;
+        s_off[lane] = off;
+        if (lane == 0) s_off[32] = total;
+        __syncwarp();
         const int nk = min(32, q1 - q);
-        for (int t0 = 0; t0 < total; t0 += 32) {
-          const int t = t0 + lane;
-          // owner lane: the last lane whose offset is <= t
+        for (int t0 = 0; t0 < total; t0 += 32 * kSecondU) {
+          int xs[kSecondU];
           int owner = 0;
-          for (int l = 1; l < nk; ++l)
-            if (__shfl_sync(0xffffffffu, off, l) <= t) owner = l;
-          const int obase = __shfl_sync(0xffffffffu, kb, owner);
-          const int ooff = __shfl_sync(0xffffffffu, off, owner);
-          if (t < total) {
-            const int x = sci[obase + (t - ooff)];
-            if (state[x] == 0) bm_set(bm, rank[x]);
+#pragma unroll
+          for (int u = 0; u < kSecondU; ++u) {
+            const int t = t0 + lane + 32 * u;
+            xs[u] = -1;
+            if (t < total) {
+              while (owner + 1 < nk && s_off[owner + 1] <= t) ++owner;
+              xs[u] = __ldg(sci + s_kb[owner] + (t - s_off[owner]));
+            }
           }
+#pragma unroll
+          for (int u = 0; u < kSecondU; ++u)
+            if (xs[u] >= 0 && in_v(inV, xs[u])) bm_set(bm, xs[u]);
         }
+        __syncwarp();
       }
-      __syncwarp();
     }
     // Wbar of this pass is V of the next one
-    for (int t = lane; t < nwbar; t += 32) state[wbar[t]] = 0;
+    for (int t = lane; t < nwbar; t += 32) {
+      const int j = wbar[t];
+      atomicOr(inV + (j >> 5), 1u << (j & 31));
+    }
     __syncwarp();
   }
   if (lane == 0) meta[0] = g;
@@ -595,24 +630,36 @@ int launch_segment_sums(int nseg, const int* seg_start, const int* src, const do
   return launch_status();
 }
 
-int launch_colouring(int n, const int* srp, const int* sci, const int* rank, const int* vor,
-                     unsigned char* state, int* wbar, unsigned* bitmap, size_t bitmap_words,
-                     int* colour, int* meta, cudaStream_t s) {
+int launch_colouring(int n, const int* srp, const int* sci, unsigned* inV, int* wbar,
+                     unsigned* bitmap, size_t bitmap_words, int* colour, int* meta,
+                     cudaStream_t s) {
   if (n <= 0) return MSP_OK;
   const int n0 = (n + 31) / 32, n1 = (n0 + 31) / 32, n2 = (n1 + 31) / 32;
-  const size_t words = (size_t)n0 + n1 + n2;
-  if (words > bitmap_words) return MSP_ERR_ARG;
-  const size_t smem = words * sizeof(unsigned);
-  const size_t smem_cap = 200 * 1024;
-  int use_smem = smem <= smem_cap ? 1 : 0;
-  if (use_smem) {
-    cudaError_t e = cudaFuncSetAttribute(colouring_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_cap);
-    if (e != cudaSuccess) use_smem = 0;
+  const size_t fwords = (size_t)n0 + n1 + n2;
+  if (fwords > bitmap_words) return MSP_ERR_ARG;
+  const size_t cap = 220 * 1024;
+  const size_t fbytes = fwords * sizeof(unsigned), vbytes = (size_t)n0 * sizeof(unsigned);
+  int layout = 0;
+  size_t smem = 0;
+  if (fbytes + vbytes <= cap) {
+    layout = 3;
+    smem = fbytes + vbytes;
+  } else if (vbytes <= cap) {
+    layout = 2;  // the membership tests are the hottest accesses
+    smem = vbytes;
+  } else if (fbytes <= cap) {
+    layout = 1;
+    smem = fbytes;
   }
-  colouring_kernel<<<1, 32, use_smem ? smem : 0, s>>>(n, srp, sci, rank, vor, state, wbar,
-                                                      bitmap, use_smem, colour, meta);
+  if (smem > 0) {
+    cudaError_t e = cudaFuncSetAttribute(colouring_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+    if (e != cudaSuccess) {
+      layout = 0;
+      smem = 0;
+    }
+  }
+  colouring_kernel<<<1, 32, smem, s>>>(n, srp, sci, inV, wbar, bitmap, layout, colour, meta);
   return launch_status();
 }
 

@@ -44,12 +44,14 @@ int launch_match_ids(int n, const int* partner, const int* id, int* agg, cudaStr
 // Galerkin sums over sorted segments: out[k] = 0 + v[src[seg_start[k]]] + ... in order
 int launch_segment_sums(int nseg, const int* seg_start, const int* src, const double* v,
                         double* out, cudaStream_t s);
-// Sequential VerticesGrouping (Algorithms 4.1/4.2) by one warp.  rank/vor: order by
-// (degree desc, index asc).  scratch: n bytes state, n ints wbar list, bitmap words.
-// On return colour[v] in 1..g and meta[0] = g; meta[1] = error flag.
-int launch_colouring(int n, const int* srp, const int* sci, const int* rank, const int* vor,
-                     unsigned char* state, int* wbar, unsigned* bitmap, size_t bitmap_words,
-                     int* colour, int* meta, cudaStream_t s);
+// Sequential VerticesGrouping (Algorithms 4.1/4.2) by one warp on a symmetric graph
+// whose labels are the priority ranks (degree desc, original index asc).  scratch: inV
+// bitmap of ceil(n/32) words, n ints Wbar list, frontier bitmap words.  On return
+// colour[r] in 1..g (by label), meta[0] = g, meta[1] = error flag (a bounded loop ran
+// out).
+int launch_colouring(int n, const int* srp, const int* sci, unsigned* inV, int* wbar,
+                     unsigned* bitmap, size_t bitmap_words, int* colour, int* meta,
+                     cudaStream_t s);
 
 // ---- other setup kernels (setup_kernels.cu) ----
 // errors in the BSR pattern: unsorted / out of range columns, missing diagonal

@@ -46,12 +46,21 @@ __device__ __forceinline__ void load_row(const T* __restrict__ p, T (&r)[B]) {
   }
 }
 
+// acc + a . x  (one FMA per product: FP64 FMA issue is the binding resource of the
+// FP64 block kernels on GB300)
 template <int B, typename T>
-__device__ __forceinline__ T row_dot(const T (&a)[B], const T (&x)[B]) {
-  T s = a[0] * x[0];
+__device__ __forceinline__ T fma_row(const T (&a)[B], const T (&x)[B], T acc) {
 #pragma unroll
-  for (int c = 1; c < B; ++c) s = fma(a[c], x[c], s);
-  return s;
+  for (int c = 0; c < B; ++c) acc = fma(a[c], x[c], acc);
+  return acc;
+}
+
+// acc - a . x
+template <int B, typename T>
+__device__ __forceinline__ T fnma_row(const T (&a)[B], const T (&x)[B], T acc) {
+#pragma unroll
+  for (int c = 0; c < B; ++c) acc = fma(-a[c], x[c], acc);
+  return acc;
 }
 
 // sum over the GP lanes of a group (all lanes of the group participate)
@@ -79,7 +88,7 @@ __global__ void __launch_bounds__(kThreads) bsr_spmv_kernel(int nb, const int* _
   for (int i = blockIdx.x * gpb + threadIdx.x / GP; i < nb; i += stride) {
     if (lane >= B) continue;
     const int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
-    T acc = T(0);
+    T acc = RES ? g[(size_t)i * B + lane] : T(0);
     int p = p0;
     for (; p + 1 < p1; p += 2) {  // two blocks in flight
       const int j0 = __ldg(ci + p), j1 = __ldg(ci + p + 1);
@@ -88,17 +97,17 @@ __global__ void __launch_bounds__(kThreads) bsr_spmv_kernel(int nb, const int* _
       load_row<B>(v + ((size_t)(p + 1) * B + lane) * B, a1);
       load_row<B>(x + (size_t)j0 * B, x0);
       load_row<B>(x + (size_t)j1 * B, x1);
-      acc += row_dot<B>(a0, x0);
-      acc += row_dot<B>(a1, x1);
+      acc = RES ? fnma_row<B>(a0, x0, acc) : fma_row<B>(a0, x0, acc);
+      acc = RES ? fnma_row<B>(a1, x1, acc) : fma_row<B>(a1, x1, acc);
     }
     if (p < p1) {
       const int j0 = __ldg(ci + p);
       T a0[B], x0[B];
       load_row<B>(v + ((size_t)p * B + lane) * B, a0);
       load_row<B>(x + (size_t)j0 * B, x0);
-      acc += row_dot<B>(a0, x0);
+      acc = RES ? fnma_row<B>(a0, x0, acc) : fma_row<B>(a0, x0, acc);
     }
-    y[(size_t)i * B + lane] = RES ? g[(size_t)i * B + lane] - acc : acc;
+    y[(size_t)i * B + lane] = acc;
   }
 }
 
@@ -120,15 +129,15 @@ __global__ void __launch_bounds__(kThreads) bsr_restrict_p_kernel(
     const bool active = (i < nb) && (lane < B);
     if (active) {
       const int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
-      T acc = T(0);
+      T acc = g[(size_t)i * B + lane];
       for (int p = p0; p < p1; ++p) {
         const int j = __ldg(ci + p);
         T a[B], xx[B];
         load_row<B>(v + ((size_t)p * B + lane) * B, a);
         load_row<B>(w + (size_t)j * B, xx);
-        acc += row_dot<B>(a, xx);
+        acc = fnma_row<B>(a, xx, acc);
       }
-      res = g[(size_t)i * B + lane] - acc;
+      res = acc;
       res = omega ? res * omega[(size_t)i * B + lane] : (lane == 0 ? res : T(0));
     }
     res = group_sum<GP>(res);
@@ -202,7 +211,7 @@ __global__ void __launch_bounds__(kThreads) bilu_fwd_kernel(
       load_row<B>(lu + ((size_t)p * B + lane) * B, a);
 #pragma unroll
       for (int c = 0; c < B; ++c) yy[c] = y[(size_t)j * B + c];
-      acc -= row_dot<B>(a, yy);
+      acc = fnma_row<B>(a, yy, acc);
     }
     y[(size_t)i * B + lane] = acc;
   }
@@ -231,7 +240,7 @@ __global__ void __launch_bounds__(kThreads) bilu_bwd_kernel(
         load_row<B>(lu + ((size_t)p * B + lane) * B, a);
 #pragma unroll
         for (int c = 0; c < B; ++c) xx[c] = x[(size_t)j * B + c];
-        acc -= row_dot<B>(a, xx);
+        acc = fnma_row<B>(a, xx, acc);
       }
     }
     T out = T(0);
@@ -315,7 +324,7 @@ __global__ void prolong_add_kernel(int n, const int* __restrict__ agg, const T* 
     x[i] += xc[agg[i]];
 }
 
-// x = Ainv b, one warp per row
+// x = Ainv b, one warp per row, four independent accumulators per lane
 template <typename T>
 __global__ void __launch_bounds__(kThreads) dense_gemv_kernel(int n, const double* __restrict__ A,
                                                              const T* __restrict__ b,
@@ -324,9 +333,16 @@ __global__ void __launch_bounds__(kThreads) dense_gemv_kernel(int n, const doubl
   const int wpb = blockDim.x / kWarp;
   for (int r = blockIdx.x * wpb + threadIdx.x / kWarp; r < n; r += gridDim.x * wpb) {
     const double* row = A + (size_t)r * n;
-    double s = 0.0;
-    for (int c = lane; c < n; c += kWarp) s = fma(__ldg(row + c), (double)b[c], s);
-    s = group_sum<kWarp>(s);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int c = lane;
+    for (; c + 3 * kWarp < n; c += 4 * kWarp) {
+      s0 = fma(__ldg(row + c), (double)__ldg(b + c), s0);
+      s1 = fma(__ldg(row + c + kWarp), (double)__ldg(b + c + kWarp), s1);
+      s2 = fma(__ldg(row + c + 2 * kWarp), (double)__ldg(b + c + 2 * kWarp), s2);
+      s3 = fma(__ldg(row + c + 3 * kWarp), (double)__ldg(b + c + 3 * kWarp), s3);
+    }
+    for (; c < n; c += kWarp) s0 = fma(__ldg(row + c), (double)__ldg(b + c), s0);
+    double s = group_sum<kWarp>((s0 + s1) + (s2 + s3));
     if (lane == 0) x[r] = (T)s;
   }
 }

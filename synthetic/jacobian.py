@@ -191,10 +191,23 @@ def random_rhs(a: BSRMatrix, seed: int) -> np.ndarray:
 
 
 def perturb_values(a: BSRMatrix, seed: int, rel: float = 0.05) -> np.ndarray:
-    """A Newton-like next Jacobian with the same pattern: every stored entry multiplied
-    by an independent U[1-rel, 1+rel] factor."""
+    """A Newton-like next Jacobian with the same pattern: every entry of every
+    off-diagonal block is multiplied by an independent U[1-rel, 1+rel] factor and each
+    diagonal block absorbs the change of its row's couplings, so that the diagonal stays
+    "accumulation minus the sum of the off-diagonal blocks" (a per-entry perturbation
+    of the diagonal too would unbalance cells whose couplings dwarf their accumulation
+    term and can make the system nearly singular)."""
     rng = np.random.default_rng(seed)
-    return a.values * rng.uniform(1.0 - rel, 1.0 + rel, size=a.values.shape)
+    rows = np.repeat(np.arange(a.nb), np.diff(a.row_ptr))
+    off = rows != a.col_idx
+    v = a.values.copy()
+    new_off = a.values[off] * rng.uniform(1.0 - rel, 1.0 + rel, size=a.values[off].shape)
+    delta = np.zeros((a.nb, a.b, a.b))
+    np.add.at(delta, rows[off], new_off - a.values[off])
+    v[off] = new_off
+    dpos = np.nonzero(~off)[0]
+    v[dpos] = a.values[dpos] - delta[rows[dpos]]
+    return v
 
 
 def poisson3d_bsr(nx: int, ny: int, nz: int) -> BSRMatrix:

@@ -38,8 +38,16 @@ def test_spe10_counts_formula():
 def test_perturbation_and_rhs():
     a = box_jacobian(5, 4, 3, 4, 3, n_wells=2)
     v = perturb_values(a, 1)
-    r = v / a.values
-    ok = a.values != 0
+    rows = np.repeat(np.arange(a.nb), np.diff(a.row_ptr))
+    off = rows != a.col_idx
+    r = v[off] / a.values[off]
+    ok = a.values[off] != 0
     assert np.all((r[ok] >= 0.95) & (r[ok] <= 1.05))
+    # block row sums (the accumulation terms) are unchanged
+    s0 = np.zeros((a.nb, a.b, a.b))
+    s1 = np.zeros((a.nb, a.b, a.b))
+    np.add.at(s0, rows, a.values)
+    np.add.at(s1, rows, v)
+    assert np.allclose(s0, s1, rtol=1e-12, atol=1e-9)
     rhs = random_rhs(a, 2).reshape(a.nb, a.b)
     assert np.all(rhs[a.n_cells:, 1:] == 0.0)
