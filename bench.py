@@ -142,6 +142,25 @@ def traffic_for(site):
     return None
 
 
+def combine_over_ranks(times_ms):
+    """Max over ranks of each local time (the slowest replica bounds the job); a no-op
+    without an initialised process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return list(times_ms)
+    dev = torch.device("cuda", torch.cuda.current_device()) \
+        if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor(list(times_ms), dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def total_throughput(steps, world, ms):
+    """Whole-job solves/s: every replica solved `steps` systems within `ms`."""
+    return steps * world / (ms / 1000.0)
+
+
 def make_inputs(args, rank):
     from synthetic import grid_spe10, perturb_values, random_rhs
     a = grid_spe10(seed=2209 + rank, nx=args.nx, ny=args.ny, nz=args.nz)
@@ -256,12 +275,9 @@ def run_native(args):
         e2e = {"ms": e2e_ms, "h2d": (a.nnzb * a.b * a.b + a.n) * 8, "d2h": a.n * 8}
 
     # max over ranks
-    if world > 1:
-        t = torch.tensor([ms, e2e["ms"] if e2e else 0.0], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_ms = float(t[0]), float(t[1])
-        if e2e:
-            e2e["ms"] = e2e_ms
+    ms, e2e_ms = combine_over_ranks([ms, e2e["ms"] if e2e else 0.0])
+    if e2e:
+        e2e["ms"] = e2e_ms
     solver_levels = solver.num_levels
     level_info = [msp.msp_level_info(solver.h, l) for l in range(solver_levels)]
     solver.close()
@@ -271,7 +287,7 @@ def run_native(args):
         return None
 
     total_solves = args.steps * world
-    value = total_solves / (ms / 1000.0)
+    value = total_throughput(args.steps, world, ms)
     its = [i["iterations"] for i in infos]
     setups = sum(i["setup_performed"] for i in infos)
     peak, peak_kind = load_peaks()

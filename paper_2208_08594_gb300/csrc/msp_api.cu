@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -1071,21 +1072,34 @@ int fgmres(msp_handle h, double tol, int* iters, double* relres, double* relres_
                                         false, s));
       }
       ++it;
-      // classical Gram-Schmidt, twice (CGS2): h = V^T w, w -= V h, repeated; the norm of
-      // w comes with the second update
+      // classical Gram-Schmidt with a conditional second pass (DGKS: repeat the pass
+      // iff it shrank w below 1/sqrt(2) of its norm; the test runs on the device).
+      // w is stored right after V_j, so one multi-dot over K+1 vectors gives the
+      // projections h and ||w||^2.
       const int K = j + 1;
-      for (int pass = 0; pass < 2; ++pass) {
-        double* hc = pass == 0 ? h->hdev.p : h->ydev.p;
-        {
-          Probe pr("krylov_multi_dot", (double)(K + 1) * n * 8.0, s);
-          MSP_TRY(launch_multi_dot(n, V, n, K, w, h->partial.p, nbk, s));
-        }
-        MSP_TRY(launch_reduce_partials(K, nbk, h->partial.p, hc, false, s));
-        Probe pr("krylov_multi_axpy", (double)(K + 2) * n * 8.0, s);
-        MSP_TRY(launch_multi_axpy_norm(n, V, n, K, hc, w, h->partial.p, nbk, s));
+      {
+        Probe pr("krylov_multi_dot", (double)(K + 1) * n * 8.0, s);
+        MSP_TRY(launch_multi_dot(n, V, n, K + 1, w, h->partial.p, nbk, s));
       }
-      MSP_TRY(launch_reduce_partials(K, 1, h->ydev.p, h->hdev.p, true, s));  // h = h1 + h2
+      MSP_TRY(launch_reduce_partials(K + 1, nbk, h->partial.p, h->hdev.p, false, s));
+      {
+        Probe pr("krylov_multi_axpy", (double)(K + 2) * n * 8.0, s);
+        MSP_TRY(launch_multi_axpy_norm(n, V, n, K, h->hdev.p, w, h->partial.p, nbk, s));
+      }
       MSP_TRY(launch_reduce_partials(1, nbk, h->partial.p, h->nrm.p, false, s));
+      int* gate = h->ifl.p + 1;
+      MSP_TRY(launch_reorth_gate(h->nrm.p, h->hdev.p + K, gate, s));
+      {
+        Probe pr("krylov_reorth_dot", 0.0, s);
+        MSP_TRY(launch_multi_dot(n, V, n, K, w, h->partial.p, nbk, s, gate));
+      }
+      MSP_TRY(launch_reduce_partials(K, nbk, h->partial.p, h->ydev.p, false, s, gate));
+      {
+        Probe pr("krylov_reorth_axpy", 0.0, s);
+        MSP_TRY(launch_multi_axpy_norm(n, V, n, K, h->ydev.p, w, h->partial.p, nbk, s, gate));
+      }
+      MSP_TRY(launch_reduce_partials(K, 1, h->ydev.p, h->hdev.p, true, s, gate));  // h += h2
+      MSP_TRY(launch_reduce_partials(1, nbk, h->partial.p, h->nrm.p, false, s, gate));
       MSP_TRY(launch_normalize(n, w, h->nrm.p, w, h->nrm.p + 1, s));
       MSP_CUDA_TRY(cudaMemcpyAsync(h->h_pin, h->hdev.p, K * sizeof(double), cudaMemcpyDeviceToHost, s));
       MSP_CUDA_TRY(cudaMemcpyAsync(h->h_pin + 64, h->nrm.p + 1, sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -379,8 +379,10 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 __global__ void __launch_bounds__(kThreads) multi_dot_kernel(size_t n, const double* __restrict__ V,
                                                             size_t ldv, int K,
                                                             const double* __restrict__ w,
-                                                            double* __restrict__ partial) {
+                                                            double* __restrict__ partial,
+                                                            const int* __restrict__ gate) {
   __shared__ double sh[kThreads / kWarp];
+  if (gate && *gate == 0) return;
   for (int k0 = 0; k0 < K; k0 += kDotChunk) {
     const int kc = min(kDotChunk, K - k0);
     double acc[kDotChunk];
@@ -402,20 +404,26 @@ __global__ void __launch_bounds__(kThreads) multi_dot_kernel(size_t n, const dou
   }
 }
 
+// one warp per output k: lanes sum strided partials, then a fixed-order shuffle tree
 __global__ void reduce_partials_kernel(int K, int nblocks, const double* __restrict__ partial,
-                                       double* __restrict__ out, bool accumulate) {
-  const int k = threadIdx.x;
+                                       double* __restrict__ out, bool accumulate,
+                                       const int* __restrict__ gate) {
+  if (gate && *gate == 0) return;
+  const int k = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
+  const int lane = threadIdx.x % kWarp;
   if (k >= K) return;
   double s = 0.0;
-  for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * kMaxK + k];
-  out[k] = accumulate ? out[k] + s : s;
+  for (int b = lane; b < nblocks; b += kWarp) s += partial[(size_t)b * kMaxK + k];
+  s = group_sum<kWarp>(s);
+  if (lane == 0) out[k] = accumulate ? out[k] + s : s;
 }
 
 __global__ void __launch_bounds__(kThreads) multi_axpy_norm_kernel(
     size_t n, const double* __restrict__ V, size_t ldv, int K, const double* __restrict__ h,
-    double* __restrict__ w, double* __restrict__ partial) {
+    double* __restrict__ w, double* __restrict__ partial, const int* __restrict__ gate) {
   __shared__ double sh[kThreads / kWarp];
   __shared__ double hs[kMaxK];
+  if (gate && *gate == 0) return;
   for (int k = threadIdx.x; k < K; k += blockDim.x) hs[k] = h[k];
   __syncthreads();
   double nrm = 0.0;
@@ -441,15 +449,23 @@ __global__ void __launch_bounds__(kThreads) norm2_partial_kernel(size_t n, const
   if (threadIdx.x == 0) partial[(size_t)blockIdx.x * kMaxK] = t;
 }
 
-// in place allowed (v == w)
+// in place allowed (v == w); multiplies by the reciprocal (an FP64 division per element
+// would make this kernel FP64-ALU bound)
 __global__ void normalize_kernel(size_t n, const double* w, const double* __restrict__ nrm2,
                                  double* v, double* __restrict__ hn) {
   const double h = sqrt(nrm2[0]);
   if (blockIdx.x == 0 && threadIdx.x == 0) hn[0] = h;
   if (h == 0.0) return;
+  const double rh = 1.0 / h;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x)
-    v[i] = w[i] / h;
+    v[i] = w[i] * rh;
+}
+
+// DGKS test after one Gram-Schmidt pass: gate = 1 iff ||w_after||^2 < ||w_before||^2 / 2
+__global__ void reorth_gate_kernel(const double* __restrict__ nrm_after,
+                                   const double* __restrict__ nrm_before, int* gate) {
+  gate[0] = nrm_after[0] < 0.5 * nrm_before[0] ? 1 : 0;
 }
 
 __global__ void update_x_kernel(size_t n, const double* __restrict__ Z, size_t ldz, int K,
@@ -653,23 +669,27 @@ int launch_cast_f2d(size_t n, const float* in, double* out, cudaStream_t s) {
 int krylov_blocks() { return sm_count() * 4; }
 
 int launch_multi_dot(size_t n, const double* V, size_t ldv, int K, const double* w,
-                     double* partial, int nblocks, cudaStream_t s) {
+                     double* partial, int nblocks, cudaStream_t s, const int* gate) {
   if (K > kMaxK) return MSP_ERR_ARG;
-  multi_dot_kernel<<<nblocks, kThreads, 0, s>>>(n, V, ldv, K, w, partial);
+  multi_dot_kernel<<<nblocks, kThreads, 0, s>>>(n, V, ldv, K, w, partial, gate);
   return launch_status();
 }
 
 int launch_reduce_partials(int K, int nblocks, const double* partial, double* out,
-                           bool accumulate, cudaStream_t s) {
+                           bool accumulate, cudaStream_t s, const int* gate) {
   if (K > kMaxK) return MSP_ERR_ARG;
-  reduce_partials_kernel<<<1, kMaxK, 0, s>>>(K, nblocks, partial, out, accumulate);
+  if (K <= 0) return MSP_OK;
+  const int wpb = 4;  // warps (outputs) per block
+  reduce_partials_kernel<<<(K + wpb - 1) / wpb, wpb * kWarp, 0, s>>>(K, nblocks, partial, out,
+                                                                     accumulate, gate);
   return launch_status();
 }
 
 int launch_multi_axpy_norm(size_t n, const double* V, size_t ldv, int K, const double* h,
-                           double* w, double* partial, int nblocks, cudaStream_t s) {
+                           double* w, double* partial, int nblocks, cudaStream_t s,
+                           const int* gate) {
   if (K > kMaxK) return MSP_ERR_ARG;
-  multi_axpy_norm_kernel<<<nblocks, kThreads, 0, s>>>(n, V, ldv, K, h, w, partial);
+  multi_axpy_norm_kernel<<<nblocks, kThreads, 0, s>>>(n, V, ldv, K, h, w, partial, gate);
   return launch_status();
 }
 
@@ -682,6 +702,12 @@ int launch_norm2_partial(size_t n, const double* x, double* partial, int nblocks
 int launch_normalize(size_t n, const double* w, const double* nrm2, double* v, double* hn,
                      cudaStream_t s) {
   normalize_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, w, nrm2, v, hn);
+  return launch_status();
+}
+
+int launch_reorth_gate(const double* nrm_after, const double* nrm_before, int* gate,
+                       cudaStream_t s) {
+  reorth_gate_kernel<<<1, 1, 0, s>>>(nrm_after, nrm_before, gate);
   return launch_status();
 }
 
