@@ -185,6 +185,34 @@ int msp_stats_count(void);
 int msp_stats_get(int index, char* name, int name_len, long long* launches, double* total_ms,
                   double* bytes);
 
+
+/* ---- allocation-free entry point ----
+ * The paper has no counterpart: this exists for callers that cannot allocate device
+ * memory, e.g. code running inside a memory pool that owns the whole GPU, code that
+ * must not let cudaMalloc/cudaFree synchronise the device, or environments where the
+ * CUDA allocator is replaced.  It computes what msp_setup computes for the block graph
+ * (the colouring returned by msp_colour0: adjacency matrix, then VerticesGrouping,
+ * Algorithms 4.1/4.2) without allocating: its scratch is one fixed device array of
+ * about 5.8 MB inside the library, which every GPU that loads the library holds until
+ * the process exits.
+ *   n               block rows, 1 <= n <= 65536 (larger: MSP_ERR_ARG, nothing runs)
+ *   d_row_ptr       int32[n+1], device; row_ptr[0] = 0, row_ptr[n] - n <= 1048576
+ *   d_col_idx       int32[row_ptr[n]], device; ascending within a row, diagonal present,
+ *                   off-diagonal pattern structurally symmetric, <= 1023 per row
+ *                   (otherwise MSP_ERR_PATTERN / MSP_ERR_ARG)
+ *   d_colour        int32[n], device, output: colour 1..g of every row
+ *   h_ncolours      host, output: g
+ * Calls no cudaMalloc, cudaFree or allocating library routine.  The first call on a
+ * device looks up the device address of the scratch array (cudaGetSymbolAddress), so
+ * make that first call before any stream capture.  Every call reuses the same array,
+ * which keeps the previous call's contents: calls that overlap on the GPU (other
+ * streams, other host threads) race on it and must be serialised by the caller.
+ * Synchronises `stream`.  msp_noalloc_error() describes the last rejection of this
+ * thread. */
+int msp_vertices_grouping_noalloc(int32_t n, const int32_t* d_row_ptr, const int32_t* d_col_idx,
+                                  int32_t* d_colour, int32_t* h_ncolours, void* stream);
+const char* msp_noalloc_error(void);
+
 #ifdef __cplusplus
 }
 #endif

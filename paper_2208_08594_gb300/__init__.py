@@ -14,10 +14,12 @@ from ._native import (MSP_NOT_CONVERGED, MSP_OK, MSP_PREC_MSP, MSP_PREC_N_ONLY, 
                       msp_level_get, msp_level_info, msp_num_levels, msp_setup, msp_solve,
                       msp_solve_host, msp_spmv, msp_status_string, msp_update_values,
                       msp_update_values_host, msp_stats_enable, msp_stats_reset,
-                      msp_stats_launches, msp_stats_get)
+                      msp_stats_launches, msp_stats_get, msp_vertices_grouping_noalloc,
+                      NOALLOC_MAX_VERTICES)
 
 __all__ = ["Solver", "MspError", "msp_setup", "msp_update_values", "msp_update_values_host",
            "msp_stats_enable", "msp_stats_reset", "msp_stats_launches", "msp_stats_get",
+           "msp_vertices_grouping_noalloc", "NOALLOC_MAX_VERTICES",
            "msp_solve",
            "msp_solve_host", "msp_free", "msp_apply_precond", "msp_spmv", "msp_num_levels",
            "msp_level_info", "msp_level_get", "msp_colour0", "msp_config_default",

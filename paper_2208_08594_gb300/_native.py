@@ -27,7 +27,11 @@ EXPORTS = ("msp_config_default", "msp_setup", "msp_update_values", "msp_update_v
            "msp_solve_host", "msp_free", "msp_status_string", "msp_apply_precond", "msp_spmv",
            "msp_num_levels", "msp_level_info", "msp_level_get", "msp_colour0",
            "msp_last_error", "msp_stats_enable", "msp_stats_reset", "msp_stats_launches",
-           "msp_stats_count", "msp_stats_get")
+           "msp_stats_count", "msp_stats_get", "msp_vertices_grouping_noalloc",
+           "msp_noalloc_error")
+
+# largest n accepted by msp_vertices_grouping_noalloc (size of its fixed scratch)
+NOALLOC_MAX_VERTICES = 1 << 16
 
 
 class MspConfig(C.Structure):
@@ -96,8 +100,12 @@ def lib(build_if_missing: bool = True):
     L.msp_stats_launches.restype = C.c_longlong
     L.msp_stats_count.argtypes = []
     L.msp_stats_get.argtypes = [I, C.c_char_p, I, P, P, P]
+    L.msp_vertices_grouping_noalloc.argtypes = [C.c_int32, P, P, P, C.POINTER(C.c_int32), P]
+    L.msp_noalloc_error.argtypes = []
+    L.msp_noalloc_error.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("msp_status_string", "msp_last_error", "msp_stats_launches"):
+        if name not in ("msp_status_string", "msp_last_error", "msp_stats_launches",
+                        "msp_noalloc_error"):
             getattr(L, name).restype = I
     _lib = L
     return L
@@ -275,3 +283,15 @@ def msp_stats_get():
         if L.msp_stats_get(k, name, 64, C.byref(n), C.byref(ms), C.byref(by)) == MSP_OK:
             out[name.value.decode()] = (n.value, ms.value, by.value)
     return out
+
+
+def msp_vertices_grouping_noalloc(n: int, row_ptr, col_idx, colour, stream=None) -> int:
+    """Colouring of a structurally symmetric block pattern without any device
+    allocation (for callers that cannot allocate); returns the number of colours."""
+    g = C.c_int32()
+    st = lib().msp_vertices_grouping_noalloc(int(n), _ptr(row_ptr), _ptr(col_idx), _ptr(colour),
+                                             C.byref(g), _stream(stream))
+    if st != MSP_OK:
+        raise MspError(st, "msp_vertices_grouping_noalloc: " +
+                       lib().msp_noalloc_error().decode())
+    return g.value
