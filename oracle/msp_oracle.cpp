@@ -1173,6 +1173,13 @@ int orc_spmv(void* p, const double* x, double* y) {
   return ORC_OK;
 }
 
+// Change MaxIt of later solves (the CPU baseline times single Arnoldi steps).
+int orc_set_max_it(void* p, int max_it) {
+  if (max_it < 0) return ORC_ERR_ARG;
+  static_cast<Handle*>(p)->cfg.max_it = max_it;
+  return ORC_OK;
+}
+
 int orc_num_levels(void* p) { return (int)static_cast<Handle*>(p)->levels.size(); }
 int orc_colours_l0(void* p) { return static_cast<Handle*>(p)->g0; }
 int orc_setup_calls(void* p) { return static_cast<Handle*>(p)->setup_calls; }
