@@ -172,7 +172,10 @@ int msp_colour0(msp_handle h, int32_t* h_colour);
 /* ---- launch statistics (process-wide; instrumentation for benchmarks) ----
  * mode 0: off; 1: count every kernel launch of this library; 2: also time each launch
  * of the solve phase with CUDA events recorded on its stream and add up the
- * algorithmic bytes it moves, per call site.  Timing adds two event records per launch. */
+ * algorithmic bytes it moves, per call site (the preconditioner then runs launch by
+ * launch instead of as its CUDA graph); 3: as 2, but the preconditioner keeps running
+ * as its graph and only the launches outside it (Krylov kernels) are timed.  Timing
+ * adds two event records per timed launch. */
 int msp_stats_enable(int mode);
 /* Forget all counts and timings. */
 int msp_stats_reset(void);

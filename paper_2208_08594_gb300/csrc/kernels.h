@@ -37,11 +37,12 @@ int launch_prolong_p(int b, int nb, const T* e, T* w, cudaStream_t s);
 
 // ---------------- solve phase: scalar CSR AMG levels ----------------
 // PGS-MC on rows [r0, r1) of one colour: x_i = (b_i - sum_{j != i} a_ij x_j) / a_ii;
-// lower_only: entries right of the diagonal are skipped (x there is still zero).
+// lower_only: entries right of the diagonal are skipped (x there is still zero);
+// avg_row: mean stored entries per row of the level (chooses the lanes per row).
 template <typename T>
 int launch_csr_gs_colour(int r0, int r1, const int* rp, const int* ci, const T* v,
                          const int* dpos, const T* rdiag, const T* b, T* x, bool lower_only,
-                         cudaStream_t s);
+                         int avg_row, cudaStream_t s);
 // bc[I] = sum over members i of aggregate I (ascending) of (b_i - (A x)_i)
 template <typename T>
 int launch_csr_residual_restrict(int nc, const int* mptr, const int* members, const int* rp,

@@ -782,7 +782,8 @@ int vcycle(msp_handle h, const PView<T>& P, int l, cudaStream_t s) {
       const long long e = L.cc.lower[c] + (sw == 0 ? 0 : L.cc.upper[c]);
       Probe pr("amg_gs_sweep", sweep_bytes(L.cptr[c], L.cptr[c + 1], e, sT + 4, 3 * sT + 12), s);
       MSP_TRY(launch_csr_gs_colour<T>(L.cptr[c], L.cptr[c + 1], L.A.rp.p, L.A.ci.p, P.lv[l],
-                                      L.dpos.p, P.lrd[l], P.lb[l], P.lx[l], sw == 0, s));
+                                      L.dpos.p, P.lrd[l], P.lb[l], P.lx[l], sw == 0,
+                                      L.A.nnz / std::max(1, n), s));
     }
   {
     Probe pr("amg_residual_restrict",
@@ -800,7 +801,8 @@ int vcycle(msp_handle h, const PView<T>& P, int l, cudaStream_t s) {
       const long long e = L.cc.lower[c] + L.cc.upper[c];
       Probe pr("amg_gs_sweep", sweep_bytes(L.cptr[c], L.cptr[c + 1], e, sT + 4, 3 * sT + 12), s);
       MSP_TRY(launch_csr_gs_colour<T>(L.cptr[c], L.cptr[c + 1], L.A.rp.p, L.A.ci.p, P.lv[l],
-                                      L.dpos.p, P.lrd[l], P.lb[l], P.lx[l], false, s));
+                                      L.dpos.p, P.lrd[l], P.lb[l], P.lx[l], false,
+                                      L.A.nnz / std::max(1, n), s));
     }
   return MSP_OK;
 }
@@ -946,11 +948,11 @@ int capture_graph(msp_handle h) {
 }
 
 // w = B g on FP64 colour-ordered vectors, in the configured precision.  Replays the
-// captured graph, except while per-launch timing is on (stats mode 2).
+// captured graph, except while every launch is timed (stats mode 2).
 int apply_precond(msp_handle h, const double* g, double* w, cudaStream_t s) {
   const size_t n = (size_t)h->nb * h->b;
   const bool fp32 = h->cfg.precision == MSP_PRECISION_FP32;
-  if (g_stats_mode >= 2) {
+  if (g_stats_mode == 2) {
     if (fp32) {
       MSP_TRY(launch_cast_d2f(n, g, h->g32.p, s));
       MSP_TRY(apply_precond_t<float>(h, view32(h), h->g32.p, h->w32.p, s));
@@ -1431,7 +1433,7 @@ int msp_spmv(msp_handle h, const double* d_x, double* d_y, void* stream) {
 }
 
 int msp_stats_enable(int mode) {
-  if (mode < 0 || mode > 2) return MSP_ERR_ARG;
+  if (mode < 0 || mode > 3) return MSP_ERR_ARG;
   std::lock_guard<std::mutex> lk(g_stats_mu);
   g_stats_mode = mode;
   return MSP_OK;

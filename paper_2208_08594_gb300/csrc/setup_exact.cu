@@ -362,15 +362,67 @@ __device__ __forceinline__ bool in_v(const unsigned* inV, int v) {
 
 constexpr int kSecondU = 8;  // second-circle entries gathered per lane per round
 
+// Warp 1 of the colouring CTA: while warp 0 processes its pick, load the two-hop
+// neighbourhood of the frontier's current first vertex (the likely next pick) so warp
+// 0 finds it in L1.  It only reads; the bitmap it reads is being changed by warp 0, so
+// what it finds is a hint, checked for range, and a wrong guess costs nothing but the
+// loads.  Its wait for a new pick is bounded and it stops when warp 0 is done.
+__device__ void colouring_prefetcher(int n, const int* __restrict__ srp, const int* __restrict__ sci,
+                                     const Bitmap3& bm, volatile int* hint, volatile int* done,
+                                     volatile int* sink) {
+  const int lane = threadIdx.x % 32;
+  const volatile unsigned* l0 = bm.l0;
+  const volatile unsigned* l1 = bm.l1;
+  const volatile unsigned* l2 = bm.l2;
+  int last = -2, acc = 0;
+  const long long limit = 256LL * n + (1LL << 20);
+  for (long long it = 0; it < limit; ++it) {
+    if (*done) break;
+    const int v = *hint;
+    if (v == last) continue;
+    last = v;
+    // racy first set bit of the frontier
+    int c = -1;
+    for (int base = 0; base < bm.n2 && c < 0; base += 32) {
+      const unsigned w = (base + lane < bm.n2) ? l2[base + lane] : 0u;
+      const unsigned m = __ballot_sync(0xffffffffu, w != 0u);
+      if (m) {
+        const int i2 = base + __ffs(m) - 1;
+        const unsigned w2 = l2[i2];
+        if (w2) {
+          const int i1 = i2 * 32 + __ffs(w2) - 1;
+          const unsigned w1 = i1 < bm.n1 ? l1[i1] : 0u;
+          if (w1) {
+            const int i0 = i1 * 32 + __ffs(w1) - 1;
+            const unsigned w0 = i0 < bm.n0 ? l0[i0] : 0u;
+            if (w0) c = i0 * 32 + __ffs(w0) - 1;
+          }
+        }
+        break;
+      }
+    }
+    c = __shfl_sync(0xffffffffu, c, 0);
+    if (c < 0 || c >= n) continue;
+    const int q0 = __ldg(srp + c), q1 = __ldg(srp + c + 1);
+    for (int q = q0 + lane; q < q1; q += 32) {
+      const int k = __ldg(sci + q);
+      const int kb = __ldg(srp + k), ke = __ldg(srp + k + 1);
+      for (int e = kb; e < ke; e += 8) acc += __ldg(sci + e);  // one load per 32 bytes
+    }
+  }
+  if (acc == 0x7fffffff) *sink = acc;  // keeps the loads
+}
+
 // layout flags: bit 0 = frontier bitmap in shared memory, bit 1 = inV in shared memory
-__global__ void __launch_bounds__(32) colouring_kernel(int n, const int* __restrict__ srp,
+__global__ void __launch_bounds__(64) colouring_kernel(int n, const int* __restrict__ srp,
                                                        const int* __restrict__ sci,
                                                        unsigned* ginV, int* wbar,
                                                        unsigned* gbitmap, int layout,
                                                        int* colour, int* meta) {
   extern __shared__ unsigned smem_bits[];
   __shared__ int s_kb[32], s_off[33];
-  const int lane = threadIdx.x;
+  __shared__ volatile int s_hint, s_done, s_sink;
+  const int lane = threadIdx.x % 32;
   Bitmap3 bm;
   bm.n0 = (n + 31) / 32;
   bm.n1 = (bm.n0 + 31) / 32;
@@ -381,17 +433,30 @@ __global__ void __launch_bounds__(32) colouring_kernel(int n, const int* __restr
   bm.l0 = fbase;
   bm.l1 = fbase + bm.n0;
   bm.l2 = fbase + bm.n0 + bm.n1;
-  for (int k = lane; k < fw; k += 32) fbase[k] = 0u;
-  for (int k = lane; k < bm.n0; k += 32) {
-    const int rem = n - 32 * k;
-    inV[k] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+  if (threadIdx.x == 0) {
+    s_hint = -1;
+    s_done = 0;
   }
-  __syncwarp();
+  if (threadIdx.x < 32) {
+    for (int k = lane; k < fw; k += 32) fbase[k] = 0u;
+    for (int k = lane; k < bm.n0; k += 32) {
+      const int rem = n - 32 * k;
+      inV[k] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x >= 32) {
+    colouring_prefetcher(n, srp, sci, bm, &s_hint, &s_done, &s_sink);
+    return;
+  }
   int coloured = 0, g = 0;
   while (coloured < n) {
     ++g;
     if (g > n) {  // every pass colours at least one vertex
-      if (lane == 0) meta[1] = 1;
+      if (lane == 0) {
+        meta[1] = 1;
+        s_done = 1;
+      }
       return;
     }
     int cursor = 0, nwbar = 0;
@@ -403,7 +468,10 @@ __global__ void __launch_bounds__(32) colouring_kernel(int n, const int* __restr
       // frontier first (hat W), dropping stale entries
       while (true) {
         if (++picks > max_picks) {
-          if (lane == 0) meta[1] = 1;
+          if (lane == 0) {
+            meta[1] = 1;
+            s_done = 1;
+          }
           return;
         }
         const int r = bm_find_first(bm, lane);
@@ -435,6 +503,7 @@ __global__ void __launch_bounds__(32) colouring_kernel(int n, const int* __restr
       if (lane == 0) {
         atomicAnd(inV + (v >> 5), ~(1u << (v & 31)));
         colour[v] = g;
+        s_hint = v;  // lets the prefetcher move on to the next likely pick
       }
       ++coloured;
       const int q0 = __ldg(srp + v), q1 = __ldg(srp + v + 1);
@@ -512,7 +581,10 @@ __global__ void __launch_bounds__(32) colouring_kernel(int n, const int* __restr
     }
     __syncwarp();
   }
-  if (lane == 0) meta[0] = g;
+  if (lane == 0) {
+    meta[0] = g;
+    s_done = 1;
+  }
 }
 
 }  // namespace
@@ -659,7 +731,7 @@ int launch_colouring(int n, const int* srp, const int* sci, unsigned* inV, int* 
       smem = 0;
     }
   }
-  colouring_kernel<<<1, 32, smem, s>>>(n, srp, sci, inV, wbar, bitmap, layout, colour, meta);
+  colouring_kernel<<<1, 64, smem, s>>>(n, srp, sci, inV, wbar, bitmap, layout, colour, meta);
   return launch_status();
 }
 

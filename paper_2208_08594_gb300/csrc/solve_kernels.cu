@@ -268,52 +268,58 @@ __global__ void prolong_p_kernel(int b, int nb, const T* __restrict__ e, T* __re
 // ----------------------------------------------------------------------------------
 constexpr int kTpr = 8;
 
-template <typename T>
+template <typename T, int TPR>
 __global__ void __launch_bounds__(kThreads) csr_gs_colour_kernel(
     int r0, int r1, const int* __restrict__ rp, const int* __restrict__ ci,
     const T* __restrict__ v, const int* __restrict__ dpos, const T* __restrict__ rdiag,
     const T* __restrict__ b, T* __restrict__ x, bool lower_only) {
-  const int lane = threadIdx.x % kTpr;
-  const int rpb = blockDim.x / kTpr;
+  const int lane = threadIdx.x % TPR;
+  const int rpb = blockDim.x / TPR;
   for (int base = r0 + blockIdx.x * rpb; base < r1; base += gridDim.x * rpb) {
-    const int i = base + threadIdx.x / kTpr;
+    const int i = base + threadIdx.x / TPR;
     T s = T(0);
     if (i < r1) {
       const int p0 = __ldg(rp + i), pd = __ldg(dpos + i);
       const int p1 = lower_only ? pd : __ldg(rp + i + 1);
-      for (int p = p0 + lane; p < p1; p += kTpr) {
+      for (int p = p0 + lane; p < p1; p += TPR) {
         if (p == pd) continue;
         s = fma(__ldg(v + p), x[__ldg(ci + p)], s);
       }
     }
-    s = group_sum<kTpr>(s);
+    s = group_sum<TPR>(s);
     if (i < r1 && lane == 0) x[i] = (b[i] - s) * rdiag[i];
   }
 }
 
-// one group of kTpr lanes per coarse row I; members of I processed in ascending order
+// one warp per coarse row I: the members of I (ascending) are handled 4 at a time by
+// 8-lane sub-groups, each striding one member's row; member residuals are then summed
+// in a fixed tree
 template <typename T>
 __global__ void __launch_bounds__(kThreads) csr_residual_restrict_kernel(
     int nc, const int* __restrict__ mptr, const int* __restrict__ members,
     const int* __restrict__ rp, const int* __restrict__ ci, const T* __restrict__ v,
     const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ bc) {
-  const int lane = threadIdx.x % kTpr;
-  const int rpb = blockDim.x / kTpr;
-  for (int base = blockIdx.x * rpb; base < nc; base += gridDim.x * rpb) {
-    const int I = base + threadIdx.x / kTpr;
+  const int lane = threadIdx.x % kWarp, sub = lane / 8, sl = lane % 8;
+  const int wpb = blockDim.x / kWarp;
+  for (int I = blockIdx.x * wpb + threadIdx.x / kWarp; I < nc; I += gridDim.x * wpb) {
+    const int m0 = __ldg(mptr + I), m1 = __ldg(mptr + I + 1);
     T total = T(0);
-    if (I < nc) {
-      const int m0 = __ldg(mptr + I), m1 = __ldg(mptr + I + 1);
-      for (int m = m0; m < m1; ++m) {
-        const int i = __ldg(members + m);
-        T s = T(0);
+    for (int mb = m0; mb < m1; mb += 4) {
+      const int m = mb + sub;
+      T s = T(0);
+      int i = -1;
+      if (m < m1) {
+        i = __ldg(members + m);
         const int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
-        for (int p = p0 + lane; p < p1; p += kTpr) s = fma(__ldg(v + p), __ldg(x + __ldg(ci + p)), s);
-        total += (lane == 0 ? b[i] : T(0)) - s;
+        for (int p = p0 + sl; p < p1; p += 8) s = fma(__ldg(v + p), __ldg(x + __ldg(ci + p)), s);
       }
+      s = group_sum<8>(s);
+      T r = (i >= 0 && sl == 0) ? b[i] - s : T(0);
+      r += __shfl_xor_sync(0xffffffffu, r, 8);
+      r += __shfl_xor_sync(0xffffffffu, r, 16);
+      total += r;
     }
-    total = group_sum<kTpr>(total);
-    if (I < nc && lane == 0) bc[I] = total;
+    if (lane == 0) bc[I] = total;
   }
 }
 
@@ -622,11 +628,20 @@ int launch_prolong_p(int b, int nb, const T* e, T* w, cudaStream_t s) {
 template <typename T>
 int launch_csr_gs_colour(int r0, int r1, const int* rp, const int* ci, const T* v,
                          const int* dpos, const T* rdiag, const T* b, T* x, bool lower_only,
-                         cudaStream_t s) {
+                         int avg_row, cudaStream_t s) {
   if (r1 <= r0) return MSP_OK;
-  const unsigned grid = grid_groups(r1 - r0, kTpr);
-  csr_gs_colour_kernel<T><<<grid, kThreads, 0, s>>>(r0, r1, rp, ci, v, dpos, rdiag, b, x,
-                                                    lower_only);
+  // lanes per row from the average row length of the level (entries read per sweep)
+  const int len = lower_only ? (avg_row + 1) / 2 : avg_row;
+  if (len <= 4) {
+    csr_gs_colour_kernel<T, 4><<<grid_groups(r1 - r0, 4), kThreads, 0, s>>>(
+        r0, r1, rp, ci, v, dpos, rdiag, b, x, lower_only);
+  } else if (len <= 12) {
+    csr_gs_colour_kernel<T, 8><<<grid_groups(r1 - r0, 8), kThreads, 0, s>>>(
+        r0, r1, rp, ci, v, dpos, rdiag, b, x, lower_only);
+  } else {
+    csr_gs_colour_kernel<T, 16><<<grid_groups(r1 - r0, 16), kThreads, 0, s>>>(
+        r0, r1, rp, ci, v, dpos, rdiag, b, x, lower_only);
+  }
   return launch_status();
 }
 
@@ -635,7 +650,7 @@ int launch_csr_residual_restrict(int nc, const int* mptr, const int* members, co
                                  const int* ci, const T* v, const T* b, const T* x, T* bc,
                                  cudaStream_t s) {
   if (nc <= 0) return MSP_OK;
-  const unsigned grid = grid_groups(nc, kTpr);
+  const unsigned grid = grid_groups(nc, kWarp);
   csr_residual_restrict_kernel<T><<<grid, kThreads, 0, s>>>(nc, mptr, members, rp, ci, v, b,
                                                             x, bc);
   return launch_status();
@@ -759,7 +774,7 @@ int launch_scatter_blocks(int nb, int b, const int* perm, const double* in, doub
                                   const T*, const T*, const T*, T*, T*, cudaStream_t);      \
   template int launch_prolong_p<T>(int, int, const T*, T*, cudaStream_t);                   \
   template int launch_csr_gs_colour<T>(int, int, const int*, const int*, const T*,          \
-                                       const int*, const T*, const T*, T*, bool,            \
+                                       const int*, const T*, const T*, T*, bool, int,       \
                                        cudaStream_t);                                       \
   template int launch_csr_residual_restrict<T>(int, const int*, const int*, const int*,     \
                                                const int*, const T*, const T*, const T*,    \
