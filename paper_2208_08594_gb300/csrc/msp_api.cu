@@ -771,6 +771,7 @@ int vcycle(msp_handle h, const PView<T>& P, int l, cudaStream_t s) {
   Level& L = h->levels[l];
   const int n = L.A.n;
   const double sT = sizeof(T);
+
   if (l + 1 == (int)h->levels.size()) {
     Probe pr("coarse_gemv", (double)n * n * 8.0 + 2.0 * n * sT, s);
     return launch_dense_gemv<T>(n, h->cinv.p, P.lb[l], P.lx[l], s);
@@ -1425,8 +1426,11 @@ int msp_spmv(msp_handle h, const double* d_x, double* d_y, void* stream) {
   if (!h || !d_x || !d_y) return MSP_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   MSP_TRY(launch_gather_blocks(h->nb, h->b, h->perm0.p, d_x, h->bperm.p, s));
-  MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, h->bperm.p, nullptr,
-                                  h->xperm.p, false, s));
+  {
+    Probe pr("api_spmv", bsr_bytes(h, 8.0, 1), s);
+    MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, h->bperm.p,
+                                    nullptr, h->xperm.p, false, s));
+  }
   MSP_TRY(launch_scatter_blocks(h->nb, h->b, h->perm0.p, h->xperm.p, d_y, s));
   MSP_CUDA_TRY(cudaStreamSynchronize(s));
   return MSP_OK;

@@ -7,7 +7,6 @@
 // 8/16-byte vector loads and consecutive groups read consecutive block rows.
 #include <cuda_runtime.h>
 
-#include <cstring>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -24,21 +23,33 @@ struct Gp {
 };
 
 // Load B consecutive values with the widest aligned vector loads (rows start at
-// multiples of B*sizeof(T) bytes from a 256-byte aligned allocation).
+// multiples of B*sizeof(T) bytes from a 256-byte aligned allocation).  Components are
+// assigned one by one: copying a loaded vector into the array as raw bytes would put
+// the array in local memory.
 template <int B, typename T>
 __device__ __forceinline__ void load_row(const T* __restrict__ p, T (&r)[B]) {
-  constexpr int bytes = B * (int)sizeof(T);
-  if constexpr (bytes % 16 == 0) {
+  if constexpr (sizeof(T) == 8 && B % 2 == 0) {
 #pragma unroll
-    for (int k = 0; k < bytes / 16; ++k) {
-      float4 t = __ldg(reinterpret_cast<const float4*>(p) + k);
-      memcpy(reinterpret_cast<char*>(r) + 16 * k, &t, 16);
+    for (int k = 0; k < B / 2; ++k) {
+      const double2 t = __ldg(reinterpret_cast<const double2*>(p) + k);
+      r[2 * k] = t.x;
+      r[2 * k + 1] = t.y;
     }
-  } else if constexpr (bytes % 8 == 0) {
+  } else if constexpr (sizeof(T) == 4 && B % 4 == 0) {
 #pragma unroll
-    for (int k = 0; k < bytes / 8; ++k) {
-      float2 t = __ldg(reinterpret_cast<const float2*>(p) + k);
-      memcpy(reinterpret_cast<char*>(r) + 8 * k, &t, 8);
+    for (int k = 0; k < B / 4; ++k) {
+      const float4 t = __ldg(reinterpret_cast<const float4*>(p) + k);
+      r[4 * k] = t.x;
+      r[4 * k + 1] = t.y;
+      r[4 * k + 2] = t.z;
+      r[4 * k + 3] = t.w;
+    }
+  } else if constexpr (sizeof(T) == 4 && B % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < B / 2; ++k) {
+      const float2 t = __ldg(reinterpret_cast<const float2*>(p) + k);
+      r[2 * k] = t.x;
+      r[2 * k + 1] = t.y;
     }
   } else {
 #pragma unroll
@@ -291,35 +302,29 @@ __global__ void __launch_bounds__(kThreads) csr_gs_colour_kernel(
   }
 }
 
-// one warp per coarse row I: the members of I (ascending) are handled 4 at a time by
-// 8-lane sub-groups, each striding one member's row; member residuals are then summed
-// in a fixed tree
+// one group of kTpr lanes per coarse row I; members of I processed in ascending order
 template <typename T>
 __global__ void __launch_bounds__(kThreads) csr_residual_restrict_kernel(
     int nc, const int* __restrict__ mptr, const int* __restrict__ members,
     const int* __restrict__ rp, const int* __restrict__ ci, const T* __restrict__ v,
     const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ bc) {
-  const int lane = threadIdx.x % kWarp, sub = lane / 8, sl = lane % 8;
-  const int wpb = blockDim.x / kWarp;
-  for (int I = blockIdx.x * wpb + threadIdx.x / kWarp; I < nc; I += gridDim.x * wpb) {
-    const int m0 = __ldg(mptr + I), m1 = __ldg(mptr + I + 1);
+  const int lane = threadIdx.x % kTpr;
+  const int rpb = blockDim.x / kTpr;
+  for (int base = blockIdx.x * rpb; base < nc; base += gridDim.x * rpb) {
+    const int I = base + threadIdx.x / kTpr;
     T total = T(0);
-    for (int mb = m0; mb < m1; mb += 4) {
-      const int m = mb + sub;
-      T s = T(0);
-      int i = -1;
-      if (m < m1) {
-        i = __ldg(members + m);
+    if (I < nc) {
+      const int m0 = __ldg(mptr + I), m1 = __ldg(mptr + I + 1);
+      for (int m = m0; m < m1; ++m) {
+        const int i = __ldg(members + m);
+        T s = T(0);
         const int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
-        for (int p = p0 + sl; p < p1; p += 8) s = fma(__ldg(v + p), __ldg(x + __ldg(ci + p)), s);
+        for (int p = p0 + lane; p < p1; p += kTpr) s = fma(__ldg(v + p), __ldg(x + __ldg(ci + p)), s);
+        total += (lane == 0 ? b[i] : T(0)) - s;
       }
-      s = group_sum<8>(s);
-      T r = (i >= 0 && sl == 0) ? b[i] - s : T(0);
-      r += __shfl_xor_sync(0xffffffffu, r, 8);
-      r += __shfl_xor_sync(0xffffffffu, r, 16);
-      total += r;
     }
-    if (lane == 0) bc[I] = total;
+    total = group_sum<kTpr>(total);
+    if (I < nc && lane == 0) bc[I] = total;
   }
 }
 
@@ -650,7 +655,7 @@ int launch_csr_residual_restrict(int nc, const int* mptr, const int* members, co
                                  const int* ci, const T* v, const T* b, const T* x, T* bc,
                                  cudaStream_t s) {
   if (nc <= 0) return MSP_OK;
-  const unsigned grid = grid_groups(nc, kWarp);
+  const unsigned grid = grid_groups(nc, kTpr);
   csr_residual_restrict_kernel<T><<<grid, kThreads, 0, s>>>(nc, mptr, members, rp, ci, v, b,
                                                             x, bc);
   return launch_status();
