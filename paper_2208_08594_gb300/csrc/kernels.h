@@ -12,10 +12,19 @@ namespace msp {
 template <typename T>
 int launch_bsr_spmv(int b, int nb, const int* rp, const int* ci, const T* v, const T* x,
                     const T* g, T* y, bool residual, cudaStream_t s);
-// rP[i] = omega_i^T (g_i - (A w)_i)   (omega == nullptr: first unknown only)
+// rP[i] = omega_i^T (g_i - (A w)_i)   (omega == nullptr: first unknown only); r != nullptr
+// also receives g - A w
 template <typename T>
 int launch_bsr_restrict_p(int b, int nb, const int* rp, const int* ci, const T* v,
-                          const T* w, const T* g, const T* omega, T* rP, cudaStream_t s);
+                          const T* w, const T* g, const T* omega, T* rP, T* r, cudaStream_t s);
+// r_i <- r_i - sum_j A_ij[:, 0] e_j and w_i[0] += e_i (r, w: nb*b values; c0: column 0 of
+// every block, nnzb*b values; e: one value per block row)
+template <typename T>
+int launch_bsr_col0_update(int b, int nb, const int* rp, const int* ci, const T* c0, const T* e,
+                           T* r, T* w, cudaStream_t s);
+// c0[p*b + r] = v[(p*b + r)*b]
+template <typename T>
+int launch_extract_col0(size_t nnzb, int b, const T* v, T* c0, cudaStream_t s);
 // stage N: one block-GS sweep over the rows [r0, r1) of one colour on the (b-1)x(b-1)
 // sub-blocks aN; reads/writes the concentration slots of w (stride b); lower_only for
 // the first sweep from zero (later colours still hold zero).
@@ -47,7 +56,7 @@ int launch_csr_gs_colour(int r0, int r1, const int* rp, const int* ci, const T* 
 template <typename T>
 int launch_csr_residual_restrict(int nc, const int* mptr, const int* members, const int* rp,
                                  const int* ci, const T* v, const T* b, const T* x, T* bc,
-                                 cudaStream_t s);
+                                 int avg_row, cudaStream_t s);
 // x_i += xc[agg[i]]
 template <typename T>
 int launch_prolong_add(int n, const int* agg, const T* xc, T* x, cudaStream_t s);

@@ -298,13 +298,14 @@ struct msp_handle_s {
   int g0 = 0;
   msp::DevBuf<int> rp, ci, dpos, src;  // colour-ordered BSR pattern, source nonzero
   msp::DevBuf<double> vals;            // colour-ordered current values
+  msp::DevBuf<double> c0;              // column 0 of every block of vals (FP64 preconditioner)
   msp::DevBuf<double> staging;         // user values before the gather
   // setup products
   msp::DevBuf<double> omega, dNinv, aN, lu, uinv, cinv;
   int ncoarse = 0;
   std::vector<msp::Level> levels;
   // FP32 copies
-  msp::DevBuf<float> vals32, omega32, dNinv32, aN32, lu32, uinv32;
+  msp::DevBuf<float> vals32, c0_32, omega32, dNinv32, aN32, lu32, uinv32;
   // preconditioner work vectors
   msp::DevBuf<double> pr, py, px;
   msp::DevBuf<float> g32, w32, pr32, py32, px32;
@@ -714,7 +715,7 @@ int value_setup(msp_handle h, cudaStream_t s) {
 // ---------------------------------------------------------------------------------
 template <typename T>
 struct PView {
-  const T *vals, *omega, *aN, *dNinv, *lu, *uinv;
+  const T *vals, *c0, *omega, *aN, *dNinv, *lu, *uinv;
   std::vector<const T*> lv, lrd;
   std::vector<T*> lb, lx;
   T *r, *y, *x;
@@ -723,6 +724,7 @@ struct PView {
 PView<double> view64(msp_handle h) {
   PView<double> p;
   p.vals = h->vals.p;
+  p.c0 = h->c0.p;
   p.omega = h->cfg.decoupling ? h->omega.p : nullptr;
   p.aN = h->aN.p;
   p.dNinv = h->dNinv.p;
@@ -743,6 +745,7 @@ PView<double> view64(msp_handle h) {
 PView<float> view32(msp_handle h) {
   PView<float> p;
   p.vals = h->vals32.p;
+  p.c0 = h->c0_32.p;
   p.omega = h->cfg.decoupling ? h->omega32.p : nullptr;
   p.aN = h->aN32.p;
   p.dNinv = h->dNinv32.p;
@@ -790,7 +793,8 @@ int vcycle(msp_handle h, const PView<T>& P, int l, cudaStream_t s) {
     Probe pr("amg_residual_restrict",
              (double)L.A.nnz * (sT + 4) + (double)n * (3 * sT + 12) + (double)L.nc * (sT + 4), s);
     MSP_TRY(launch_csr_residual_restrict<T>(L.nc, L.mptr.p, L.members.p, L.A.rp.p, L.A.ci.p,
-                                            P.lv[l], P.lb[l], P.lx[l], P.lb[l + 1], s));
+                                            P.lv[l], P.lb[l], P.lx[l], P.lb[l + 1],
+                                            L.A.nnz / std::max(1, n), s));
   }
   MSP_TRY(vcycle<T>(h, P, l + 1, s));
   {
@@ -837,16 +841,24 @@ inline double bsr_bytes(msp_handle h, double sT, double vecs) {
 }
 
 template <typename T>
-int stage_P(msp_handle h, const PView<T>& P, const T* g, T* w, cudaStream_t s) {
-  const double sT = sizeof(T);
+int stage_P(msp_handle h, const PView<T>& P, const T* g, T* w, T* r, cudaStream_t s) {
+  // r != nullptr: leave in r the residual g - A w of the corrected w (stage R's input),
+  // as (g - A w_before) - A Pi_P e instead of a second pass over the whole matrix
+  const double sT = sizeof(T), b = h->b;
   {
-    Probe pr("stageP_residual_restrict", bsr_bytes(h, sT, 2) + (double)h->nb * sT, s);
+    Probe pr("stageP_residual_restrict", bsr_bytes(h, sT, r ? 3 : 2) + (double)h->nb * sT, s);
     MSP_TRY(launch_bsr_restrict_p<T>(h->b, h->nb, h->rp.p, h->ci.p, P.vals, w, g, P.omega,
-                                     P.lb[0], s));
+                                     P.lb[0], r, s));
   }
   MSP_TRY(vcycle<T>(h, P, 0, s));
-  Probe pr("stageP_prolong", (double)h->nb * 3 * sT, s);
-  return launch_prolong_p<T>(h->b, h->nb, P.lx[0], w, s);
+  if (!r) {
+    Probe pr("stageP_prolong", (double)h->nb * 3 * sT, s);
+    return launch_prolong_p<T>(h->b, h->nb, P.lx[0], w, s);
+  }
+  Probe pr("stageP_correct_residual",
+           (double)h->nnzb * (b * sT + 4) + (double)(h->nb + 1) * 4 +
+               (double)h->nb * sT * (1 + 2 * b + 2), s);
+  return launch_bsr_col0_update<T>(h->b, h->nb, h->rp.p, h->ci.p, P.c0, P.lx[0], r, w, s);
 }
 
 template <typename T>
@@ -886,7 +898,7 @@ int apply_precond_t(msp_handle h, const PView<T>& P, const T* g, T* w, cudaStrea
       return stage_N<T>(h, P, g, w, s);
     case MSP_PREC_P_ONLY:
       MSP_CUDA_TRY(cudaMemsetAsync(w, 0, n * sizeof(T), s));
-      return stage_P<T>(h, P, g, w, s);
+      return stage_P<T>(h, P, g, w, nullptr, s);
     case MSP_PREC_R_ONLY:
       MSP_CUDA_TRY(cudaMemsetAsync(w, 0, n * sizeof(T), s));
       return stage_R<T>(h, P, g, w, s);
@@ -898,13 +910,10 @@ int apply_precond_t(msp_handle h, const PView<T>& P, const T* g, T* w, cudaStrea
     MSP_TRY(stage_N<T>(h, P, g, w, s));
   else
     MSP_CUDA_TRY(cudaMemsetAsync(w, 0, n * sizeof(T), s));
-  // r = g - A w; w += Pi_P B_P Pi_P^T r  (residual fused into the restriction)
-  MSP_TRY(stage_P<T>(h, P, g, w, s));
-  // r = g - A w; w += R r
-  {
-    Probe pr("msp_residual_spmv", bsr_bytes(h, sizeof(T), 2), s);
-    MSP_TRY(launch_bsr_spmv<T>(h->b, h->nb, h->rp.p, h->ci.p, P.vals, w, g, P.r, true, s));
-  }
+  // r = g - A w; w += Pi_P B_P Pi_P^T r  (residual fused into the restriction); the
+  // residual r = g - A w of stage R comes out of the same stage
+  MSP_TRY(stage_P<T>(h, P, g, w, P.r, s));
+  // w += R r
   return stage_R<T>(h, P, P.r, w, s);
 }
 
@@ -984,7 +993,9 @@ int alloc_work(msp_handle h) {
   MSP_TRY(h->px.alloc(n));
   MSP_TRY(h->pg64.alloc(n));
   MSP_TRY(h->pw64.alloc(n));
+  if (h->cfg.precision == MSP_PRECISION_FP64) MSP_TRY(h->c0.alloc((size_t)h->nnzb * h->b));
   if (h->cfg.precision == MSP_PRECISION_FP32) {
+    MSP_TRY(h->c0_32.alloc((size_t)h->nnzb * h->b));
     MSP_TRY(h->g32.alloc(n));
     MSP_TRY(h->w32.alloc(n));
     MSP_TRY(h->pr32.alloc(n));
@@ -1019,9 +1030,11 @@ int norm2(msp_handle h, const double* x, size_t n, double* out, cudaStream_t s) 
 int refresh_values(msp_handle h, const double* d_user_values, cudaStream_t s) {
   const int bb = h->b * h->b;
   MSP_TRY(launch_gather_values((size_t)h->nnzb, bb, h->src.p, d_user_values, h->vals.p, s));
-  if (h->cfg.precision == MSP_PRECISION_FP32)
+  if (h->cfg.precision == MSP_PRECISION_FP32) {
     MSP_TRY(launch_cast_vals((size_t)h->nnzb * bb, h->vals.p, h->vals32.p, s));
-  return MSP_OK;
+    return launch_extract_col0<float>(h->nnzb, h->b, h->vals32.p, h->c0_32.p, s);
+  }
+  return launch_extract_col0<double>(h->nnzb, h->b, h->vals.p, h->c0.p, s);
 }
 
 // ---------------------------------------------------------------------------------

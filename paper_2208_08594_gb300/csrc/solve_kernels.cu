@@ -7,6 +7,7 @@
 // 8/16-byte vector loads and consecutive groups read consecutive block rows.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -123,13 +124,13 @@ __global__ void __launch_bounds__(kThreads) bsr_spmv_kernel(int nb, const int* _
 }
 
 // ----------------------------------------------------------------------------------
-// rP[i] = omega_i^T (g_i - (A w)_i)
+// rP[i] = omega_i^T (g_i - (A w)_i); with WR the residual g - A w is also stored in r
 // ----------------------------------------------------------------------------------
-template <int B, typename T>
+template <int B, typename T, bool WR>
 __global__ void __launch_bounds__(kThreads) bsr_restrict_p_kernel(
     int nb, const int* __restrict__ rp, const int* __restrict__ ci, const T* __restrict__ v,
     const T* __restrict__ w, const T* __restrict__ g, const T* __restrict__ omega,
-    T* __restrict__ rP) {
+    T* __restrict__ rP, T* __restrict__ r) {
   constexpr int GP = Gp<B>::v;
   const int lane = threadIdx.x % GP;
   const int gpb = blockDim.x / GP;
@@ -141,19 +142,77 @@ __global__ void __launch_bounds__(kThreads) bsr_restrict_p_kernel(
     if (active) {
       const int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
       T acc = g[(size_t)i * B + lane];
-      for (int p = p0; p < p1; ++p) {
-        const int j = __ldg(ci + p);
-        T a[B], xx[B];
-        load_row<B>(v + ((size_t)p * B + lane) * B, a);
-        load_row<B>(w + (size_t)j * B, xx);
-        acc = fnma_row<B>(a, xx, acc);
+      int p = p0;
+      for (; p + 1 < p1; p += 2) {  // two blocks in flight, same order as one at a time
+        const int j0 = __ldg(ci + p), j1 = __ldg(ci + p + 1);
+        T a0[B], a1[B], x0[B], x1[B];
+        load_row<B>(v + ((size_t)p * B + lane) * B, a0);
+        load_row<B>(v + ((size_t)(p + 1) * B + lane) * B, a1);
+        load_row<B>(w + (size_t)j0 * B, x0);
+        load_row<B>(w + (size_t)j1 * B, x1);
+        acc = fnma_row<B>(a0, x0, acc);
+        acc = fnma_row<B>(a1, x1, acc);
       }
-      res = acc;
-      res = omega ? res * omega[(size_t)i * B + lane] : (lane == 0 ? res : T(0));
+      if (p < p1) {
+        const int j0 = __ldg(ci + p);
+        T a0[B], x0[B];
+        load_row<B>(v + ((size_t)p * B + lane) * B, a0);
+        load_row<B>(w + (size_t)j0 * B, x0);
+        acc = fnma_row<B>(a0, x0, acc);
+      }
+      if (WR) r[(size_t)i * B + lane] = acc;
+      res = omega ? acc * omega[(size_t)i * B + lane] : (lane == 0 ? acc : T(0));
     }
     res = group_sum<GP>(res);
     if (i < nb && lane == 0) rP[i] = res;
   }
+}
+
+// ----------------------------------------------------------------------------------
+// Pressure correction of stage P applied to the residual as well as to w:
+//   r_i <- r_i - sum_j A_ij[:, 0] e_j,   w_i[0] <- w_i[0] + e_i
+// With r = g - A w on entry this leaves r = g - A (w + Pi_P e), the residual that stage R
+// starts from, reading one column of each block (c0, b values per block) instead of
+// the whole block.
+// ----------------------------------------------------------------------------------
+template <int B, typename T>
+__global__ void __launch_bounds__(kThreads) bsr_col0_update_kernel(
+    int nb, const int* __restrict__ rp, const int* __restrict__ ci, const T* __restrict__ c0,
+    const T* __restrict__ e, T* __restrict__ r, T* __restrict__ w) {
+  constexpr int GP = Gp<B>::v;
+  const int lane = threadIdx.x % GP;
+  const int gpb = blockDim.x / GP;
+  const int stride = gridDim.x * gpb;
+  for (int i = blockIdx.x * gpb + threadIdx.x / GP; i < nb; i += stride) {
+    if (lane >= B) continue;
+    const int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
+    T acc = r[(size_t)i * B + lane];
+    int p = p0;
+    for (; p + 3 < p1; p += 4) {  // four blocks in flight
+      const int j0 = __ldg(ci + p), j1 = __ldg(ci + p + 1);
+      const int j2 = __ldg(ci + p + 2), j3 = __ldg(ci + p + 3);
+      const T a0 = __ldg(c0 + (size_t)p * B + lane), a1 = __ldg(c0 + (size_t)(p + 1) * B + lane);
+      const T a2 = __ldg(c0 + (size_t)(p + 2) * B + lane), a3 = __ldg(c0 + (size_t)(p + 3) * B + lane);
+      const T e0 = __ldg(e + j0), e1 = __ldg(e + j1), e2 = __ldg(e + j2), e3 = __ldg(e + j3);
+      acc = fma(-a0, e0, acc);
+      acc = fma(-a1, e1, acc);
+      acc = fma(-a2, e2, acc);
+      acc = fma(-a3, e3, acc);
+    }
+    for (; p < p1; ++p) acc = fma(-__ldg(c0 + (size_t)p * B + lane), __ldg(e + __ldg(ci + p)), acc);
+    r[(size_t)i * B + lane] = acc;
+    if (lane == 0) w[(size_t)i * B] += __ldg(e + i);
+  }
+}
+
+// c0[p * b + r] = v[p * b * b + r * b]: column 0 (the pressure column) of every block
+template <typename T>
+__global__ void extract_col0_kernel(size_t nnzb, int b, const T* __restrict__ v,
+                                    T* __restrict__ c0) {
+  const size_t total = nnzb * (size_t)b;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x)
+    c0[t] = v[t * b];
 }
 
 // ----------------------------------------------------------------------------------
@@ -177,13 +236,35 @@ __global__ void __launch_bounds__(kThreads) bgs_colour_kernel(
       acc = g[(size_t)i * B + 1 + lane];
       const int p0 = __ldg(rp + i), pd = __ldg(dpos + i), p1 = __ldg(rp + i + 1);
       const int pend = lower_only ? pd : p1;
-      for (int p = p0; p < pend; ++p) {
-        if (p == pd) continue;
-        const int j = __ldg(ci + p);
-        const T* xr = w + (size_t)j * B + 1;
+      // w rows of other colours: none of them is written by this launch
+      auto load = [&](int p, T (&a)[BN], T (&xx)[BN]) {
+        const T* xr = w + (size_t)__ldg(ci + p) * B + 1;
         const T* ar = aN + ((size_t)p * BN + lane) * BN;
 #pragma unroll
-        for (int c = 0; c < BN; ++c) acc = fma(-__ldg(ar + c), xr[c], acc);
+        for (int c = 0; c < BN; ++c) {
+          a[c] = __ldg(ar + c);
+          xx[c] = __ldg(xr + c);
+        }
+      };
+      int p = p0;
+      for (; p + 1 < pend; p += 2) {  // two blocks in flight, same order as one at a time
+        T a0[BN], x0[BN], a1[BN], x1[BN];
+        load(p, a0, x0);
+        load(p + 1, a1, x1);  // the diagonal block is read but not applied
+        if (p != pd) {
+#pragma unroll
+          for (int c = 0; c < BN; ++c) acc = fma(-a0[c], x0[c], acc);
+        }
+        if (p + 1 != pd) {
+#pragma unroll
+          for (int c = 0; c < BN; ++c) acc = fma(-a1[c], x1[c], acc);
+        }
+      }
+      if (p < pend && p != pd) {
+        T a0[BN], x0[BN];
+        load(p, a0, x0);
+#pragma unroll
+        for (int c = 0; c < BN; ++c) acc = fma(-a0[c], x0[c], acc);
       }
     }
     // x_i = D_N,i^{-1} acc : gather the BN partial results of the group
@@ -216,13 +297,24 @@ __global__ void __launch_bounds__(kThreads) bilu_fwd_kernel(
     if (lane >= B) continue;
     T acc = r[(size_t)i * B + lane];
     const int p0 = __ldg(rp + i), pd = __ldg(dpos + i);
-    for (int p = p0; p < pd; ++p) {
-      const int j = __ldg(ci + p);
-      T a[B], yy[B];
-      load_row<B>(lu + ((size_t)p * B + lane) * B, a);
-#pragma unroll
-      for (int c = 0; c < B; ++c) yy[c] = y[(size_t)j * B + c];
-      acc = fnma_row<B>(a, yy, acc);
+    // y rows of earlier colours: none of them is written by this launch
+    int p = p0;
+    for (; p + 1 < pd; p += 2) {  // two blocks in flight, same order as one at a time
+      const int j0 = __ldg(ci + p), j1 = __ldg(ci + p + 1);
+      T a0[B], a1[B], y0[B], y1[B];
+      load_row<B>(lu + ((size_t)p * B + lane) * B, a0);
+      load_row<B>(lu + ((size_t)(p + 1) * B + lane) * B, a1);
+      load_row<B>(y + (size_t)j0 * B, y0);
+      load_row<B>(y + (size_t)j1 * B, y1);
+      acc = fnma_row<B>(a0, y0, acc);
+      acc = fnma_row<B>(a1, y1, acc);
+    }
+    if (p < pd) {
+      const int j0 = __ldg(ci + p);
+      T a0[B], y0[B];
+      load_row<B>(lu + ((size_t)p * B + lane) * B, a0);
+      load_row<B>(y + (size_t)j0 * B, y0);
+      acc = fnma_row<B>(a0, y0, acc);
     }
     y[(size_t)i * B + lane] = acc;
   }
@@ -245,13 +337,24 @@ __global__ void __launch_bounds__(kThreads) bilu_bwd_kernel(
     if (active) {
       acc = y[(size_t)i * B + lane];
       const int pd = __ldg(dpos + i), p1 = __ldg(rp + i + 1);
-      for (int p = pd + 1; p < p1; ++p) {
-        const int j = __ldg(ci + p);
-        T a[B], xx[B];
-        load_row<B>(lu + ((size_t)p * B + lane) * B, a);
-#pragma unroll
-        for (int c = 0; c < B; ++c) xx[c] = x[(size_t)j * B + c];
-        acc = fnma_row<B>(a, xx, acc);
+      // x rows of later colours: none of them is written by this launch
+      int p = pd + 1;
+      for (; p + 1 < p1; p += 2) {  // two blocks in flight, same order as one at a time
+        const int j0 = __ldg(ci + p), j1 = __ldg(ci + p + 1);
+        T a0[B], a1[B], x0[B], x1[B];
+        load_row<B>(lu + ((size_t)p * B + lane) * B, a0);
+        load_row<B>(lu + ((size_t)(p + 1) * B + lane) * B, a1);
+        load_row<B>(x + (size_t)j0 * B, x0);
+        load_row<B>(x + (size_t)j1 * B, x1);
+        acc = fnma_row<B>(a0, x0, acc);
+        acc = fnma_row<B>(a1, x1, acc);
+      }
+      if (p < p1) {
+        const int j0 = __ldg(ci + p);
+        T a0[B], x0[B];
+        load_row<B>(lu + ((size_t)p * B + lane) * B, a0);
+        load_row<B>(x + (size_t)j0 * B, x0);
+        acc = fnma_row<B>(a0, x0, acc);
       }
     }
     T out = T(0);
@@ -277,7 +380,6 @@ __global__ void prolong_p_kernel(int b, int nb, const T* __restrict__ e, T* __re
 // ----------------------------------------------------------------------------------
 // scalar CSR level kernels: TPR lanes per row
 // ----------------------------------------------------------------------------------
-constexpr int kTpr = 8;
 
 template <typename T, int TPR>
 __global__ void __launch_bounds__(kThreads) csr_gs_colour_kernel(
@@ -302,16 +404,16 @@ __global__ void __launch_bounds__(kThreads) csr_gs_colour_kernel(
   }
 }
 
-// one group of kTpr lanes per coarse row I; members of I processed in ascending order
-template <typename T>
+// one group of TPR lanes per coarse row I; members of I processed in ascending order
+template <typename T, int TPR>
 __global__ void __launch_bounds__(kThreads) csr_residual_restrict_kernel(
     int nc, const int* __restrict__ mptr, const int* __restrict__ members,
     const int* __restrict__ rp, const int* __restrict__ ci, const T* __restrict__ v,
     const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ bc) {
-  const int lane = threadIdx.x % kTpr;
-  const int rpb = blockDim.x / kTpr;
+  const int lane = threadIdx.x % TPR;
+  const int rpb = blockDim.x / TPR;
   for (int base = blockIdx.x * rpb; base < nc; base += gridDim.x * rpb) {
-    const int I = base + threadIdx.x / kTpr;
+    const int I = base + threadIdx.x / TPR;
     T total = T(0);
     if (I < nc) {
       const int m0 = __ldg(mptr + I), m1 = __ldg(mptr + I + 1);
@@ -319,11 +421,11 @@ __global__ void __launch_bounds__(kThreads) csr_residual_restrict_kernel(
         const int i = __ldg(members + m);
         T s = T(0);
         const int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
-        for (int p = p0 + lane; p < p1; p += kTpr) s = fma(__ldg(v + p), __ldg(x + __ldg(ci + p)), s);
+        for (int p = p0 + lane; p < p1; p += TPR) s = fma(__ldg(v + p), __ldg(x + __ldg(ci + p)), s);
         total += (lane == 0 ? b[i] : T(0)) - s;
       }
     }
-    total = group_sum<kTpr>(total);
+    total = group_sum<TPR>(total);
     if (I < nc && lane == 0) bc[I] = total;
   }
 }
@@ -566,12 +668,35 @@ int launch_bsr_spmv(int b, int nb, const int* rp, const int* ci, const T* v, con
 
 template <typename T>
 int launch_bsr_restrict_p(int b, int nb, const int* rp, const int* ci, const T* v, const T* w,
-                          const T* g, const T* omega, T* rP, cudaStream_t s) {
+                          const T* g, const T* omega, T* rP, T* r, cudaStream_t s) {
   if (nb <= 0) return MSP_OK;
   MSP_B_SWITCH(b, {
     const unsigned grid = grid_groups(nb, Gp<B_>::v);
-    bsr_restrict_p_kernel<B_, T><<<grid, kThreads, 0, s>>>(nb, rp, ci, v, w, g, omega, rP);
+    if (r)
+      bsr_restrict_p_kernel<B_, T, true><<<grid, kThreads, 0, s>>>(nb, rp, ci, v, w, g, omega,
+                                                                   rP, r);
+    else
+      bsr_restrict_p_kernel<B_, T, false><<<grid, kThreads, 0, s>>>(nb, rp, ci, v, w, g, omega,
+                                                                    rP, r);
   });
+  return launch_status();
+}
+
+template <typename T>
+int launch_bsr_col0_update(int b, int nb, const int* rp, const int* ci, const T* c0, const T* e,
+                           T* r, T* w, cudaStream_t s) {
+  if (nb <= 0) return MSP_OK;
+  MSP_B_SWITCH(b, {
+    const unsigned grid = grid_groups(nb, Gp<B_>::v);
+    bsr_col0_update_kernel<B_, T><<<grid, kThreads, 0, s>>>(nb, rp, ci, c0, e, r, w);
+  });
+  return launch_status();
+}
+
+template <typename T>
+int launch_extract_col0(size_t nnzb, int b, const T* v, T* c0, cudaStream_t s) {
+  if (!nnzb) return MSP_OK;
+  extract_col0_kernel<T><<<grid_for(nnzb * b, kThreads), kThreads, 0, s>>>(nnzb, b, v, c0);
   return launch_status();
 }
 
@@ -630,34 +755,45 @@ int launch_prolong_p(int b, int nb, const T* e, T* w, cudaStream_t s) {
   return launch_status();
 }
 
+// Lanes per row for the scalar CSR kernels, from the entries a row reads.  In FP64 the
+// shuffle tree costs one FP64 add per lane and step, on a GPU whose FP64 rate is ~1/32 of
+// its FP32 rate, so short rows take one thread each; FP32 rows favour coalesced lanes.
+template <typename T>
+int csr_lanes(int len) {
+  if constexpr (sizeof(T) == 8)
+    return len <= 8 ? 1 : len <= 16 ? 2 : len <= 48 ? 4 : 8;
+  else
+    return len <= 4 ? 4 : len <= 12 ? 8 : 16;
+}
+
+#define MSP_TPR_SWITCH(tpr, ...)          \
+  switch (tpr) {                         \
+    case 1: { constexpr int TPR_ = 1; __VA_ARGS__; } break;   \
+    case 2: { constexpr int TPR_ = 2; __VA_ARGS__; } break;   \
+    case 4: { constexpr int TPR_ = 4; __VA_ARGS__; } break;   \
+    case 8: { constexpr int TPR_ = 8; __VA_ARGS__; } break;   \
+    default: { constexpr int TPR_ = 16; __VA_ARGS__; } break; \
+  }
+
 template <typename T>
 int launch_csr_gs_colour(int r0, int r1, const int* rp, const int* ci, const T* v,
                          const int* dpos, const T* rdiag, const T* b, T* x, bool lower_only,
                          int avg_row, cudaStream_t s) {
   if (r1 <= r0) return MSP_OK;
-  // lanes per row from the average row length of the level (entries read per sweep)
-  const int len = lower_only ? (avg_row + 1) / 2 : avg_row;
-  if (len <= 4) {
-    csr_gs_colour_kernel<T, 4><<<grid_groups(r1 - r0, 4), kThreads, 0, s>>>(
-        r0, r1, rp, ci, v, dpos, rdiag, b, x, lower_only);
-  } else if (len <= 12) {
-    csr_gs_colour_kernel<T, 8><<<grid_groups(r1 - r0, 8), kThreads, 0, s>>>(
-        r0, r1, rp, ci, v, dpos, rdiag, b, x, lower_only);
-  } else {
-    csr_gs_colour_kernel<T, 16><<<grid_groups(r1 - r0, 16), kThreads, 0, s>>>(
-        r0, r1, rp, ci, v, dpos, rdiag, b, x, lower_only);
-  }
+  const int tpr = csr_lanes<T>(lower_only ? (avg_row + 1) / 2 : avg_row);
+  MSP_TPR_SWITCH(tpr, csr_gs_colour_kernel<T, TPR_><<<grid_groups(r1 - r0, TPR_), kThreads, 0, s>>>(
+                          r0, r1, rp, ci, v, dpos, rdiag, b, x, lower_only));
   return launch_status();
 }
 
 template <typename T>
 int launch_csr_residual_restrict(int nc, const int* mptr, const int* members, const int* rp,
                                  const int* ci, const T* v, const T* b, const T* x, T* bc,
-                                 cudaStream_t s) {
+                                 int avg_row, cudaStream_t s) {
   if (nc <= 0) return MSP_OK;
-  const unsigned grid = grid_groups(nc, kTpr);
-  csr_residual_restrict_kernel<T><<<grid, kThreads, 0, s>>>(nc, mptr, members, rp, ci, v, b,
-                                                            x, bc);
+  const int tpr = std::min(8, csr_lanes<T>(avg_row));
+  MSP_TPR_SWITCH(tpr, csr_residual_restrict_kernel<T, TPR_><<<grid_groups(nc, TPR_), kThreads, 0, s>>>(
+                          nc, mptr, members, rp, ci, v, b, x, bc));
   return launch_status();
 }
 
@@ -769,7 +905,10 @@ int launch_scatter_blocks(int nb, int b, const int* perm, const double* in, doub
   template int launch_bsr_spmv<T>(int, int, const int*, const int*, const T*, const T*,     \
                                   const T*, T*, bool, cudaStream_t);                        \
   template int launch_bsr_restrict_p<T>(int, int, const int*, const int*, const T*,         \
-                                        const T*, const T*, const T*, T*, cudaStream_t);    \
+                                        const T*, const T*, const T*, T*, T*, cudaStream_t); \
+  template int launch_bsr_col0_update<T>(int, int, const int*, const int*, const T*,        \
+                                         const T*, T*, T*, cudaStream_t);                   \
+  template int launch_extract_col0<T>(size_t, int, const T*, T*, cudaStream_t);             \
   template int launch_bgs_colour<T>(int, int, int, const int*, const int*, const int*,      \
                                     const T*, const T*, const T*, T*, bool, bool,           \
                                     cudaStream_t);                                          \
@@ -783,7 +922,7 @@ int launch_scatter_blocks(int nb, int b, const int* perm, const double* in, doub
                                        cudaStream_t);                                       \
   template int launch_csr_residual_restrict<T>(int, const int*, const int*, const int*,     \
                                                const int*, const T*, const T*, const T*,    \
-                                               T*, cudaStream_t);                           \
+                                               T*, int, cudaStream_t);                      \
   template int launch_prolong_add<T>(int, const int*, const T*, T*, cudaStream_t);          \
   template int launch_dense_gemv<T>(int, const double*, const T*, T*, cudaStream_t);
 MSP_INST(double)
