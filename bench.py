@@ -41,8 +41,22 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "solves/s to 1e-6 rel. residual (1.1M cells x4)"
-ROOFLINE_SITE = "krylov_spmv"
-ROOFLINE_KERNEL = "bsr_spmv_kernel"
+# timing call sites of the library (msp_stats_*) -> the kernel each one launches
+SITE_KERNELS = {
+    "krylov_spmv": "bsr_spmv_kernel", "api_spmv": "bsr_spmv_kernel",
+    "krylov_multi_dot": "multi_dot_kernel", "krylov_reorth_dot": "multi_dot_kernel",
+    "krylov_multi_axpy": "multi_axpy_norm_kernel",
+    "krylov_reorth_axpy": "multi_axpy_norm_kernel",
+    "stageN_bgs_sweep": "bgs_colour_kernel",
+    "stageP_residual_restrict": "bsr_restrict_p_kernel",
+    "stageP_correct_residual": "bsr_col0_update_kernel",
+    "stageP_prolong": "prolong_p_kernel",
+    "stageR_bilu_fwd": "bilu_fwd_kernel", "stageR_bilu_bwd": "bilu_bwd_kernel",
+    "amg_prolong": "prolong_add_kernel", "coarse_gemv": "dense_gemv_kernel",
+}
+SITE_PREFIX_KERNELS = {"amg_gs_pre_l": "csr_gs_colour_kernel",
+                       "amg_gs_post_l": "csr_gs_colour_kernel",
+                       "amg_residual_restrict_l": "csr_residual_restrict_kernel"}
 # FP64 block kernels do one FMA per 8-byte value: at the measured 1.19 TFLOP/s FP64 FMA
 # rate they cannot move more than 1.19e12 / 2 * 8 bytes/s
 FP64_FMA_CEILING_GBPS = 1.19e12 / 2 * 8 / 1e9
@@ -62,7 +76,7 @@ def parse():
     p.add_argument("--nz", type=int, default=85)
     p.add_argument("--value-sets", type=int, default=4)
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--profile-steps", type=int, default=1)
+    p.add_argument("--profile-steps", type=int, default=0)
     return p.parse_args()
 
 
@@ -70,6 +84,23 @@ def workload_name(args):
     return "spe10-shaped %dx%dx%d + 4 wells, 4x4 BSR, %s" % (
         args.nx, args.ny, args.nz, "FP64" if args.precision == "fp64" else
         "FP32 preconditioner / FP64 Krylov")
+
+
+def kernels_from_sites(sites):
+    """{kernel: [launches, ms, bytes]} summed over the call sites that launch it
+    (containers such as the whole graph replay are left out)."""
+    out = {}
+    for site, (n, ms, by) in sites.items():
+        k = SITE_KERNELS.get(site)
+        if k is None:
+            k = next((v for p, v in SITE_PREFIX_KERNELS.items() if site.startswith(p)), None)
+        if k is None:
+            continue
+        acc = out.setdefault(k, [0, 0.0, 0.0])
+        acc[0] += n
+        acc[1] += ms
+        acc[2] += by
+    return out
 
 
 def load_peaks():
@@ -131,17 +162,20 @@ class ClockSampler:
 
 
 def kernel_source_sha(kernel):
-    """Hash of one kernel's source text in csrc/ (from its definition to the next
-    separator line), so a committed ncu figure can be matched to the code it measured."""
+    """Hash of the source a kernel is compiled from: the whole .cu file in csrc/ that
+    defines it (its helpers live there too) and the shared headers, so a committed ncu
+    figure can be matched to the code it measured."""
     import glob
     import re
-    for path in sorted(glob.glob(os.path.join(ROOT, "paper_2208_08594_gb300", "csrc", "*.cu"))):
+    csrc = os.path.join(ROOT, "paper_2208_08594_gb300", "csrc")
+    for path in sorted(glob.glob(os.path.join(csrc, "*.cu"))):
         src = open(path).read()
-        m = re.search(r"__global__ void[^;{]*?\b%s\(" % re.escape(kernel), src)
-        if m:
-            end = src.find("\n// ---", m.end())
-            body = src[m.start():end if end > 0 else len(src)]
-            return hashlib.sha256(body.encode()).hexdigest()[:16]
+        if re.search(r"__global__ void[^;{]*?\b%s\(" % re.escape(kernel), src):
+            h = hashlib.sha256(src.encode())
+            for hdr in ("common.cuh", "kernels.h"):
+                with open(os.path.join(csrc, hdr)) as f:
+                    h.update(f.read().encode())
+            return h.hexdigest()[:16]
     return None
 
 
@@ -231,10 +265,10 @@ def run_native(args):
     for k in range(args.warmup):
         step(k, warm)
 
-    # headline: the preconditioner as its CUDA graph, every kernel launch counted, the
-    # launches outside the graph (Krylov SpMV and orthogonalisation) timed with events
+    # headline: the preconditioner replayed as its CUDA graph; every kernel launch is
+    # counted, nothing is timed inside the region but the region itself
     msp.msp_stats_reset()
-    msp.msp_stats_enable(3)
+    msp.msp_stats_enable(1)
     clocks = ClockSampler(torch.cuda.current_device())
     infos = []
     if world > 1:
@@ -253,23 +287,40 @@ def run_native(args):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     launches = msp.msp_stats_launches()
+
+    # instrumented: the same steps again, the graph re-captured with a pair of CUDA event
+    # nodes around every call site inside it and the launches outside it timed with
+    # events on the solver stream: per-site device time of every kernel launch
+    msp.msp_stats_reset()
+    msp.msp_stats_enable(3)
+    live_infos = []
+    torch.cuda.synchronize()
+    i0 = torch.cuda.Event(enable_timing=True)
+    i1 = torch.cuda.Event(enable_timing=True)
+    i0.record(stream)
+    for k in range(args.steps):
+        step(args.warmup + k, live_infos)
+    i1.record(stream)
+    torch.cuda.synchronize()
+    live_ms = i0.elapsed_time(i1)
     live = msp.msp_stats_get()
 
-    # profile: the same steps launched eagerly, every launch timed with CUDA events on
-    # its stream (per-call-site breakdown)
-    msp.msp_stats_reset()
-    msp.msp_stats_enable(2)
-    prof_infos = []
-    torch.cuda.synchronize()
-    p0 = torch.cuda.Event(enable_timing=True)
-    p1 = torch.cuda.Event(enable_timing=True)
-    p0.record(stream)
-    for k in range(args.profile_steps):
-        step(args.warmup + k, prof_infos)
-    p1.record(stream)
-    torch.cuda.synchronize()
-    prof_ms = p0.elapsed_time(p1)
-    stats = msp.msp_stats_get()
+    # optional: the steps launched eagerly (no graph), every launch timed
+    stats, prof_ms = {}, None
+    if args.profile_steps > 0:
+        msp.msp_stats_reset()
+        msp.msp_stats_enable(2)
+        prof_infos = []
+        torch.cuda.synchronize()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for k in range(args.profile_steps):
+            step(args.warmup + k, prof_infos)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        prof_ms = p0.elapsed_time(p1) / args.profile_steps
+        stats = msp.msp_stats_get()
     msp.msp_stats_enable(0)
 
     # end to end through the host-buffer entry points
@@ -312,27 +363,38 @@ def run_native(args):
     its = [i["iterations"] for i in infos]
     setups = sum(i["setup_performed"] for i in infos)
     peak, peak_kind = load_peaks()
-    # Roofline of the dominant kernel.  The ncu launch list of this workload ranks
-    # bsr_spmv_kernel first (its two call sites: the Krylov product and the MSP residual);
-    # its Krylov call site runs outside the preconditioner graph, so its launches were
-    # timed with CUDA events on the solver stream inside the headline timed region.
+    # Per kernel: the instrumented pass's call sites grouped by the kernel they launch;
+    # the roofline is reported for the kernel with the most device time (the same
+    # ranking as the shares of the ncu launch list under profiles/).
+    kern = kernels_from_sites(live)
     roofline = None
-    site = ROOFLINE_SITE
-    if site in live and live[site][0] > 0:
-        n_l, tot_ms, tot_b = live[site]
+    if kern:
+        name, (n_l, tot_ms, tot_b) = max(kern.items(), key=lambda kv: kv[1][1])
         achieved = (tot_b / n_l) / ((tot_ms / n_l) / 1000.0) / 1e9
-        roofline = {"bound": "hbm", "kernel": ROOFLINE_KERNEL, "call_site": site,
+        roofline = {"bound": "hbm", "kernel": name,
                     "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind,
                     "unit": "GB/s", "frac": round(achieved / peak, 4),
-                    "traffic": traffic_for(ROOFLINE_KERNEL),
-                    "algorithmic_bytes_per_launch": tot_b / n_l,
+                    "traffic": traffic_for(name),
+                    "algorithmic_bytes_per_launch": round(tot_b / n_l, 1),
                     "avg_launch_ms": round(tot_ms / n_l, 5), "launches": n_l,
-                    "fp64_fma_ceiling_GBps": round(FP64_FMA_CEILING_GBPS, 1),
-                    "measured": "CUDA events around every launch of this call site on the "
-                                "solver stream during the timed region"}
-    breakdown = {k: {"launches": v[0], "ms": round(v[1], 3),
-                     "GBps": round(v[2] / (v[1] / 1000.0) / 1e9, 1) if v[1] > 0 else None}
-                 for k, v in sorted(stats.items(), key=lambda kv: -kv[1][1])}
+                    "share_of_step": round(tot_ms / live_ms, 4),
+                    "measured": "CUDA event pairs around every call site (one launch, or "
+                                "the consecutive launches of one kernel over the colours of "
+                                "a sweep), as event nodes inside the preconditioner's CUDA "
+                                "graph and event records on the solver stream outside it, "
+                                "over a second timed pass of the same steps"}
+    kernels = {k: {"launches_per_step": round(v[0] / args.steps, 1),
+                   "ms_per_step": round(v[1] / args.steps, 3),
+                   "GBps": round(v[2] / (v[1] / 1000.0) / 1e9, 1) if v[1] > 0 else None,
+                   "frac": round(v[2] / (v[1] / 1000.0) / 1e9 / peak, 4) if v[1] > 0 else None}
+               for k, v in sorted(kern.items(), key=lambda kv: -kv[1][1])}
+    sites = {k: {"launches_per_step": round(v[0] / args.steps, 1),
+                 "ms_per_step": round(v[1] / args.steps, 3),
+                 "GBps": round(v[2] / (v[1] / 1000.0) / 1e9, 1) if v[1] > 0 else None}
+             for k, v in sorted(live.items(), key=lambda kv: -kv[1][1])}
+    eager = {k: {"launches": v[0], "ms": round(v[1], 3),
+                 "GBps": round(v[2] / (v[1] / 1000.0) / 1e9, 1) if v[1] > 0 else None}
+             for k, v in sorted(stats.items(), key=lambda kv: -kv[1][1])}
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
@@ -343,6 +405,7 @@ def run_native(args):
                    "block_rows": a.nb, "nnzb": a.nnzb, "mu": args.mu,
                    "restart": 30, "tol": TOL, "levels": solver_levels,
                    "level_sizes": [li[0] for li in level_info],
+                   "level_nnz": [li[1] for li in level_info],
                    "level_colours": [li[2] for li in level_info],
                    "iterations": its, "setups_in_timed_steps": setups,
                    "setup_s_first": round(setup_s, 3),
@@ -350,10 +413,15 @@ def run_native(args):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "gpu_launches": launches,
         "roofline": roofline,
-        "kernel_breakdown": breakdown,
-        "profiled_ms_per_step": round(prof_ms / max(1, args.profile_steps), 3),
+        "fp64_fma_ceiling_GBps": round(FP64_FMA_CEILING_GBPS, 1),
+        "kernels": kernels,
+        "sites": sites,
+        "instrumented_ms_per_step": round(live_ms / args.steps, 3),
         "clocks": clk,
     }
+    if eager:
+        out["eager_sites"] = eager
+        out["eager_ms_per_step"] = round(prof_ms, 3)
     if e2e:
         out["e2e"] = {"value": round(total_solves / (e2e["ms"] / 1000.0), 4), "unit": "solves/s",
                       "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]}

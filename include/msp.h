@@ -174,14 +174,18 @@ int msp_colour0(msp_handle h, int32_t* h_colour);
  * of the solve phase with CUDA events recorded on its stream and add up the
  * algorithmic bytes it moves, per call site (the preconditioner then runs launch by
  * launch instead of as its CUDA graph); 3: as 2, but the preconditioner keeps running
- * as its graph and only the launches outside it (Krylov kernels) are timed.  Timing
- * adds two event records per timed launch. */
+ * as its CUDA graph, re-captured with a pair of event-record nodes around every call
+ * site inside it (site "precond_graph" times each whole replay).  Timing adds two event
+ * records per timed launch; in mode 3 each replay first waits for the timings of the
+ * previous one.  Switching into or out of mode 3 re-captures the graph at the next
+ * preconditioner application. */
 int msp_stats_enable(int mode);
-/* Forget all counts and timings. */
+/* Zero all counts and timings (call-site names are kept). */
 int msp_stats_reset(void);
 /* Kernel launches counted since the last reset (mode >= 1). */
 long long msp_stats_launches(void);
-/* Number of timed call sites (waits for pending timings). */
+/* Number of call sites seen so far, timed or not since the last reset (waits for
+ * pending timings). */
 int msp_stats_count(void);
 /* Call site `index`: its name (NUL-terminated, truncated to name_len), launches, summed
  * CUDA-event milliseconds and summed algorithmic bytes.  Any output may be NULL. */

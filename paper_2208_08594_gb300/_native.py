@@ -274,13 +274,14 @@ def msp_stats_launches() -> int:
 
 
 def msp_stats_get():
-    """{site: (launches, total_ms, bytes)} of the timed call sites."""
+    """{site: (launches, total_ms, bytes)} of the call sites timed since the last reset."""
     L = lib()
     out = {}
     for k in range(L.msp_stats_count()):
         name = C.create_string_buffer(64)
         n, ms, by = C.c_longlong(), C.c_double(), C.c_double()
-        if L.msp_stats_get(k, name, 64, C.byref(n), C.byref(ms), C.byref(by)) == MSP_OK:
+        if L.msp_stats_get(k, name, 64, C.byref(n), C.byref(ms), C.byref(by)) == MSP_OK \
+                and n.value > 0:
             out[name.value.decode()] = (n.value, ms.value, by.value)
     return out
 

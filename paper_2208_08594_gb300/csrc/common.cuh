@@ -43,7 +43,9 @@ int launch_check(const char* file, int line);
 // of the launch.  Counting of all launches is on when the mode is >= 1.
 class Probe {
  public:
-  Probe(const char* site, double bytes, cudaStream_t s);
+  // `launches`: kernel launches the probe brackets (consecutive launches of one kernel
+  // are timed as a group: an event pair per launch would cost more than a small launch)
+  Probe(const char* site, double bytes, cudaStream_t s, int launches = 1);
   ~Probe();
   Probe(const Probe&) = delete;
   Probe& operator=(const Probe&) = delete;
@@ -52,6 +54,9 @@ class Probe {
   int site_ = -1;
   cudaEvent_t e0_ = nullptr, e1_ = nullptr;
   cudaStream_t s_ = nullptr;
+  double bytes_ = 0.0;
+  int launches_ = 1;
+  bool in_graph_ = false;  // recorded as event nodes of a graph being captured
 };
 
 // Owning device buffer (cudaMallocAsync / cudaFreeAsync would tie lifetime to a stream;

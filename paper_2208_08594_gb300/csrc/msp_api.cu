@@ -48,6 +48,14 @@ struct StatSite {
 struct PendingTiming {
   int site;
   cudaEvent_t e0, e1;
+  bool graph_owned;  // event nodes of a captured graph: not returned to the pool
+};
+// a timed site inside a captured graph: its two event-record nodes
+struct GraphProbe {
+  int site;
+  cudaEvent_t e0, e1;
+  double bytes;
+  int launches;
 };
 std::mutex g_stats_mu;
 int g_stats_mode = 0;
@@ -57,6 +65,9 @@ long long g_launches = 0;
 thread_local bool t_capturing = false;
 thread_local long long t_cap_launches = 0;
 thread_local double t_cap_bytes = 0.0;
+// stats mode 3 at capture time: every probe also becomes a pair of event-record nodes
+thread_local bool t_cap_timed = false;
+thread_local std::vector<GraphProbe> t_cap_probes;
 std::vector<StatSite> g_sites;
 std::vector<PendingTiming> g_pending;
 std::vector<cudaEvent_t> g_free_events;
@@ -79,14 +90,23 @@ int site_index(const char* name) {
   return (int)g_sites.size() - 1;
 }
 
+// algorithmic bytes known only after a launch (device-side decisions) for a timed site
+void stats_add_bytes(const char* site, double bytes) {
+  if (g_stats_mode < 2) return;
+  std::lock_guard<std::mutex> lk(g_stats_mu);
+  g_sites[site_index(site)].bytes += bytes;
+}
+
 // fold finished timings into the sites (waits for the recorded events)
 void resolve_pending() {
   for (auto& p : g_pending) {
     float ms = 0.f;
     if (cudaEventSynchronize(p.e1) == cudaSuccess && cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess)
       g_sites[p.site].ms += ms;
-    g_free_events.push_back(p.e0);
-    g_free_events.push_back(p.e1);
+    if (!p.graph_owned) {
+      g_free_events.push_back(p.e0);
+      g_free_events.push_back(p.e1);
+    }
   }
   g_pending.clear();
 }
@@ -109,9 +129,18 @@ int launch_check(const char* file, int line) {
   return MSP_OK;
 }
 
-Probe::Probe(const char* site, double bytes, cudaStream_t s) : s_(s) {
+Probe::Probe(const char* site, double bytes, cudaStream_t s, int launches)
+    : s_(s), bytes_(bytes), launches_(launches) {
   if (t_capturing) {
     t_cap_bytes += bytes;
+    if (!t_cap_timed) return;
+    std::lock_guard<std::mutex> lk(g_stats_mu);
+    e0_ = take_event();
+    e1_ = take_event();
+    if (!e0_ || !e1_) return;
+    site_ = site_index(site);
+    in_graph_ = true;
+    cudaEventRecordWithFlags(e0_, s_, cudaEventRecordExternal);
     return;
   }
   if (g_stats_mode < 2) return;
@@ -121,15 +150,20 @@ Probe::Probe(const char* site, double bytes, cudaStream_t s) : s_(s) {
   if (!e0_ || !e1_) return;
   site_ = site_index(site);
   g_sites[site_].bytes += bytes;
-  g_sites[site_].launches++;
+  g_sites[site_].launches += launches;
   cudaEventRecord(e0_, s_);
 }
 
 Probe::~Probe() {
   if (site_ < 0) return;
+  if (in_graph_) {
+    cudaEventRecordWithFlags(e1_, s_, cudaEventRecordExternal);
+    t_cap_probes.push_back(GraphProbe{site_, e0_, e1_, bytes_, launches_});
+    return;
+  }
   cudaEventRecord(e1_, s_);
   std::lock_guard<std::mutex> lk(g_stats_mu);
-  g_pending.push_back(PendingTiming{site_, e0_, e1_});
+  g_pending.push_back(PendingTiming{site_, e0_, e1_, false});
 }
 
 int sm_count() {
@@ -318,6 +352,8 @@ struct msp_handle_s {
   cudaGraphExec_t graph = nullptr;
   long long graph_launches = 0;  // kernels in the graph
   double graph_bytes = 0.0;      // algorithmic bytes of one replay
+  bool graph_timed = false;      // captured with event nodes around every site
+  std::vector<msp::GraphProbe> graph_probes;
   msp::DevBuf<double> pg64, pw64;
   // adaptive setup
   int setup_calls = 0;
@@ -769,6 +805,25 @@ inline double sweep_bytes(int r0, int r1, long long entries, double eb, double r
   return (double)entries * eb + (double)(r1 - r0) * rowb;
 }
 
+// timing-site names of the per-level V-cycle kernels (levels past the table share the last)
+const char* sweep_site(int l, bool pre) {
+  static const char* const pre_names[] = {
+      "amg_gs_pre_l0", "amg_gs_pre_l1", "amg_gs_pre_l2", "amg_gs_pre_l3",
+      "amg_gs_pre_l4", "amg_gs_pre_l5", "amg_gs_pre_l6", "amg_gs_pre_l7+"};
+  static const char* const post_names[] = {
+      "amg_gs_post_l0", "amg_gs_post_l1", "amg_gs_post_l2", "amg_gs_post_l3",
+      "amg_gs_post_l4", "amg_gs_post_l5", "amg_gs_post_l6", "amg_gs_post_l7+"};
+  const int k = l < 7 ? l : 7;
+  return pre ? pre_names[k] : post_names[k];
+}
+const char* restrict_site(int l) {
+  static const char* const names[] = {
+      "amg_residual_restrict_l0", "amg_residual_restrict_l1", "amg_residual_restrict_l2",
+      "amg_residual_restrict_l3", "amg_residual_restrict_l4", "amg_residual_restrict_l5",
+      "amg_residual_restrict_l6", "amg_residual_restrict_l7+"};
+  return names[std::min(l, 7)];
+}
+
 template <typename T>
 int vcycle(msp_handle h, const PView<T>& P, int l, cudaStream_t s) {
   Level& L = h->levels[l];
@@ -780,35 +835,46 @@ int vcycle(msp_handle h, const PView<T>& P, int l, cudaStream_t s) {
     return launch_dense_gemv<T>(n, h->cinv.p, P.lb[l], P.lx[l], s);
   }
   const int g = (int)L.cptr.size() - 1;
+  const int avg_row = L.A.nnz / std::max(1, n);
+  int nonempty = 0;  // colours with rows: one launch each per sweep
+  for (int c = 0; c < g; ++c) nonempty += L.cptr[c + 1] > L.cptr[c];
+  auto row_sweep_bytes = [&](int c, long long entries) {
+    return sweep_bytes(L.cptr[c], L.cptr[c + 1], entries, sT + 4, 3 * sT + 12);
+  };
   if (h->cfg.pre_sweeps <= 0) MSP_CUDA_TRY(cudaMemsetAsync(P.lx[l], 0, n * sizeof(T), s));
-  for (int sw = 0; sw < h->cfg.pre_sweeps; ++sw)
-    for (int c = 0; c < g; ++c) {
-      const long long e = L.cc.lower[c] + (sw == 0 ? 0 : L.cc.upper[c]);
-      Probe pr("amg_gs_sweep", sweep_bytes(L.cptr[c], L.cptr[c + 1], e, sT + 4, 3 * sT + 12), s);
-      MSP_TRY(launch_csr_gs_colour<T>(L.cptr[c], L.cptr[c + 1], L.A.rp.p, L.A.ci.p, P.lv[l],
-                                      L.dpos.p, P.lrd[l], P.lb[l], P.lx[l], sw == 0,
-                                      L.A.nnz / std::max(1, n), s));
-    }
+  if (h->cfg.pre_sweeps > 0) {
+    double bytes = 0.0;
+    for (int sw = 0; sw < h->cfg.pre_sweeps; ++sw)
+      for (int c = 0; c < g; ++c)
+        bytes += row_sweep_bytes(c, L.cc.lower[c] + (sw == 0 ? 0 : L.cc.upper[c]));
+    Probe pr(sweep_site(l, true), bytes, s, h->cfg.pre_sweeps * nonempty);
+    for (int sw = 0; sw < h->cfg.pre_sweeps; ++sw)
+      for (int c = 0; c < g; ++c)
+        MSP_TRY(launch_csr_gs_colour<T>(L.cptr[c], L.cptr[c + 1], L.A.rp.p, L.A.ci.p, P.lv[l],
+                                        L.dpos.p, P.lrd[l], P.lb[l], P.lx[l], sw == 0, avg_row,
+                                        s));
+  }
   {
-    Probe pr("amg_residual_restrict",
+    Probe pr(restrict_site(l),
              (double)L.A.nnz * (sT + 4) + (double)n * (3 * sT + 12) + (double)L.nc * (sT + 4), s);
     MSP_TRY(launch_csr_residual_restrict<T>(L.nc, L.mptr.p, L.members.p, L.A.rp.p, L.A.ci.p,
-                                            P.lv[l], P.lb[l], P.lx[l], P.lb[l + 1],
-                                            L.A.nnz / std::max(1, n), s));
+                                            P.lv[l], P.lb[l], P.lx[l], P.lb[l + 1], avg_row, s));
   }
   MSP_TRY(vcycle<T>(h, P, l + 1, s));
   {
     Probe pr("amg_prolong", (double)n * (3 * sT + 4), s);
     MSP_TRY(launch_prolong_add<T>(n, L.agg.p, P.lx[l + 1], P.lx[l], s));
   }
-  for (int sw = 0; sw < h->cfg.post_sweeps; ++sw)
-    for (int c = g - 1; c >= 0; --c) {
-      const long long e = L.cc.lower[c] + L.cc.upper[c];
-      Probe pr("amg_gs_sweep", sweep_bytes(L.cptr[c], L.cptr[c + 1], e, sT + 4, 3 * sT + 12), s);
-      MSP_TRY(launch_csr_gs_colour<T>(L.cptr[c], L.cptr[c + 1], L.A.rp.p, L.A.ci.p, P.lv[l],
-                                      L.dpos.p, P.lrd[l], P.lb[l], P.lx[l], false,
-                                      L.A.nnz / std::max(1, n), s));
-    }
+  if (h->cfg.post_sweeps > 0) {
+    double bytes = 0.0;
+    for (int c = 0; c < g; ++c) bytes += row_sweep_bytes(c, L.cc.lower[c] + L.cc.upper[c]);
+    Probe pr(sweep_site(l, false), bytes * h->cfg.post_sweeps, s,
+             h->cfg.post_sweeps * nonempty);
+    for (int sw = 0; sw < h->cfg.post_sweeps; ++sw)
+      for (int c = g - 1; c >= 0; --c)
+        MSP_TRY(launch_csr_gs_colour<T>(L.cptr[c], L.cptr[c + 1], L.A.rp.p, L.A.ci.p, P.lv[l],
+                                        L.dpos.p, P.lrd[l], P.lb[l], P.lx[l], false, avg_row, s));
+  }
   return MSP_OK;
 }
 
@@ -820,15 +886,17 @@ int stage_N(msp_handle h, const PView<T>& P, const T* g, T* w, cudaStream_t s) {
     return MSP_OK;
   }
   const double sT = sizeof(T), bn = b - 1;
+  double bytes = 0.0;
   for (int sw = 0; sw < h->cfg.bgs_sweeps; ++sw)
-    for (int c = 0; c < h->g0; ++c) {
-      const long long e = h->cc0.lower[c] + (sw == 0 ? 0 : h->cc0.upper[c]);
-      Probe pr("stageN_bgs_sweep",
-               sweep_bytes(h->cptr0[c], h->cptr0[c + 1], e, bn * bn * sT + 4,
-                           (2 * bn + 1 + bn * bn) * sT + 12), s);
+    for (int c = 0; c < h->g0; ++c)
+      bytes += sweep_bytes(h->cptr0[c], h->cptr0[c + 1],
+                           h->cc0.lower[c] + (sw == 0 ? 0 : h->cc0.upper[c]), bn * bn * sT + 4,
+                           (2 * bn + 1 + bn * bn) * sT + 12);
+  Probe pr("stageN_bgs_sweep", bytes, s, h->cfg.bgs_sweeps * h->g0);
+  for (int sw = 0; sw < h->cfg.bgs_sweeps; ++sw)
+    for (int c = 0; c < h->g0; ++c)
       MSP_TRY(launch_bgs_colour<T>(b, h->cptr0[c], h->cptr0[c + 1], h->rp.p, h->ci.p, h->dpos.p,
                                    P.aN, P.dNinv, g, w, sw == 0, sw == 0, s));
-    }
   return MSP_OK;
 }
 
@@ -865,20 +933,23 @@ template <typename T>
 int stage_R(msp_handle h, const PView<T>& P, const T* r, T* w, cudaStream_t s) {
   const int b = h->b;
   const double sT = sizeof(T), bb = (double)b * b;
+  double fwd = 0.0, bwd = 0.0;
   for (int c = 0; c < h->g0; ++c) {
-    Probe pr("stageR_bilu_fwd",
-             sweep_bytes(h->cptr0[c], h->cptr0[c + 1], h->cc0.lower[c], bb * sT + 4,
-                         3.0 * b * sT + 12), s);
-    MSP_TRY(launch_bilu_fwd<T>(b, h->cptr0[c], h->cptr0[c + 1], h->rp.p, h->ci.p, h->dpos.p, P.lu,
-                               r, P.y, s));
+    fwd += sweep_bytes(h->cptr0[c], h->cptr0[c + 1], h->cc0.lower[c], bb * sT + 4,
+                       3.0 * b * sT + 12);
+    bwd += sweep_bytes(h->cptr0[c], h->cptr0[c + 1], h->cc0.upper[c], bb * sT + 4,
+                       (5.0 * b + bb) * sT + 12);
   }
-  for (int c = h->g0 - 1; c >= 0; --c) {
-    Probe pr("stageR_bilu_bwd",
-             sweep_bytes(h->cptr0[c], h->cptr0[c + 1], h->cc0.upper[c], bb * sT + 4,
-                         (5.0 * b + bb) * sT + 12), s);
-    MSP_TRY(launch_bilu_bwd<T>(b, h->cptr0[c], h->cptr0[c + 1], h->rp.p, h->ci.p, h->dpos.p, P.lu,
-                               P.uinv, P.y, P.x, w, s));
+  {
+    Probe pr("stageR_bilu_fwd", fwd, s, h->g0);
+    for (int c = 0; c < h->g0; ++c)
+      MSP_TRY(launch_bilu_fwd<T>(b, h->cptr0[c], h->cptr0[c + 1], h->rp.p, h->ci.p, h->dpos.p,
+                                 P.lu, r, P.y, s));
   }
+  Probe pr("stageR_bilu_bwd", bwd, s, h->g0);
+  for (int c = h->g0 - 1; c >= 0; --c)
+    MSP_TRY(launch_bilu_bwd<T>(b, h->cptr0[c], h->cptr0[c + 1], h->rp.p, h->ci.p, h->dpos.p,
+                               P.lu, P.uinv, P.y, P.x, w, s));
   return MSP_OK;
 }
 
@@ -917,9 +988,22 @@ int apply_precond_t(msp_handle h, const PView<T>& P, const T* g, T* w, cudaStrea
   return stage_R<T>(h, P, P.r, w, s);
 }
 
+void release_graph_probes(std::vector<GraphProbe>& probes) {
+  if (probes.empty()) return;
+  std::lock_guard<std::mutex> lk(g_stats_mu);
+  resolve_pending();  // no pending timing may still name these events
+  for (auto& gp : probes) {
+    g_free_events.push_back(gp.e0);
+    g_free_events.push_back(gp.e1);
+  }
+  probes.clear();
+}
+
 void drop_graph(msp_handle h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
   h->graph = nullptr;
+  release_graph_probes(h->graph_probes);
+  h->graph_timed = false;
 }
 
 // Capture Algorithm 3.1 on the fixed buffers (pg -> pw) into a CUDA graph; it stays
@@ -933,15 +1017,18 @@ int capture_graph(msp_handle h) {
   t_capturing = true;
   t_cap_launches = 0;
   t_cap_bytes = 0.0;
+  t_cap_timed = g_stats_mode == 3;
+  t_cap_probes.clear();
   const int st = fp32 ? apply_precond_t<float>(h, view32(h), h->g32.p, h->w32.p, h->cap_stream)
                       : apply_precond_t<double>(h, view64(h), h->pg64.p, h->pw64.p, h->cap_stream);
   t_capturing = false;
+  std::vector<GraphProbe> probes;
+  probes.swap(t_cap_probes);
   const cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
-  if (st != MSP_OK) {
+  if (st != MSP_OK || e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
-    return st;
-  }
-  if (e != cudaSuccess) {
+    release_graph_probes(probes);
+    if (st != MSP_OK) return st;
     set_last_cuda_error(e, "cudaStreamEndCapture", __FILE__, __LINE__);
     return MSP_ERR_CUDA;
   }
@@ -949,11 +1036,14 @@ int capture_graph(msp_handle h) {
   cudaGraphDestroy(g);
   if (ei != cudaSuccess) {
     h->graph = nullptr;
+    release_graph_probes(probes);
     set_last_cuda_error(ei, "cudaGraphInstantiate", __FILE__, __LINE__);
     return MSP_ERR_CUDA;
   }
   h->graph_launches = t_cap_launches;
   h->graph_bytes = t_cap_bytes;
+  h->graph_timed = t_cap_timed;
+  h->graph_probes = std::move(probes);
   return MSP_OK;
 }
 
@@ -970,15 +1060,29 @@ int apply_precond(msp_handle h, const double* g, double* w, cudaStream_t s) {
     }
     return apply_precond_t<double>(h, view64(h), g, w, s);
   }
+  // stats mode 3 replays a graph with event nodes around every site; other modes a plain one
+  if (h->graph && h->graph_timed != (g_stats_mode == 3)) drop_graph(h);
   if (!h->graph) MSP_TRY(capture_graph(h));
   if (fp32)
     MSP_TRY(launch_cast_d2f(n, g, h->g32.p, s));
   else
     MSP_CUDA_TRY(cudaMemcpyAsync(h->pg64.p, g, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  MSP_CUDA_TRY(cudaGraphLaunch(h->graph, s));
+  if (h->graph_timed) {  // this replay re-records the events of the previous one
+    std::lock_guard<std::mutex> lk(g_stats_mu);
+    resolve_pending();
+  }
+  {
+    Probe pr("precond_graph", h->graph_bytes, s);  // timed in stats mode 3
+    MSP_CUDA_TRY(cudaGraphLaunch(h->graph, s));
+  }
   if (g_stats_mode >= 1) {
     std::lock_guard<std::mutex> lk(g_stats_mu);
     g_launches += h->graph_launches;
+    for (const auto& gp : h->graph_probes) {
+      g_sites[gp.site].launches += gp.launches;
+      g_sites[gp.site].bytes += gp.bytes;
+      g_pending.push_back(PendingTiming{gp.site, gp.e0, gp.e1, true});
+    }
   }
   if (fp32) return launch_cast_f2d(n, h->w32.p, w, s);
   MSP_CUDA_TRY(cudaMemcpyAsync(w, h->pw64.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1119,7 +1223,14 @@ int fgmres(msp_handle h, double tol, int* iters, double* relres, double* relres_
       MSP_TRY(launch_normalize(n, w, h->nrm.p, w, h->nrm.p + 1, s));
       MSP_CUDA_TRY(cudaMemcpyAsync(h->h_pin, h->hdev.p, K * sizeof(double), cudaMemcpyDeviceToHost, s));
       MSP_CUDA_TRY(cudaMemcpyAsync(h->h_pin + 64, h->nrm.p + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+      MSP_CUDA_TRY(cudaMemcpyAsync(h->h_pin + 65, gate, sizeof(int), cudaMemcpyDeviceToHost, s));
       MSP_CUDA_TRY(cudaStreamSynchronize(s));
+      int reorth = 0;
+      std::memcpy(&reorth, h->h_pin + 65, sizeof(int));
+      if (reorth) {  // the second pass ran: credit its bytes to its timed sites
+        stats_add_bytes("krylov_reorth_dot", (double)(K + 1) * n * 8.0);
+        stats_add_bytes("krylov_reorth_axpy", (double)(K + 2) * n * 8.0);
+      }
       for (int i = 0; i < K; ++i) H[(size_t)i * m + j] = h->h_pin[i];
       const double hn = h->h_pin[64];
       H[(size_t)(j + 1) * m + j] = hn;
@@ -1459,7 +1570,8 @@ int msp_stats_enable(int mode) {
 int msp_stats_reset(void) {
   std::lock_guard<std::mutex> lk(g_stats_mu);
   resolve_pending();
-  g_sites.clear();
+  // names stay (captured graphs keep their site indices); the counters restart
+  for (auto& st : g_sites) st = StatSite{st.name};
   g_launches = 0;
   return MSP_OK;
 }
