@@ -54,9 +54,12 @@ SITE_KERNELS = {
     "stageR_bilu_fwd": "bilu_fwd_kernel", "stageR_bilu_bwd": "bilu_bwd_kernel",
     "amg_prolong": "prolong_add_kernel", "coarse_gemv": "dense_gemv_kernel",
 }
-SITE_PREFIX_KERNELS = {"amg_gs_pre_l": "csr_gs_colour_kernel",
-                       "amg_gs_post_l": "csr_gs_colour_kernel",
-                       "amg_residual_restrict_l": "csr_residual_restrict_kernel"}
+SITE_PREFIX_KERNELS = {"amg_gs_pre_l": "ell_gs_colour_kernel",
+                       "amg_gs_post_l": "ell_gs_colour_kernel",
+                       "amg_gs_csr_pre_l": "csr_gs_colour_kernel",
+                       "amg_gs_csr_post_l": "csr_gs_colour_kernel",
+                       "amg_residual_restrict_l": "ell_residual_restrict_kernel",
+                       "amg_residual_restrict_csr_l": "csr_residual_restrict_kernel"}
 # FP64 block kernels do one FMA per 8-byte value: at the measured 1.19 TFLOP/s FP64 FMA
 # rate they cannot move more than 1.19e12 / 2 * 8 bytes/s
 FP64_FMA_CEILING_GBPS = 1.19e12 / 2 * 8 / 1e9

@@ -53,6 +53,19 @@ int launch_csr_gs_colour(int r0, int r1, const int* rp, const int* ci, const T* 
                          const int* dpos, const T* rdiag, const T* b, T* x, bool lower_only,
                          int avg_row, cudaStream_t s);
 // bc[I] = sum over members i of aggregate I (ascending) of (b_i - (A x)_i)
+// the same sweep over the ELL copy of the level (K in {8, 16, 24, 32} slots per row, slot
+// k of row i at i*K + k; meta from launch_build_ell; rows with meta < 0 use rp/ci/v)
+template <typename T>
+int launch_ell_gs_colour(int K, int r0, int r1, const int* ell_ci, const T* ell_v,
+                         const int* meta, const int* rp, const int* ci, const T* v,
+                         const int* dpos, const T* rdiag, const T* b, T* x, bool lower_only,
+                         cudaStream_t s);
+// the same restriction over the ELL copy of the level (diag: a_ii of every row)
+template <typename T>
+int launch_ell_residual_restrict(int K, int nc, const int* mptr, const int* members,
+                                 const int* ell_ci, const T* ell_v, const int* meta,
+                                 const T* diag, const int* rp, const int* ci, const T* v,
+                                 const T* b, const T* x, T* bc, cudaStream_t s);
 template <typename T>
 int launch_csr_residual_restrict(int nc, const int* mptr, const int* members, const int* rp,
                                  const int* ci, const T* v, const T* b, const T* x, T* bc,

@@ -15,6 +15,8 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <string>
@@ -279,8 +281,22 @@ struct ColourCounts {
   std::vector<long long> lower, upper;
 };
 
+// Slots per row of a level's ELL copy: the smallest of 8, 16, 24, 32 that leaves at most
+// max(16, n / 1024) rows longer (those keep the CSR path); 0 if none does.
+int ell_width(const std::vector<int>& rp, int n) {
+  int hist[4] = {0, 0, 0, 0};  // rows with more than 8, 16, 24, 32 off-diagonal entries
+  for (int i = 0; i < n; ++i) {
+    const int len = rp[i + 1] - rp[i] - 1;
+    for (int t = 0; t < 4; ++t) hist[t] += len > 8 * (t + 1);
+  }
+  const int allowed = std::max(16, n / 1024);
+  for (int t = 0; t < 4; ++t)
+    if (hist[t] <= allowed) return 8 * (t + 1);
+  return 0;
+}
+
 int colour_counts(const int* d_rp, const int* d_dpos, int n, const std::vector<int>& cptr,
-                  ColourCounts& cc, cudaStream_t s) {
+                  ColourCounts& cc, cudaStream_t s, int* ell_k = nullptr) {
   std::vector<int> rp(n + 1), dp(n);
   MSP_CUDA_TRY(cudaMemcpyAsync(rp.data(), d_rp, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
   MSP_CUDA_TRY(cudaMemcpyAsync(dp.data(), d_dpos, n * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -293,6 +309,7 @@ int colour_counts(const int* d_rp, const int* d_dpos, int n, const std::vector<i
       cc.lower[c] += dp[i] - rp[i];
       cc.upper[c] += rp[i + 1] - dp[i] - 1;
     }
+  if (ell_k) *ell_k = ell_width(rp, n);
   return MSP_OK;
 }
 
@@ -306,8 +323,13 @@ struct Level {
   DevBuf<int> agg;          // -> next level index
   DevBuf<int> mptr, members;  // members of every next-level aggregate (ascending)
   int nc = 0;
+  // ELL copy of the off-diagonal entries for the colour sweeps (ell_k slots per row; 0:
+  // the level is swept in CSR form)
+  int ell_k = 0;
+  DevBuf<int> ell_ci, ell_meta;
+  DevBuf<double> ell_v, ell_diag;
   // FP32 copies (mixed precision)
-  DevBuf<float> v32, rdiag32;
+  DevBuf<float> v32, rdiag32, ell_v32, ell_diag32;
   // work vectors
   DevBuf<double> b64, x64;
   DevBuf<float> b32, x32;
@@ -536,13 +558,27 @@ int pairwise_pass(msp_handle h, const DCsr& A, double beta, unsigned long long s
   return MSP_OK;
 }
 
-int level_extras(msp_handle h, Level& L, bool smoothed, cudaStream_t s) {
+// `ell`: also build the ELL copy the colour sweeps read (levels whose colour classes are
+// small enough for the sweeps to be bound by load latency)
+int level_extras(msp_handle h, Level& L, bool smoothed, bool ell, cudaStream_t s) {
   MSP_TRY(L.dpos.alloc(L.A.n));
   MSP_TRY(L.rdiag.alloc(L.A.n));
   MSP_TRY(launch_diag_pos(L.A.n, L.A.rp.p, L.A.ci.p, L.dpos.p, s));
+  L.ell_k = 0;
   if (smoothed) {
     MSP_TRY(launch_rdiag(L.A.n, L.dpos.p, L.A.v.p, L.rdiag.p, h->flags.p, s));
-    MSP_TRY(colour_counts(L.A.rp.p, L.dpos.p, L.A.n, L.cptr, L.cc, s));
+    int k = 0;
+    MSP_TRY(colour_counts(L.A.rp.p, L.dpos.p, L.A.n, L.cptr, L.cc, s, ell ? &k : nullptr));
+    if (k > 0) {
+      const size_t slots = (size_t)k * L.A.n;
+      MSP_TRY(L.ell_ci.alloc(slots));
+      MSP_TRY(L.ell_v.alloc(slots));
+      MSP_TRY(L.ell_meta.alloc(L.A.n));
+      MSP_TRY(L.ell_diag.alloc(L.A.n));
+      MSP_TRY(launch_build_ell(L.A.n, k, L.A.rp.p, L.A.ci.p, L.A.v.p, L.dpos.p, L.ell_ci.p,
+                               L.ell_v.p, L.ell_meta.p, L.ell_diag.p, s));
+      L.ell_k = k;
+    }
   }
   MSP_TRY(L.b64.alloc(L.A.n));
   MSP_TRY(L.x64.alloc(L.A.n));
@@ -551,6 +587,12 @@ int level_extras(msp_handle h, Level& L, bool smoothed, cudaStream_t s) {
     MSP_TRY(L.rdiag32.alloc(L.A.n));
     MSP_TRY(launch_cast_vals(L.A.nnz, L.A.v.p, L.v32.p, s));
     MSP_TRY(launch_cast_vals(L.A.n, L.rdiag.p, L.rdiag32.p, s));
+    if (L.ell_k > 0) {
+      MSP_TRY(L.ell_v32.alloc((size_t)L.ell_k * L.A.n));
+      MSP_TRY(launch_cast_vals((size_t)L.ell_k * L.A.n, L.ell_v.p, L.ell_v32.p, s));
+      MSP_TRY(L.ell_diag32.alloc(L.A.n));
+      MSP_TRY(launch_cast_vals(L.A.n, L.ell_diag.p, L.ell_diag32.p, s));
+    }
     MSP_TRY(L.b32.alloc(L.A.n));
     MSP_TRY(L.x32.alloc(L.A.n));
   }
@@ -703,7 +745,7 @@ int value_setup(msp_handle h, cudaStream_t s) {
   }
   if (h->levels.back().A.n > cfg.coarse_hard_max) return MSP_ERR_ARG;
   for (size_t l = 0; l < h->levels.size(); ++l)
-    MSP_TRY(level_extras(h, h->levels[l], l + 1 < h->levels.size(), s));
+    MSP_TRY(level_extras(h, h->levels[l], l + 1 < h->levels.size(), true, s));
   if (sync_flags(h, s) != MSP_OK) return h->h_flags->code;
   {
     Probe pr("setup:coarse_inverse", 0.0, s);
@@ -752,7 +794,8 @@ int value_setup(msp_handle h, cudaStream_t s) {
 template <typename T>
 struct PView {
   const T *vals, *c0, *omega, *aN, *dNinv, *lu, *uinv;
-  std::vector<const T*> lv, lrd;
+  // per level: values, 1/diagonal, ELL values, diagonal
+  std::vector<const T*> lv, lrd, lev, led;
   std::vector<T*> lb, lx;
   T *r, *y, *x;
 };
@@ -769,6 +812,8 @@ PView<double> view64(msp_handle h) {
   for (auto& L : h->levels) {
     p.lv.push_back(L.A.v.p);
     p.lrd.push_back(L.rdiag.p);
+    p.lev.push_back(L.ell_v.p);
+    p.led.push_back(L.ell_diag.p);
     p.lb.push_back(L.b64.p);
     p.lx.push_back(L.x64.p);
   }
@@ -790,6 +835,8 @@ PView<float> view32(msp_handle h) {
   for (auto& L : h->levels) {
     p.lv.push_back(L.v32.p);
     p.lrd.push_back(L.rdiag32.p);
+    p.lev.push_back(L.ell_v32.p);
+    p.led.push_back(L.ell_diag32.p);
     p.lb.push_back(L.b32.p);
     p.lx.push_back(L.x32.p);
   }
@@ -805,23 +852,16 @@ inline double sweep_bytes(int r0, int r1, long long entries, double eb, double r
   return (double)entries * eb + (double)(r1 - r0) * rowb;
 }
 
-// timing-site names of the per-level V-cycle kernels (levels past the table share the last)
-const char* sweep_site(int l, bool pre) {
-  static const char* const pre_names[] = {
-      "amg_gs_pre_l0", "amg_gs_pre_l1", "amg_gs_pre_l2", "amg_gs_pre_l3",
-      "amg_gs_pre_l4", "amg_gs_pre_l5", "amg_gs_pre_l6", "amg_gs_pre_l7+"};
-  static const char* const post_names[] = {
-      "amg_gs_post_l0", "amg_gs_post_l1", "amg_gs_post_l2", "amg_gs_post_l3",
-      "amg_gs_post_l4", "amg_gs_post_l5", "amg_gs_post_l6", "amg_gs_post_l7+"};
-  const int k = l < 7 ? l : 7;
-  return pre ? pre_names[k] : post_names[k];
-}
-const char* restrict_site(int l) {
-  static const char* const names[] = {
-      "amg_residual_restrict_l0", "amg_residual_restrict_l1", "amg_residual_restrict_l2",
-      "amg_residual_restrict_l3", "amg_residual_restrict_l4", "amg_residual_restrict_l5",
-      "amg_residual_restrict_l6", "amg_residual_restrict_l7+"};
-  return names[std::min(l, 7)];
+// timing-site name "<prefix><level>" (levels past 6 share "<prefix>7+"); the strings live
+// as long as the process
+const char* level_site(const char* prefix, int l) {
+  static std::mutex mu;
+  static std::map<std::string, std::unique_ptr<std::string>> names;
+  const std::string key = prefix + (l < 7 ? std::to_string(l) : std::string("7+"));
+  std::lock_guard<std::mutex> lk(mu);
+  auto& p = names[key];
+  if (!p) p = std::make_unique<std::string>(key);
+  return p->c_str();
 }
 
 template <typename T>
@@ -836,44 +876,79 @@ int vcycle(msp_handle h, const PView<T>& P, int l, cudaStream_t s) {
   }
   const int g = (int)L.cptr.size() - 1;
   const int avg_row = L.A.nnz / std::max(1, n);
-  int nonempty = 0;  // colours with rows: one launch each per sweep
-  for (int c = 0; c < g; ++c) nonempty += L.cptr[c + 1] > L.cptr[c];
-  auto row_sweep_bytes = [&](int c, long long entries) {
-    return sweep_bytes(L.cptr[c], L.cptr[c + 1], entries, sT + 4, 3 * sT + 12);
+  // ELL copy for the full sweeps and for small colour classes (latency-bound); the CSR
+  // form for the lower-triangle sweep of a large class (bandwidth-bound: ELL would also
+  // read the slots right of the diagonal)
+  auto use_ell = [&](int c, bool lower_only) {
+    return L.ell_k > 0 && !(lower_only && L.cptr[c + 1] - L.cptr[c] > 16384);
+  };
+  auto sweep = [&](int c, bool lower_only) {
+    if (use_ell(c, lower_only))
+      return launch_ell_gs_colour<T>(L.ell_k, L.cptr[c], L.cptr[c + 1], L.ell_ci.p, P.lev[l],
+                                     L.ell_meta.p, L.A.rp.p, L.A.ci.p, P.lv[l], L.dpos.p,
+                                     P.lrd[l], P.lb[l], P.lx[l], lower_only, s);
+    return launch_csr_gs_colour<T>(L.cptr[c], L.cptr[c + 1], L.A.rp.p, L.A.ci.p, P.lv[l],
+                                   L.dpos.p, P.lrd[l], P.lb[l], P.lx[l], lower_only, avg_row, s);
+  };
+  // one smoothing phase: its colour launches in order, timed in runs of one kernel
+  struct SweepLaunch {
+    int c;
+    bool lower_only;
+  };
+  auto phase = [&](const std::vector<SweepLaunch>& order, bool pre) -> int {
+    size_t k = 0;
+    while (k < order.size()) {
+      const bool ell = use_ell(order[k].c, order[k].lower_only);
+      size_t e = k;
+      double bytes = 0.0;
+      int launches = 0;
+      for (; e < order.size() && use_ell(order[e].c, order[e].lower_only) == ell; ++e) {
+        const int c = order[e].c;
+        bytes += sweep_bytes(L.cptr[c], L.cptr[c + 1],
+                             L.cc.lower[c] + (order[e].lower_only ? 0 : L.cc.upper[c]), sT + 4,
+                             3 * sT + 12);
+        launches += L.cptr[c + 1] > L.cptr[c];
+      }
+      const char* site = ell ? (pre ? "amg_gs_pre_l" : "amg_gs_post_l")
+                             : (pre ? "amg_gs_csr_pre_l" : "amg_gs_csr_post_l");
+      Probe pr(level_site(site, l), bytes, s, launches);
+      for (; k < e; ++k) MSP_TRY(sweep(order[k].c, order[k].lower_only));
+    }
+    return MSP_OK;
   };
   if (h->cfg.pre_sweeps <= 0) MSP_CUDA_TRY(cudaMemsetAsync(P.lx[l], 0, n * sizeof(T), s));
-  if (h->cfg.pre_sweeps > 0) {
-    double bytes = 0.0;
+  {
+    std::vector<SweepLaunch> order;
     for (int sw = 0; sw < h->cfg.pre_sweeps; ++sw)
-      for (int c = 0; c < g; ++c)
-        bytes += row_sweep_bytes(c, L.cc.lower[c] + (sw == 0 ? 0 : L.cc.upper[c]));
-    Probe pr(sweep_site(l, true), bytes, s, h->cfg.pre_sweeps * nonempty);
-    for (int sw = 0; sw < h->cfg.pre_sweeps; ++sw)
-      for (int c = 0; c < g; ++c)
-        MSP_TRY(launch_csr_gs_colour<T>(L.cptr[c], L.cptr[c + 1], L.A.rp.p, L.A.ci.p, P.lv[l],
-                                        L.dpos.p, P.lrd[l], P.lb[l], P.lx[l], sw == 0, avg_row,
-                                        s));
+      for (int c = 0; c < g; ++c) order.push_back({c, sw == 0});
+    MSP_TRY(phase(order, true));
   }
   {
-    Probe pr(restrict_site(l),
-             (double)L.A.nnz * (sT + 4) + (double)n * (3 * sT + 12) + (double)L.nc * (sT + 4), s);
-    MSP_TRY(launch_csr_residual_restrict<T>(L.nc, L.mptr.p, L.members.p, L.A.rp.p, L.A.ci.p,
-                                            P.lv[l], P.lb[l], P.lx[l], P.lb[l + 1], avg_row, s));
+    const double bytes =
+        (double)L.A.nnz * (sT + 4) + (double)n * (3 * sT + 12) + (double)L.nc * (sT + 4);
+    if (L.ell_k > 0) {
+      Probe pr(level_site("amg_residual_restrict_l", l), bytes, s);
+      MSP_TRY(launch_ell_residual_restrict<T>(L.ell_k, L.nc, L.mptr.p, L.members.p, L.ell_ci.p,
+                                              P.lev[l], L.ell_meta.p, P.led[l], L.A.rp.p,
+                                              L.A.ci.p, P.lv[l], P.lb[l], P.lx[l], P.lb[l + 1],
+                                              s));
+    } else {
+      Probe pr(level_site("amg_residual_restrict_csr_l", l), bytes, s);
+      MSP_TRY(launch_csr_residual_restrict<T>(L.nc, L.mptr.p, L.members.p, L.A.rp.p,
+                                              L.A.ci.p, P.lv[l], P.lb[l], P.lx[l], P.lb[l + 1],
+                                              avg_row, s));
+    }
   }
   MSP_TRY(vcycle<T>(h, P, l + 1, s));
   {
     Probe pr("amg_prolong", (double)n * (3 * sT + 4), s);
     MSP_TRY(launch_prolong_add<T>(n, L.agg.p, P.lx[l + 1], P.lx[l], s));
   }
-  if (h->cfg.post_sweeps > 0) {
-    double bytes = 0.0;
-    for (int c = 0; c < g; ++c) bytes += row_sweep_bytes(c, L.cc.lower[c] + L.cc.upper[c]);
-    Probe pr(sweep_site(l, false), bytes * h->cfg.post_sweeps, s,
-             h->cfg.post_sweeps * nonempty);
+  {
+    std::vector<SweepLaunch> order;
     for (int sw = 0; sw < h->cfg.post_sweeps; ++sw)
-      for (int c = g - 1; c >= 0; --c)
-        MSP_TRY(launch_csr_gs_colour<T>(L.cptr[c], L.cptr[c + 1], L.A.rp.p, L.A.ci.p, P.lv[l],
-                                        L.dpos.p, P.lrd[l], P.lb[l], P.lx[l], false, avg_row, s));
+      for (int c = g - 1; c >= 0; --c) order.push_back({c, false});
+    MSP_TRY(phase(order, false));
   }
   return MSP_OK;
 }

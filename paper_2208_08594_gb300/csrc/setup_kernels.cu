@@ -85,6 +85,39 @@ __global__ void diag_pos_kernel(int n, const int* __restrict__ rp, const int* __
   }
 }
 
+// ELL copy of the off-diagonal entries of a CSR level matrix for the colour sweeps and the
+// restriction: slot k of row i at i*K + k, in the row's CSR order; unused slots hold (i, 0);
+// diag[i] = a_ii.  meta[i] = number of off-diagonal entries | (entries left of the
+// diagonal) << 16, or -1 for a row with more than K of them (that row keeps only its CSR
+// form and every slot is unused).
+__global__ void build_ell_kernel(int n, int K, const int* __restrict__ rp,
+                                 const int* __restrict__ ci, const double* __restrict__ v,
+                                 const int* __restrict__ dpos, int* __restrict__ ell_ci,
+                                 double* __restrict__ ell_v, int* __restrict__ meta,
+                                 double* __restrict__ diag) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int p0 = rp[i], p1 = rp[i + 1], pd = dpos[i];
+    diag[i] = v[pd];
+    const int len = p1 - p0 - 1;
+    int k = 0;
+    if (len <= K) {
+      for (int p = p0; p < p1; ++p) {
+        if (p == pd) continue;
+        ell_ci[(size_t)i * K + k] = ci[p];
+        ell_v[(size_t)i * K + k] = v[p];
+        ++k;
+      }
+      meta[i] = len | ((pd - p0) << 16);
+    } else {
+      meta[i] = -1;
+    }
+    for (; k < K; ++k) {
+      ell_ci[(size_t)i * K + k] = i;
+      ell_v[(size_t)i * K + k] = 0.0;
+    }
+  }
+}
+
 __global__ void rdiag_kernel(int n, const int* __restrict__ dpos, const double* __restrict__ v,
                              double* __restrict__ rdiag, DevFlags* flags) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -338,6 +371,14 @@ int launch_extract_N(int b, size_t nnzb, const double* v, double* aN, cudaStream
 int launch_diag_pos(int n, const int* rp, const int* ci, int* dpos, cudaStream_t s) {
   if (n <= 0) return MSP_OK;
   diag_pos_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, rp, ci, dpos);
+  return launch_status();
+}
+
+int launch_build_ell(int n, int K, const int* rp, const int* ci, const double* v, const int* dpos,
+                     int* ell_ci, double* ell_v, int* meta, double* diag, cudaStream_t s) {
+  if (n <= 0 || K <= 0) return MSP_OK;
+  build_ell_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, K, rp, ci, v, dpos, ell_ci,
+                                                              ell_v, meta, diag);
   return launch_status();
 }
 

@@ -62,6 +62,11 @@ int launch_gather_values(size_t nnz, int bb, const int* src, const double* in, d
                          cudaStream_t s);
 int launch_extract_N(int b, size_t nnzb, const double* v, double* aN, cudaStream_t s);
 int launch_diag_pos(int n, const int* rp, const int* ci, int* dpos, cudaStream_t s);
+// ELL copy (K slots per row, slot k of row i at i*K + k) of the off-diagonal entries of a
+// CSR level matrix; meta[i] = count | (entries left of the diagonal) << 16, or -1 for rows
+// longer than K (their slots hold (i, 0)); diag[i] = a_ii
+int launch_build_ell(int n, int K, const int* rp, const int* ci, const double* v, const int* dpos,
+                     int* ell_ci, double* ell_v, int* meta, double* diag, cudaStream_t s);
 int launch_rdiag(int n, const int* dpos, const double* v, double* rdiag, DevFlags* flags,
                  cudaStream_t s);
 // BILU(0) factorisation of the rows [r0, r1) of one colour (rows of earlier colours done)

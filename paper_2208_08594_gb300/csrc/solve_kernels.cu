@@ -390,8 +390,12 @@ __global__ void __launch_bounds__(kThreads) csr_gs_colour_kernel(
   const int rpb = blockDim.x / TPR;
   for (int base = r0 + blockIdx.x * rpb; base < r1; base += gridDim.x * rpb) {
     const int i = base + threadIdx.x / TPR;
-    T s = T(0);
+    T s = T(0), bi = T(0), di = T(0);
     if (i < r1) {
+      if (lane == 0) {  // issued with the row's first loads, not after the reduction
+        bi = __ldg(b + i);
+        di = __ldg(rdiag + i);
+      }
       const int p0 = __ldg(rp + i), pd = __ldg(dpos + i);
       const int p1 = lower_only ? pd : __ldg(rp + i + 1);
       for (int p = p0 + lane; p < p1; p += TPR) {
@@ -400,7 +404,113 @@ __global__ void __launch_bounds__(kThreads) csr_gs_colour_kernel(
       }
     }
     s = group_sum<TPR>(s);
-    if (i < r1 && lane == 0) x[i] = (b[i] - s) * rdiag[i];
+    if (i < r1 && lane == 0) x[i] = (bi - s) * di;
+  }
+}
+
+// One colour of a PGS-MC sweep over the ELL copy of a level: TPR lanes per row, lane t
+// owning slots t, t + TPR, ... of the row's K (row-major: slot k of row i at i*K + k).
+// Every lane loads all its slots whatever the row's length (unused slots hold (i, 0)), so
+// the only load that waits for another is the gather of x: two dependent trips to memory
+// instead of three (row pointer, then entries, then x).  Rows longer than K (meta < 0)
+// walk their CSR row instead.
+template <typename T, int K, int TPR>
+__global__ void __launch_bounds__(kThreads) ell_gs_colour_kernel(
+    int r0, int r1, const int* __restrict__ ell_ci, const T* __restrict__ ell_v,
+    const int* __restrict__ meta, const int* __restrict__ rp, const int* __restrict__ ci,
+    const T* __restrict__ v, const int* __restrict__ dpos, const T* __restrict__ rdiag,
+    const T* __restrict__ b, T* __restrict__ x, bool lower_only) {
+  constexpr int S = (K + TPR - 1) / TPR;  // slots per lane
+  const int lane = threadIdx.x % TPR;
+  const int rpb = blockDim.x / TPR;
+  for (int base = r0 + blockIdx.x * rpb; base < r1; base += gridDim.x * rpb) {
+    const int i = base + threadIdx.x / TPR;
+    T s = T(0), bi = T(0), di = T(0);
+    if (i < r1) {
+      const int m = __ldg(meta + i);
+      if (lane == 0) {
+        bi = __ldg(b + i);
+        di = __ldg(rdiag + i);
+      }
+      int j[S];
+      T a[S], xj[S];
+#pragma unroll
+      for (int q = 0; q < S; ++q) {
+        const int k = lane + q * TPR;
+        j[q] = k < K ? __ldg(ell_ci + (size_t)i * K + k) : i;
+        a[q] = k < K ? __ldg(ell_v + (size_t)i * K + k) : T(0);
+      }
+#pragma unroll
+      for (int q = 0; q < S; ++q) xj[q] = x[j[q]];
+      // lower_only: x of the later colours is stale, only the entries left of the diagonal
+      const int used = lower_only ? (m >> 16) : K;
+#pragma unroll
+      for (int q = 0; q < S; ++q)
+        if (lane + q * TPR < used) s = fma(a[q], xj[q], s);
+      if (m < 0) {
+        const int p0 = __ldg(rp + i), pd = __ldg(dpos + i);
+        const int p1 = lower_only ? pd : __ldg(rp + i + 1);
+        for (int p = p0 + lane; p < p1; p += TPR) {
+          if (p == pd) continue;
+          s = fma(__ldg(v + p), x[__ldg(ci + p)], s);
+        }
+      }
+    }
+    s = group_sum<TPR>(s);
+    if (i < r1 && lane == 0) x[i] = (bi - s) * di;
+  }
+}
+
+// bc[I] = sum over the members i of aggregate I of (b_i - (A x)_i), over the ELL copy of
+// the level: a group of 4*TPR lanes per aggregate takes four members at a time, TPR lanes
+// per member and S slots per lane, so the member list, the entries and the gather of x
+// are the only dependent trips to memory.  Rows longer than K (meta < 0) walk their CSR
+// row (diagonal included) instead of the slots and the diagonal term.
+template <typename T, int K, int TPR>
+__global__ void __launch_bounds__(kThreads) ell_residual_restrict_kernel(
+    int nc, const int* __restrict__ mptr, const int* __restrict__ members,
+    const int* __restrict__ ell_ci, const T* __restrict__ ell_v, const int* __restrict__ meta,
+    const T* __restrict__ diag, const int* __restrict__ rp, const int* __restrict__ ci,
+    const T* __restrict__ v, const T* __restrict__ b, const T* __restrict__ x,
+    T* __restrict__ bc) {
+  constexpr int kMembers = 4, G = kMembers * TPR, S = (K + TPR - 1) / TPR;
+  const int lane = threadIdx.x % G;
+  const int ms = lane / TPR, t = lane % TPR;
+  const int gpb = blockDim.x / G;
+  for (int base = blockIdx.x * gpb; base < nc; base += gridDim.x * gpb) {
+    const int I = base + threadIdx.x / G;
+    T total = T(0);
+    if (I < nc) {
+      const int m0 = __ldg(mptr + I), m1 = __ldg(mptr + I + 1);
+      for (int mb = m0 + ms; mb < m1; mb += kMembers) {
+        const int i = __ldg(members + mb);
+        const int m = __ldg(meta + i);
+        if (t == 0) total += __ldg(b + i);
+        int j[S];
+        T a[S], xj[S];
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+          const int k = t + q * TPR;
+          j[q] = k < K ? __ldg(ell_ci + (size_t)i * K + k) : i;
+          a[q] = k < K ? __ldg(ell_v + (size_t)i * K + k) : T(0);
+        }
+        const T di = t == 0 ? __ldg(diag + i) : T(0);
+        const T xi = t == 0 ? __ldg(x + i) : T(0);
+#pragma unroll
+        for (int q = 0; q < S; ++q) xj[q] = __ldg(x + j[q]);
+        if (m >= 0) {
+          total = fma(-di, xi, total);
+#pragma unroll
+          for (int q = 0; q < S; ++q) total = fma(-a[q], xj[q], total);
+        } else {
+          const int p1 = __ldg(rp + i + 1);
+          for (int p = __ldg(rp + i) + t; p < p1; p += TPR)
+            total = fma(-__ldg(v + p), __ldg(x + __ldg(ci + p)), total);
+        }
+      }
+    }
+    total = group_sum<G>(total);
+    if (I < nc && lane == 0) bc[I] = total;
   }
 }
 
@@ -787,6 +897,29 @@ int launch_csr_gs_colour(int r0, int r1, const int* rp, const int* ci, const T* 
 }
 
 template <typename T>
+int launch_ell_gs_colour(int K, int r0, int r1, const int* ell_ci, const T* ell_v,
+                         const int* meta, const int* rp, const int* ci, const T* v,
+                         const int* dpos, const T* rdiag, const T* b, T* x, bool lower_only,
+                         cudaStream_t s) {
+  if (r1 <= r0) return MSP_OK;
+  switch (K) {
+#define MSP_ELL_CASE(KK, TT)                                                                \
+  case KK:                                                                                  \
+    ell_gs_colour_kernel<T, KK, TT><<<grid_groups(r1 - r0, TT), kThreads, 0, s>>>(          \
+        r0, r1, ell_ci, ell_v, meta, rp, ci, v, dpos, rdiag, b, x, lower_only);            \
+    break;
+    MSP_ELL_CASE(8, 2)
+    MSP_ELL_CASE(16, 4)
+    MSP_ELL_CASE(24, 8)
+    MSP_ELL_CASE(32, 8)
+#undef MSP_ELL_CASE
+    default:
+      return MSP_ERR_ARG;
+  }
+  return launch_status();
+}
+
+template <typename T>
 int launch_csr_residual_restrict(int nc, const int* mptr, const int* members, const int* rp,
                                  const int* ci, const T* v, const T* b, const T* x, T* bc,
                                  int avg_row, cudaStream_t s) {
@@ -794,6 +927,29 @@ int launch_csr_residual_restrict(int nc, const int* mptr, const int* members, co
   const int tpr = std::min(8, csr_lanes<T>(avg_row));
   MSP_TPR_SWITCH(tpr, csr_residual_restrict_kernel<T, TPR_><<<grid_groups(nc, TPR_), kThreads, 0, s>>>(
                           nc, mptr, members, rp, ci, v, b, x, bc));
+  return launch_status();
+}
+
+template <typename T>
+int launch_ell_residual_restrict(int K, int nc, const int* mptr, const int* members,
+                                 const int* ell_ci, const T* ell_v, const int* meta,
+                                 const T* diag, const int* rp, const int* ci, const T* v,
+                                 const T* b, const T* x, T* bc, cudaStream_t s) {
+  if (nc <= 0) return MSP_OK;
+  switch (K) {
+#define MSP_ELLR_CASE(KK, TT)                                                               \
+  case KK:                                                                                  \
+    ell_residual_restrict_kernel<T, KK, TT><<<grid_groups(nc, 4 * TT), kThreads, 0, s>>>(   \
+        nc, mptr, members, ell_ci, ell_v, meta, diag, rp, ci, v, b, x, bc);                \
+    break;
+    MSP_ELLR_CASE(8, 2)
+    MSP_ELLR_CASE(16, 4)
+    MSP_ELLR_CASE(24, 8)
+    MSP_ELLR_CASE(32, 8)
+#undef MSP_ELLR_CASE
+    default:
+      return MSP_ERR_ARG;
+  }
   return launch_status();
 }
 
@@ -920,6 +1076,13 @@ int launch_scatter_blocks(int nb, int b, const int* perm, const double* in, doub
   template int launch_csr_gs_colour<T>(int, int, const int*, const int*, const T*,          \
                                        const int*, const T*, const T*, T*, bool, int,       \
                                        cudaStream_t);                                       \
+  template int launch_ell_gs_colour<T>(int, int, int, const int*, const T*, const int*,      \
+                                       const int*, const int*, const T*, const int*,      \
+                                       const T*, const T*, T*, bool, cudaStream_t);       \
+  template int launch_ell_residual_restrict<T>(int, int, const int*, const int*, const int*, \
+                                               const T*, const int*, const T*, const int*,  \
+                                               const int*, const T*, const T*, const T*, T*, \
+                                               cudaStream_t);                               \
   template int launch_csr_residual_restrict<T>(int, const int*, const int*, const int*,     \
                                                const int*, const T*, const T*, const T*,    \
                                                T*, int, cudaStream_t);                      \
