@@ -224,14 +224,16 @@ __global__ void __launch_bounds__(kThreads) bgs_colour_kernel(
     const int* __restrict__ dpos, const T* __restrict__ aN, const T* __restrict__ dNinv,
     const T* __restrict__ g, T* __restrict__ w, bool lower_only, bool zero_pressure) {
   constexpr int BN = B - 1;
-  constexpr int GP = Gp<BN>::v;
-  const int lane = threadIdx.x % GP;
-  const int gpb = blockDim.x / GP;
-  const int grp = threadIdx.x / GP;
-  for (int base = r0 + blockIdx.x * gpb; base < r1; base += gridDim.x * gpb) {
-    const int i = base + grp;
+  // BN lanes per row, packed 32 / BN rows to a warp (b = 4: 10 rows, 30 lanes busy)
+  constexpr int R = kWarp / BN;
+  const int wl = threadIdx.x % kWarp;
+  const int slot = wl / BN, lane = wl % BN;
+  const int rpb = (blockDim.x / kWarp) * R;
+  const int first = (threadIdx.x / kWarp) * R + slot;
+  for (int base = r0 + blockIdx.x * rpb; base < r1; base += gridDim.x * rpb) {
+    const int i = base + first;
     T acc = T(0);
-    const bool active = (i < r1) && (lane < BN);
+    const bool active = (slot < R) && (i < r1);
     if (active) {
       acc = g[(size_t)i * B + 1 + lane];
       const int p0 = __ldg(rp + i), pd = __ldg(dpos + i), p1 = __ldg(rp + i + 1);
@@ -267,12 +269,13 @@ __global__ void __launch_bounds__(kThreads) bgs_colour_kernel(
         for (int c = 0; c < BN; ++c) acc = fma(-a0[c], x0[c], acc);
       }
     }
-    // x_i = D_N,i^{-1} acc : gather the BN partial results of the group
+    // x_i = D_N,i^{-1} acc : gather the BN partial results of the row's lanes
     T out = T(0);
-    const T* di = dNinv + ((size_t)(active ? i : 0) * BN + (lane < BN ? lane : 0)) * BN;
+    const T* di = dNinv + ((size_t)(active ? i : 0) * BN + lane) * BN;
+    const int src = slot * BN;
 #pragma unroll
     for (int c = 0; c < BN; ++c) {
-      T ac = __shfl_sync(0xffffffffu, acc, c, GP);
+      const T ac = __shfl_sync(0xffffffffu, acc, (src + c) & (kWarp - 1));
       if (active) out = fma(__ldg(di + c), ac, out);
     }
     if (active) {
@@ -599,13 +602,42 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;  // valid in thread 0
 }
 
+// 8 accumulators per lane summed over the warp by a transposing butterfly: at each level a
+// lane keeps half of its values and receives the other half from its partner, 9 shuffles
+// and 9 FP64 adds per lane in all (8 separate trees would take 40 adds, a sixth of the
+// kernel's FP64 work at this size).  Lane l with l % 4 == 0 returns accumulator
+// 4*bit4(l) + 2*bit3(l) + bit2(l).
+__device__ __forceinline__ double transpose_sum8(double (&a)[8], int lane) {
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double send = h16 ? a[q] : a[q + 4];
+    const double keep = h16 ? a[q + 4] : a[q];
+    a[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const double send = h8 ? a[q] : a[q + 2];
+    const double keep = h8 ? a[q + 2] : a[q];
+    a[q] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  const double send = h4 ? a[0] : a[1];
+  const double keep = h4 ? a[1] : a[0];
+  double r = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  r += __shfl_xor_sync(0xffffffffu, r, 2);
+  r += __shfl_xor_sync(0xffffffffu, r, 1);
+  return r;
+}
+
 __global__ void __launch_bounds__(kThreads) multi_dot_kernel(size_t n, const double* __restrict__ V,
                                                             size_t ldv, int K,
                                                             const double* __restrict__ w,
                                                             double* __restrict__ partial,
                                                             const int* __restrict__ gate) {
-  __shared__ double sh[kThreads / kWarp];
+  static_assert(kDotChunk == 8 && kThreads == 256, "the reduction below is for 8 x 8 warps");
+  __shared__ double sh[kThreads / kWarp][kDotChunk];
   if (gate && *gate == 0) return;
+  const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp;
   for (int k0 = 0; k0 < K; k0 += kDotChunk) {
     const int kc = min(kDotChunk, K - k0);
     double acc[kDotChunk];
@@ -618,11 +650,15 @@ __global__ void __launch_bounds__(kThreads) multi_dot_kernel(size_t n, const dou
       for (int k = 0; k < kDotChunk; ++k)
         if (k < kc) acc[k] = fma(__ldg(V + (size_t)(k0 + k) * ldv + i), wi, acc[k]);
     }
+    const double r = transpose_sum8(acc, lane);
+    __syncthreads();  // the previous chunk's reads of sh are done
+    if ((lane & 3) == 0) sh[wid][((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)] = r;
+    __syncthreads();
+    if (threadIdx.x < kc) {  // fixed order over the warps
+      double t = 0.0;
 #pragma unroll
-    for (int k = 0; k < kDotChunk; ++k) {
-      if (k >= kc) break;
-      double t = block_sum(acc[k], sh);
-      if (threadIdx.x == 0) partial[(size_t)blockIdx.x * kMaxK + k0 + k] = t;
+      for (int w2 = 0; w2 < kThreads / kWarp; ++w2) t += sh[w2][threadIdx.x];
+      partial[(size_t)blockIdx.x * kMaxK + k0 + threadIdx.x] = t;
     }
   }
 }
@@ -818,7 +854,7 @@ int launch_bgs_colour(int b, int r0, int r1, const int* rp, const int* ci, const
   switch (b) {
 #define MSP_BGS_CASE(BB)                                                                   \
   case BB: {                                                                               \
-    const unsigned grid = grid_groups(r1 - r0, Gp<BB - 1>::v);                             \
+    const unsigned grid = grid_for((size_t)(r1 - r0) * kWarp / (kWarp / (BB - 1)), kThreads); \
     bgs_colour_kernel<BB, T><<<grid, kThreads, 0, s>>>(r0, r1, rp, ci, dpos, aN, dNinv, g, \
                                                        w, lower_only, zero_pressure);      \
   } break;
