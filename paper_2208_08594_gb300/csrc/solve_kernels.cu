@@ -550,26 +550,43 @@ __global__ void prolong_add_kernel(int n, const int* __restrict__ agg, const T* 
     x[i] += xc[agg[i]];
 }
 
-// x = Ainv b, one warp per row, four independent accumulators per lane
+// x = Ainv b: four warps per row (interleaved 32-column slices, four accumulators per
+// lane), the warps' sums added in a fixed order through shared memory
+constexpr int kGemvWarpsPerRow = 4;
 template <typename T>
 __global__ void __launch_bounds__(kThreads) dense_gemv_kernel(int n, const double* __restrict__ A,
                                                              const T* __restrict__ b,
                                                              T* __restrict__ x) {
-  const int lane = threadIdx.x % kWarp;
-  const int wpb = blockDim.x / kWarp;
-  for (int r = blockIdx.x * wpb + threadIdx.x / kWarp; r < n; r += gridDim.x * wpb) {
-    const double* row = A + (size_t)r * n;
+  constexpr int kW = kGemvWarpsPerRow, kStep = kW * kWarp;
+  constexpr int kRows = kThreads / kWarp / kW;  // rows per block
+  __shared__ double part[kThreads / kWarp];
+  const int lane = threadIdx.x % kWarp, wib = threadIdx.x / kWarp;
+  const int sub = wib % kW;
+  // the loop bound depends on the block only: every thread reaches both barriers
+  for (int r0 = blockIdx.x * kRows; r0 < n; r0 += gridDim.x * kRows) {
+    const int r = r0 + wib / kW;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int c = lane;
-    for (; c + 3 * kWarp < n; c += 4 * kWarp) {
-      s0 = fma(__ldg(row + c), (double)__ldg(b + c), s0);
-      s1 = fma(__ldg(row + c + kWarp), (double)__ldg(b + c + kWarp), s1);
-      s2 = fma(__ldg(row + c + 2 * kWarp), (double)__ldg(b + c + 2 * kWarp), s2);
-      s3 = fma(__ldg(row + c + 3 * kWarp), (double)__ldg(b + c + 3 * kWarp), s3);
+    if (r < n) {
+      const double* row = A + (size_t)r * n;
+      int c = sub * kWarp + lane;
+      for (; c + 3 * kStep < n; c += 4 * kStep) {
+        s0 = fma(__ldg(row + c), (double)__ldg(b + c), s0);
+        s1 = fma(__ldg(row + c + kStep), (double)__ldg(b + c + kStep), s1);
+        s2 = fma(__ldg(row + c + 2 * kStep), (double)__ldg(b + c + 2 * kStep), s2);
+        s3 = fma(__ldg(row + c + 3 * kStep), (double)__ldg(b + c + 3 * kStep), s3);
+      }
+      for (; c < n; c += kStep) s0 = fma(__ldg(row + c), (double)__ldg(b + c), s0);
     }
-    for (; c < n; c += kWarp) s0 = fma(__ldg(row + c), (double)__ldg(b + c), s0);
-    double s = group_sum<kWarp>((s0 + s1) + (s2 + s3));
-    if (lane == 0) x[r] = (T)s;
+    const double s = group_sum<kWarp>((s0 + s1) + (s2 + s3));
+    __syncthreads();  // the previous rows' reads of part are done
+    if (lane == 0) part[wib] = s;
+    __syncthreads();
+    if (threadIdx.x < kRows && r0 + (int)threadIdx.x < n) {
+      double t = 0.0;
+#pragma unroll
+      for (int q = 0; q < kW; ++q) t += part[threadIdx.x * kW + q];
+      x[r0 + threadIdx.x] = (T)t;
+    }
   }
 }
 
@@ -999,7 +1016,8 @@ int launch_prolong_add(int n, const int* agg, const T* xc, T* x, cudaStream_t s)
 template <typename T>
 int launch_dense_gemv(int n, const double* Ainv, const T* b, T* x, cudaStream_t s) {
   if (n <= 0) return MSP_OK;
-  dense_gemv_kernel<T><<<grid_groups(n, kWarp), kThreads, 0, s>>>(n, Ainv, b, x);
+  dense_gemv_kernel<T><<<grid_groups(n, kGemvWarpsPerRow * kWarp), kThreads, 0, s>>>(n, Ainv, b,
+                                                                                    x);
   return launch_status();
 }
 

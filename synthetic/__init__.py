@@ -4,7 +4,7 @@ This package only draws random numbers and lays them out as block-sparse (BSR)
 arrays; it contains none of the solver's arithmetic.
 """
 from .jacobian import (BSRMatrix, box_jacobian, grid_small, grid_spe10, perturb_values,
-                       random_rhs, poisson3d_bsr, chain_bsr, diagonal_bsr)
+                       newton_sequence, random_rhs, poisson3d_bsr, chain_bsr, diagonal_bsr)
 
 __all__ = ["BSRMatrix", "box_jacobian", "grid_small", "grid_spe10", "perturb_values",
-           "random_rhs", "poisson3d_bsr", "chain_bsr", "diagonal_bsr"]
+           "newton_sequence", "random_rhs", "poisson3d_bsr", "chain_bsr", "diagonal_bsr"]

@@ -34,6 +34,7 @@ within each block row and the diagonal block is always stored.
 """
 from __future__ import annotations
 
+import dataclasses
 from dataclasses import dataclass
 
 import numpy as np
@@ -208,6 +209,25 @@ def perturb_values(a: BSRMatrix, seed: int, rel: float = 0.05) -> np.ndarray:
     dpos = np.nonzero(~off)[0]
     v[dpos] = a.values[dpos] - delta[rows[dpos]]
     return v
+
+
+def newton_sequence(a: BSRMatrix, time_steps: int, newton_steps: int, seed: int,
+                    rel_newton: float = 0.02, rel_step: float = 0.2) -> list:
+    """Values of the Jacobians a time-stepping Newton solver would see, same pattern:
+    ``time_steps`` x ``newton_steps`` arrays, each derived from the previous one by
+    ``perturb_values`` (so the drift accumulates): U[1 - rel_step, 1 + rel_step] factors
+    on the first Newton step of a time step (the state moved a whole step), and
+    U[1 - rel_newton, 1 + rel_newton] between Newton steps.  The first array is the
+    first time step's first Jacobian, ``a``'s values perturbed once by ``rel_step``."""
+    out = []
+    cur = a
+    for t in range(time_steps):
+        for k in range(newton_steps):
+            rel = rel_step if k == 0 else rel_newton
+            v = perturb_values(cur, seed + 1000 * t + k, rel)
+            out.append(v)
+            cur = dataclasses.replace(cur, values=v)
+    return out
 
 
 def poisson3d_bsr(nx: int, ny: int, nz: int) -> BSRMatrix:

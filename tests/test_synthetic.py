@@ -2,7 +2,8 @@
 present, symmetric pattern, wells after the cells) and the SPE10-shaped counts."""
 import numpy as np
 
-from synthetic import box_jacobian, grid_small, grid_spe10, perturb_values, random_rhs
+from synthetic import (box_jacobian, grid_small, grid_spe10, newton_sequence, perturb_values,
+                       random_rhs)
 
 
 def _pattern_ok(a):
@@ -51,3 +52,29 @@ def test_perturbation_and_rhs():
     assert np.allclose(s0, s1, rtol=1e-12, atol=1e-9)
     rhs = random_rhs(a, 2).reshape(a.nb, a.b)
     assert np.all(rhs[a.n_cells:, 1:] == 0.0)
+
+
+def test_newton_sequence_drift():
+    a = box_jacobian(5, 4, 3, 4, 3, n_wells=2)
+    seq = newton_sequence(a, 3, 2, seed=9, rel_newton=0.02, rel_step=0.2)
+    assert len(seq) == 6
+    again = newton_sequence(a, 3, 2, seed=9, rel_newton=0.02, rel_step=0.2)
+    assert all(np.array_equal(x, y) for x, y in zip(seq, again))
+    rows = np.repeat(np.arange(a.nb), np.diff(a.row_ptr))
+    off = rows != a.col_idx
+    prev = a.values
+    for k, v in enumerate(seq):
+        rel = 0.2 if k % 2 == 0 else 0.02
+        ok = prev[off] != 0
+        r = v[off][ok] / prev[off][ok]
+        assert np.all((r >= 1 - rel) & (r <= 1 + rel))  # each step perturbs the previous one
+        s0 = np.zeros((a.nb, a.b, a.b))
+        s1 = np.zeros((a.nb, a.b, a.b))
+        np.add.at(s0, rows, a.values)
+        np.add.at(s1, rows, v)
+        assert np.allclose(s0, s1, rtol=1e-12, atol=1e-9)  # accumulation terms kept
+        prev = v
+    # the drift accumulates: the last Jacobian is further from the first than the second is
+    d1 = np.abs(seq[1][off] - seq[0][off]).sum()
+    d5 = np.abs(seq[5][off] - seq[0][off]).sum()
+    assert d5 > d1
