@@ -431,8 +431,27 @@ int colour_graph(msp_handle h, int n, const int* rp, const int* ci, int nnz, Dev
   MSP_TRY(colour_r.alloc(n));
   MSP_TRY(colour.alloc(n));
   MSP_CUDA_TRY(cudaMemsetAsync(meta.p, 0, 2 * sizeof(int), s));
-  MSP_TRY(launch_colouring(n, rrp.p, rci.p, inV.p, wbar.p, bitmap.p, words, colour_r.p, meta.p,
-                           s));
+  // two-hop lists of the relabelled graph (the second circle of every vertex as one run),
+  // unless they would pass int offsets or 2 GB: then the colouring gathers the rows itself
+  DevBuf<int> tcnt, tp, tl;
+  DevBuf<unsigned long long> ttotal;
+  MSP_TRY(tcnt.alloc(n));
+  MSP_TRY(ttotal.alloc(1));
+  MSP_TRY(launch_twohop_count(n, rrp.p, rci.p, tcnt.p, ttotal.p, s));
+  unsigned long long htotal = 0;
+  MSP_CUDA_TRY(cudaMemcpyAsync(&htotal, ttotal.p, sizeof(htotal), cudaMemcpyDeviceToHost, s));
+  MSP_CUDA_TRY(cudaStreamSynchronize(s));
+  const bool twohop = htotal < (1ull << 31) - 1 && htotal * sizeof(int) <= (2ull << 30);
+  if (twohop) {
+    MSP_TRY(tp.alloc((size_t)n + 1));
+    MSP_TRY(tl.alloc(std::max<size_t>(1, (size_t)htotal)));
+    MSP_TRY(exclusive_scan_int(h->ss, n, tcnt.p, tp.p, s));
+    const int last = (int)htotal;
+    MSP_CUDA_TRY(cudaMemcpyAsync(tp.p + n, &last, sizeof(int), cudaMemcpyHostToDevice, s));
+    MSP_TRY(launch_twohop_fill(n, rrp.p, rci.p, tp.p, tl.p, s));
+  }
+  MSP_TRY(launch_colouring(n, rrp.p, rci.p, twohop ? tp.p : nullptr, twohop ? tl.p : nullptr,
+                           inV.p, wbar.p, bitmap.p, words, colour_r.p, meta.p, s));
   map_kernel<<<grid1(n), kThreads, 0, s>>>(n, colour_r.p, rank.p, colour.p);  // colour[v] = colour_r[rank[v]]
   MSP_TRY(launch_status());
   int hm[2] = {0, 0};

@@ -276,7 +276,8 @@ int msp_vertices_grouping_noalloc(int32_t n, const int32_t* d_row_ptr, const int
   MSP_TRY(launch_status());
   na_relabel_fill_kernel<<<grid, 256, 0, s>>>(n, d_row_ptr, d_col_idx, rank, vor, rp2, ci2);
   MSP_TRY(launch_status());
-  MSP_TRY(launch_colouring(n, rp2, ci2, inV, wbar, bits, kNaBitWords, colour_r, meta + 2, s));
+  MSP_TRY(launch_colouring(n, rp2, ci2, nullptr, nullptr, inV, wbar, bits, kNaBitWords,
+                           colour_r, meta + 2, s));
   na_map_kernel<<<grid, 256, 0, s>>>(n, colour_r, rank, d_colour);
   MSP_TRY(launch_status());
   MSP_CUDA_TRY(cudaMemcpyAsync(h_meta + 2, meta + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));

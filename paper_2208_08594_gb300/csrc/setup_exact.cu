@@ -310,7 +310,9 @@ __global__ void segment_sums_kernel(int nseg, const int* __restrict__ seg_start,
 // are dropped when popped: that is the else branch of Algorithm 4.1, which only moves
 // such a vertex to Wbar where it already is.  With an empty frontier the pick is the
 // smallest label still in V (a cursor that only moves forward).  Both bitmaps live in
-// shared memory when they fit; the second circle is gathered with every lane issuing
+// shared memory when they fit.  The second circle is read from the graph's two-hop lists
+// when they are given (one contiguous run per vertex, loaded together with the
+// neighbours); otherwise it is gathered from the neighbours' rows with every lane issuing
 // its loads back to back (owner rows looked up in shared memory).
 // ----------------------------------------------------------------------------------
 struct Bitmap3 {
@@ -368,6 +370,7 @@ constexpr int kSecondU = 8;  // second-circle entries gathered per lane per roun
 // what it finds is a hint, checked for range, and a wrong guess costs nothing but the
 // loads.  Its wait for a new pick is bounded and it stops when warp 0 is done.
 __device__ void colouring_prefetcher(int n, const int* __restrict__ srp, const int* __restrict__ sci,
+                                     const int* __restrict__ tp, const int* __restrict__ tl,
                                      const Bitmap3& bm, volatile int* hint, volatile int* done,
                                      volatile int* sink) {
   const int lane = threadIdx.x % 32;
@@ -403,6 +406,11 @@ __device__ void colouring_prefetcher(int n, const int* __restrict__ srp, const i
     }
     c = __shfl_sync(0xffffffffu, c, 0);
     if (c < 0 || c >= n) continue;
+    if (tp) {
+      const int e1 = __ldg(tp + c + 1);
+      for (int e = __ldg(tp + c) + 8 * lane; e < e1; e += 256) acc += __ldg(tl + e);
+      continue;
+    }
     const int q0 = __ldg(srp + c), q1 = __ldg(srp + c + 1);
     for (int q = q0 + lane; q < q1; q += 32) {
       const int k = __ldg(sci + q);
@@ -416,6 +424,8 @@ __device__ void colouring_prefetcher(int n, const int* __restrict__ srp, const i
 // layout flags: bit 0 = frontier bitmap in shared memory, bit 1 = inV in shared memory
 __global__ void __launch_bounds__(64) colouring_kernel(int n, const int* __restrict__ srp,
                                                        const int* __restrict__ sci,
+                                                       const int* __restrict__ tp,
+                                                       const int* __restrict__ tl,
                                                        unsigned* ginV, int* wbar,
                                                        unsigned* gbitmap, int layout,
                                                        int* colour, int* meta) {
@@ -446,7 +456,7 @@ __global__ void __launch_bounds__(64) colouring_kernel(int n, const int* __restr
   }
   __syncthreads();
   if (threadIdx.x >= 32) {
-    colouring_prefetcher(n, srp, sci, bm, &s_hint, &s_done, &s_sink);
+    colouring_prefetcher(n, srp, sci, tp, tl, bm, &s_hint, &s_done, &s_sink);
     return;
   }
   int coloured = 0, g = 0;
@@ -507,6 +517,19 @@ __global__ void __launch_bounds__(64) colouring_kernel(int n, const int* __restr
       }
       ++coloured;
       const int q0 = __ldg(srp + v), q1 = __ldg(srp + v + 1);
+      // with two-hop lists the whole second circle is one contiguous run: its first round
+      // is loaded here, alongside the neighbours, before they leave V
+      int t0 = 0, t1 = 0;
+      int xs0[kSecondU];
+      if (tp) {
+        t0 = __ldg(tp + v);
+        t1 = __ldg(tp + v + 1);
+#pragma unroll
+        for (int u = 0; u < kSecondU; ++u) {
+          const int t = t0 + lane + 32 * u;
+          xs0[u] = t < t1 ? __ldg(tl + t) : -1;
+        }
+      }
       // Wbar = Wbar u (S_v n V), V = V / S_v  (all chunks first)
       int kb0 = 0, kl0 = 0;  // row of this lane's neighbour in the first chunk
       for (int q = q0; q < q1; q += 32) {
@@ -515,7 +538,7 @@ __global__ void __launch_bounds__(64) colouring_kernel(int n, const int* __restr
         int j = -1;
         if (qq < q1) {
           j = __ldg(sci + qq);
-          if (q == q0) {
+          if (q == q0 && !tp) {
             kb0 = __ldg(srp + j);
             kl0 = __ldg(srp + j + 1) - kb0;
           }
@@ -528,6 +551,24 @@ __global__ void __launch_bounds__(64) colouring_kernel(int n, const int* __restr
       }
       __syncwarp();
       // hat W = hat W u hat S_v: undetermined vertices of the second circle
+      if (tp) {
+#pragma unroll
+        for (int u = 0; u < kSecondU; ++u)
+          if (xs0[u] >= 0 && in_v(inV, xs0[u])) bm_set(bm, xs0[u]);
+        for (int t = t0 + 32 * kSecondU; t < t1; t += 32 * kSecondU) {
+          int xs[kSecondU];
+#pragma unroll
+          for (int u = 0; u < kSecondU; ++u) {
+            const int tt = t + lane + 32 * u;
+            xs[u] = tt < t1 ? __ldg(tl + tt) : -1;
+          }
+#pragma unroll
+          for (int u = 0; u < kSecondU; ++u)
+            if (xs[u] >= 0 && in_v(inV, xs[u])) bm_set(bm, xs[u]);
+        }
+        __syncwarp();
+        continue;
+      }
       for (int q = q0; q < q1; q += 32) {
         const int qq = q + lane;
         int kb = kb0, kl = kl0;
@@ -702,9 +743,9 @@ int launch_segment_sums(int nseg, const int* seg_start, const int* src, const do
   return launch_status();
 }
 
-int launch_colouring(int n, const int* srp, const int* sci, unsigned* inV, int* wbar,
-                     unsigned* bitmap, size_t bitmap_words, int* colour, int* meta,
-                     cudaStream_t s) {
+int launch_colouring(int n, const int* srp, const int* sci, const int* tp, const int* tl,
+                     unsigned* inV, int* wbar, unsigned* bitmap, size_t bitmap_words,
+                     int* colour, int* meta, cudaStream_t s) {
   if (n <= 0) return MSP_OK;
   const int n0 = (n + 31) / 32, n1 = (n0 + 31) / 32, n2 = (n1 + 31) / 32;
   const size_t fwords = (size_t)n0 + n1 + n2;
@@ -731,7 +772,8 @@ int launch_colouring(int n, const int* srp, const int* sci, unsigned* inV, int* 
       smem = 0;
     }
   }
-  colouring_kernel<<<1, 64, smem, s>>>(n, srp, sci, inV, wbar, bitmap, layout, colour, meta);
+  colouring_kernel<<<1, 64, smem, s>>>(n, srp, sci, tp, tl, inV, wbar, bitmap, layout, colour,
+                                       meta);
   return launch_status();
 }
 

@@ -85,6 +85,44 @@ __global__ void diag_pos_kernel(int n, const int* __restrict__ rp, const int* __
   }
 }
 
+// Two-hop lists of a graph for VerticesGrouping: for every vertex v the rows of its
+// neighbours, concatenated in the order of v's row (the second circle of Algorithm 4.1,
+// with repeats and with v's own neighbours, which the colouring filters out).
+__global__ void twohop_count_kernel(int n, const int* __restrict__ srp,
+                                    const int* __restrict__ sci, int* __restrict__ cnt,
+                                    unsigned long long* __restrict__ total) {
+  __shared__ unsigned long long part[kThreads / 32];
+  unsigned long long mine = 0;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    int c = 0;
+    for (int q = srp[v]; q < srp[v + 1]; ++q) {
+      const int k = sci[q];
+      c += srp[k + 1] - srp[k];
+    }
+    cnt[v] = c;
+    mine += (unsigned long long)c;
+  }
+  for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+  if (threadIdx.x % 32 == 0) part[threadIdx.x / 32] = mine;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += part[w];
+    atomicAdd(total, t);
+  }
+}
+
+__global__ void twohop_fill_kernel(int n, const int* __restrict__ srp, const int* __restrict__ sci,
+                                   const int* __restrict__ tp, int* __restrict__ tl) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    int pos = tp[v];
+    for (int q = srp[v]; q < srp[v + 1]; ++q) {
+      const int k = sci[q];
+      for (int e = srp[k]; e < srp[k + 1]; ++e) tl[pos++] = sci[e];
+    }
+  }
+}
+
 // ELL copy of the off-diagonal entries of a CSR level matrix for the colour sweeps and the
 // restriction: slot k of row i at i*K + k, in the row's CSR order; unused slots hold (i, 0);
 // diag[i] = a_ii.  meta[i] = number of off-diagonal entries | (entries left of the
@@ -371,6 +409,21 @@ int launch_extract_N(int b, size_t nnzb, const double* v, double* aN, cudaStream
 int launch_diag_pos(int n, const int* rp, const int* ci, int* dpos, cudaStream_t s) {
   if (n <= 0) return MSP_OK;
   diag_pos_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, rp, ci, dpos);
+  return launch_status();
+}
+
+int launch_twohop_count(int n, const int* srp, const int* sci, int* cnt, unsigned long long* total,
+                        cudaStream_t s) {
+  if (n <= 0) return MSP_OK;
+  MSP_CUDA_TRY(cudaMemsetAsync(total, 0, sizeof(unsigned long long), s));
+  twohop_count_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, srp, sci, cnt, total);
+  return launch_status();
+}
+
+int launch_twohop_fill(int n, const int* srp, const int* sci, const int* tp, int* tl,
+                       cudaStream_t s) {
+  if (n <= 0) return MSP_OK;
+  twohop_fill_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, srp, sci, tp, tl);
   return launch_status();
 }
 

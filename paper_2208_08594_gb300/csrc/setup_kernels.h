@@ -48,10 +48,10 @@ int launch_segment_sums(int nseg, const int* seg_start, const int* src, const do
 // whose labels are the priority ranks (degree desc, original index asc).  scratch: inV
 // bitmap of ceil(n/32) words, n ints Wbar list, frontier bitmap words.  On return
 // colour[r] in 1..g (by label), meta[0] = g, meta[1] = error flag (a bounded loop ran
-// out).
-int launch_colouring(int n, const int* srp, const int* sci, unsigned* inV, int* wbar,
-                     unsigned* bitmap, size_t bitmap_words, int* colour, int* meta,
-                     cudaStream_t s);
+// out).  tp/tl: the graph's two-hop lists (launch_twohop_*), or both nullptr.
+int launch_colouring(int n, const int* srp, const int* sci, const int* tp, const int* tl,
+                     unsigned* inV, int* wbar, unsigned* bitmap, size_t bitmap_words,
+                     int* colour, int* meta, cudaStream_t s);
 
 // ---- other setup kernels (setup_kernels.cu) ----
 // errors in the BSR pattern: unsorted / out of range columns, missing diagonal
@@ -62,6 +62,12 @@ int launch_gather_values(size_t nnz, int bb, const int* src, const double* in, d
                          cudaStream_t s);
 int launch_extract_N(int b, size_t nnzb, const double* v, double* aN, cudaStream_t s);
 int launch_diag_pos(int n, const int* rp, const int* ci, int* dpos, cudaStream_t s);
+// two-hop lists of a graph (srp/sci): cnt[v] = sum over the neighbours k of v of deg(k),
+// *total = their sum; then tl[tp[v] ...] = the neighbours' rows concatenated in row order
+int launch_twohop_count(int n, const int* srp, const int* sci, int* cnt, unsigned long long* total,
+                        cudaStream_t s);
+int launch_twohop_fill(int n, const int* srp, const int* sci, const int* tp, int* tl,
+                       cudaStream_t s);
 // ELL copy (K slots per row, slot k of row i at i*K + k) of the off-diagonal entries of a
 // CSR level matrix; meta[i] = count | (entries left of the diagonal) << 16, or -1 for rows
 // longer than K (their slots hold (i, 0)); diag[i] = a_ii
