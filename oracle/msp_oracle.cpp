@@ -6,7 +6,7 @@
 // baseline of the benchmark may load it.  It shares no code with the CUDA library.
 //
 // Every step follows the paper in order and notation; where the paper is silent the
-// reading taken is stated at the step (readings D1..D16).  Compile with
+// reading taken is stated at the step.  Compile with
 // -ffp-contract=off: setup arithmetic that feeds integer decisions (the decoupling
 // weights, the pressure matrix, the Galerkin sums, the strength of connection) must be
 // rounded exactly as written so the CUDA path can reproduce its integer outputs.
@@ -17,7 +17,8 @@
 // and its red-black closed form, Krylov finite termination, exact-preconditioner
 // one-step convergence (Section 3.2), the adaptive-setup decision trace, and the full
 // solve against a dense LU solution.  Against Napov-Notay's own NPAIR the aggregation is
-// "parity unpinned": the paper only cites it, the oracle follows reading D5.
+// "parity unpinned": the paper only cites it; the oracle's reading of it is stated at
+// pairwise_matching.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -51,16 +52,16 @@ typedef struct {
   int restart;       // m of FGMRES(m)
   int max_it;        // MaxIt
   int coarse_max;    // coarsest AMG size (Section 5: 10000)
-  int npass;         // pairwise matching passes per level (reading D5: 2)
-  int pre_sweeps;    // PGS-MC sweeps before coarse correction (reading D6: 1)
-  int post_sweeps;   // PGS-MC sweeps after coarse correction (reading D6: 1)
-  int bgs_sweeps;    // block GS sweeps of stage N (reading D8: 1)
-  int decoupling;    // 1 = quasi-IMPES (reading D2), 0 = literal Pi_P^T A Pi_P
+  int npass;         // pairwise matching passes per level (2: aggregates of up to 4)
+  int pre_sweeps;    // PGS-MC sweeps before coarse correction (1, forward)
+  int post_sweeps;   // PGS-MC sweeps after coarse correction (1, backward)
+  int bgs_sweeps;    // block GS sweeps of stage N (1, forward from zero)
+  int decoupling;    // 1 = quasi-IMPES weights (Pi_P^T unspecified), 0 = literal Pi_P^T A Pi_P
   int bilu_order;    // 0 = level-0 colour order, 1 = natural order
   int precond;       // PREC_*; 0 = MSP (Alg 3.1)
   int max_levels;    // AMG level cap
-  double beta;       // strong-coupling threshold (reading D5: 0.25)
-  unsigned long long agg_seed;  // visit-order hash seed (reading D5)
+  double beta;       // strong-coupling threshold (0.25)
+  unsigned long long agg_seed;  // visit-order hash seed of the pairwise matching
   int coarse_hard_max;          // refuse a coarsest level above this size
 } orc_config;
 
@@ -133,9 +134,9 @@ Csr adjacency(int n, const int* rp, const int* ci) {
 // Algorithm 4.1 (VerticesSplitting).  Inputs: the current vertex set V (in_V flags) and
 // S; outputs W (an independent set, in selection order) and Wbar.  |S_i| (Table 1) is
 // the degree in the full graph S.
-//   D1: "any take" a max-|S_i| vertex -> the smallest index among the maxima.
-//   D3: Wbar gets S_i restricted to V (vertices coloured earlier are not re-added).
-//   D4: the second circle of v_i is the union over k in S_i of S_k, minus S_i u {i};
+//   "any take" a max-|S_i| vertex -> the smallest index among the maxima.
+//   Wbar gets S_i restricted to V (vertices coloured earlier are not re-added).
+//   The second circle of v_i is the union over k in S_i of S_k, minus S_i u {i};
 //       hat S_i keeps its vertices whose colour is undetermined, i.e. that are in V.
 // hat W may hold vertices that have since left V; picking one takes the else branch of
 // the algorithm (it is adjacent to W), exactly as written.
@@ -339,8 +340,8 @@ void blk_gemv(int b, const double* X, const double* v, double* y) {
 }
 
 // ---------------------------------------------------------------------------------
-// Unsmoothed aggregation by nonsymmetric pairwise matching (Section 5 cites NPAIR;
-// reading D5 fixes the details):
+// Unsmoothed aggregation by nonsymmetric pairwise matching (Section 5 only cites NPAIR;
+// the details read here):
 //   strength s_ij = -(a_ij + a_ji)/2 over the symmetrised off-diagonal pattern;
 //   j is a candidate of i iff s_ij >= beta * max_k s_ik and that maximum is > 0;
 //   nodes are visited by ascending (splitmix64(i ^ seed), i); an unmatched node pairs
@@ -458,7 +459,9 @@ Csr galerkin(const Csr& a, const std::vector<int>& agg, int nc) {
 // GS update to every vertex of V_l.  The matrix is in colour order (colour class l is
 // the index range cptr[l-1]..cptr[l]-1).  Written as the sequential sweep in colour
 // order, which is what the parallel sweep computes (the vertices of one colour are
-// mutually independent).  Forward = colours 1..g; backward = g..1 (reading D6).
+// mutually independent).  Forward = colours 1..g; backward = g..1 (the paper gives
+// neither the number nor the direction of the sweeps: one forward pre-sweep and one
+// backward post-sweep are taken).
 // ---------------------------------------------------------------------------------
 void gs_sweep(const Csr& a, const std::vector<int>& cptr, const double* b, double* x,
               bool forward) {
@@ -545,7 +548,7 @@ struct Handle {
   int g0 = 0;
   Bsr Ap;                        // P A P^T in level-0 colour order (current values)
   std::vector<int> ap_src;       // Ap nonzero -> A0 nonzero
-  // setup products (frozen between setups, reading D10)
+  // setup products (frozen between setups: on reuse only the matrix values change)
   std::vector<double> omega;     // nb * b: first row of D_i^{-1} (quasi-IMPES weights)
   std::vector<double> dN_inv;    // nb * (b-1)^2: inverses of the N diagonal sub-blocks
   std::vector<double> aN;        // nnzb * (b-1)^2: N sub-blocks of Ap at setup
@@ -614,7 +617,8 @@ int value_setup(Handle& h) {
   auto t0 = Clock::now();
   const int nb = h.nb, b = h.b, bb = b * b, bn = b - 1;
   const Bsr& A = h.Ap;
-  // diagonal block inverses and quasi-IMPES weights omega_i = D_i^{-T} e_0 (reading D2)
+  // diagonal block inverses and quasi-IMPES weights omega_i = D_i^{-T} e_0 (the paper does
+  // not specify Pi_P^T; the volume-balance row has no spatial coupling)
   std::vector<double> dinv((size_t)nb * bb);
   h.omega.assign((size_t)nb * b, 0.0);
   for (int i = 0; i < nb; ++i) {
@@ -709,7 +713,8 @@ int value_setup(Handle& h) {
         return ORC_ERR_SINGULAR;
     }
   }
-  // stage R: block ILU(0) on P A P^T in the chosen row order (reading D8)
+  // stage R: block ILU(0) on P A P^T in the level-0 colour order (fill and order are
+  // not given in the paper)
   {
     h.bilu_perm.resize(nb);
     if (h.cfg.bilu_order == 0) {
@@ -784,7 +789,8 @@ void bsr_spmv(const Bsr& a, const double* x, double* y) {
   }
 }
 
-// V-cycle on level l: x = B_l b (x starts at zero), Section 5 settings, readings D6/D7.
+// V-cycle on level l: x = B_l b (x starts at zero), Section 5 settings; one forward pre-
+// and one backward post-sweep, coarse correction added unscaled (not given in the paper).
 void vcycle(const Handle& h, int l, const double* b, double* x) {
   const Level& L = h.levels[l];
   const int n = L.A.n;
@@ -870,7 +876,8 @@ void stage_R(const Handle& h, const double* r, double* w) {
 }
 
 // Algorithm 3.1 (MSP preconditioning), w = B g, w starting at zero; A is the current
-// matrix, the stage operators come from the last setup (reading D10).
+// matrix, the stage operators come from the last setup (Section 3.2 reuses the
+// preconditioner, not the matrix: the residual steps use the current A).
 void apply_precond(const Handle& h, const double* g, double* w) {
   const size_t n = (size_t)h.nb * h.b;
   std::fill(w, w + n, 0.0);

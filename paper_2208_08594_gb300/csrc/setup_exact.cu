@@ -301,14 +301,15 @@ __global__ void segment_sums_kernel(int nseg, const int* __restrict__ seg_start,
 
 // ----------------------------------------------------------------------------------
 // Sequential VerticesGrouping by one warp on the graph relabelled by priority rank
-// (degree desc, index asc), so that "the vertex Algorithm 4.1 picks" (D1) is simply
-// the smallest label.  inV is a bitmap of the vertices in V of the current pass
-// (test-and-clear with atomics, so the lanes can remove neighbours concurrently); a
-// vertex leaves V when it is coloured or moved to Wbar, and the Wbar list of a pass is
-// V of the next one.  The frontier hat W is a three-level bitmap, so its first set bit
-// is the next pick.  Stale frontier entries (vertices that left V as neighbours of W)
-// are dropped when popped: that is the else branch of Algorithm 4.1, which only moves
-// such a vertex to Wbar where it already is.  With an empty frontier the pick is the
+// (degree desc, index asc), so that the vertex Algorithm 4.1 picks (the largest degree,
+// the smallest index among equals) is simply the smallest label.  inV is a bitmap of the
+// vertices in V of the current pass (test-and-clear with atomics, so the lanes can remove
+// neighbours concurrently); a vertex leaves V when it is coloured or moved to Wbar, and
+// the Wbar list of a pass is V of the next one.  The frontier hat W is a three-level
+// bitmap, so its first set bit is the next pick.  A vertex that leaves V as a neighbour
+// of W leaves the frontier at the same time (the else branch of Algorithm 4.1 would only
+// move it to Wbar, where it already is); an entry found outside V when popped is still
+// dropped.  With an empty frontier the pick is the
 // smallest label still in V (a cursor that only moves forward).  Both bitmaps live in
 // shared memory when they fit.  The second circle is read from the graph's two-hop lists
 // when they are given (one contiguous run per vertex, loaded together with the
@@ -346,6 +347,19 @@ __device__ void bm_clear(const Bitmap3& bm, int r) {
     const unsigned w1 = bm.l1[i1] & ~(1u << (i0 & 31));
     bm.l1[i1] = w1;
     if (w1 == 0u) bm.l2[i2] &= ~(1u << (i1 & 31));
+  }
+}
+
+// clear bit r where several lanes may clear bits concurrently (and nobody sets): only the
+// lane that empties a word clears its bit one level up
+__device__ void bm_clear_atomic(const Bitmap3& bm, int r) {
+  const int i0 = r >> 5, i1 = r >> 10, i2 = r >> 15;
+  const unsigned b0 = 1u << (r & 31);
+  const unsigned o0 = atomicAnd(bm.l0 + i0, ~b0);
+  if (o0 == b0) {
+    const unsigned b1 = 1u << (i0 & 31);
+    const unsigned o1 = atomicAnd(bm.l1 + i1, ~b1);
+    if (o1 == b1) atomicAnd(bm.l2 + i2, ~(1u << (i1 & 31)));
   }
 }
 
@@ -544,6 +558,9 @@ __global__ void __launch_bounds__(64) colouring_kernel(int n, const int* __restr
           }
           const unsigned bit = 1u << (j & 31);
           take = (atomicAnd(inV + (j >> 5), ~bit) & bit) != 0u;
+          // a vertex leaving V also leaves the frontier now, rather than being popped and
+          // dropped later (same picks: the frontier's first vertex still in V)
+          if (take) bm_clear_atomic(bm, j);
         }
         const unsigned m = __ballot_sync(0xffffffffu, take);
         if (take) wbar[nwbar + __popc(m & ((1u << lane) - 1u))] = j;

@@ -1,5 +1,5 @@
-"""Pins for the oracle's pressure stage: pairwise aggregation (reading D5 of the NPAIR
-citation in Section 5), the Galerkin coarse operators, and UA-AMG convergence on the
+"""Pins for the oracle's pressure stage: pairwise aggregation (the oracle's reading of the
+NPAIR citation in Section 5), the Galerkin coarse operators, and UA-AMG convergence on the
 3-D Poisson problem; plus the pressure matrix of the decoupled restriction."""
 import numpy as np
 import pytest
@@ -114,8 +114,9 @@ def test_hierarchy_on_compositional_grid():
 
 
 def test_pressure_matrix_is_decoupled_restriction():
-    """A_P[i,j] = omega_i^T A_ij e_0 with omega_i^T = e_0^T D_i^-1 (reading D2 of the
-    Pi_P^T in Eq. MSP); without decoupling it is A_ij[0,0]."""
+    """A_P[i,j] = omega_i^T A_ij e_0 with omega_i^T = e_0^T D_i^-1 (quasi-IMPES weights, the
+    reading taken of the unspecified Pi_P^T in Eq. MSP); without decoupling it is
+    A_ij[0,0]."""
     a = box_jacobian(4, 3, 3, 3, 21, n_wells=1)
     for dec in (1, 0):
         o = oracle.Oracle(a, decoupling=dec)

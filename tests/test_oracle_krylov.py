@@ -128,7 +128,7 @@ def test_adaptive_setup_trace():
 
 
 def test_reuse_keeps_stage_operators_but_uses_current_matrix():
-    """Reading D10: without a new setup the residual steps of Algorithm 3.1 use the
+    """On reuse (Section 3.2) the residual steps of Algorithm 3.1 use the
     current A while B_N, B_P and R stay those of the last setup."""
     a = grid_spe10(nx=6, ny=5, nz=4)
     o = oracle.Oracle(a, mu=10 ** 6, coarse_max=20)
