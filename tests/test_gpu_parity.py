@@ -156,6 +156,30 @@ def test_poisson_multilevel():
     g.close()
 
 
+def test_long_rows_take_the_csr_path():
+    """A well perforating 45 cells gives the AMG levels rows with more than 32 off-diagonal
+    entries; the colour sweeps and the restriction read those rows from the CSR form, the
+    others from the ELL copy.  Application and solve still match the oracle."""
+    a = box_jacobian(5, 5, 45, 3, 31, n_wells=1)
+    g, o = _pair(a, coarse_max=60)
+    smoothed = g.num_levels - 1
+    assert smoothed >= 2
+    long_rows = [int((np.diff(g.level(l)["row_ptr"]) - 1 > 32).sum()) for l in range(smoothed)]
+    assert long_rows[0] >= 1 and sum(long_rows) >= 2, long_rows
+    for seed in (3, 4):
+        x = random_rhs(a, seed)
+        w = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+        g.apply_precond(_vec(x), w)
+        ref = o.apply_precond(x)
+        assert np.abs(w.cpu().numpy() - ref).max() / np.abs(ref).max() <= TOL_APPLY
+    rhs = random_rhs(a, 5)
+    xd = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+    info = g.solve(_vec(rhs), xd, 1e-6)
+    _, io = o.solve(rhs, 1e-6)
+    assert info["status"] == 0 and abs(info["iterations"] - io["iterations"]) <= 1
+    g.close()
+
+
 def test_zero_and_nonfinite_rhs():
     a = grid_spe10(nx=6, ny=5, nz=4)
     g, _ = _pair(a, coarse_max=20)
