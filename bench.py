@@ -73,6 +73,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    p.add_argument("--colouring", default="alg41", choices=["alg41", "jp"],
+                   help="Algorithms 4.1/4.2 (the paper's) or greedy in Jones-Plassmann "
+                        "priority order (parallel rounds)")
     p.add_argument("--mu", type=int, default=180)
     p.add_argument("--nx", type=int, default=60)
     p.add_argument("--ny", type=int, default=220)
@@ -91,9 +94,14 @@ def parse():
 
 
 def workload_name(args):
-    return "spe10-shaped %dx%dx%d + 4 wells, 4x4 BSR, %s" % (
+    return "spe10-shaped %dx%dx%d + 4 wells, 4x4 BSR, %s%s" % (
         args.nx, args.ny, args.nz, "FP64" if args.precision == "fp64" else
-        "FP32 preconditioner / FP64 Krylov")
+        "FP32 preconditioner / FP64 Krylov",
+        ", Jones-Plassmann-order colouring" if args.colouring == "jp" else "")
+
+
+def colouring_of(args, msp):
+    return msp.MSP_COLOURING_JP if args.colouring == "jp" else msp.MSP_COLOURING_ALG41
 
 
 def kernels_from_sites(sites):
@@ -258,7 +266,8 @@ def run_native(args):
 
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    solver = msp.Solver(a.nb, a.b, d_rp, d_ci, d_v0, mu=args.mu, precision=prec)
+    solver = msp.Solver(a.nb, a.b, d_rp, d_ci, d_v0, mu=args.mu, precision=prec,
+                        colouring=colouring_of(args, msp))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     nsets = len(d_sets)
@@ -527,7 +536,8 @@ def run_mu_sweep(args):
     def run(mu):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        solver = msp.Solver(a.nb, a.b, d_rp, d_ci, d_vals[0], mu=mu, precision=prec)
+        solver = msp.Solver(a.nb, a.b, d_rp, d_ci, d_vals[0], mu=mu, precision=prec,
+                            colouring=colouring_of(args, msp))
         torch.cuda.synchronize()
         t_first = time.perf_counter() - t0
         setups, setup_s, iters, its, unconverged = 0, t_first, 0, [], 0

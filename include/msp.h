@@ -65,6 +65,13 @@ extern "C" {
 #define MSP_PRECISION_FP64 0
 #define MSP_PRECISION_FP32 1 /* stage N/P/R values and arithmetic in FP32 */
 
+/* Colouring of every graph the preconditioner colours (msp_config.colouring). */
+#define MSP_COLOURING_ALG41 0 /* VerticesGrouping, Algorithms 4.1/4.2 (the paper's) */
+#define MSP_COLOURING_JP 1    /* greedy first-fit in Jones-Plassmann priority order (larger
+                               * degree first, then the high word of SplitMix64(v ^
+                               * 0x4A6F6E6573504C), then index), computed in parallel rounds;
+                               * not from the paper: a faster SETUP with different colours */
+
 typedef struct msp_handle_s* msp_handle;
 
 typedef struct {
@@ -84,6 +91,7 @@ typedef struct {
   unsigned long long agg_seed; /* seed of the matching visit order */
   int coarse_hard_max;         /* refuse a coarsest level larger than this */
   int precision;               /* MSP_PRECISION_* */
+  int colouring;               /* MSP_COLOURING_* */
 } msp_config;
 
 typedef struct {

@@ -22,7 +22,7 @@ class OrcConfig(C.Structure):
                 ("post_sweeps", C.c_int), ("bgs_sweeps", C.c_int), ("decoupling", C.c_int),
                 ("bilu_order", C.c_int), ("precond", C.c_int), ("max_levels", C.c_int),
                 ("beta", C.c_double), ("agg_seed", C.c_ulonglong),
-                ("coarse_hard_max", C.c_int)]
+                ("coarse_hard_max", C.c_int), ("colouring", C.c_int)]
 
 
 class OrcInfo(C.Structure):
@@ -62,6 +62,8 @@ def lib():
         _lib.orc_bilu_pivots.argtypes = [P, P]
         _lib.orc_vertices_grouping.restype = C.c_int
         _lib.orc_vertices_grouping.argtypes = [C.c_int, P, P, P]
+        _lib.orc_jp_colouring.restype = C.c_int
+        _lib.orc_jp_colouring.argtypes = [C.c_int, P, P, P]
         _lib.orc_pgs_mc.restype = C.c_int
         _lib.orc_pgs_mc.argtypes = [C.c_int, P, P, P, C.c_int, P, P, P, C.c_int]
         _lib.orc_pairwise.restype = C.c_int
@@ -195,6 +197,16 @@ def vertices_grouping(n, row_ptr, col_idx):
     rp, ci = _i32(row_ptr), _i32(col_idx)
     c = np.zeros(n, np.int32)
     g = lib().orc_vertices_grouping(n, _p(rp), _p(ci), _p(c))
+    return c, g
+
+
+def jp_colouring(n, row_ptr, col_idx):
+    """Greedy first-fit colouring of a pattern in Jones-Plassmann priority order (degree
+    descending, then the high word of SplitMix64(v ^ seed), then index); returns
+    (colour[1..g], g)."""
+    rp, ci = _i32(row_ptr), _i32(col_idx)
+    c = np.zeros(n, np.int32)
+    g = lib().orc_jp_colouring(n, _p(rp), _p(ci), _p(c))
     return c, g
 
 

@@ -24,6 +24,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <tuple>
 #include <map>
 #include <set>
 #include <utility>
@@ -63,6 +64,8 @@ typedef struct {
   double beta;       // strong-coupling threshold (0.25)
   unsigned long long agg_seed;  // visit-order hash seed of the pairwise matching
   int coarse_hard_max;          // refuse a coarsest level above this size
+  int colouring;                // 0 = VerticesGrouping (Alg 4.1/4.2), 1 = greedy in
+                                // Jones-Plassmann priority order (not the paper's)
 } orc_config;
 
 typedef struct {
@@ -228,6 +231,38 @@ int vertices_grouping(const Csr& S, std::vector<int>& colour) {
     std::fill(in_V.begin(), in_V.end(), 0);
     for (int v : Wbar) in_V[v] = 1;
     remaining = (int)Wbar.size();
+  }
+  return g;
+}
+
+// Greedy first-fit colouring in Jones-Plassmann priority order: an alternative to
+// Algorithms 4.1/4.2 that a GPU computes in parallel rounds with the same result
+// (a vertex's colour depends only on the colours of its higher-priority neighbours).
+// Priority: larger degree first, then the smaller high word of SplitMix64(v ^ seed),
+// then the smaller index.  colour[v] = the smallest c >= 1 used by no higher-priority
+// neighbour.  Returns the number of colours.
+constexpr uint64_t kJpSeed = 0x4A6F6E6573504CULL;
+uint64_t splitmix64(uint64_t x);
+int jp_greedy_colouring(const Csr& S, std::vector<int>& colour) {
+  const int n = S.n;
+  std::vector<std::tuple<int, uint32_t, int>> order(n);
+  for (int v = 0; v < n; ++v)
+    order[v] = {-(S.rp[v + 1] - S.rp[v]), (uint32_t)(splitmix64((uint64_t)v ^ kJpSeed) >> 32),
+                v};
+  std::sort(order.begin(), order.end());
+  colour.assign(n, 0);
+  int g = 0;
+  std::vector<int> seen(n + 2, -1);  // seen[c] == v: colour c taken around v
+  for (const auto& t : order) {
+    const int v = std::get<2>(t);
+    for (int q = S.rp[v]; q < S.rp[v + 1]; ++q) {
+      const int c = colour[S.ci[q]];  // 0 for the neighbours not coloured yet
+      if (c > 0) seen[c] = v;
+    }
+    int c = 1;
+    while (seen[c] == v) ++c;
+    colour[v] = c;
+    g = std::max(g, c);
   }
   return g;
 }
@@ -572,7 +607,8 @@ struct Handle {
 void pattern_setup(Handle& h) {
   const int nb = h.nb, b = h.b, bb = b * b;
   Csr S = adjacency(nb, h.A0.rp.data(), h.A0.ci.data());
-  h.g0 = vertices_grouping(S, h.colour0);
+  h.g0 = h.cfg.colouring == 1 ? jp_greedy_colouring(S, h.colour0)
+                              : vertices_grouping(S, h.colour0);
   colour_permutation(h.colour0, h.g0, h.perm0, h.cptr0);
   h.iperm0.resize(nb);
   for (int k = 0; k < nb; ++k) h.iperm0[h.perm0[k]] = k;
@@ -674,7 +710,8 @@ int value_setup(Handle& h) {
     if (nc > h.cfg.coarse_max && l + 2 < h.cfg.max_levels) {
       Csr Sc = adjacency(nc, Ac.rp.data(), Ac.ci.data());
       std::vector<int> colour;
-      int g = vertices_grouping(Sc, colour);
+      int g = h.cfg.colouring == 1 ? jp_greedy_colouring(Sc, colour)
+                                   : vertices_grouping(Sc, colour);
       colour_permutation(colour, g, C.perm, C.cptr);
       C.A = permute_csr(Ac, C.perm);
     } else {
@@ -1062,6 +1099,7 @@ void orc_config_default(orc_config* c) {
   c->beta = 0.25;
   c->agg_seed = 0x2208085940ULL;
   c->coarse_hard_max = 20000;
+  c->colouring = 0;
 }
 
 void* orc_create(const orc_config* cfg, int nb, int b, const int* rp, const int* ci,
@@ -1242,6 +1280,14 @@ int orc_bilu_pivots(void* p, double* out) {
 }
 
 // Standalone Algorithm 4.2 on a pattern: colour[v] in 1..g; returns g.
+int orc_jp_colouring(int n, const int* rp, const int* ci, int* colour) {
+  Csr S = adjacency(n, rp, ci);
+  std::vector<int> c;
+  const int g = jp_greedy_colouring(S, c);
+  std::copy(c.begin(), c.end(), colour);
+  return g;
+}
+
 int orc_vertices_grouping(int n, const int* rp, const int* ci, int* colour) {
   Csr S = adjacency(n, rp, ci);
   std::vector<int> c;

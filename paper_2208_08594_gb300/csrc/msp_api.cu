@@ -402,13 +402,9 @@ int reset_flags(msp_handle h, cudaStream_t s) {
   return MSP_OK;
 }
 
-// VerticesGrouping of the graph of a CSR/BSR pattern: colour[v] in 1..g, perm (colour
-// order -> index), cptr (host).
-int colour_graph(msp_handle h, int n, const int* rp, const int* ci, int nnz, DevBuf<int>& colour,
-                 DevBuf<int>& perm, std::vector<int>& cptr, int* g_out, cudaStream_t s) {
-  DevBuf<int> srp, sci;
-  int snnz = 0;
-  MSP_TRY(build_adjacency(h->ss, n, rp, ci, nnz, srp, sci, &snnz, s));
+// VerticesGrouping (Algorithms 4.1/4.2) of the symmetric graph srp/sci: colour[v] in 1..g
+int vertices_grouping_gpu(msp_handle h, int n, const DevBuf<int>& srp, const DevBuf<int>& sci,
+                          int snnz, DevBuf<int>& colour, int* g_out, cudaStream_t s) {
   DevBuf<unsigned long long> keys;
   DevBuf<int> vor, rank, wbar, meta, rrp, rci, rsrc, colour_r;
   DevBuf<unsigned> bitmap, inV;
@@ -458,7 +454,56 @@ int colour_graph(msp_handle h, int n, const int* rp, const int* ci, int nnz, Dev
   MSP_CUDA_TRY(cudaMemcpyAsync(hm, meta.p, sizeof(hm), cudaMemcpyDeviceToHost, s));
   MSP_CUDA_TRY(cudaStreamSynchronize(s));
   if (hm[1] != 0) return MSP_ERR_TIMEOUT;
-  const int g = hm[0];
+  *g_out = hm[0];
+  return MSP_OK;
+}
+
+// Greedy first-fit colouring in Jones-Plassmann priority order of the symmetric graph
+// srp/sci (MSP_COLOURING_JP): colour[v] in 1..g, by parallel rounds
+constexpr unsigned long long kJpSeed = 0x4A6F6E6573504CULL;
+int jp_colouring_gpu(msp_handle h, int n, const int* srp, const int* sci, DevBuf<int>& colour,
+                     int* g_out, cudaStream_t s) {
+  DevBuf<unsigned long long> keys;
+  DevBuf<int> order, rank, counters;
+  MSP_TRY(keys.alloc(n));
+  MSP_TRY(order.alloc(n));
+  MSP_TRY(rank.alloc(n));
+  MSP_TRY(counters.alloc(2));
+  MSP_TRY(colour.alloc(n));
+  MSP_TRY(launch_jp_keys(n, srp, kJpSeed, keys.p, order.p, s));
+  MSP_TRY(sort_pairs_u64(h->ss, n, keys.p, order.p, 64, s));
+  MSP_TRY(launch_scatter_inverse(n, order.p, rank.p, s));  // rank[order[k]] = k
+  MSP_CUDA_TRY(cudaMemsetAsync(colour.p, 0, (size_t)n * sizeof(int), s));
+  MSP_CUDA_TRY(cudaMemsetAsync(counters.p, 0, 2 * sizeof(int), s));
+  // every round colours at least the first uncoloured vertex in priority order
+  const long long max_rounds = (long long)n + 8;
+  int hc[2] = {0, 0};
+  for (long long rounds = 0; hc[0] < n;) {
+    if (rounds > max_rounds) return MSP_ERR_TIMEOUT;
+    for (int r = 0; r < 8; ++r)
+      MSP_TRY(launch_jp_round(n, srp, sci, rank.p, colour.p, counters.p, s));
+    rounds += 8;
+    MSP_CUDA_TRY(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    MSP_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  *g_out = hc[1];
+  return MSP_OK;
+}
+
+// VerticesGrouping of the graph of a CSR/BSR pattern: colour[v] in 1..g, perm (colour
+// order -> index), cptr (host).
+int colour_graph(msp_handle h, int n, const int* rp, const int* ci, int nnz, DevBuf<int>& colour,
+                 DevBuf<int>& perm, std::vector<int>& cptr, int* g_out, cudaStream_t s) {
+  DevBuf<int> srp, sci;
+  int snnz = 0;
+  MSP_TRY(build_adjacency(h->ss, n, rp, ci, nnz, srp, sci, &snnz, s));
+  int g = 0;
+  if (h->cfg.colouring == MSP_COLOURING_JP)
+    MSP_TRY(jp_colouring_gpu(h, n, srp.p, sci.p, colour, &g, s));
+  else
+    MSP_TRY(vertices_grouping_gpu(h, n, srp, sci, snnz, colour, &g, s));
+  DevBuf<unsigned long long> keys;
+  MSP_TRY(keys.alloc(n));
   // colour permutation: stable sort by (colour, index)
   colour_keys_kernel<<<grid1(n), kThreads, 0, s>>>(n, colour.p, keys.p);
   MSP_TRY(launch_status());
@@ -1428,7 +1473,8 @@ bool config_ok(const msp_config& c, int b) {
          c.npass >= 1 && c.npass <= 4 && c.pre_sweeps >= 0 && c.post_sweeps >= 0 &&
          c.bgs_sweeps >= 0 && c.bilu_order == 0 && c.precond >= 0 && c.precond <= 4 &&
          c.max_levels >= 1 && c.beta >= 0.0 && c.coarse_hard_max >= 1 &&
-         (c.precision == MSP_PRECISION_FP64 || c.precision == MSP_PRECISION_FP32) && b >= 1 &&
+         (c.precision == MSP_PRECISION_FP64 || c.precision == MSP_PRECISION_FP32) &&
+         (c.colouring == MSP_COLOURING_ALG41 || c.colouring == MSP_COLOURING_JP) && b >= 1 &&
          b <= 8;
 }
 
@@ -1457,6 +1503,7 @@ int msp_config_default(msp_config* c) {
   c->agg_seed = 0x2208085940ULL;
   c->coarse_hard_max = 20000;
   c->precision = MSP_PRECISION_FP64;
+  c->colouring = MSP_COLOURING_ALG41;
   return MSP_OK;
 }
 

@@ -85,6 +85,77 @@ __global__ void diag_pos_kernel(int n, const int* __restrict__ rp, const int* __
   }
 }
 
+// Greedy first-fit colouring in Jones-Plassmann priority order (an alternative to
+// Algorithms 4.1/4.2): priority keys, then rounds in which every vertex whose higher-
+// priority neighbours are all coloured takes the smallest colour none of them has.  A
+// vertex's colour depends only on those neighbours' final colours, so the result is the
+// sequential greedy's in priority order whatever the rounds' timing (a neighbour coloured
+// in the same round and not yet seen only delays a vertex to the next round).
+__device__ __forceinline__ unsigned long long jp_splitmix64(unsigned long long x) {
+  // SplitMix64 output function (Vigna)
+  unsigned long long z = x + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// key: larger degree first, then the smaller high word of SplitMix64(v ^ seed); a stable
+// sort of the keys in index order breaks the remaining ties by index
+__global__ void jp_keys_kernel(int n, const int* __restrict__ srp, unsigned long long seed,
+                               unsigned long long* __restrict__ key, int* __restrict__ idx) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const unsigned long long deg = (unsigned long long)(srp[v + 1] - srp[v]);
+    key[v] = ((0x7FFFFFFFull - deg) << 32) | (jp_splitmix64((unsigned long long)v ^ seed) >> 32);
+    idx[v] = v;
+  }
+}
+
+__global__ void jp_round_kernel(int n, const int* __restrict__ srp, const int* __restrict__ sci,
+                                const int* __restrict__ rank, int* colour,
+                                int* __restrict__ counters) {
+  int done_here = 0, gmax = 0;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    if (colour[v] != 0) continue;
+    const int rv = rank[v];
+    const int q0 = srp[v], q1 = srp[v + 1];
+    unsigned long long used = 0;  // colours 1..64 of the higher-priority neighbours
+    bool ready = true, high = false;
+    for (int q = q0; q < q1; ++q) {
+      const int u = sci[q];
+      if (rank[u] > rv) continue;
+      const int cu = *(volatile int*)(colour + u);
+      if (cu == 0) {
+        ready = false;
+        break;
+      }
+      if (cu <= 64)
+        used |= 1ull << (cu - 1);
+      else
+        high = true;
+    }
+    if (!ready) continue;
+    int c = __ffsll(~used);  // smallest colour in 1..64 not taken (0 if all 64 are)
+    if (c == 0 || high) {  // rare: a colour above 64 among the neighbours
+      c = 1;
+      for (bool taken = true; taken; ++c) {
+        taken = false;
+        for (int q = q0; q < q1 && !taken; ++q) {
+          const int u = sci[q];
+          taken = rank[u] < rv && *(volatile int*)(colour + u) == c;
+        }
+        if (!taken) break;
+      }
+    }
+    colour[v] = c;
+    ++done_here;
+    gmax = max(gmax, c);
+  }
+  if (done_here) {
+    atomicAdd(counters, done_here);
+    atomicMax(counters + 1, gmax);
+  }
+}
+
 // Two-hop lists of a graph for VerticesGrouping: for every vertex v the rows of its
 // neighbours, concatenated in the order of v's row (the second circle of Algorithm 4.1,
 // with repeats and with v's own neighbours, which the colouring filters out).
@@ -409,6 +480,21 @@ int launch_extract_N(int b, size_t nnzb, const double* v, double* aN, cudaStream
 int launch_diag_pos(int n, const int* rp, const int* ci, int* dpos, cudaStream_t s) {
   if (n <= 0) return MSP_OK;
   diag_pos_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, rp, ci, dpos);
+  return launch_status();
+}
+
+int launch_jp_keys(int n, const int* srp, unsigned long long seed, unsigned long long* key,
+                   int* idx, cudaStream_t s) {
+  if (n <= 0) return MSP_OK;
+  jp_keys_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, srp, seed, key, idx);
+  return launch_status();
+}
+
+int launch_jp_round(int n, const int* srp, const int* sci, const int* rank, int* colour,
+                    int* counters, cudaStream_t s) {
+  if (n <= 0) return MSP_OK;
+  jp_round_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, srp, sci, rank, colour,
+                                                             counters);
   return launch_status();
 }
 

@@ -62,6 +62,15 @@ int launch_gather_values(size_t nnz, int bb, const int* src, const double* in, d
                          cudaStream_t s);
 int launch_extract_N(int b, size_t nnzb, const double* v, double* aN, cudaStream_t s);
 int launch_diag_pos(int n, const int* rp, const int* ci, int* dpos, cudaStream_t s);
+// Jones-Plassmann priority keys of a symmetric graph (larger degree first, then the high
+// word of SplitMix64(v ^ seed)); idx[v] = v for a stable key-value sort
+int launch_jp_keys(int n, const int* srp, unsigned long long seed, unsigned long long* key,
+                   int* idx, cudaStream_t s);
+// one round: every uncoloured vertex whose higher-priority (smaller rank) neighbours are
+// all coloured takes the smallest colour none of them has; counters[0] += vertices
+// coloured, counters[1] = max(counters[1], colour)
+int launch_jp_round(int n, const int* srp, const int* sci, const int* rank, int* colour,
+                    int* counters, cudaStream_t s);
 // two-hop lists of a graph (srp/sci): cnt[v] = sum over the neighbours k of v of deg(k),
 // *total = their sum; then tl[tp[v] ...] = the neighbours' rows concatenated in row order
 int launch_twohop_count(int n, const int* srp, const int* sci, int* cnt, unsigned long long* total,

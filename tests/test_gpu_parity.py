@@ -180,6 +180,36 @@ def test_long_rows_take_the_csr_path():
     g.close()
 
 
+@pytest.mark.parametrize("name", ["spe10_like_b4", "wells_b2", "b6_ragged"])
+def test_jp_colouring_option_matches_oracle(name):
+    """msp_config.colouring = MSP_COLOURING_JP (greedy in Jones-Plassmann priority order,
+    parallel rounds on the GPU): every colouring bit-exact with the oracle's sequential
+    greedy, the whole hierarchy identical, application and solve in tolerance."""
+    a, cfg = CASES[name]()
+    g, o = _pair(a, colouring=msp.MSP_COLOURING_JP, **cfg)
+    cg, ng = g.colour0()
+    co, no = o.colour0()
+    assert ng == no and np.array_equal(cg, co)
+    assert g.num_levels == o.num_levels
+    for l in range(o.num_levels):
+        lg, lo = g.level(l), o.level(l)
+        for key in ("perm", "cptr", "agg", "row_ptr", "col_idx"):
+            assert np.array_equal(lg[key], lo[key]), (l, key)
+        assert np.array_equal(lg["values"], lo["values"]), l
+    x = random_rhs(a, 1)
+    w = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+    g.apply_precond(_vec(x), w)
+    ref = o.apply_precond(x)
+    assert np.abs(w.cpu().numpy() - ref).max() / np.abs(ref).max() <= TOL_APPLY
+    rhs = random_rhs(a, 11)
+    xd = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+    info = g.solve(_vec(rhs), xd, 1e-6)
+    _, io = o.solve(rhs, 1e-6)
+    assert info["status"] == 0 and abs(info["iterations"] - io["iterations"]) <= 1
+    g.close()
+    o.close()
+
+
 def test_zero_and_nonfinite_rhs():
     a = grid_spe10(nx=6, ny=5, nz=4)
     g, _ = _pair(a, coarse_max=20)

@@ -131,3 +131,70 @@ def test_valid_on_larger_grid_with_wells(oracle_lib):
     a = box_jacobian(30, 20, 10, 2, 5, layered=True, kz_ratio=0.1, n_wells=4)
     colour, g = oracle_lib.vertices_grouping(a.nb, a.row_ptr, a.col_idx)
     check_valid(a.nb, a.row_ptr, a.col_idx, colour, g)
+
+
+# ---- greedy colouring in Jones-Plassmann priority order (an alternative to Alg 4.1/4.2)
+
+def _splitmix64(x):
+    """SplitMix64 output function (Vigna), written from its published definition."""
+    m = (1 << 64) - 1
+    z = (x + 0x9E3779B97F4A7C15) & m
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & m
+    return z ^ (z >> 31)
+
+
+JP_SEED = 0x4A6F6E6573504C
+
+
+def brute_force_jp(n, rp, ci):
+    """First-fit greedy in priority order (degree descending, then the high word of
+    SplitMix64(v ^ seed), then index) with Python sets: the colouring the parallel
+    Jones-Plassmann rounds must reproduce."""
+    S = _adj_sets(n, rp, ci)
+    order = sorted(range(n), key=lambda v: (-len(S[v]), _splitmix64(v ^ JP_SEED) >> 32, v))
+    colour = [0] * n
+    for v in order:
+        used = {colour[u] for u in S[v]}
+        c = 1
+        while c in used:
+            c += 1
+        colour[v] = c
+    return colour
+
+
+def _random_graph(n, p, seed):
+    rng = np.random.default_rng(seed)
+    edges = [(i, j) for i in range(n) for j in range(i + 1, n) if rng.random() < p]
+    return csr_from_edges(n, edges)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_jp_matches_brute_force(oracle_lib, seed):
+    n = 40 + 7 * seed
+    rp, ci = _random_graph(n, 0.12, seed)
+    c, g = oracle_lib.jp_colouring(n, rp, ci)
+    ref = brute_force_jp(n, rp, ci)
+    assert list(c) == ref and g == max(ref)
+
+
+def test_jp_colouring_properties(oracle_lib):
+    a = box_jacobian(9, 8, 6, 3, 2, n_wells=2)
+    n = a.nb
+    c, g = oracle_lib.jp_colouring(n, a.row_ptr, a.col_idx)
+    S = _adj_sets(n, a.row_ptr, a.col_idx)
+    assert all(c[v] != c[u] for v in range(n) for u in S[v])          # proper
+    assert g <= max(len(s) for s in S) + 1
+    for v in range(n):                                                # first fit (Grundy)
+        around = {int(c[u]) for u in S[v]}
+        assert all(k in around for k in range(1, int(c[v])))
+
+
+def test_jp_complete_graph_and_star(oracle_lib):
+    n = 9
+    rp, ci = csr_from_edges(n, [(i, j) for i in range(n) for j in range(i + 1, n)])
+    c, g = oracle_lib.jp_colouring(n, rp, ci)
+    assert g == n and sorted(c) == list(range(1, n + 1))
+    rp, ci = csr_from_edges(n, [(0, j) for j in range(1, n)])           # star: centre first
+    c, g = oracle_lib.jp_colouring(n, rp, ci)
+    assert g == 2 and c[0] == 1 and all(x == 2 for x in c[1:])
