@@ -674,9 +674,20 @@ int coarse_inverse(msp_handle h, const DCsr& C, cudaStream_t s) {
   MSP_TRY(cp.alloc(n));
   MSP_TRY(h->cinv.alloc((size_t)n * n));
   MSP_TRY(launch_csr_to_dense(n, C.rp.p, C.ci.p, C.v.p, A.p, s));
-  for (int k = 0; k < n; ++k) {
-    MSP_TRY(launch_gj_pivot(n, k, A.p, col.p, piv.p, h->flags.p, s));
-    MSP_TRY(launch_gj_update(n, k, A.p, col.p, s));
+  // blocked: the steps of a panel of 32 columns transform the panel only, then one
+  // rank-32 update applies them to the other columns (row swaps act on whole rows)
+  constexpr int kPanel = 32;
+  DevBuf<double> T;
+  MSP_TRY(T.alloc((size_t)kPanel * n));
+  for (int k0 = 0; k0 < n; k0 += kPanel) {
+    const int nb = std::min(kPanel, n - k0);
+    for (int k = k0; k < k0 + nb; ++k) {
+      MSP_TRY(launch_gj_pivot(n, k, k0, k0 + nb, A.p, col.p, piv.p, h->flags.p, s));
+      MSP_TRY(launch_gj_update(n, k, k0, nb, A.p, col.p, s));
+    }
+    MSP_CUDA_TRY(cudaMemcpyAsync(T.p, A.p + (size_t)k0 * n, (size_t)nb * n * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, s));
+    MSP_TRY(launch_gj_panel_apply(n, k0, nb, A.p, T.p, s));
   }
   if (sync_flags(h, s) != MSP_OK) return h->h_flags->code;
   std::vector<int> hp(n), cols(n);

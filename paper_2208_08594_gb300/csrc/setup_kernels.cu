@@ -356,8 +356,12 @@ __global__ void csr_to_dense_kernel(int n, const int* __restrict__ rp, const int
 
 // pivot search in column k (rows k..n-1, first maximum), row swap, pivot row scaling,
 // and a copy of column k (after the swap) for the rank-1 update
-__global__ void gj_pivot_kernel(int n, int k, double* __restrict__ A, double* __restrict__ col,
-                                int* __restrict__ piv, DevFlags* flags) {
+// Gauss-Jordan step k, pivot part: partial pivoting in column k (rows k..n-1), rows k and
+// the pivot row swapped over all columns, col = column k, row k scaled by 1/pivot over the
+// columns [j0, j1) being transformed now (the current panel)
+__global__ void gj_pivot_kernel(int n, int k, int j0, int j1, double* __restrict__ A,
+                                double* __restrict__ col, int* __restrict__ piv,
+                                DevFlags* flags) {
   __shared__ double sv[1024];
   __shared__ int si[1024];
   double best = -1.0;
@@ -399,22 +403,77 @@ __global__ void gj_pivot_kernel(int n, int k, double* __restrict__ A, double* __
   for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = A[(size_t)i * n + k];
   __syncthreads();
   const double inv = 1.0 / col[k];
-  for (int j = threadIdx.x; j < n; j += blockDim.x)
+  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x)
     A[(size_t)k * n + j] = (j == k) ? inv : A[(size_t)k * n + j] * inv;
 }
 
-__global__ void gj_update_kernel(int n, int k, double* __restrict__ A,
+// Gauss-Jordan step k, elimination part over the columns [j0, j0 + w): rows i != k
+__global__ void gj_update_kernel(int n, int k, int j0, int w, double* __restrict__ A,
                                  const double* __restrict__ col) {
   const double* rowk = A + (size_t)k * n;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < (size_t)n * n;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < (size_t)n * w;
        t += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t / n), j = (int)(t % n);
+    const int i = (int)(t / w), j = j0 + (int)(t % w);
     if (i == k) continue;
     const double f = col[i];
+    double* a = A + (size_t)i * n + j;
     if (j == k)
-      A[t] = -f * rowk[k];
+      *a = -f * rowk[k];
     else
-      A[t] -= f * rowk[j];
+      *a -= f * rowk[j];
+  }
+}
+
+// After the steps of a panel of columns K = [k0, k0 + nb) have transformed the panel: the
+// same steps applied to every other column c at once.  They compose to
+// I + sum_q (P_q - e_q) e_q^T with P the panel's columns, so
+//   c[i] += sum_q P[i][q] c[k0 + q] for the rows outside K,
+//   c[i]  = sum_q P[i][q] c[k0 + q] for the rows in K,
+// with c[k0 + q] the values before the update (T, a copy of the rows K).  64 x 64 tiles of
+// A, 4 x 4 per thread, the panel and T staged in shared memory.
+constexpr int kGjPanel = 32;
+__global__ void __launch_bounds__(256) gj_panel_apply_kernel(int n, int k0, int nb,
+                                                             double* __restrict__ A,
+                                                             const double* __restrict__ T) {
+  __shared__ double sP[64][kGjPanel + 1];
+  __shared__ double sT[kGjPanel][64];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+  for (int t = threadIdx.x; t < 64 * kGjPanel; t += 256) {
+    const int r = t / kGjPanel, q = t % kGjPanel;
+    sP[r][q] = (r0 + r < n && q < nb) ? A[(size_t)(r0 + r) * n + k0 + q] : 0.0;
+    const int qq = t / 64, c = t % 64;
+    sT[qq][c] = (qq < nb && c0 + c < n) ? T[(size_t)qq * n + c0 + c] : 0.0;
+  }
+  __syncthreads();
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  for (int q = 0; q < nb; ++q) {
+    double p[4], tv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) p[a] = sP[ty + 16 * a][q];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) tv[b] = sT[q][tx + 16 * b];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fma(p[a], tv[b], acc[a][b]);
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = r0 + ty + 16 * a;
+    if (i >= n) continue;
+    const bool in_k = i >= k0 && i < k0 + nb;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = c0 + tx + 16 * b;
+      if (j >= n || (j >= k0 && j < k0 + nb)) continue;
+      double* a_ij = A + (size_t)i * n + j;
+      *a_ij = in_k ? acc[a][b] : *a_ij + acc[a][b];
+    }
   }
 }
 
@@ -560,14 +619,21 @@ int launch_csr_to_dense(int n, const int* rp, const int* ci, const double* v, do
   return launch_status();
 }
 
-int launch_gj_pivot(int n, int k, double* A, double* col, int* piv, DevFlags* flags,
-                    cudaStream_t s) {
-  gj_pivot_kernel<<<1, 1024, 0, s>>>(n, k, A, col, piv, flags);
+int launch_gj_pivot(int n, int k, int j0, int j1, double* A, double* col, int* piv,
+                    DevFlags* flags, cudaStream_t s) {
+  gj_pivot_kernel<<<1, 1024, 0, s>>>(n, k, j0, j1, A, col, piv, flags);
   return launch_status();
 }
 
-int launch_gj_update(int n, int k, double* A, const double* col, cudaStream_t s) {
-  gj_update_kernel<<<grid_for((size_t)n * n, kThreads), kThreads, 0, s>>>(n, k, A, col);
+int launch_gj_update(int n, int k, int j0, int w, double* A, const double* col, cudaStream_t s) {
+  gj_update_kernel<<<grid_for((size_t)n * w, kThreads), kThreads, 0, s>>>(n, k, j0, w, A, col);
+  return launch_status();
+}
+
+int launch_gj_panel_apply(int n, int k0, int nb, double* A, const double* T, cudaStream_t s) {
+  if (nb <= 0 || nb > kGjPanel) return MSP_ERR_ARG;
+  const dim3 grid((n + 63) / 64, (n + 63) / 64);
+  gj_panel_apply_kernel<<<grid, 256, 0, s>>>(n, k0, nb, A, T);
   return launch_status();
 }
 

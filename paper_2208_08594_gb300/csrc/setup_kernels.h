@@ -90,10 +90,14 @@ int launch_bilu_factor(int b, int r0, int r1, const int* rp, const int* ci, cons
 // dense copy of a CSR matrix (n x n row-major)
 int launch_csr_to_dense(int n, const int* rp, const int* ci, const double* v, double* A,
                         cudaStream_t s);
-// one Gauss-Jordan step of the in-place dense inversion
-int launch_gj_pivot(int n, int k, double* A, double* col, int* piv, DevFlags* flags,
-                    cudaStream_t s);
-int launch_gj_update(int n, int k, double* A, const double* col, cudaStream_t s);
+// blocked in-place Gauss-Jordan inversion of a dense n x n matrix: step k on the columns
+// [j0, j1) of its panel (pivot search and row swap always over the whole matrix)
+int launch_gj_pivot(int n, int k, int j0, int j1, double* A, double* col, int* piv,
+                    DevFlags* flags, cudaStream_t s);
+int launch_gj_update(int n, int k, int j0, int w, double* A, const double* col, cudaStream_t s);
+// the steps of the panel [k0, k0 + nb) (nb <= 32) applied to every other column; T = the
+// rows k0..k0+nb-1 of A (n values each) before this call
+int launch_gj_panel_apply(int n, int k0, int nb, double* A, const double* T, cudaStream_t s);
 int launch_gj_unscramble(int n, const int* colperm, const double* A, double* out,
                          cudaStream_t s);
 int launch_cast_vals(size_t n, const double* in, float* out, cudaStream_t s);
