@@ -59,6 +59,8 @@ SITE_PREFIX_KERNELS = {"amg_gs_pre_l": "ell_gs_colour_kernel",
                        "amg_gs_csr_pre_l": "csr_gs_colour_kernel",
                        "amg_gs_csr_post_l": "csr_gs_colour_kernel",
                        "amg_residual_restrict_l": "ell_residual_restrict_kernel",
+                       "amg_pjac_l": "jacobi_sweep_kernel",
+                       "amg_pgs_no_l": "pgs_no_sweep_kernel",
                        "amg_residual_restrict_csr_l": "csr_residual_restrict_kernel"}
 # FP64 block kernels do one FMA per 8-byte value: at the measured 1.19 TFLOP/s FP64 FMA
 # rate they cannot move more than 1.19e12 / 2 * 8 bytes/s
@@ -73,6 +75,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    p.add_argument("--smoother", default="pgs_mc", choices=["pgs_mc", "pjac", "pgs_no"],
+                   help="AMG smoother: PGS-MC (the paper's), PJAC-NO or PGS-NO "
+                        "(Section 5.1.1, Table 2)")
     p.add_argument("--colouring", default="alg41", choices=["alg41", "jp"],
                    help="Algorithms 4.1/4.2 (the paper's) or greedy in Jones-Plassmann "
                         "priority order (parallel rounds)")
@@ -97,11 +102,18 @@ def workload_name(args):
     return "spe10-shaped %dx%dx%d + 4 wells, 4x4 BSR, %s%s" % (
         args.nx, args.ny, args.nz, "FP64" if args.precision == "fp64" else
         "FP32 preconditioner / FP64 Krylov",
-        ", Jones-Plassmann-order colouring" if args.colouring == "jp" else "")
+        ", Jones-Plassmann-order colouring" if args.colouring == "jp" else "") + (
+        ", AMG smoother %s" % {"pjac": "PJAC-NO", "pgs_no": "PGS-NO"}[args.smoother]
+        if args.smoother != "pgs_mc" else "")
 
 
 def colouring_of(args, msp):
     return msp.MSP_COLOURING_JP if args.colouring == "jp" else msp.MSP_COLOURING_ALG41
+
+
+def smoother_of(args, msp):
+    return {"pgs_mc": msp.MSP_SMOOTHER_PGS_MC, "pjac": msp.MSP_SMOOTHER_PJAC,
+            "pgs_no": msp.MSP_SMOOTHER_PGS_NO}[args.smoother]
 
 
 def kernels_from_sites(sites):
@@ -267,7 +279,7 @@ def run_native(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     solver = msp.Solver(a.nb, a.b, d_rp, d_ci, d_v0, mu=args.mu, precision=prec,
-                        colouring=colouring_of(args, msp))
+                        colouring=colouring_of(args, msp), smoother=smoother_of(args, msp))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     nsets = len(d_sets)
@@ -537,7 +549,7 @@ def run_mu_sweep(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         solver = msp.Solver(a.nb, a.b, d_rp, d_ci, d_vals[0], mu=mu, precision=prec,
-                            colouring=colouring_of(args, msp))
+                            colouring=colouring_of(args, msp), smoother=smoother_of(args, msp))
         torch.cuda.synchronize()
         t_first = time.perf_counter() - t0
         setups, setup_s, iters, its, unconverged = 0, t_first, 0, [], 0

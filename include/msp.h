@@ -65,6 +65,13 @@ extern "C" {
 #define MSP_PRECISION_FP64 0
 #define MSP_PRECISION_FP32 1 /* stage N/P/R values and arithmetic in FP32 */
 
+/* Smoother of the AMG levels (msp_config.smoother); Section 5.1.1 compares the three. */
+#define MSP_SMOOTHER_PGS_MC 0 /* multi-colour Gauss-Seidel, Algorithm 4.3 (the paper's) */
+#define MSP_SMOOTHER_PJAC 1   /* PJAC-NO: Jacobi, all rows from the values at the start */
+#define MSP_SMOOTHER_PGS_NO 2 /* PGS-NO: chunks of 16 consecutive rows swept at once, each
+                               * Gauss-Seidel in order (the other chunks at their values
+                               * from the start of the sweep); coarse levels uncoloured */
+
 /* Colouring of every graph the preconditioner colours (msp_config.colouring). */
 #define MSP_COLOURING_ALG41 0 /* VerticesGrouping, Algorithms 4.1/4.2 (the paper's) */
 #define MSP_COLOURING_JP 1    /* greedy first-fit in Jones-Plassmann priority order (larger
@@ -92,6 +99,7 @@ typedef struct {
   int coarse_hard_max;         /* refuse a coarsest level larger than this */
   int precision;               /* MSP_PRECISION_* */
   int colouring;               /* MSP_COLOURING_* */
+  int smoother;                /* MSP_SMOOTHER_* */
 } msp_config;
 
 typedef struct {

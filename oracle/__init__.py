@@ -22,7 +22,8 @@ class OrcConfig(C.Structure):
                 ("post_sweeps", C.c_int), ("bgs_sweeps", C.c_int), ("decoupling", C.c_int),
                 ("bilu_order", C.c_int), ("precond", C.c_int), ("max_levels", C.c_int),
                 ("beta", C.c_double), ("agg_seed", C.c_ulonglong),
-                ("coarse_hard_max", C.c_int), ("colouring", C.c_int)]
+                ("coarse_hard_max", C.c_int), ("colouring", C.c_int),
+                ("smoother", C.c_int)]
 
 
 class OrcInfo(C.Structure):
@@ -64,6 +65,10 @@ def lib():
         _lib.orc_vertices_grouping.argtypes = [C.c_int, P, P, P]
         _lib.orc_jp_colouring.restype = C.c_int
         _lib.orc_jp_colouring.argtypes = [C.c_int, P, P, P]
+        _lib.orc_jacobi_sweep.restype = None
+        _lib.orc_jacobi_sweep.argtypes = [C.c_int, P, P, P, P, P]
+        _lib.orc_pgs_no_sweep.restype = None
+        _lib.orc_pgs_no_sweep.argtypes = [C.c_int, P, P, P, P, P, C.c_int]
         _lib.orc_pgs_mc.restype = C.c_int
         _lib.orc_pgs_mc.argtypes = [C.c_int, P, P, P, C.c_int, P, P, P, C.c_int]
         _lib.orc_pairwise.restype = C.c_int
@@ -208,6 +213,26 @@ def jp_colouring(n, row_ptr, col_idx):
     c = np.zeros(n, np.int32)
     g = lib().orc_jp_colouring(n, _p(rp), _p(ci), _p(c))
     return c, g
+
+
+PGS_NO_CHUNK = 16  # rows per chunk of the PGS-NO sweep
+
+
+def jacobi_sweep(row_ptr, col_idx, values, b, x):
+    """One PJAC-NO sweep (natural order) from x; returns the new x."""
+    rp, ci, v = _i32(row_ptr), _i32(col_idx), _f64(values)
+    bb, xx = _f64(b), _f64(x).copy()
+    lib().orc_jacobi_sweep(len(rp) - 1, _p(rp), _p(ci), _p(v), _p(bb), _p(xx))
+    return xx
+
+
+def pgs_no_sweep(row_ptr, col_idx, values, b, x, forward=True):
+    """One PGS-NO sweep (chunks of PGS_NO_CHUNK rows, Gauss-Seidel inside a chunk, the
+    other chunks at their values from the start of the sweep) from x; returns the new x."""
+    rp, ci, v = _i32(row_ptr), _i32(col_idx), _f64(values)
+    bb, xx = _f64(b), _f64(x).copy()
+    lib().orc_pgs_no_sweep(len(rp) - 1, _p(rp), _p(ci), _p(v), _p(bb), _p(xx), int(forward))
+    return xx
 
 
 def pgs_mc(row_ptr, col_idx, values, cptr, b, x, forward=True):

@@ -66,6 +66,7 @@ typedef struct {
   int coarse_hard_max;          // refuse a coarsest level above this size
   int colouring;                // 0 = VerticesGrouping (Alg 4.1/4.2), 1 = greedy in
                                 // Jones-Plassmann priority order (not the paper's)
+  int smoother;                 // AMG smoother: 0 = PGS-MC, 1 = PJAC-NO, 2 = PGS-NO
 } orc_config;
 
 typedef struct {
@@ -517,6 +518,47 @@ void gs_sweep(const Csr& a, const std::vector<int>& cptr, const double* b, doubl
   }
 }
 
+// The smoothers the paper compares PGS-MC with (Section 5.1.1, Table 2), in natural
+// (storage) order.  PJAC-NO: every row from the values at the start of the sweep.
+void jacobi_sweep(const Csr& a, const double* b, double* x) {
+  const std::vector<double> x0(x, x + a.n);
+  for (int i = 0; i < a.n; ++i) {
+    double acc = b[i], d = 0.0;
+    for (int p = a.rp[i]; p < a.rp[i + 1]; ++p) {
+      const int j = a.ci[p];
+      if (j == i)
+        d = a.v[p];
+      else
+        acc -= a.v[p] * x0[j];
+    }
+    x[i] = acc / d;
+  }
+}
+
+// PGS-NO, read as the deterministic hybrid form of a Gauss-Seidel run in parallel in
+// natural order: chunks of kPgsNoChunk consecutive rows are swept at the same time,
+// each in order (forward) or reverse order (backward) with its own rows' new values and
+// the other rows' values from the start of the sweep.
+constexpr int kPgsNoChunk = 16;
+void pgs_no_sweep(const Csr& a, const double* b, double* x, bool forward) {
+  const std::vector<double> x0(x, x + a.n);
+  for (int c0 = 0; c0 < a.n; c0 += kPgsNoChunk) {
+    const int c1 = std::min(c0 + kPgsNoChunk, a.n);
+    for (int t = 0; t < c1 - c0; ++t) {
+      const int i = forward ? c0 + t : c1 - 1 - t;
+      double acc = b[i], d = 0.0;
+      for (int p = a.rp[i]; p < a.rp[i + 1]; ++p) {
+        const int j = a.ci[p];
+        if (j == i)
+          d = a.v[p];
+        else
+          acc -= a.v[p] * ((j >= c0 && j < c1) ? x[j] : x0[j]);
+      }
+      x[i] = acc / d;
+    }
+  }
+}
+
 // r = b - A x
 void residual_csr(const Csr& a, const double* b, const double* x, double* r) {
   for (int i = 0; i < a.n; ++i) {
@@ -707,7 +749,13 @@ int value_setup(Handle& h) {
     if ((double)nc > 0.9 * (double)F.A.n) break;  // coarsening stalled
     Csr Ac = galerkin(F.A, agg, nc);
     Level C;
-    if (nc > h.cfg.coarse_max && l + 2 < h.cfg.max_levels) {
+    if (nc > h.cfg.coarse_max && l + 2 < h.cfg.max_levels && h.cfg.smoother != 0) {
+      // PJAC-NO / PGS-NO need no colouring: natural order, one class
+      C.perm.resize(nc);
+      for (int i = 0; i < nc; ++i) C.perm[i] = i;
+      C.cptr = {0, nc};
+      C.A = std::move(Ac);
+    } else if (nc > h.cfg.coarse_max && l + 2 < h.cfg.max_levels) {
       Csr Sc = adjacency(nc, Ac.rp.data(), Ac.ci.data());
       std::vector<int> colour;
       int g = h.cfg.colouring == 1 ? jp_greedy_colouring(Sc, colour)
@@ -835,14 +883,22 @@ void vcycle(const Handle& h, int l, const double* b, double* x) {
     dense_lu_solve(n, h.coarse_lu, h.coarse_piv, b, x);
     return;
   }
+  auto smooth = [&](bool forward) {
+    if (h.cfg.smoother == 1)
+      jacobi_sweep(L.A, b, x);
+    else if (h.cfg.smoother == 2)
+      pgs_no_sweep(L.A, b, x, forward);
+    else
+      gs_sweep(L.A, L.cptr, b, x, forward);
+  };
   std::fill(x, x + n, 0.0);
-  for (int s = 0; s < h.cfg.pre_sweeps; ++s) gs_sweep(L.A, L.cptr, b, x, true);
+  for (int s = 0; s < h.cfg.pre_sweeps; ++s) smooth(true);
   std::vector<double> r(n), bc(L.nc, 0.0), xc(L.nc);
   residual_csr(L.A, b, x, r.data());
   for (int i = 0; i < n; ++i) bc[L.agg[i]] += r[i];  // restriction P^T r
   vcycle(h, l + 1, bc.data(), xc.data());
   for (int i = 0; i < n; ++i) x[i] += xc[L.agg[i]];  // prolongation by injection
-  for (int s = 0; s < h.cfg.post_sweeps; ++s) gs_sweep(L.A, L.cptr, b, x, false);
+  for (int s = 0; s < h.cfg.post_sweeps; ++s) smooth(false);
 }
 
 // w += Pi_N B_N Pi_N^T r : block GS on the (b-1)x(b-1) sub-blocks, colour order, x0 = 0
@@ -1100,6 +1156,7 @@ void orc_config_default(orc_config* c) {
   c->agg_seed = 0x2208085940ULL;
   c->coarse_hard_max = 20000;
   c->colouring = 0;
+  c->smoother = 0;
 }
 
 void* orc_create(const orc_config* cfg, int nb, int b, const int* rp, const int* ci,
@@ -1280,6 +1337,27 @@ int orc_bilu_pivots(void* p, double* out) {
 }
 
 // Standalone Algorithm 4.2 on a pattern: colour[v] in 1..g; returns g.
+// Standalone PJAC-NO / PGS-NO sweeps on a CSR matrix (x updated in place).
+void orc_jacobi_sweep(int n, const int* rp, const int* ci, const double* v, const double* b,
+                      double* x) {
+  Csr a;
+  a.n = n;
+  a.rp.assign(rp, rp + n + 1);
+  a.ci.assign(ci, ci + rp[n]);
+  a.v.assign(v, v + rp[n]);
+  jacobi_sweep(a, b, x);
+}
+
+void orc_pgs_no_sweep(int n, const int* rp, const int* ci, const double* v, const double* b,
+                      double* x, int forward) {
+  Csr a;
+  a.n = n;
+  a.rp.assign(rp, rp + n + 1);
+  a.ci.assign(ci, ci + rp[n]);
+  a.v.assign(v, v + rp[n]);
+  pgs_no_sweep(a, b, x, forward != 0);
+}
+
 int orc_jp_colouring(int n, const int* rp, const int* ci, int* colour) {
   Csr S = adjacency(n, rp, ci);
   std::vector<int> c;

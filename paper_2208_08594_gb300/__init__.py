@@ -10,7 +10,8 @@ from __future__ import annotations
 from . import _native
 from ._native import (MSP_NOT_CONVERGED, MSP_OK, MSP_PREC_MSP, MSP_PREC_N_ONLY, MSP_PREC_NONE,
                       MSP_PREC_P_ONLY, MSP_PREC_R_ONLY, MSP_PRECISION_FP32, MSP_PRECISION_FP64,
-                      MSP_COLOURING_ALG41, MSP_COLOURING_JP,
+                      MSP_COLOURING_ALG41, MSP_COLOURING_JP, MSP_SMOOTHER_PGS_MC,
+                      MSP_SMOOTHER_PJAC, MSP_SMOOTHER_PGS_NO,
                       MspError, msp_apply_precond, msp_colour0, msp_config_default, msp_free,
                       msp_level_get, msp_level_info, msp_num_levels, msp_setup, msp_solve,
                       msp_solve_host, msp_spmv, msp_status_string, msp_update_values,
@@ -26,7 +27,8 @@ __all__ = ["Solver", "MspError", "msp_setup", "msp_update_values", "msp_update_v
            "msp_level_info", "msp_level_get", "msp_colour0", "msp_config_default",
            "msp_status_string", "MSP_OK", "MSP_NOT_CONVERGED", "MSP_PREC_MSP", "MSP_PREC_NONE",
            "MSP_PREC_R_ONLY", "MSP_PREC_P_ONLY", "MSP_PREC_N_ONLY", "MSP_PRECISION_FP64",
-           "MSP_PRECISION_FP32", "MSP_COLOURING_ALG41", "MSP_COLOURING_JP"]
+           "MSP_PRECISION_FP32", "MSP_COLOURING_ALG41", "MSP_COLOURING_JP",
+           "MSP_SMOOTHER_PGS_MC", "MSP_SMOOTHER_PJAC", "MSP_SMOOTHER_PGS_NO"]
 
 
 class Solver:

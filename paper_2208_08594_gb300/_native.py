@@ -21,6 +21,7 @@ MSP_ERR_TIMEOUT, MSP_ERR_CUDA = -7, -8
 MSP_PREC_MSP, MSP_PREC_NONE, MSP_PREC_R_ONLY, MSP_PREC_P_ONLY, MSP_PREC_N_ONLY = 0, 1, 2, 3, 4
 MSP_PRECISION_FP64, MSP_PRECISION_FP32 = 0, 1
 MSP_COLOURING_ALG41, MSP_COLOURING_JP = 0, 1
+MSP_SMOOTHER_PGS_MC, MSP_SMOOTHER_PJAC, MSP_SMOOTHER_PGS_NO = 0, 1, 2
 
 # every entry point declared in include/msp.h
 EXPORTS = ("msp_config_default", "msp_setup", "msp_update_values", "msp_update_values_host",
@@ -41,7 +42,8 @@ class MspConfig(C.Structure):
                 ("post_sweeps", C.c_int), ("bgs_sweeps", C.c_int), ("decoupling", C.c_int),
                 ("bilu_order", C.c_int), ("precond", C.c_int), ("max_levels", C.c_int),
                 ("beta", C.c_double), ("agg_seed", C.c_ulonglong),
-                ("coarse_hard_max", C.c_int), ("precision", C.c_int), ("colouring", C.c_int)]
+                ("coarse_hard_max", C.c_int), ("precision", C.c_int), ("colouring", C.c_int),
+                ("smoother", C.c_int)]
 
 
 class MspSolveInfo(C.Structure):

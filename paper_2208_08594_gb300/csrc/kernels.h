@@ -66,6 +66,15 @@ int launch_ell_residual_restrict(int K, int nc, const int* mptr, const int* memb
                                  const int* ell_ci, const T* ell_v, const int* meta,
                                  const T* diag, const int* rp, const int* ci, const T* v,
                                  const T* b, const T* x, T* bc, cudaStream_t s);
+// PJAC-NO and PGS-NO sweeps in storage order (x0: the values at the start of the sweep,
+// a separate copy; PGS-NO sweeps chunks of 16 consecutive rows)
+template <typename T>
+int launch_jacobi_sweep(int n, const int* rp, const int* ci, const T* v, const int* dpos,
+                        const T* rdiag, const T* b, const T* x0, T* x, cudaStream_t s);
+template <typename T>
+int launch_pgs_no_sweep(int n, const int* rp, const int* ci, const T* v, const int* dpos,
+                        const T* rdiag, const T* b, const T* x0, T* x, bool forward,
+                        cudaStream_t s);
 template <typename T>
 int launch_csr_residual_restrict(int nc, const int* mptr, const int* members, const int* rp,
                                  const int* ci, const T* v, const T* b, const T* x, T* bc,

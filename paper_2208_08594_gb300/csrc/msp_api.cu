@@ -330,9 +330,9 @@ struct Level {
   DevBuf<double> ell_v, ell_diag;
   // FP32 copies (mixed precision)
   DevBuf<float> v32, rdiag32, ell_v32, ell_diag32;
-  // work vectors
-  DevBuf<double> b64, x64;
-  DevBuf<float> b32, x32;
+  // work vectors (t: the start values of a PJAC-NO / PGS-NO sweep)
+  DevBuf<double> b64, x64, t64;
+  DevBuf<float> b32, x32, t32;
 };
 
 }  // namespace
@@ -646,6 +646,8 @@ int level_extras(msp_handle h, Level& L, bool smoothed, bool ell, cudaStream_t s
   }
   MSP_TRY(L.b64.alloc(L.A.n));
   MSP_TRY(L.x64.alloc(L.A.n));
+  const bool copies = smoothed && h->cfg.smoother != MSP_SMOOTHER_PGS_MC;
+  if (copies) MSP_TRY(L.t64.alloc(L.A.n));
   if (h->cfg.precision == MSP_PRECISION_FP32) {
     MSP_TRY(L.v32.alloc(L.A.nnz));
     MSP_TRY(L.rdiag32.alloc(L.A.n));
@@ -659,6 +661,7 @@ int level_extras(msp_handle h, Level& L, bool smoothed, bool ell, cudaStream_t s
     }
     MSP_TRY(L.b32.alloc(L.A.n));
     MSP_TRY(L.x32.alloc(L.A.n));
+    if (copies) MSP_TRY(L.t32.alloc(L.A.n));
   }
   return MSP_OK;
 }
@@ -773,7 +776,8 @@ int value_setup(msp_handle h, cudaStream_t s) {
     Level C;
     DevBuf<int> ipc;
     MSP_TRY(ipc.alloc(nc));
-    if (nc > cfg.coarse_max && l + 2 < cfg.max_levels) {
+    const bool smoothed = nc > cfg.coarse_max && l + 2 < cfg.max_levels;
+    if (smoothed && cfg.smoother == MSP_SMOOTHER_PGS_MC) {
       DevBuf<int> colour;
       int g = 0;
       {
@@ -797,6 +801,7 @@ int value_setup(msp_handle h, cudaStream_t s) {
       MSP_TRY(launch_iota(nc, C.perm.p, s));
       MSP_TRY(launch_iota(nc, ipc.p, s));
       C.A = std::move(Ac);
+      if (smoothed) C.cptr = {0, nc};  // PJAC-NO / PGS-NO: natural order, one class
     }
     Level& F = h->levels[l];
     MSP_TRY(F.agg.alloc(nF));
@@ -871,7 +876,7 @@ struct PView {
   const T *vals, *c0, *omega, *aN, *dNinv, *lu, *uinv;
   // per level: values, 1/diagonal, ELL values, diagonal
   std::vector<const T*> lv, lrd, lev, led;
-  std::vector<T*> lb, lx;
+  std::vector<T*> lb, lx, lt;
   T *r, *y, *x;
 };
 
@@ -891,6 +896,7 @@ PView<double> view64(msp_handle h) {
     p.led.push_back(L.ell_diag.p);
     p.lb.push_back(L.b64.p);
     p.lx.push_back(L.x64.p);
+    p.lt.push_back(L.t64.p);
   }
   p.r = h->pr.p;
   p.y = h->py.p;
@@ -914,6 +920,7 @@ PView<float> view32(msp_handle h) {
     p.led.push_back(L.ell_diag32.p);
     p.lb.push_back(L.b32.p);
     p.lx.push_back(L.x32.p);
+    p.lt.push_back(L.t32.p);
   }
   p.r = h->pr32.p;
   p.y = h->py32.p;
@@ -991,8 +998,25 @@ int vcycle(msp_handle h, const PView<T>& P, int l, cudaStream_t s) {
     }
     return MSP_OK;
   };
+  // PJAC-NO / PGS-NO (Section 5.1.1): every sweep reads the values from its start (a copy)
+  const bool natural = h->cfg.smoother != MSP_SMOOTHER_PGS_MC;
+  auto natural_sweep = [&](bool forward, bool from_zero) -> int {
+    if (from_zero) MSP_CUDA_TRY(cudaMemsetAsync(P.lx[l], 0, n * sizeof(T), s));
+    MSP_CUDA_TRY(cudaMemcpyAsync(P.lt[l], P.lx[l], n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    const double bytes = (double)L.A.nnz * (sT + 4) + (double)n * (4 * sT + 12);
+    if (h->cfg.smoother == MSP_SMOOTHER_PJAC) {
+      Probe pr(level_site("amg_pjac_l", l), bytes, s);
+      return launch_jacobi_sweep<T>(n, L.A.rp.p, L.A.ci.p, P.lv[l], L.dpos.p, P.lrd[l], P.lb[l],
+                                    P.lt[l], P.lx[l], s);
+    }
+    Probe pr(level_site("amg_pgs_no_l", l), bytes, s);
+    return launch_pgs_no_sweep<T>(n, L.A.rp.p, L.A.ci.p, P.lv[l], L.dpos.p, P.lrd[l], P.lb[l],
+                                  P.lt[l], P.lx[l], forward, s);
+  };
   if (h->cfg.pre_sweeps <= 0) MSP_CUDA_TRY(cudaMemsetAsync(P.lx[l], 0, n * sizeof(T), s));
-  {
+  if (natural) {
+    for (int sw = 0; sw < h->cfg.pre_sweeps; ++sw) MSP_TRY(natural_sweep(true, sw == 0));
+  } else {
     std::vector<SweepLaunch> order;
     for (int sw = 0; sw < h->cfg.pre_sweeps; ++sw)
       for (int c = 0; c < g; ++c) order.push_back({c, sw == 0});
@@ -1019,7 +1043,9 @@ int vcycle(msp_handle h, const PView<T>& P, int l, cudaStream_t s) {
     Probe pr("amg_prolong", (double)n * (3 * sT + 4), s);
     MSP_TRY(launch_prolong_add<T>(n, L.agg.p, P.lx[l + 1], P.lx[l], s));
   }
-  {
+  if (natural) {
+    for (int sw = 0; sw < h->cfg.post_sweeps; ++sw) MSP_TRY(natural_sweep(false, false));
+  } else {
     std::vector<SweepLaunch> order;
     for (int sw = 0; sw < h->cfg.post_sweeps; ++sw)
       for (int c = g - 1; c >= 0; --c) order.push_back({c, false});
@@ -1485,7 +1511,8 @@ bool config_ok(const msp_config& c, int b) {
          c.bgs_sweeps >= 0 && c.bilu_order == 0 && c.precond >= 0 && c.precond <= 4 &&
          c.max_levels >= 1 && c.beta >= 0.0 && c.coarse_hard_max >= 1 &&
          (c.precision == MSP_PRECISION_FP64 || c.precision == MSP_PRECISION_FP32) &&
-         (c.colouring == MSP_COLOURING_ALG41 || c.colouring == MSP_COLOURING_JP) && b >= 1 &&
+         (c.colouring == MSP_COLOURING_ALG41 || c.colouring == MSP_COLOURING_JP) &&
+         c.smoother >= MSP_SMOOTHER_PGS_MC && c.smoother <= MSP_SMOOTHER_PGS_NO && b >= 1 &&
          b <= 8;
 }
 
@@ -1515,6 +1542,7 @@ int msp_config_default(msp_config* c) {
   c->coarse_hard_max = 20000;
   c->precision = MSP_PRECISION_FP64;
   c->colouring = MSP_COLOURING_ALG41;
+  c->smoother = MSP_SMOOTHER_PGS_MC;
   return MSP_OK;
 }
 

@@ -517,6 +517,73 @@ __global__ void __launch_bounds__(kThreads) ell_residual_restrict_kernel(
   }
 }
 
+// The smoothers Section 5.1.1 compares PGS-MC with, in natural (storage) order.
+// PJAC-NO: x_i = (b_i - sum_{j != i} a_ij x0_j) / a_ii for every row (x0: the values at
+// the start of the sweep, a separate copy).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) jacobi_sweep_kernel(
+    int n, const int* __restrict__ rp, const int* __restrict__ ci, const T* __restrict__ v,
+    const int* __restrict__ dpos, const T* __restrict__ rdiag, const T* __restrict__ b,
+    const T* __restrict__ x0, T* __restrict__ x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1), pd = __ldg(dpos + i);
+    T s = T(0);
+    for (int p = p0; p < p1; ++p)
+      if (p != pd) s = fma(__ldg(v + p), __ldg(x0 + __ldg(ci + p)), s);
+    x[i] = (__ldg(b + i) - s) * __ldg(rdiag + i);
+  }
+}
+
+// PGS-NO: Gauss-Seidel through each chunk of kPgsNoChunk consecutive rows in order
+// (forward) or reverse order (backward) with the chunk's new values; rows of other chunks
+// are read at their values from the start of the sweep (x0).  One lane per row, two
+// chunks per warp: every lane first sums its row's terms outside the chunk (all at
+// once), then the chunk's rows take their turn one after another, each adding its
+// terms inside the chunk (warp barrier between turns, so each sees the rows before it).
+constexpr int kPgsNoChunk = 16;
+template <typename T>
+__global__ void __launch_bounds__(kThreads) pgs_no_sweep_kernel(
+    int n, const int* __restrict__ rp, const int* __restrict__ ci, const T* __restrict__ v,
+    const int* __restrict__ dpos, const T* __restrict__ rdiag, const T* __restrict__ b,
+    const T* __restrict__ x0, T* x, bool forward) {
+  static_assert(kWarp % kPgsNoChunk == 0, "whole chunks per warp");
+  constexpr int kPerWarp = kWarp / kPgsNoChunk;
+  const int nchunks = (n + kPgsNoChunk - 1) / kPgsNoChunk;
+  const int t = threadIdx.x % kPgsNoChunk;
+  const int warps = gridDim.x * (blockDim.x / kWarp);
+  const int wid = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
+  // the loop bound depends on the warp only: every lane reaches the warp barriers
+  for (int wbase = wid * kPerWarp; wbase < nchunks; wbase += warps * kPerWarp) {
+    const int c = wbase + (threadIdx.x % kWarp) / kPgsNoChunk;
+    const int c0 = c * kPgsNoChunk, c1 = min(c0 + kPgsNoChunk, n);
+    const int i = c0 + t;
+    const bool active = c < nchunks && i < c1;
+    T off = T(0), bi = T(0), di = T(0);
+    int p0 = 0, p1 = 0;
+    if (active) {
+      p0 = __ldg(rp + i);
+      p1 = __ldg(rp + i + 1);
+      bi = __ldg(b + i);
+      di = __ldg(rdiag + i);
+      for (int p = p0; p < p1; ++p) {
+        const int j = __ldg(ci + p);
+        if (j < c0 || j >= c1) off = fma(__ldg(v + p), __ldg(x0 + j), off);
+      }
+    }
+    for (int turn = 0; turn < kPgsNoChunk; ++turn) {
+      if (active && t == (forward ? turn : kPgsNoChunk - 1 - turn)) {
+        T s = off;
+        for (int p = p0; p < p1; ++p) {
+          const int j = __ldg(ci + p);
+          if (j >= c0 && j < c1 && j != i) s = fma(__ldg(v + p), x[j], s);
+        }
+        x[i] = (bi - s) * di;
+      }
+      __syncwarp();
+    }
+  }
+}
+
 // one group of TPR lanes per coarse row I; members of I processed in ascending order
 template <typename T, int TPR>
 __global__ void __launch_bounds__(kThreads) csr_residual_restrict_kernel(
@@ -984,6 +1051,26 @@ int launch_csr_residual_restrict(int nc, const int* mptr, const int* members, co
 }
 
 template <typename T>
+int launch_jacobi_sweep(int n, const int* rp, const int* ci, const T* v, const int* dpos,
+                        const T* rdiag, const T* b, const T* x0, T* x, cudaStream_t s) {
+  if (n <= 0) return MSP_OK;
+  jacobi_sweep_kernel<T><<<grid_for(n, kThreads), kThreads, 0, s>>>(n, rp, ci, v, dpos, rdiag,
+                                                                      b, x0, x);
+  return launch_status();
+}
+
+template <typename T>
+int launch_pgs_no_sweep(int n, const int* rp, const int* ci, const T* v, const int* dpos,
+                        const T* rdiag, const T* b, const T* x0, T* x, bool forward,
+                        cudaStream_t s) {
+  if (n <= 0) return MSP_OK;
+  const size_t lanes = (size_t)((n + kPgsNoChunk - 1) / kPgsNoChunk) * kPgsNoChunk;
+  pgs_no_sweep_kernel<T><<<grid_for(lanes, kThreads), kThreads, 0, s>>>(n, rp, ci, v, dpos,
+                                                                        rdiag, b, x0, x, forward);
+  return launch_status();
+}
+
+template <typename T>
 int launch_ell_residual_restrict(int K, int nc, const int* mptr, const int* members,
                                  const int* ell_ci, const T* ell_v, const int* meta,
                                  const T* diag, const int* rp, const int* ci, const T* v,
@@ -1137,6 +1224,10 @@ int launch_scatter_blocks(int nb, int b, const int* perm, const double* in, doub
                                                const T*, const int*, const T*, const int*,  \
                                                const int*, const T*, const T*, const T*, T*, \
                                                cudaStream_t);                               \
+  template int launch_jacobi_sweep<T>(int, const int*, const int*, const T*, const int*,    \
+                                      const T*, const T*, const T*, T*, cudaStream_t);      \
+  template int launch_pgs_no_sweep<T>(int, const int*, const int*, const T*, const int*,    \
+                                      const T*, const T*, const T*, T*, bool, cudaStream_t); \
   template int launch_csr_residual_restrict<T>(int, const int*, const int*, const int*,     \
                                                const int*, const T*, const T*, const T*,    \
                                                T*, int, cudaStream_t);                      \

@@ -210,6 +210,37 @@ def test_jp_colouring_option_matches_oracle(name):
     o.close()
 
 
+@pytest.mark.parametrize("smoother", ["PJAC", "PGS_NO"])
+@pytest.mark.parametrize("name", ["spe10_like_b4", "wells_b2"])
+def test_alternative_smoothers_match_oracle(name, smoother):
+    """PJAC-NO and PGS-NO as the AMG smoother (Section 5.1.1): the uncoloured hierarchy
+    bit-exact, application and solve in tolerance."""
+    a, cfg = CASES[name]()
+    sm = getattr(msp, "MSP_SMOOTHER_" + smoother)
+    g, o = _pair(a, smoother=sm, **cfg)
+    assert g.num_levels == o.num_levels
+    for l in range(o.num_levels):
+        lg, lo = g.level(l), o.level(l)
+        for key in ("perm", "cptr", "agg", "row_ptr", "col_idx"):
+            assert np.array_equal(lg[key], lo[key]), (l, key)
+        assert np.array_equal(lg["values"], lo["values"]), l
+        if 0 < l < o.num_levels - 1:
+            assert lg["ncolours"] == 1
+    for seed in (1, 2):
+        x = random_rhs(a, seed)
+        w = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+        g.apply_precond(_vec(x), w)
+        ref = o.apply_precond(x)
+        assert np.abs(w.cpu().numpy() - ref).max() / np.abs(ref).max() <= TOL_APPLY
+    rhs = random_rhs(a, 11)
+    xd = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+    info = g.solve(_vec(rhs), xd, 1e-6)
+    _, io = o.solve(rhs, 1e-6)
+    assert info["status"] == 0 and abs(info["iterations"] - io["iterations"]) <= 1
+    g.close()
+    o.close()
+
+
 def test_zero_and_nonfinite_rhs():
     a = grid_spe10(nx=6, ny=5, nz=4)
     g, _ = _pair(a, coarse_max=20)

@@ -143,3 +143,66 @@ def test_stage_n_is_block_gs_on_concentration_subsystem():
     rhs = gvec.reshape(a.nb, a.b)[perm][:, 1:].reshape(-1)
     ref = np.linalg.solve(L, rhs).reshape(a.nb, bn)
     assert np.allclose(w[perm][:, 1:], ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+# ---- the smoothers the paper compares PGS-MC with (Section 5.1.1, Table 2)
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_jacobi_sweep_closed_form(seed):
+    """PJAC-NO: x1 = D^-1 (b - (A - D) x0); from zero it is D^-1 b."""
+    m, a = _scalar_pressure_like(seed)
+    rng = np.random.default_rng(seed)
+    b, x0 = rng.normal(size=m.shape[0]), rng.normal(size=m.shape[0])
+    d = m.diagonal()
+    x = oracle.jacobi_sweep(m.indptr, m.indices, m.data, b, x0)
+    ref = (b - (m @ x0 - d * x0)) / d
+    assert np.allclose(x, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+    x = oracle.jacobi_sweep(m.indptr, m.indices, m.data, b, np.zeros_like(b))
+    assert np.allclose(x, b / d, rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("seed,forward", [(1, True), (2, False), (3, True)])
+def test_pgs_no_sweep_is_block_jacobi_of_triangular_solves(seed, forward):
+    """PGS-NO: every chunk of 16 rows solves its lower (forward) or upper (backward)
+    triangle with the rest of its rows and the other chunks at their old values."""
+    m, a = _scalar_pressure_like(seed)
+    n = m.shape[0]
+    rng = np.random.default_rng(seed)
+    b, x0 = rng.normal(size=n), rng.normal(size=n)
+    x = oracle.pgs_no_sweep(m.indptr, m.indices, m.data, b, x0, forward)
+    c = oracle.PGS_NO_CHUNK
+    ref = np.empty(n)
+    for c0 in range(0, n, c):
+        c1 = min(c0 + c, n)
+        blk = m[c0:c1, c0:c1].tocsr()
+        rhs = b[c0:c1] - (m[c0:c1] @ x0 - blk @ x0[c0:c1])     # other chunks, old values
+        tri = sp.tril(blk) if forward else sp.triu(blk)
+        rhs = rhs - (blk - tri) @ x0[c0:c1]                      # own rows not yet swept
+        ref[c0:c1] = spl.spsolve_triangular(tri.tocsr(), rhs, lower=forward)
+    assert np.allclose(x, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_pgs_no_on_one_chunk_is_gauss_seidel_and_on_diagonal_is_jacobi():
+    m, a = _scalar_pressure_like(4, dims=(4, 2, 2))   # 16 cells + 2 wells: one chunk + 2 rows
+    n = m.shape[0]
+    b = np.random.default_rng(4).normal(size=n)
+    x = oracle.pgs_no_sweep(m.indptr, m.indices, m.data, b, np.zeros(n), True)
+    sub = m[:16, :16].tocsr()
+    ref = spl.spsolve_triangular(sp.tril(sub).tocsr(), b[:16], lower=True)
+    assert np.allclose(x[:16], ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+    dg = sp.diags(np.arange(1.0, 41.0)).tocsr()
+    bd = np.ones(40)
+    assert np.allclose(oracle.pgs_no_sweep(dg.indptr, dg.indices, dg.data, bd, np.zeros(40)),
+                       bd / np.arange(1.0, 41.0))
+
+
+@pytest.mark.parametrize("smoother", [1, 2])
+def test_alternative_smoothers_solve(smoother):
+    """MSP-GMRES with PJAC-NO or PGS-NO in the AMG still solves to tolerance; the coarse
+    levels are kept in natural order as one class."""
+    a = box_jacobian(9, 7, 6, 3, 11, layered=True, kz_ratio=0.1, n_wells=1)
+    o = oracle.Oracle(a, coarse_max=40, smoother=smoother)
+    for l in range(1, o.num_levels - 1):
+        assert o.level(l)["ncolours"] == 1
+    x, info = o.solve(random_rhs(a, 2))
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-6
