@@ -65,6 +65,17 @@ def lib():
         _lib.orc_vertices_grouping.argtypes = [C.c_int, P, P, P]
         _lib.orc_jp_colouring.restype = C.c_int
         _lib.orc_jp_colouring.argtypes = [C.c_int, P, P, P]
+        _lib.orc_wells_create.restype = P
+        _lib.orc_wells_create.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P,
+                                          C.POINTER(C.c_int)]
+        _lib.orc_wells_free.argtypes = [P]
+        _lib.orc_wells_nnzb.restype = C.c_int
+        _lib.orc_wells_nnzb.argtypes = [P]
+        _lib.orc_wells_get.argtypes = [P, P, P, P]
+        _lib.orc_wells_update_values.restype = C.c_int
+        _lib.orc_wells_update_values.argtypes = [P, P]
+        _lib.orc_wells_reduce_rhs.argtypes = [P, P, P]
+        _lib.orc_wells_recover.argtypes = [P, P, P, P]
         _lib.orc_jacobi_sweep.restype = None
         _lib.orc_jacobi_sweep.argtypes = [C.c_int, P, P, P, P, P]
         _lib.orc_pgs_no_sweep.restype = None
@@ -213,6 +224,60 @@ def jp_colouring(n, row_ptr, col_idx):
     c = np.zeros(n, np.int32)
     g = lib().orc_jp_colouring(n, _p(rp), _p(ci), _p(c))
     return c, g
+
+
+class Wells:
+    """Elimination of the last ``n_wells`` block rows (the well unknowns of Eq.
+    Jacobian-system): the Schur complement on the reservoir rows, the reduced right-hand
+    side and the recovery of the well unknowns."""
+
+    def __init__(self, a, n_wells):
+        self.nb, self.b, self.nw = int(a.nb), int(a.b), int(n_wells)
+        self.nr = self.nb - self.nw
+        self._rp, self._ci = _i32(a.row_ptr), _i32(a.col_idx)
+        v = _f64(a.values)
+        st = C.c_int(0)
+        self._h = lib().orc_wells_create(self.nb, self.b, self.nw, _p(self._rp), _p(self._ci),
+                                         _p(v), C.byref(st))
+        if not self._h:
+            raise OracleError("orc_wells_create failed with status %d" % st.value)
+
+    def close(self):
+        if self._h:
+            lib().orc_wells_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reduced(self):
+        """(row_ptr, col_idx, values) of the Schur complement (nr block rows)."""
+        nnzb = lib().orc_wells_nnzb(self._h)
+        rp = np.zeros(self.nr + 1, np.int32)
+        ci = np.zeros(nnzb, np.int32)
+        v = np.zeros(nnzb * self.b * self.b)
+        lib().orc_wells_get(self._h, _p(rp), _p(ci), _p(v))
+        return rp, ci, v
+
+    def update_values(self, values):
+        v = _f64(values)
+        if lib().orc_wells_update_values(self._h, _p(v)) != 0:
+            raise OracleError("orc_wells_update_values")
+
+    def reduce_rhs(self, g):
+        g = _f64(g)
+        gs = np.zeros(self.nr * self.b)
+        lib().orc_wells_reduce_rhs(self._h, _p(g), _p(gs))
+        return gs
+
+    def recover(self, g, xs):
+        g, xs = _f64(g), _f64(xs)
+        x = np.zeros(self.nb * self.b)
+        lib().orc_wells_recover(self._h, _p(g), _p(xs), _p(x))
+        return x
 
 
 PGS_NO_CHUNK = 16  # rows per chunk of the PGS-NO sweep

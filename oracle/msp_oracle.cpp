@@ -1134,6 +1134,109 @@ int check_pattern(int nb, const int* rp, const int* ci) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------------
+// Eliminating the well unknowns (Eq. Jacobian-system: reservoir rows R first, well rows
+// W last): the Schur complement A_S = A_RR - A_RW A_WW^{-1} A_WR on the reservoir rows,
+// the right-hand side g_R - A_RW A_WW^{-1} g_W, and afterwards
+// x_W = A_WW^{-1} (g_W - A_WR x_R).  A_WW must be block diagonal (wells not coupled to
+// each other) and every reservoir row may couple to one well at most.
+// ---------------------------------------------------------------------------------
+struct Wells {
+  int nb = 0, b = 0, nw = 0, nr = 0;  // block rows: all, wells (the last nw), reservoir
+  Bsr A;                              // the full matrix (current values)
+  Bsr S;                              // the reduced matrix on the reservoir rows
+  std::vector<double> winv;           // nw b x b: A_WW^{-1}
+  std::vector<int> well_of, cw_pos;   // reservoir row -> its well and the A_RW block, or -1
+  // per reduced nonzero: the A_RR block (or -1), the well (or -1), the A_RW and A_WR blocks
+  std::vector<int> s_orig, s_well, s_cw, s_wc;
+};
+
+int find_block(const Bsr& A, int i, int j) {
+  const auto b0 = A.ci.begin() + A.rp[i], b1 = A.ci.begin() + A.rp[i + 1];
+  const auto it = std::lower_bound(b0, b1, j);
+  return (it != b1 && *it == j) ? (int)(it - A.ci.begin()) : -1;
+}
+
+int wells_values(Wells& W) {
+  const int b = W.b, bb = b * b;
+  for (int w = 0; w < W.nw; ++w) {
+    const int r = W.nr + w, pd = find_block(W.A, r, r);
+    if (pd < 0 || !gj_inverse(b, &W.A.v[(size_t)pd * bb], &W.winv[(size_t)w * bb]))
+      return ORC_ERR_SINGULAR;
+  }
+  std::vector<double> t(bb);
+  for (size_t p = 0; p < W.s_orig.size(); ++p) {
+    double* out = &W.S.v[p * bb];
+    for (int k = 0; k < bb; ++k) out[k] = W.s_orig[p] >= 0 ? W.A.v[(size_t)W.s_orig[p] * bb + k] : 0.0;
+    if (W.s_well[p] < 0) continue;
+    const double* acw = &W.A.v[(size_t)W.s_cw[p] * bb];
+    const double* wi = &W.winv[(size_t)W.s_well[p] * bb];
+    const double* awc = &W.A.v[(size_t)W.s_wc[p] * bb];
+    for (int r = 0; r < b; ++r)  // t = A_RW A_WW^{-1}
+      for (int c = 0; c < b; ++c) {
+        double acc = 0.0;
+        for (int k = 0; k < b; ++k) acc += acw[r * b + k] * wi[k * b + c];
+        t[r * b + c] = acc;
+      }
+    for (int r = 0; r < b; ++r)  // out -= t A_WR
+      for (int c = 0; c < b; ++c) {
+        double acc = 0.0;
+        for (int k = 0; k < b; ++k) acc += t[r * b + k] * awc[k * b + c];
+        out[r * b + c] -= acc;
+      }
+  }
+  return ORC_OK;
+}
+
+int wells_build(Wells& W) {
+  const int nr = W.nr;
+  const Bsr& A = W.A;
+  W.well_of.assign(nr, -1);
+  W.cw_pos.assign(nr, -1);
+  for (int i = 0; i < W.nb; ++i)
+    for (int p = A.rp[i]; p < A.rp[i + 1]; ++p) {
+      const int j = A.ci[p];
+      if (i >= nr && j >= nr && j != i) return ORC_ERR_ARG;  // wells coupled to each other
+      if (i < nr && j >= nr) {
+        if (W.well_of[i] >= 0) return ORC_ERR_ARG;  // a second well on one cell
+        W.well_of[i] = j - nr;
+        W.cw_pos[i] = p;
+      }
+    }
+  W.S.nb = nr;
+  W.S.b = W.b;
+  W.S.rp.assign(nr + 1, 0);
+  W.S.ci.clear();
+  W.s_orig.clear();
+  W.s_well.clear();
+  W.s_cw.clear();
+  W.s_wc.clear();
+  for (int c = 0; c < nr; ++c) {
+    std::vector<int> cols;
+    for (int p = A.rp[c]; p < A.rp[c + 1]; ++p)
+      if (A.ci[p] < nr) cols.push_back(A.ci[p]);
+    const int w = W.well_of[c];
+    if (w >= 0)
+      for (int p = A.rp[nr + w]; p < A.rp[nr + w + 1]; ++p)
+        if (A.ci[p] < nr) cols.push_back(A.ci[p]);
+    std::sort(cols.begin(), cols.end());
+    cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+    for (int j : cols) {
+      W.S.ci.push_back(j);
+      W.s_orig.push_back(find_block(A, c, j));
+      const int wc = w >= 0 ? find_block(A, nr + w, j) : -1;
+      W.s_well.push_back(wc >= 0 ? w : -1);
+      W.s_cw.push_back(wc >= 0 ? W.cw_pos[c] : -1);
+      W.s_wc.push_back(wc);
+    }
+    W.S.rp[c + 1] = (int)W.S.ci.size();
+  }
+  W.S.v.assign(W.S.ci.size() * (size_t)W.b * W.b, 0.0);
+  W.winv.assign((size_t)W.nw * W.b * W.b, 0.0);
+  return wells_values(W);
+}
+
+
 // =================================================================================
 // C interface (ctypes)
 // =================================================================================
@@ -1356,6 +1459,102 @@ void orc_pgs_no_sweep(int n, const int* rp, const int* ci, const double* v, cons
   a.ci.assign(ci, ci + rp[n]);
   a.v.assign(v, v + rp[n]);
   pgs_no_sweep(a, b, x, forward != 0);
+}
+
+void* orc_wells_create(int nb, int b, int nw, const int* rp, const int* ci, const double* v,
+                       int* status) {
+  *status = ORC_OK;
+  if (nb <= 0 || b <= 0 || nw < 1 || nw >= nb) {
+    *status = ORC_ERR_ARG;
+    return nullptr;
+  }
+  if ((*status = check_pattern(nb, rp, ci)) != ORC_OK) return nullptr;
+  auto* W = new Wells();
+  W->nb = nb;
+  W->b = b;
+  W->nw = nw;
+  W->nr = nb - nw;
+  W->A.nb = nb;
+  W->A.b = b;
+  W->A.rp.assign(rp, rp + nb + 1);
+  W->A.ci.assign(ci, ci + rp[nb]);
+  W->A.v.assign(v, v + (size_t)rp[nb] * b * b);
+  *status = wells_build(*W);
+  if (*status != ORC_OK) {
+    delete W;
+    return nullptr;
+  }
+  return W;
+}
+
+void orc_wells_free(void* h) { delete static_cast<Wells*>(h); }
+
+int orc_wells_nnzb(void* h) { return (int)static_cast<Wells*>(h)->S.ci.size(); }
+
+void orc_wells_get(void* h, int* rp, int* ci, double* v) {
+  const Wells& W = *static_cast<Wells*>(h);
+  std::copy(W.S.rp.begin(), W.S.rp.end(), rp);
+  std::copy(W.S.ci.begin(), W.S.ci.end(), ci);
+  std::copy(W.S.v.begin(), W.S.v.end(), v);
+}
+
+int orc_wells_update_values(void* h, const double* v) {
+  Wells& W = *static_cast<Wells*>(h);
+  std::copy(v, v + W.A.v.size(), W.A.v.begin());
+  return wells_values(W);
+}
+
+// gs = g_R - A_RW A_WW^{-1} g_W
+void orc_wells_reduce_rhs(void* h, const double* g, double* gs) {
+  const Wells& W = *static_cast<Wells*>(h);
+  const int b = W.b, bb = b * b;
+  std::vector<double> y(b);
+  for (int c = 0; c < W.nr; ++c) {
+    for (int k = 0; k < b; ++k) gs[(size_t)c * b + k] = g[(size_t)c * b + k];
+    const int w = W.well_of[c];
+    if (w < 0) continue;
+    const double* wi = &W.winv[(size_t)w * bb];
+    const double* gw = &g[(size_t)(W.nr + w) * b];
+    for (int r = 0; r < b; ++r) {
+      double acc = 0.0;
+      for (int k = 0; k < b; ++k) acc += wi[r * b + k] * gw[k];
+      y[r] = acc;
+    }
+    const double* acw = &W.A.v[(size_t)W.cw_pos[c] * bb];
+    for (int r = 0; r < b; ++r) {
+      double acc = 0.0;
+      for (int k = 0; k < b; ++k) acc += acw[r * b + k] * y[k];
+      gs[(size_t)c * b + r] -= acc;
+    }
+  }
+}
+
+// x_R = xs; x_W = A_WW^{-1} (g_W - A_WR x_R)
+void orc_wells_recover(void* h, const double* g, const double* xs, double* x) {
+  const Wells& W = *static_cast<Wells*>(h);
+  const int b = W.b, bb = b * b;
+  std::copy(xs, xs + (size_t)W.nr * b, x);
+  std::vector<double> r(b);
+  for (int w = 0; w < W.nw; ++w) {
+    const int row = W.nr + w;
+    for (int k = 0; k < b; ++k) r[k] = g[(size_t)row * b + k];
+    for (int p = W.A.rp[row]; p < W.A.rp[row + 1]; ++p) {
+      const int c = W.A.ci[p];
+      if (c == row) continue;
+      const double* awc = &W.A.v[(size_t)p * bb];
+      for (int i = 0; i < b; ++i) {
+        double acc = 0.0;
+        for (int k = 0; k < b; ++k) acc += awc[i * b + k] * xs[(size_t)c * b + k];
+        r[i] -= acc;
+      }
+    }
+    const double* wi = &W.winv[(size_t)w * bb];
+    for (int i = 0; i < b; ++i) {
+      double acc = 0.0;
+      for (int k = 0; k < b; ++k) acc += wi[i * b + k] * r[k];
+      x[(size_t)row * b + i] = acc;
+    }
+  }
 }
 
 int orc_jp_colouring(int n, const int* rp, const int* ci, int* colour) {
