@@ -81,6 +81,9 @@ def parse():
     p.add_argument("--colouring", default="alg41", choices=["alg41", "jp"],
                    help="Algorithms 4.1/4.2 (the paper's) or greedy in Jones-Plassmann "
                         "priority order (parallel rounds)")
+    p.add_argument("--wells", default="rows", choices=["rows", "eliminate"],
+                   help="wells as ordinary block rows of the solved system (default), or "
+                        "eliminated by the Schur complement of A_WW before the solve")
     p.add_argument("--mu", type=int, default=180)
     p.add_argument("--nx", type=int, default=60)
     p.add_argument("--ny", type=int, default=220)
@@ -104,7 +107,8 @@ def workload_name(args):
         "FP32 preconditioner / FP64 Krylov",
         ", Jones-Plassmann-order colouring" if args.colouring == "jp" else "") + (
         ", AMG smoother %s" % {"pjac": "PJAC-NO", "pgs_no": "PGS-NO"}[args.smoother]
-        if args.smoother != "pgs_mc" else "")
+        if args.smoother != "pgs_mc" else "") + (
+        ", wells eliminated (Schur complement)" if args.wells == "eliminate" else "")
 
 
 def colouring_of(args, msp):
@@ -278,8 +282,16 @@ def run_native(args):
 
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    solver = msp.Solver(a.nb, a.b, d_rp, d_ci, d_v0, mu=args.mu, precision=prec,
-                        colouring=colouring_of(args, msp), smoother=smoother_of(args, msp))
+    opts = dict(mu=args.mu, precision=prec, colouring=colouring_of(args, msp),
+                smoother=smoother_of(args, msp))
+    if args.wells == "eliminate":
+        solver = msp.WellEliminatedSolver(a.nb, a.b, a.n_wells, d_rp, d_ci, d_v0, **opts)
+        inner = solver.solver
+        reduced = {"reduced_block_rows": solver.wells.nr,
+                   "reduced_nnzb": int(solver.wells.col_idx.numel())}
+    else:
+        solver = inner = msp.Solver(a.nb, a.b, d_rp, d_ci, d_v0, **opts)
+        reduced = {}
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     nsets = len(d_sets)
@@ -367,10 +379,21 @@ def run_native(args):
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
+        if args.wells == "eliminate":
+            stage_v = torch.empty_like(d_v0)
+            stage_r = torch.empty(a.n, dtype=torch.float64, device=dev)
         for k in range(args.steps):
             kk = (args.warmup + k) % nsets
-            solver.update_values_host(pin_sets[kk].numpy())
-            info = solver.solve_host(pin_rhs[kk].numpy(), pin_x.numpy(), TOL)
+            if args.wells == "eliminate":
+                # the full system's values and right-hand side in, the solution out
+                stage_v.copy_(pin_sets[kk], non_blocking=True)
+                solver.update_values(stage_v)
+                stage_r.copy_(pin_rhs[kk], non_blocking=True)
+                info = solver.solve(stage_r, x, TOL)
+                pin_x.copy_(x, non_blocking=True)
+            else:
+                solver.update_values_host(pin_sets[kk].numpy())
+                info = solver.solve_host(pin_rhs[kk].numpy(), pin_x.numpy(), TOL)
             e2e_infos.append(info)
         f1.record(stream)
         torch.cuda.synchronize()
@@ -381,8 +404,8 @@ def run_native(args):
     ms, e2e_ms = combine_over_ranks([ms, e2e["ms"] if e2e else 0.0])
     if e2e:
         e2e["ms"] = e2e_ms
-    solver_levels = solver.num_levels
-    level_info = [msp.msp_level_info(solver.h, l) for l in range(solver_levels)]
+    solver_levels = inner.num_levels
+    level_info = [msp.msp_level_info(inner.h, l) for l in range(solver_levels)]
     solver.close()
     if world > 1:
         dist.destroy_process_group()
@@ -433,7 +456,7 @@ def run_native(args):
         "dtype": "f64" if args.precision == "fp64" else "f32-precond/f64-krylov",
         "data": "synthetic (seeded SPE10-shaped Jacobian; SPE10 data not available)",
         "config": {"workload": workload_name(args), "cells": args.nx * args.ny * args.nz,
-                   "block_rows": a.nb, "nnzb": a.nnzb, "mu": args.mu,
+                   "block_rows": a.nb, "nnzb": a.nnzb, **reduced, "mu": args.mu,
                    "restart": 30, "tol": TOL, "levels": solver_levels,
                    "level_sizes": [li[0] for li in level_info],
                    "level_nnz": [li[1] for li in level_info],
@@ -468,11 +491,18 @@ def oracle_sample(args, its_mean, setup_frac, steps, warmup):
     setups, seconds per iteration, setup seconds)."""
     import oracle
     from synthetic import grid_spe10, random_rhs
+    from synthetic import BSRMatrix
     a = grid_spe10(seed=2209, nx=args.nx, ny=args.ny, nz=args.nz)
+    rhs = random_rhs(a, 7000)
     t0 = time.perf_counter()
+    if getattr(args, "wells", "rows") == "eliminate":
+        W = oracle.Wells(a, a.n_wells)
+        rp, ci, v = W.reduced()
+        rhs = W.reduce_rhs(rhs)
+        a = BSRMatrix(nb=W.nr, b=a.b, row_ptr=rp, col_idx=ci, values=v.reshape(-1, a.b, a.b),
+                      n_cells=W.nr)
     o = oracle.Oracle(a, mu=10 ** 9)
     setup_s = time.perf_counter() - t0
-    rhs = random_rhs(a, 7000)
     per = []
     for k in range(warmup + steps):
         o.set_max_it(1)

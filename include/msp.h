@@ -236,6 +236,56 @@ int msp_vertices_grouping_noalloc(int32_t n, const int32_t* d_row_ptr, const int
                                   int32_t* d_colour, int32_t* h_ncolours, void* stream);
 const char* msp_noalloc_error(void);
 
+/* ---- Elimination of the well unknowns (Schur complement) ----------------------------
+ * For the Jacobian with implicit wells [A_RR A_RW; A_WR A_WW] (Eq. Jacobian-system,
+ * Section 2.2.4), stored as one BSR matrix whose last nw block rows are the wells:
+ *   A_S = A_RR - A_RW A_WW^-1 A_WR       (reduced matrix on the nr = nb - nw cell rows)
+ *   g_S = g_R - A_RW A_WW^-1 g_W         (msp_wells_reduce_rhs)
+ *   x_W = A_WW^-1 (g_W - A_WR x_R)       (msp_wells_recover, x_R = solution of A_S)
+ * Accepted layout: a cell row couples to at most one well, and a well row to no other
+ * well (A_WW block diagonal); otherwise MSP_ERR_ARG.  Row c of A_S has the columns of
+ * A_RR's row c, plus, where well w perforates c, the cell columns of well row w (so the
+ * cells of one well become mutually coupled).  Each block is formed as
+ * t = A_cw A_ww^-1, then A_RR[c,j] - t A_wj, every b x b product summed over k in order
+ * without fused multiply-add, so it is reproducible bit for bit.  The reduced system is
+ * then handed to msp_setup / msp_update_values / msp_solve like any other matrix. */
+typedef struct msp_wells_s* msp_wells;
+
+/* Analyse the layout, build the pattern of A_S and compute its values, A_WW^-1 and the
+ * blocks the right-hand-side and recovery steps need.  nb >= 2, 1 <= b <= 8,
+ * 1 <= nw < nb, nnzb = row_ptr[nb]; the pattern as for msp_setup.  Errors: MSP_ERR_ARG
+ * (sizes, or a layout not accepted above), MSP_ERR_PATTERN, MSP_ERR_NONFINITE,
+ * MSP_ERR_SINGULAR_BLOCK (a well's diagonal block), MSP_ERR_NOMEM, MSP_ERR_CUDA.
+ * Synchronises the stream.  On error *out is NULL. */
+int msp_wells_setup(msp_wells* out, int32_t nb, int32_t b, int32_t nw,
+                    const int32_t* d_row_ptr, const int32_t* d_col_idx, const double* d_values,
+                    int64_t nnzb, void* stream);
+
+/* The reduced matrix: nr block rows, *nnzb blocks; row_ptr int32[nr+1], col_idx
+ * int32[nnzb], values float64[nnzb*b*b] are DEVICE arrays owned by W, valid until
+ * msp_wells_free; the values change with msp_wells_update_values.  Any output pointer
+ * may be NULL. */
+int msp_wells_reduced(msp_wells W, int32_t* nr, int64_t* nnzb, const int32_t** d_row_ptr,
+                      const int32_t** d_col_idx, const double** d_values);
+
+/* New values of the full matrix (same pattern, nnzb*b*b doubles, device): recomputes
+ * A_S, A_WW^-1 and the kept blocks.  Errors: MSP_ERR_NONFINITE, MSP_ERR_SINGULAR_BLOCK,
+ * MSP_ERR_CUDA.  Synchronises the stream. */
+int msp_wells_update_values(msp_wells W, const double* d_values, void* stream);
+
+/* d_gs[nr*b] = g_R - A_RW A_WW^-1 g_W for d_g[nb*b] (device; may not alias).
+ * Asynchronous on `stream`. */
+int msp_wells_reduce_rhs(msp_wells W, const double* d_g, double* d_gs, void* stream);
+
+/* d_x[nb*b] = [x_R; A_WW^-1 (g_W - A_WR x_R)] with x_R = d_xs[nr*b] (device; d_x may
+ * be d_xs, which must then hold nb*b doubles; d_x may not alias d_g).  The blocks of a
+ * well row are taken in column order.  Asynchronous on `stream`. */
+int msp_wells_recover(msp_wells W, const double* d_g, const double* d_xs, double* d_x,
+                      void* stream);
+
+/* Release W (NULL is accepted); waits for the device to finish its work. */
+int msp_wells_free(msp_wells W);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,9 +17,13 @@ from ._native import (MSP_NOT_CONVERGED, MSP_OK, MSP_PREC_MSP, MSP_PREC_N_ONLY, 
                       msp_solve_host, msp_spmv, msp_status_string, msp_update_values,
                       msp_update_values_host, msp_stats_enable, msp_stats_reset,
                       msp_stats_launches, msp_stats_get, msp_vertices_grouping_noalloc,
-                      NOALLOC_MAX_VERTICES)
+                      NOALLOC_MAX_VERTICES, msp_wells_setup, msp_wells_reduced,
+                      msp_wells_update_values, msp_wells_reduce_rhs, msp_wells_recover,
+                      msp_wells_free)
 
-__all__ = ["Solver", "MspError", "msp_setup", "msp_update_values", "msp_update_values_host",
+__all__ = ["Solver", "Wells", "WellEliminatedSolver", "MspError", "msp_wells_setup",
+           "msp_wells_reduced", "msp_wells_update_values", "msp_wells_reduce_rhs",
+           "msp_wells_recover", "msp_wells_free", "msp_setup", "msp_update_values", "msp_update_values_host",
            "msp_stats_enable", "msp_stats_reset", "msp_stats_launches", "msp_stats_get",
            "msp_vertices_grouping_noalloc", "NOALLOC_MAX_VERTICES",
            "msp_solve",
@@ -81,3 +85,69 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class Wells:
+    """Schur-complement elimination of the well unknowns (the last ``nw`` block rows) of a
+    BSR matrix held in CUDA tensors: ``A_S = A_RR - A_RW A_WW^-1 A_WR`` on the cell rows.
+    ``reduced()`` gives zero-copy views of the reduced matrix (valid while this object
+    lives)."""
+
+    def __init__(self, nb, b, nw, row_ptr, col_idx, values, stream=None):
+        self.nb, self.b, self.nw = int(nb), int(b), int(nw)
+        self.W = msp_wells_setup(self.nb, self.b, self.nw, row_ptr, col_idx, values, stream)
+        self.nr, self.row_ptr, self.col_idx, self.values = msp_wells_reduced(self.W, self.b)
+
+    def reduced(self):
+        return self.row_ptr, self.col_idx, self.values
+
+    def update_values(self, values, stream=None):
+        msp_wells_update_values(self.W, values, stream)
+
+    def reduce_rhs(self, g, gs, stream=None):
+        msp_wells_reduce_rhs(self.W, g, gs, stream)
+
+    def recover(self, g, xs, x, stream=None):
+        msp_wells_recover(self.W, g, xs, x, stream)
+
+    def close(self):
+        if self.W:
+            self.row_ptr = self.col_idx = self.values = None
+            msp_wells_free(self.W)
+            self.W = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class WellEliminatedSolver:
+    """FGMRES + MSP on the reduced system of :class:`Wells`: ``solve`` forms the reduced
+    right-hand side, solves on the cell rows and recovers the well unknowns."""
+
+    def __init__(self, nb, b, nw, row_ptr, col_idx, values, stream=None, **config):
+        import torch
+        self.wells = Wells(nb, b, nw, row_ptr, col_idx, values, stream)
+        rp, ci, v = self.wells.reduced()
+        self.solver = Solver(self.wells.nr, b, rp, ci, v, stream, **config)
+        n = self.wells.nr * b
+        self.gs = torch.empty(n, dtype=torch.float64, device=values.device)
+        self.xs = torch.empty(n, dtype=torch.float64, device=values.device)
+
+    def update_values(self, values, stream=None):
+        self.wells.update_values(values, stream)
+        self.solver.update_values(self.wells.values, stream)
+
+    def solve(self, rhs, x, rel_tol=1e-6, stream=None):
+        """Solve with the full right-hand side ``rhs`` (nb*b) into ``x`` (nb*b); the
+        tolerance applies to the reduced system."""
+        self.wells.reduce_rhs(rhs, self.gs, stream)
+        info = self.solver.solve(self.gs, self.xs, rel_tol, stream)
+        self.wells.recover(rhs, self.xs, x, stream)
+        return info
+
+    def close(self):
+        self.solver.close()
+        self.wells.close()

@@ -30,7 +30,9 @@ EXPORTS = ("msp_config_default", "msp_setup", "msp_update_values", "msp_update_v
            "msp_num_levels", "msp_level_info", "msp_level_get", "msp_colour0",
            "msp_last_error", "msp_stats_enable", "msp_stats_reset", "msp_stats_launches",
            "msp_stats_count", "msp_stats_get", "msp_vertices_grouping_noalloc",
-           "msp_noalloc_error")
+           "msp_noalloc_error", "msp_wells_setup", "msp_wells_reduced",
+           "msp_wells_update_values", "msp_wells_reduce_rhs", "msp_wells_recover",
+           "msp_wells_free")
 
 # largest n accepted by msp_vertices_grouping_noalloc (size of its fixed scratch)
 NOALLOC_MAX_VERTICES = 1 << 16
@@ -106,6 +108,14 @@ def lib(build_if_missing: bool = True):
     L.msp_vertices_grouping_noalloc.argtypes = [C.c_int32, P, P, P, C.POINTER(C.c_int32), P]
     L.msp_noalloc_error.argtypes = []
     L.msp_noalloc_error.restype = C.c_char_p
+    L.msp_wells_setup.argtypes = [C.POINTER(P), C.c_int32, C.c_int32, C.c_int32, P, P, P,
+                                  C.c_int64, P]
+    L.msp_wells_reduced.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_int64),
+                                    C.POINTER(P), C.POINTER(P), C.POINTER(P)]
+    L.msp_wells_update_values.argtypes = [P, P, P]
+    L.msp_wells_reduce_rhs.argtypes = [P, P, P, P]
+    L.msp_wells_recover.argtypes = [P, P, P, P, P]
+    L.msp_wells_free.argtypes = [P]
     for name in EXPORTS:
         if name not in ("msp_status_string", "msp_last_error", "msp_stats_launches",
                         "msp_noalloc_error"):
@@ -299,3 +309,64 @@ def msp_vertices_grouping_noalloc(n: int, row_ptr, col_idx, colour, stream=None)
         raise MspError(st, "msp_vertices_grouping_noalloc: " +
                        lib().msp_noalloc_error().decode())
     return g.value
+
+
+class _DeviceArray:
+    """A device array owned by the library, exposed through __cuda_array_interface__ so
+    that torch.as_tensor makes a zero-copy view of it."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 2}
+
+
+def msp_wells_setup(nb: int, b: int, nw: int, row_ptr, col_idx, values, stream=None):
+    import torch
+    _check_dev(row_ptr, torch.int32, nb + 1, "row_ptr")
+    _check_dev(col_idx, torch.int32, None, "col_idx")
+    nnzb = col_idx.numel()
+    _check_dev(values, torch.float64, nnzb * b * b, "values")
+    W = C.c_void_p()
+    st = lib().msp_wells_setup(C.byref(W), nb, b, nw, _ptr(row_ptr), _ptr(col_idx),
+                               _ptr(values), nnzb, _stream(stream))
+    if st != MSP_OK:
+        raise MspError(st, "msp_wells_setup")
+    return W
+
+
+def msp_wells_reduced(W, b: int):
+    """(nr, row_ptr, col_idx, values) of the reduced matrix as views (torch
+    tensors on the current device, not to be written) of the arrays W owns."""
+    import torch
+    nr, nnzb = C.c_int32(), C.c_int64()
+    rp, ci, v = C.c_void_p(), C.c_void_p(), C.c_void_p()
+    st = lib().msp_wells_reduced(W, C.byref(nr), C.byref(nnzb), C.byref(rp), C.byref(ci),
+                                 C.byref(v))
+    if st != MSP_OK:
+        raise MspError(st, "msp_wells_reduced")
+    view = lambda p, n, t: torch.as_tensor(_DeviceArray(p.value, n, t), device="cuda")
+    return (nr.value, view(rp, nr.value + 1, "<i4"), view(ci, nnzb.value, "<i4"),
+            view(v, nnzb.value * b * b, "<f8"))
+
+
+def msp_wells_update_values(W, values, stream=None):
+    st = lib().msp_wells_update_values(W, _ptr(values), _stream(stream))
+    if st != MSP_OK:
+        raise MspError(st, "msp_wells_update_values")
+
+
+def msp_wells_reduce_rhs(W, g, gs, stream=None):
+    st = lib().msp_wells_reduce_rhs(W, _ptr(g), _ptr(gs), _stream(stream))
+    if st != MSP_OK:
+        raise MspError(st, "msp_wells_reduce_rhs")
+
+
+def msp_wells_recover(W, g, xs, x, stream=None):
+    st = lib().msp_wells_recover(W, _ptr(g), _ptr(xs), _ptr(x), _stream(stream))
+    if st != MSP_OK:
+        raise MspError(st, "msp_wells_recover")
+
+
+def msp_wells_free(W):
+    if W:
+        lib().msp_wells_free(W)

@@ -1,9 +1,9 @@
 """Build ``libmsp.so`` (the C-ABI solver library) for sm_103a with nvcc, in tree.
 
 Every ``csrc/*.cu`` is compiled in parallel to an object in ``_build/`` and linked into
-``paper_2208_08594_gb300/libmsp.so``.  ``setup_exact.cu`` is compiled with
-``-fmad=false`` (no fused multiply-add) because its floating-point results decide
-integer outputs that must be reproducible bit for bit.
+``paper_2208_08594_gb300/libmsp.so``.  ``setup_exact.cu`` and ``wells.cu`` are compiled
+with ``-fmad=false`` (no fused multiply-add): the first because its floating-point results
+decide integer outputs, the second because its reduced matrix is specified bit for bit.
 """
 from __future__ import annotations
 
@@ -21,7 +21,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE,
           "--expt-relaxed-constexpr"]
-NO_FMA = {"setup_exact.cu"}
+NO_FMA = {"setup_exact.cu", "wells.cu"}
 
 
 def _nvcc() -> str:
