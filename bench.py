@@ -94,6 +94,17 @@ def parse():
     p.add_argument("--mu-sweep", action="store_true",
                    help="SetupCalls / SetupRatio / Iter / Time against mu on a drifting "
                         "Newton-like sequence (Tables 3, 5, 7) instead of the benchmark")
+    p.add_argument("--serve", action="store_true",
+                   help="request-loop benchmark: Newton sequences of systems of many sizes "
+                        "arriving over time, solved through the server (p50/p99 latency)")
+    p.add_argument("--serve-reservoirs", type=int, default=8)
+    p.add_argument("--serve-cells", type=float, nargs=2, default=[1e4, 2e6])
+    p.add_argument("--serve-blocks", type=int, nargs=2, default=[4, 8])
+    p.add_argument("--serve-rate", type=float, default=200.0,
+                   help="offered requests per second (reservoir arrivals are Poisson at this "
+                        "rate divided by the mean Newton steps per reservoir)")
+    p.add_argument("--serve-slots", type=int, nargs="+", default=[1, 4])
+    p.add_argument("--serve-budget-gb", type=float, default=150.0)
     p.add_argument("--time-steps", type=int, default=6)
     p.add_argument("--newton-steps", type=int, default=3)
     p.add_argument("--rel-step", type=float, default=0.15)
@@ -621,8 +632,140 @@ def run_mu_sweep(args):
         print(json.dumps(r))
 
 
+def serve_workload(args):
+    """Seeded reservoirs: cells log-uniform in --serve-cells on a random box (nz 5-40, the
+    rest split with aspect U[1, 4]), b uniform in --serve-blocks, 0-4 wells, 3-8 Newton steps
+    whose matrices alternate between the base values and a copy perturbed by up to 5 % (the
+    values change at every step, the pattern never), one right-hand side per step."""
+    from synthetic import box_jacobian, perturb_values, random_rhs
+    rng = np.random.default_rng(4242)
+    lo, hi = np.log(args.serve_cells[0]), np.log(args.serve_cells[1])
+    out = []
+    for r in range(args.serve_reservoirs):
+        cells = float(np.exp(rng.uniform(lo, hi)))
+        nz = int(rng.integers(5, 41))
+        b = int(rng.integers(args.serve_blocks[0], args.serve_blocks[1] + 1))
+        aspect = float(rng.uniform(1.0, 4.0))
+        area = max(cells / nz, 4.0)
+        nx = max(2, int(round(np.sqrt(area / aspect))))
+        ny = max(2, int(round(area / nx)))
+        wells = int(rng.integers(0, 5))
+        steps = int(rng.integers(3, 9))
+        a = box_jacobian(nx, ny, nz, b, 9000 + r, layered=True, kz_ratio=0.1, n_wells=wells)
+        v0 = np.ascontiguousarray(a.values.reshape(-1))
+        v1 = np.ascontiguousarray(perturb_values(a, 9100 + r).reshape(-1))
+        rhs = [np.ascontiguousarray(random_rhs(a, 9200 + 10 * r + k)) for k in range(steps)]
+        out.append({"a": a, "vals": (v0, v1), "rhs": rhs, "steps": steps,
+                    "dims": (nx, ny, nz), "b": b})
+    return out
+
+
+def run_serve_once(args, res, slots, precision):
+    """Reservoirs arrive as a Poisson process; each runs its Newton sequence closed-loop (the
+    next step is submitted when the previous solve returns).  Returns per-request results
+    and the wall time from the first arrival to the last completion."""
+    import paper_2208_08594_gb300 as msp
+    mean_steps = float(np.mean([r["steps"] for r in res]))
+    rate_res = args.serve_rate / mean_steps
+    arr = np.cumsum(np.random.default_rng(77).exponential(1.0 / rate_res, size=len(res)))
+    arr -= arr[0]
+    server = msp.Server(slots=slots, hbm_budget=int(args.serve_budget_gb * 1e9), mu=args.mu,
+                        precision=precision, colouring=colouring_of(args, msp),
+                        smoother=smoother_of(args, msp))
+    xs = [np.zeros(r["a"].nb * r["a"].b) for r in res]
+    pending = {}  # ticket -> (reservoir, step)
+    next_step = [0] * len(res)
+    results = []
+    t0 = time.perf_counter()
+
+    def submit(i):
+        r, k = res[i], next_step[i]
+        a = r["a"]
+        last = k == r["steps"] - 1
+        t = server.submit(i, a.nb, a.b, r["rhs"][k], xs[i], values=r["vals"][k % 2],
+                          row_ptr=a.row_ptr, col_idx=a.col_idx, rel_tol=TOL, release=last)
+        pending[t] = (i, k)
+        next_step[i] += 1
+
+    arrived = 0
+    while arrived < len(res) or pending:
+        now = time.perf_counter() - t0
+        while arrived < len(res) and arr[arrived] <= now:
+            submit(arrived)
+            arrived += 1
+        done = []
+        for t in list(pending):
+            out = server.wait(t, 0.0)
+            if out is not None:
+                done.append((t, out))
+        for t, out in done:
+            i, k = pending.pop(t)
+            out["reservoir"], out["step"] = i, k
+            out["cells"] = res[i]["a"].nb
+            out["n"] = res[i]["a"].nb * res[i]["a"].b
+            results.append(out)
+            if next_step[i] < res[i]["steps"]:
+                submit(i)
+        if not done:
+            time.sleep(0.0005)
+    wall = time.perf_counter() - t0
+    stats = server.stats()
+    server.close()
+    return results, wall, stats
+
+
+def run_serve(args):
+    import paper_2208_08594_gb300 as msp
+    prec_of = {"fp64": msp.MSP_PRECISION_FP64, "fp32": msp.MSP_PRECISION_FP32}
+    t_gen = time.perf_counter()
+    res = serve_workload(args)
+    t_gen = time.perf_counter() - t_gen
+    cfg = msp.msp_config_default(mu=args.mu, precision=prec_of[args.precision])
+    est = [msp.msp_estimate_device_bytes(r["a"].nb, r["a"].b, r["a"].nnzb, cfg) for r in res]
+    runs = []
+    for slots in args.serve_slots:
+        results, wall, stats = run_serve_once(args, res, slots, prec_of[args.precision])
+        bad = [r for r in results if r["status"] != 0]
+        lat = np.array([r["latency_ms"] for r in results])
+        runs.append({
+            "slots": slots, "solves": len(results), "failed": len(bad), "wall_s": round(wall, 3),
+            "solves_per_s": round(len(results) / wall, 3),
+            "cell_solves_per_s": round(sum(r["cells"] for r in results) / wall, 1),
+            "p50_ms": round(float(np.percentile(lat, 50)), 1),
+            "p99_ms": round(float(np.percentile(lat, 99)), 1),
+            "mean_queue_ms": round(float(np.mean([r["queue_ms"] for r in results])), 1),
+            "setups": int(sum(r["setup"] for r in results)),
+            "asmsp_setups": int(sum(r["info"]["setup_performed"] for r in results)),
+            "iterations": int(sum(r["info"]["iterations"] for r in results)),
+            "max_rel_residual": float(max(r["info"]["rel_residual"] for r in results)),
+            "peak_charged_gb": round(stats["peak_charged_bytes"] / 1e9, 2),
+            "footprint_over_estimate": [
+                round(max(r["device_bytes"] for r in results if r["reservoir"] == i) / est[i], 3)
+                for i in range(len(res))],
+            "evictions": stats["evictions"]})
+    out = {"metric": "request loop: solves/s and p50/p99 latency", "unit": "solves/s",
+           "value": runs[-1]["solves_per_s"], "higher_is_better": True, "n_gpus": 1,
+           "dtype": "f64" if args.precision == "fp64" else "f32-precond/f64-krylov",
+           "data": "synthetic", "vs_baseline": None,
+           "config": {"workload": "%d reservoirs, cells log-uniform %.0f-%.0f, b %d-%d, "
+                                  "3-8 Newton steps each, +-5%% values" % (
+                                      args.serve_reservoirs, args.serve_cells[0],
+                                      args.serve_cells[1], args.serve_blocks[0],
+                                      args.serve_blocks[1]),
+                      "offered_requests_per_s": args.serve_rate, "mu": args.mu,
+                      "hbm_budget_gb": args.serve_budget_gb, "tol": TOL,
+                      "reservoirs": [{"dims": r["dims"], "b": r["b"], "block_rows": r["a"].nb,
+                                      "nnzb": r["a"].nnzb, "steps": r["steps"]} for r in res],
+                      "generation_s": round(t_gen, 1)},
+           "runs": runs}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
+    if args.serve:
+        run_serve(args)
+        return
     if args.mu_sweep:
         run_mu_sweep(args)
         return

@@ -153,6 +153,10 @@ int msp_solve_host(msp_handle h, const double* h_b, double* h_x, double rel_tol,
 /* Release every resource of the handle (NULL is accepted). */
 int msp_free(msp_handle h);
 
+/* Device memory the handle holds (its buffers, as allocated by the library; the CUDA
+ * graph's own memory and CUDA's per-context reserves are not included). */
+int msp_device_bytes(msp_handle h, int64_t* bytes);
+
 /* Static description of a status code. */
 const char* msp_status_string(int status);
 
@@ -285,6 +289,101 @@ int msp_wells_recover(msp_wells W, const double* d_g, const double* d_xs, double
 
 /* Release W (NULL is accepted); waits for the device to finish its work. */
 int msp_wells_free(msp_wells W);
+
+/* ---- Request loop (serving) -----------------------------------------------------------
+ * Solves of many systems arriving over time.  A system (key) is one matrix pattern; its
+ * solver handle (matrix, AMG hierarchy, stage operators) stays resident on the device
+ * between requests, so the Newton steps of a reservoir reuse SETUP through the adaptive
+ * rule of Section 3.2.  A pool of `slots` worker threads, each with its own CUDA stream,
+ * runs admitted requests concurrently, so the work of several systems overlaps on the
+ * device; a request is admitted as soon as a slot is free, its key is not busy and its
+ * system fits the device-memory budget (idle resident systems are released, least
+ * recently used first, to make room).  Requests of one key run one at a time in submit
+ * order; requests that wait for memory keep their order among themselves, while requests
+ * of resident systems may pass them.  Results do not depend on the mix: every system is
+ * solved by the same deterministic kernels on its own buffers. */
+typedef struct msp_server_s* msp_server;
+
+#define MSP_REQ_NEW_PATTERN 1 /* release the key's resident system and set it up again */
+#define MSP_REQ_RELEASE 2     /* release the key's system after this request */
+
+typedef struct {
+  int64_t key;              /* system id */
+  int32_t nb, b;            /* block rows and block size of the system */
+  int64_t nnzb;             /* blocks */
+  const int32_t* h_row_ptr; /* HOST pattern, read when the system is set up: the first */
+  const int32_t* h_col_idx; /*   request of a key, MSP_REQ_NEW_PATTERN, or after a release */
+  const double* h_values;   /* HOST nnzb*b*b values of this request's matrix; NULL keeps the
+                               key's previous values */
+  const double* h_rhs;      /* HOST nb*b right-hand side */
+  double* h_x;              /* HOST nb*b solution (written when the request completes) */
+  double rel_tol;           /* as in msp_solve */
+  int32_t flags;            /* MSP_REQ_* */
+} msp_request;
+
+typedef struct {
+  int64_t ticket, key;
+  int32_t status;     /* as msp_solve, or the setup / update error */
+  int32_t slot;       /* worker that ran it */
+  int32_t setup;      /* 1: the system was set up for this request */
+  int32_t pad;
+  msp_solve_info info;
+  double queue_ms;    /* submit -> start */
+  double run_ms;      /* start -> end (setup or value update, solve, copies) */
+  double latency_ms;  /* submit -> end */
+  int64_t device_bytes;  /* the system's footprint after the request */
+} msp_result;
+
+typedef struct {
+  int64_t submitted, completed, queued, running, rejected, evictions;
+  int64_t resident_systems, resident_bytes;
+  int64_t peak_charged_bytes; /* peak of the bytes charged against the budget (resident
+                                 systems, and the estimates of systems being set up) */
+} msp_server_stats;
+
+/* Optional replacement of the CUDA solver as the servers' executor (tests of the
+ * scheduling on hosts without a GPU, tracing).  op MSP_EXEC_RUN: run `req` on slot `slot`
+ * (set the system up if `setup` is 1, else update its values), return an msp status and
+ * store the system's device bytes afterwards in *device_bytes; op MSP_EXEC_RELEASE:
+ * release the system of req->key.  Called from the worker threads, without the server's
+ * lock held. */
+#define MSP_EXEC_RUN 0
+#define MSP_EXEC_RELEASE 1
+typedef int (*msp_server_exec_fn)(void* user, int32_t op, const msp_request* req, int32_t slot,
+                                  int32_t setup, int64_t* device_bytes);
+
+typedef struct {
+  int32_t slots;          /* worker threads / CUDA streams, 1..64 */
+  int32_t device;         /* CUDA device of the workers */
+  int64_t hbm_budget;     /* device bytes the resident systems may hold together */
+  msp_config cfg;         /* solver configuration of every system */
+  msp_server_exec_fn exec;  /* NULL: the CUDA solver */
+  void* exec_user;
+} msp_server_config;
+
+/* Estimate of a solver handle's device bytes for a system of this size, used to admit a
+ * system before it is set up (afterwards its measured footprint, msp_device_bytes, is
+ * charged instead). */
+int64_t msp_estimate_device_bytes(int32_t nb, int32_t b, int64_t nnzb, const msp_config* cfg);
+
+/* Start the workers.  Errors: MSP_ERR_ARG (slots outside 1..64, budget <= 0, config). */
+int msp_server_create(msp_server* out, const msp_server_config* cfg);
+
+/* Queue a request; *ticket identifies it.  The host arrays must stay valid and unchanged
+ * until msp_server_wait returns the ticket's result.  A request whose estimated system
+ * does not fit the whole budget is completed at once with MSP_ERR_NOMEM. */
+int msp_server_submit(msp_server S, const msp_request* req, int64_t* ticket);
+
+/* Wait up to timeout_s seconds (< 0: no limit) for a ticket; on MSP_OK *res holds its
+ * result and the ticket is retired.  MSP_ERR_TIMEOUT if it has not completed yet,
+ * MSP_ERR_ARG for an unknown ticket. */
+int msp_server_wait(msp_server S, int64_t ticket, double timeout_s, msp_result* res);
+
+int msp_server_get_stats(msp_server S, msp_server_stats* st);
+
+/* Finish every queued and running request, release every system, stop the workers.
+ * Results not yet waited for are discarded. */
+int msp_server_free(msp_server S);
 
 #ifdef __cplusplus
 }

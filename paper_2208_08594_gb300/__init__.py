@@ -19,9 +19,16 @@ from ._native import (MSP_NOT_CONVERGED, MSP_OK, MSP_PREC_MSP, MSP_PREC_N_ONLY, 
                       msp_stats_launches, msp_stats_get, msp_vertices_grouping_noalloc,
                       NOALLOC_MAX_VERTICES, msp_wells_setup, msp_wells_reduced,
                       msp_wells_update_values, msp_wells_reduce_rhs, msp_wells_recover,
-                      msp_wells_free)
+                      msp_wells_free, msp_device_bytes, msp_estimate_device_bytes,
+                      msp_server_create, msp_server_submit, msp_server_wait,
+                      msp_server_get_stats, msp_server_free, MspRequest, MSP_REQ_NEW_PATTERN,
+                      MSP_REQ_RELEASE, MSP_EXEC_RUN, MSP_EXEC_RELEASE, MSP_SERVER_EXEC_FN)
 
-__all__ = ["Solver", "Wells", "WellEliminatedSolver", "MspError", "msp_wells_setup",
+__all__ = ["Solver", "Wells", "WellEliminatedSolver", "Server", "MspError", "msp_wells_setup",
+           "msp_device_bytes", "msp_estimate_device_bytes", "msp_server_create",
+           "msp_server_submit", "msp_server_wait", "msp_server_get_stats", "msp_server_free",
+           "MspRequest", "MSP_REQ_NEW_PATTERN", "MSP_REQ_RELEASE", "MSP_EXEC_RUN",
+           "MSP_EXEC_RELEASE", "MSP_SERVER_EXEC_FN",
            "msp_wells_reduced", "msp_wells_update_values", "msp_wells_reduce_rhs",
            "msp_wells_recover", "msp_wells_free", "msp_setup", "msp_update_values", "msp_update_values_host",
            "msp_stats_enable", "msp_stats_reset", "msp_stats_launches", "msp_stats_get",
@@ -151,3 +158,72 @@ class WellEliminatedSolver:
     def close(self):
         self.solver.close()
         self.wells.close()
+
+
+class Server:
+    """Request loop over the solver (``msp_server_*``): solves of many systems, each kept
+    resident on the device under its key between requests (the adaptive SETUP reuses its
+    preconditioner), run concurrently by ``slots`` workers with one CUDA stream each and
+    admitted by a device-memory budget.  Arrays are host numpy arrays; they are kept alive
+    here until :meth:`wait` returns their ticket."""
+
+    def __init__(self, slots=4, hbm_budget=150 * 10**9, device=0, exec_fn=None, **config):
+        import numpy as np  # noqa: F401
+        self.cfg = msp_config_default(**config)
+        self._exec = exec_fn
+        self.S = msp_server_create(slots, int(hbm_budget), self.cfg, device, exec_fn)
+        self._keep = {}
+
+    def submit(self, key, nb, b, rhs, x, values=None, row_ptr=None, col_idx=None, nnzb=None,
+               rel_tol=1e-6, new_pattern=False, release=False):
+        import numpy as np
+
+        def arr(a, dtype, name):
+            if a is None:
+                return None
+            if not (isinstance(a, np.ndarray) and a.dtype == dtype and a.flags.c_contiguous):
+                raise TypeError("%s must be a C-contiguous numpy array of %s" % (name, dtype))
+            return a
+
+        rp, ci = arr(row_ptr, np.int32, "row_ptr"), arr(col_idx, np.int32, "col_idx")
+        v, g, xx = arr(values, np.float64, "values"), arr(rhs, np.float64, "rhs"), arr(x, np.float64, "x")
+        if nnzb is None:
+            if ci is None:
+                raise ValueError("nnzb is needed when col_idx is not given")
+            nnzb = ci.size
+        if g.size != nb * b or xx.size != nb * b:
+            raise ValueError("rhs and x must have nb*b entries")
+        if v is not None and v.size != nnzb * b * b:
+            raise ValueError("values must have nnzb*b*b entries")
+        req = MspRequest()
+        req.key, req.nb, req.b, req.nnzb = int(key), int(nb), int(b), int(nnzb)
+        req.h_row_ptr = rp.ctypes.data if rp is not None else None
+        req.h_col_idx = ci.ctypes.data if ci is not None else None
+        req.h_values = v.ctypes.data if v is not None else None
+        req.h_rhs, req.h_x = g.ctypes.data, xx.ctypes.data
+        req.rel_tol = float(rel_tol)
+        req.flags = (MSP_REQ_NEW_PATTERN if new_pattern else 0) | (MSP_REQ_RELEASE if release else 0)
+        t = msp_server_submit(self.S, req)
+        self._keep[t] = (rp, ci, v, g, xx)
+        return t
+
+    def wait(self, ticket, timeout=-1.0):
+        r = msp_server_wait(self.S, ticket, timeout)
+        if r is not None:
+            self._keep.pop(ticket, None)
+        return r
+
+    def stats(self):
+        return msp_server_get_stats(self.S)
+
+    def close(self):
+        if self.S:
+            msp_server_free(self.S)
+            self.S = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

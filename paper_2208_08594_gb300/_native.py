@@ -32,7 +32,9 @@ EXPORTS = ("msp_config_default", "msp_setup", "msp_update_values", "msp_update_v
            "msp_stats_count", "msp_stats_get", "msp_vertices_grouping_noalloc",
            "msp_noalloc_error", "msp_wells_setup", "msp_wells_reduced",
            "msp_wells_update_values", "msp_wells_reduce_rhs", "msp_wells_recover",
-           "msp_wells_free")
+           "msp_wells_free", "msp_device_bytes", "msp_estimate_device_bytes",
+           "msp_server_create", "msp_server_submit", "msp_server_wait", "msp_server_get_stats",
+           "msp_server_free")
 
 # largest n accepted by msp_vertices_grouping_noalloc (size of its fixed scratch)
 NOALLOC_MAX_VERTICES = 1 << 16
@@ -53,6 +55,39 @@ class MspSolveInfo(C.Structure):
                 ("setup_calls", C.c_int), ("levels", C.c_int), ("colours_l0", C.c_int),
                 ("rel_residual", C.c_double), ("rel_residual_est", C.c_double),
                 ("t_setup_ms", C.c_double), ("t_solve_ms", C.c_double)]
+
+
+MSP_REQ_NEW_PATTERN, MSP_REQ_RELEASE = 1, 2
+MSP_EXEC_RUN, MSP_EXEC_RELEASE = 0, 1
+
+
+class MspRequest(C.Structure):
+    _fields_ = [("key", C.c_int64), ("nb", C.c_int32), ("b", C.c_int32), ("nnzb", C.c_int64),
+                ("h_row_ptr", C.c_void_p), ("h_col_idx", C.c_void_p), ("h_values", C.c_void_p),
+                ("h_rhs", C.c_void_p), ("h_x", C.c_void_p), ("rel_tol", C.c_double),
+                ("flags", C.c_int32)]
+
+
+class MspResult(C.Structure):
+    _fields_ = [("ticket", C.c_int64), ("key", C.c_int64), ("status", C.c_int32),
+                ("slot", C.c_int32), ("setup", C.c_int32), ("pad", C.c_int32),
+                ("info", MspSolveInfo), ("queue_ms", C.c_double), ("run_ms", C.c_double),
+                ("latency_ms", C.c_double), ("device_bytes", C.c_int64)]
+
+
+class MspServerStats(C.Structure):
+    _fields_ = [(f, C.c_int64) for f in ("submitted", "completed", "queued", "running",
+                                         "rejected", "evictions", "resident_systems",
+                                         "resident_bytes", "peak_charged_bytes")]
+
+
+MSP_SERVER_EXEC_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int32, C.POINTER(MspRequest), C.c_int32,
+                                 C.c_int32, C.POINTER(C.c_int64))
+
+
+class MspServerConfig(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("device", C.c_int32), ("hbm_budget", C.c_int64),
+                ("cfg", MspConfig), ("exec", MSP_SERVER_EXEC_FN), ("exec_user", C.c_void_p)]
 
 
 class MspError(RuntimeError):
@@ -116,9 +151,17 @@ def lib(build_if_missing: bool = True):
     L.msp_wells_reduce_rhs.argtypes = [P, P, P, P]
     L.msp_wells_recover.argtypes = [P, P, P, P, P]
     L.msp_wells_free.argtypes = [P]
+    L.msp_device_bytes.argtypes = [P, C.POINTER(C.c_int64)]
+    L.msp_estimate_device_bytes.argtypes = [C.c_int32, C.c_int32, C.c_int64, C.POINTER(MspConfig)]
+    L.msp_estimate_device_bytes.restype = C.c_int64
+    L.msp_server_create.argtypes = [C.POINTER(P), C.POINTER(MspServerConfig)]
+    L.msp_server_submit.argtypes = [P, C.POINTER(MspRequest), C.POINTER(C.c_int64)]
+    L.msp_server_wait.argtypes = [P, C.c_int64, D, C.POINTER(MspResult)]
+    L.msp_server_get_stats.argtypes = [P, C.POINTER(MspServerStats)]
+    L.msp_server_free.argtypes = [P]
     for name in EXPORTS:
         if name not in ("msp_status_string", "msp_last_error", "msp_stats_launches",
-                        "msp_noalloc_error"):
+                        "msp_noalloc_error", "msp_estimate_device_bytes"):
             getattr(L, name).restype = I
     _lib = L
     return L
@@ -370,3 +413,66 @@ def msp_wells_recover(W, g, xs, x, stream=None):
 def msp_wells_free(W):
     if W:
         lib().msp_wells_free(W)
+
+
+def msp_device_bytes(h) -> int:
+    out = C.c_int64()
+    st = lib().msp_device_bytes(h, C.byref(out))
+    if st != MSP_OK:
+        raise MspError(st, "msp_device_bytes")
+    return out.value
+
+
+def msp_estimate_device_bytes(nb: int, b: int, nnzb: int, cfg: MspConfig = None) -> int:
+    cfg = cfg if cfg is not None else msp_config_default()
+    return lib().msp_estimate_device_bytes(nb, b, nnzb, C.byref(cfg))
+
+
+def msp_server_create(slots: int, hbm_budget: int, cfg: MspConfig = None, device: int = 0,
+                      exec_fn=None):
+    """exec_fn: optional MSP_SERVER_EXEC_FN replacing the CUDA solver (keep a reference to it
+    for the server's lifetime)."""
+    sc = MspServerConfig()
+    sc.slots, sc.device, sc.hbm_budget = int(slots), int(device), int(hbm_budget)
+    sc.cfg = cfg if cfg is not None else msp_config_default()
+    if exec_fn is not None:
+        sc.exec = exec_fn
+    S = C.c_void_p()
+    st = lib().msp_server_create(C.byref(S), C.byref(sc))
+    if st != MSP_OK:
+        raise MspError(st, "msp_server_create")
+    return S
+
+
+def msp_server_submit(S, req: MspRequest) -> int:
+    t = C.c_int64()
+    st = lib().msp_server_submit(S, C.byref(req), C.byref(t))
+    if st != MSP_OK:
+        raise MspError(st, "msp_server_submit")
+    return t.value
+
+
+def msp_server_wait(S, ticket: int, timeout_s: float = -1.0):
+    """The result of a ticket as a dict, or None if it has not completed within timeout_s."""
+    r = MspResult()
+    st = lib().msp_server_wait(S, int(ticket), float(timeout_s), C.byref(r))
+    if st == MSP_ERR_TIMEOUT:
+        return None
+    if st != MSP_OK:
+        raise MspError(st, "msp_server_wait")
+    out = {f: getattr(r, f) for f, _ in MspResult._fields_ if f not in ("info", "pad")}
+    out["info"] = _info_dict(r.info)
+    return out
+
+
+def msp_server_get_stats(S):
+    st_ = MspServerStats()
+    st = lib().msp_server_get_stats(S, C.byref(st_))
+    if st != MSP_OK:
+        raise MspError(st, "msp_server_get_stats")
+    return {f: getattr(st_, f) for f, _ in MspServerStats._fields_}
+
+
+def msp_server_free(S):
+    if S:
+        lib().msp_server_free(S)

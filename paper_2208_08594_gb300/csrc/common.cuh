@@ -59,6 +59,10 @@ class Probe {
   bool in_graph_ = false;  // recorded as event nodes of a graph being captured
 };
 
+// Net bytes of device memory the calling host thread holds through DevBuf (allocations
+// minus releases); the difference across a call is that call's change of footprint.
+extern thread_local long long t_dev_bytes;
+
 // Owning device buffer (cudaMallocAsync / cudaFreeAsync would tie lifetime to a stream;
 // the handle's buffers outlive any one stream, so plain cudaMalloc is used at setup).
 template <typename T>
@@ -84,7 +88,10 @@ struct DevBuf {
   }
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      cudaFree(p);
+      t_dev_bytes -= (long long)(n * sizeof(T));
+    }
     p = nullptr;
     n = 0;
   }
@@ -99,6 +106,7 @@ struct DevBuf {
       return e == cudaErrorMemoryAllocation ? MSP_ERR_NOMEM : MSP_ERR_CUDA;
     }
     n = count;
+    t_dev_bytes += (long long)(count * sizeof(T));
     return MSP_OK;
   }
   T* get() const { return p; }

@@ -30,7 +30,10 @@ namespace msp {
 
 namespace {
 thread_local std::string g_last_error;
+thread_local int t_bytes_scope_depth = 0;
 }
+
+thread_local long long t_dev_bytes = 0;
 
 void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
   char buf[512];
@@ -169,15 +172,13 @@ Probe::~Probe() {
 }
 
 int sm_count() {
-  static int cached = 0;
-  if (cached == 0) {
+  static const int cached = [] {  // thread-safe one-time initialisation
     int dev = 0, n = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
-      cached = n;
-    else
-      cached = 152;
-  }
+      return n;
+    return 152;
+  }();
   return cached;
 }
 
@@ -343,6 +344,7 @@ struct msp_handle_s {
   int nb = 0, b = 0;
   int64_t nnzb = 0;
   int device = 0;
+  long long dev_bytes = 0;  // device memory the handle holds through DevBuf
   msp::SortScratch* ss = nullptr;
   msp::DevBuf<msp::DevFlags> flags;
   msp::DevFlags* h_flags = nullptr;  // pinned
@@ -1495,6 +1497,22 @@ int pattern_setup(msp_handle h, const int32_t* d_rp, const int32_t* d_ci, cudaSt
   return MSP_OK;
 }
 
+// Adds the change of the calling thread's DevBuf footprint during a public call to the
+// handle's own count (the outermost call only: entry points call one another).
+struct DevBytesScope {
+  msp_handle h;
+  long long t0;
+  bool outer;
+  explicit DevBytesScope(msp_handle hh)
+      : h(hh), t0(t_dev_bytes), outer(t_bytes_scope_depth++ == 0) {}
+  ~DevBytesScope() {
+    --t_bytes_scope_depth;
+    if (outer && h) h->dev_bytes += t_dev_bytes - t0;
+  }
+  DevBytesScope(const DevBytesScope&) = delete;
+  DevBytesScope& operator=(const DevBytesScope&) = delete;
+};
+
 void destroy(msp_handle h) {
   if (!h) return;
   drop_graph(h);
@@ -1575,6 +1593,7 @@ int msp_setup(msp_handle* out, const msp_config* cfg, int32_t nb, int32_t b,
     return MSP_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   msp_handle h = nullptr;
+  const long long bytes0 = t_dev_bytes;
   try {
     h = new msp_handle_s();
     h->cfg = *cfg;
@@ -1609,12 +1628,14 @@ int msp_setup(msp_handle* out, const msp_config* cfg, int32_t nb, int32_t b,
     destroy(h);
     return MSP_ERR_CUDA;
   }
+  h->dev_bytes = t_dev_bytes - bytes0;
   *out = h;
   return MSP_OK;
 }
 
 int msp_update_values(msp_handle h, const double* d_values, void* stream) {
   if (!h || !d_values) return MSP_ERR_ARG;
+  DevBytesScope bytes_scope(h);
   cudaStream_t s = (cudaStream_t)stream;
   try {
     MSP_TRY(reset_flags(h, s));
@@ -1628,6 +1649,7 @@ int msp_update_values(msp_handle h, const double* d_values, void* stream) {
 
 int msp_update_values_host(msp_handle h, const double* h_values, void* stream) {
   if (!h || !h_values) return MSP_ERR_ARG;
+  DevBytesScope bytes_scope(h);
   cudaStream_t s = (cudaStream_t)stream;
   const size_t cnt = (size_t)h->nnzb * h->b * h->b;
   if (!h->staging.p) MSP_TRY(h->staging.alloc(cnt));
@@ -1639,6 +1661,7 @@ int msp_update_values_host(msp_handle h, const double* h_values, void* stream) {
 int msp_solve(msp_handle h, const double* d_b, double* d_x, double rel_tol,
               msp_solve_info* info, void* stream) {
   if (!h || !d_b || !d_x || !(rel_tol > 0.0)) return MSP_ERR_ARG;
+  DevBytesScope bytes_scope(h);
   cudaStream_t s = (cudaStream_t)stream;
   msp_solve_info local{};
   msp_solve_info* inf = info ? info : &local;
@@ -1695,6 +1718,7 @@ int msp_solve(msp_handle h, const double* d_b, double* d_x, double rel_tol,
 int msp_solve_host(msp_handle h, const double* h_b, double* h_x, double rel_tol,
                    msp_solve_info* info, void* stream) {
   if (!h || !h_b || !h_x) return MSP_ERR_ARG;
+  DevBytesScope bytes_scope(h);
   cudaStream_t s = (cudaStream_t)stream;
   const size_t n = (size_t)h->nb * h->b, bytes = n * sizeof(double);
   if (!h->e2e_b.p) MSP_TRY(h->e2e_b.alloc(n));
@@ -1714,6 +1738,7 @@ int msp_free(msp_handle h) {
 
 int msp_apply_precond(msp_handle h, const double* d_g, double* d_w, void* stream) {
   if (!h || !d_g || !d_w) return MSP_ERR_ARG;
+  DevBytesScope bytes_scope(h);
   cudaStream_t s = (cudaStream_t)stream;
   try {
     MSP_TRY(launch_gather_blocks(h->nb, h->b, h->perm0.p, d_g, h->bperm.p, s));
@@ -1780,6 +1805,12 @@ int msp_stats_get(int index, char* name, int name_len, long long* launches, doub
   if (launches) *launches = st.launches;
   if (total_ms) *total_ms = st.ms;
   if (bytes) *bytes = st.bytes;
+  return MSP_OK;
+}
+
+int msp_device_bytes(msp_handle h, int64_t* bytes) {
+  if (!h || !bytes) return MSP_ERR_ARG;
+  *bytes = h->dev_bytes;
   return MSP_OK;
 }
 

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared():
     src = open(os.path.join(ROOT, "include", "msp.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:int|long long|const char\*)\s+(msp_\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|int64_t|long long|const char\*)\s+(msp_\w+)\s*\(", src, re.M)))
 
 
 def test_header_declares_the_boundary():
