@@ -153,6 +153,29 @@ int msp_solve_host(msp_handle h, const double* h_b, double* h_x, double rel_tol,
 /* Release every resource of the handle (NULL is accepted). */
 int msp_free(msp_handle h);
 
+/* ---- Batched instances -------------------------------------------------------------
+ * Many independent systems with one block size solved together: the caller stacks them
+ * into one block-diagonal BSR matrix (instance k owns the block rows [off[k], off[k+1]),
+ * and its blocks couple only rows of that range) and sets it up with msp_setup.  The
+ * colouring, the aggregation, the stage operators and the coarsest direct solve of a
+ * block-diagonal matrix are block diagonal, so the one preconditioner acts on every
+ * instance separately; each instance then gets its own FGMRES (inner products, Hessenberg
+ * matrix, convergence, restarts), while every preconditioner application, SpMV and
+ * Gram-Schmidt pass is one launch over all instances. */
+
+/* Declare the instances: count >= 1, h_row_offsets[count+1] (host) strictly increasing
+ * from 0 to nb.  Errors: MSP_ERR_ARG, MSP_ERR_PATTERN (a block couples two instances). */
+int msp_set_instances(msp_handle h, int32_t count, const int32_t* h_row_offsets);
+
+/* Solve every instance to its own ||b_k - A_k x_k|| / ||b_k|| <= rel_tol (x0 = 0): d_b,
+ * d_x device arrays of nb*b doubles (natural order, may not alias); h_infos (host, may be
+ * NULL) receives one msp_solve_info per instance.  The adaptive rule of Section 3.2
+ * regenerates the preconditioner when the largest iteration count of the previous batch
+ * exceeded mu.  Returns MSP_OK if every instance converged, else the first error status or
+ * MSP_NOT_CONVERGED.  Synchronises the stream. */
+int msp_solve_batch(msp_handle h, const double* d_b, double* d_x, double rel_tol,
+                    msp_solve_info* h_infos, void* stream);
+
 /* Device memory the handle holds (its buffers, as allocated by the library; the CUDA
  * graph's own memory and CUDA's per-context reserves are not included). */
 int msp_device_bytes(msp_handle h, int64_t* bytes);

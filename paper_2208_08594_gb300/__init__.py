@@ -22,9 +22,12 @@ from ._native import (MSP_NOT_CONVERGED, MSP_OK, MSP_PREC_MSP, MSP_PREC_N_ONLY, 
                       msp_wells_free, msp_device_bytes, msp_estimate_device_bytes,
                       msp_server_create, msp_server_submit, msp_server_wait,
                       msp_server_get_stats, msp_server_free, MspRequest, MSP_REQ_NEW_PATTERN,
-                      MSP_REQ_RELEASE, MSP_EXEC_RUN, MSP_EXEC_RELEASE, MSP_SERVER_EXEC_FN)
+                      MSP_REQ_RELEASE, MSP_EXEC_RUN, MSP_EXEC_RELEASE, MSP_SERVER_EXEC_FN,
+                      msp_set_instances, msp_solve_batch)
 
-__all__ = ["Solver", "Wells", "WellEliminatedSolver", "Server", "MspError", "msp_wells_setup",
+__all__ = ["Solver", "Wells", "WellEliminatedSolver", "Server", "BatchSolver",
+           "stack_block_diagonal", "msp_set_instances", "msp_solve_batch", "MspError",
+           "msp_wells_setup",
            "msp_device_bytes", "msp_estimate_device_bytes", "msp_server_create",
            "msp_server_submit", "msp_server_wait", "msp_server_get_stats", "msp_server_free",
            "MspRequest", "MSP_REQ_NEW_PATTERN", "MSP_REQ_RELEASE", "MSP_EXEC_RUN",
@@ -227,3 +230,39 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def stack_block_diagonal(mats):
+    """Stack BSR matrices with one block size into one block-diagonal BSR matrix (host numpy
+    arrays).  ``mats``: objects with ``nb, b, row_ptr, col_idx, values``.  Returns
+    (nb, b, row_ptr, col_idx, values (flat), offsets) with offsets[k] the first block row of
+    instance k."""
+    import numpy as np
+    b = int(mats[0].b)
+    if any(int(m.b) != b for m in mats):
+        raise ValueError("all instances need the same block size")
+    offsets = np.zeros(len(mats) + 1, np.int64)
+    for k, m in enumerate(mats):
+        offsets[k + 1] = offsets[k] + int(m.nb)
+    nnz = np.cumsum([0] + [int(m.row_ptr[-1]) for m in mats])
+    rp = np.concatenate([np.asarray(m.row_ptr[:-1], np.int64) + nnz[k] for k, m in enumerate(mats)]
+                        + [np.array([nnz[-1]])])
+    ci = np.concatenate([np.asarray(m.col_idx, np.int64) + offsets[k] for k, m in enumerate(mats)])
+    v = np.concatenate([np.asarray(m.values, np.float64).reshape(-1) for m in mats])
+    return (int(offsets[-1]), b, rp.astype(np.int32), ci.astype(np.int32), v,
+            offsets.astype(np.int32))
+
+
+class BatchSolver(Solver):
+    """A :class:`Solver` over a block-diagonal stack of independent instances (see
+    :func:`stack_block_diagonal`): one preconditioner and one launch per kernel serve every
+    instance, each instance gets its own FGMRES.  ``offsets``: host sequence of the
+    instances' first block rows plus nb."""
+
+    def __init__(self, nb, b, row_ptr, col_idx, values, offsets, stream=None, **config):
+        super().__init__(nb, b, row_ptr, col_idx, values, stream, **config)
+        self.count = len(offsets) - 1
+        msp_set_instances(self.h, offsets)
+
+    def solve_batch(self, rhs, x, rel_tol=1e-6, stream=None):
+        return msp_solve_batch(self.h, self.count, rhs, x, rel_tol, stream)

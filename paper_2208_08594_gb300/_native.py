@@ -34,7 +34,7 @@ EXPORTS = ("msp_config_default", "msp_setup", "msp_update_values", "msp_update_v
            "msp_wells_update_values", "msp_wells_reduce_rhs", "msp_wells_recover",
            "msp_wells_free", "msp_device_bytes", "msp_estimate_device_bytes",
            "msp_server_create", "msp_server_submit", "msp_server_wait", "msp_server_get_stats",
-           "msp_server_free")
+           "msp_server_free", "msp_set_instances", "msp_solve_batch")
 
 # largest n accepted by msp_vertices_grouping_noalloc (size of its fixed scratch)
 NOALLOC_MAX_VERTICES = 1 << 16
@@ -152,6 +152,8 @@ def lib(build_if_missing: bool = True):
     L.msp_wells_recover.argtypes = [P, P, P, P, P]
     L.msp_wells_free.argtypes = [P]
     L.msp_device_bytes.argtypes = [P, C.POINTER(C.c_int64)]
+    L.msp_set_instances.argtypes = [P, C.c_int32, P]
+    L.msp_solve_batch.argtypes = [P, P, P, D, P, P]
     L.msp_estimate_device_bytes.argtypes = [C.c_int32, C.c_int32, C.c_int64, C.POINTER(MspConfig)]
     L.msp_estimate_device_bytes.restype = C.c_int64
     L.msp_server_create.argtypes = [C.POINTER(P), C.POINTER(MspServerConfig)]
@@ -476,3 +478,20 @@ def msp_server_get_stats(S):
 def msp_server_free(S):
     if S:
         lib().msp_server_free(S)
+
+
+def msp_set_instances(h, offsets):
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+    st = lib().msp_set_instances(h, int(off.size - 1), _ptr(off))
+    if st != MSP_OK:
+        raise MspError(st, "msp_set_instances")
+
+
+def msp_solve_batch(h, count: int, b, x, rel_tol=1e-6, stream=None):
+    """Per-instance info dicts; raises on an error status other than breakdown."""
+    infos = (MspSolveInfo * int(count))()
+    st = lib().msp_solve_batch(h, _ptr(b), _ptr(x), float(rel_tol),
+                               C.cast(infos, C.c_void_p), _stream(stream))
+    if st < 0 and st != MSP_ERR_BREAKDOWN and not any(i.status for i in infos):
+        raise MspError(st, "msp_solve_batch")
+    return [_info_dict(i) for i in infos]

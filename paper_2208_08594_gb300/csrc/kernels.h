@@ -127,4 +127,34 @@ int launch_scatter_blocks(int nb, int b, const int* perm, const double* in, doub
 
 int krylov_blocks();  // number of blocks the reduction kernels use
 
+// ---------------- batched Krylov over a block-diagonal system ----------------
+// Chunks of the (colour-ordered) vector, each inside one instance: chunk c covers the
+// elements [start[c], end[c]) of instance inst[c]; the chunks of instance i are
+// ichunks[iptr[i] .. iptr[i+1]) in increasing order.  Partials: kmax per chunk.
+struct SegChunks {
+  int n = 0;
+  const int* start = nullptr;
+  const int* end = nullptr;
+  const int* inst = nullptr;
+  const int* iptr = nullptr;
+  const int* ichunks = nullptr;
+};
+constexpr int kKrylovMaxK = 72;  // partial / coefficient stride per chunk and per instance
+// partial[c][k] = V[k] . w over chunk c (active instances only)
+int launch_seg_multi_dot(const SegChunks& sc, const int* active, const double* V, size_t ldv,
+                         int K, const double* w, double* partial, cudaStream_t s);
+// out[i][koff + k] = sum over instance i's chunks of partial[c][k] (active instances)
+int launch_seg_reduce(const SegChunks& sc, int B, int K, const int* active,
+                      const double* partial, double* out, int koff, cudaStream_t s);
+// w -= sum_k coef[i][k] V[k]; partial[c][0] = sum of the new w^2 over chunk c
+int launch_seg_multi_axpy_norm(const SegChunks& sc, const int* active, const double* V,
+                               size_t ldv, int K, const double* coef, double* w, double* partial,
+                               cudaStream_t s);
+// v = w / sqrt(nrm2[i][0]) per instance (nothing where the norm is zero)
+int launch_seg_normalize(const SegChunks& sc, const int* active, const double* w,
+                         const double* nrm2, double* v, cudaStream_t s);
+// x += sum_{k < count[i]} y[i][k] Z[k]
+int launch_seg_update_x(const SegChunks& sc, const int* count, const double* Z, size_t ldz,
+                        const double* y, double* x, cudaStream_t s);
+
 }  // namespace msp

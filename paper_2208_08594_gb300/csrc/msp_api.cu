@@ -384,6 +384,14 @@ struct msp_handle_s {
   int prev_it = -1;
   bool first_solve = true;
   bool setup_valid = false;
+  // independent instances of a block-diagonal matrix (msp_set_instances)
+  int batch = 0;                              // number of instances, 0: none
+  std::vector<int> batch_offsets;             // block-row offsets (natural order)
+  msp::DevBuf<int> seg_start, seg_end, seg_inst, seg_iptr, seg_ichunks;
+  int seg_n = 0;
+  msp::DevBuf<int> bact, bcount;              // per instance: active flag, columns used
+  msp::DevBuf<double> bpart, bh, by, bn, bydev;  // chunk partials; per instance kKrylovMaxK
+  double* h_bpin = nullptr;                   // pinned: bh, by, bn (3 * batch * kKrylovMaxK)
 };
 
 namespace msp {
@@ -1468,6 +1476,234 @@ int fgmres(msp_handle h, double tol, int* iters, double* relres, double* relres_
   return status;
 }
 
+// Chunks of the batched Krylov kernels: level-0 colour classes hold the rows of every
+// instance in increasing original index, i.e. instance by instance, so the vector splits
+// into (colour, instance) segments, cut into chunks of at most kSegChunk elements.
+constexpr int kSegChunk = 8192;
+
+SegChunks seg_chunks(msp_handle h) {
+  SegChunks sc;
+  sc.n = h->seg_n;
+  sc.start = h->seg_start.p;
+  sc.end = h->seg_end.p;
+  sc.inst = h->seg_inst.p;
+  sc.iptr = h->seg_iptr.p;
+  sc.ichunks = h->seg_ichunks.p;
+  return sc;
+}
+
+// Right-preconditioned FGMRES(m) run for every instance at once: one preconditioner
+// application and one SpMV per step serve all instances (the matrix and the preconditioner
+// are block diagonal); inner products, norms, Hessenberg matrices, rotations, convergence
+// and restarts are per instance.  Each step uses classical Gram-Schmidt with a second pass
+// (always taken).  An instance that converges or stops leaves the active set; its vectors
+// are no longer read or written.
+int fgmres_batched(msp_handle h, double tol, std::vector<int>& its, std::vector<double>& relres,
+                   std::vector<double>& relest, std::vector<int>& status, cudaStream_t s) {
+  const int B = h->batch, m = h->cfg.restart;
+  const size_t n = (size_t)h->nb * h->b;
+  const int KM = kKrylovMaxK;
+  const SegChunks sc = seg_chunks(h);
+  const double* bvec = h->bperm.p;
+  double* x = h->xperm.p;
+  double* V = h->V.p;
+  double* Z = h->Z.p;
+  double* hb = h->h_bpin;                 // B * KM: first-pass coefficients
+  double* yb = h->h_bpin + (size_t)B * KM;  // second-pass coefficients
+  double* nb2 = h->h_bpin + (size_t)2 * B * KM;  // squared norms
+  its.assign(B, 0);
+  relres.assign(B, 0.0);
+  relest.assign(B, 0.0);
+  status.assign(B, MSP_NOT_CONVERGED);
+  std::vector<int> act(B, 1), done(B, 0), stop(B, 0), jused(B, 0), brk(B, 0);
+  auto upload_act = [&](const std::vector<int>& a) -> int {
+    MSP_CUDA_TRY(cudaMemcpyAsync(h->bact.p, a.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+    // the host vector may change before the copy runs: wait for it
+    MSP_CUDA_TRY(cudaStreamSynchronize(s));
+    return MSP_OK;
+  };
+  // per-instance squared norms of a vector into nb2[i * KM]
+  auto seg_norms = [&](const double* v) -> int {
+    MSP_TRY(launch_seg_multi_dot(sc, h->bact.p, v, n, 1, v, h->bpart.p, s));
+    MSP_TRY(launch_seg_reduce(sc, B, 1, h->bact.p, h->bpart.p, h->bn.p, 0, s));
+    MSP_CUDA_TRY(cudaMemcpyAsync(nb2, h->bn.p, (size_t)B * KM * sizeof(double),
+                                 cudaMemcpyDeviceToHost, s));
+    MSP_CUDA_TRY(cudaStreamSynchronize(s));
+    return MSP_OK;
+  };
+  MSP_TRY(upload_act(act));
+  MSP_TRY(seg_norms(bvec));
+  std::vector<double> bnorm(B);
+  for (int i = 0; i < B; ++i) {
+    bnorm[i] = std::sqrt(nb2[(size_t)i * KM]);
+    if (!std::isfinite(bnorm[i])) {
+      status[i] = MSP_ERR_NONFINITE;
+      done[i] = 1;
+    } else if (bnorm[i] == 0.0) {
+      status[i] = MSP_OK;
+      done[i] = 1;
+    }
+  }
+  MSP_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  std::vector<std::vector<double>> H(B), cs(B), sn(B), sv(B);
+  for (int i = 0; i < B; ++i) {
+    H[i].assign((size_t)(m + 1) * m, 0.0);
+    cs[i].assign(m, 0.0);
+    sn[i].assign(m, 0.0);
+    sv[i].assign(m + 1, 0.0);
+  }
+  std::vector<double> est(B, 1.0), ybuf((size_t)B * KM, 0.0);
+  std::vector<int> cnt(B, 0);
+  while (true) {
+    MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, x, bvec, h->rvec.p,
+                                    true, s));
+    for (int i = 0; i < B; ++i) act[i] = !done[i];
+    MSP_TRY(upload_act(act));
+    MSP_TRY(seg_norms(h->rvec.p));
+    int ncycle = 0;
+    for (int i = 0; i < B; ++i) {
+      if (done[i]) continue;
+      const double beta = std::sqrt(nb2[(size_t)i * KM]);
+      if (!std::isfinite(beta)) {
+        status[i] = MSP_ERR_NONFINITE;
+        done[i] = 1;
+      } else if (beta / bnorm[i] <= tol) {
+        est[i] = beta / bnorm[i];
+        status[i] = MSP_OK;
+        done[i] = 1;
+      } else if (brk[i]) {
+        status[i] = MSP_ERR_BREAKDOWN;
+        relest[i] = est[i];
+        done[i] = 1;
+      } else if (its[i] >= h->cfg.max_it) {
+        done[i] = 1;
+      } else {
+        std::fill(sv[i].begin(), sv[i].end(), 0.0);
+        sv[i][0] = beta;
+        ++ncycle;
+      }
+      act[i] = !done[i];
+      stop[i] = 0;
+      jused[i] = 0;
+    }
+    if (ncycle == 0) break;
+    MSP_TRY(upload_act(act));
+    MSP_TRY(launch_seg_normalize(sc, h->bact.p, h->rvec.p, h->bn.p, V, s));
+    bool any = true;
+    for (int j = 0; j < m && any; ++j) {
+      double* vj = V + (size_t)j * n;
+      double* zj = Z + (size_t)j * n;
+      double* w = V + (size_t)(j + 1) * n;
+      MSP_TRY(apply_precond(h, vj, zj, s));
+      {
+        Probe pr("batch_spmv", bsr_bytes(h, 8.0, 1), s);
+        MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, zj, nullptr, w,
+                                        false, s));
+      }
+      const int K = j + 1;
+      {
+        Probe pr("batch_multi_dot", (double)(K + 1) * n * 8.0, s);
+        MSP_TRY(launch_seg_multi_dot(sc, h->bact.p, V, n, K + 1, w, h->bpart.p, s));
+      }
+      MSP_TRY(launch_seg_reduce(sc, B, K + 1, h->bact.p, h->bpart.p, h->bh.p, 0, s));
+      {
+        Probe pr("batch_multi_axpy", (double)(K + 2) * n * 8.0, s);
+        MSP_TRY(launch_seg_multi_axpy_norm(sc, h->bact.p, V, n, K, h->bh.p, w, h->bpart.p, s));
+      }
+      {
+        Probe pr("batch_reorth_dot", (double)(K + 1) * n * 8.0, s);
+        MSP_TRY(launch_seg_multi_dot(sc, h->bact.p, V, n, K, w, h->bpart.p, s));
+      }
+      MSP_TRY(launch_seg_reduce(sc, B, K, h->bact.p, h->bpart.p, h->by.p, 0, s));
+      {
+        Probe pr("batch_reorth_axpy", (double)(K + 2) * n * 8.0, s);
+        MSP_TRY(launch_seg_multi_axpy_norm(sc, h->bact.p, V, n, K, h->by.p, w, h->bpart.p, s));
+      }
+      MSP_TRY(launch_seg_reduce(sc, B, 1, h->bact.p, h->bpart.p, h->bn.p, 0, s));
+      MSP_TRY(launch_seg_normalize(sc, h->bact.p, w, h->bn.p, w, s));
+      MSP_CUDA_TRY(cudaMemcpyAsync(hb, h->bh.p, (size_t)B * KM * sizeof(double),
+                                   cudaMemcpyDeviceToHost, s));
+      MSP_CUDA_TRY(cudaMemcpyAsync(yb, h->by.p, (size_t)B * KM * sizeof(double),
+                                   cudaMemcpyDeviceToHost, s));
+      MSP_CUDA_TRY(cudaMemcpyAsync(nb2, h->bn.p, (size_t)B * KM * sizeof(double),
+                                   cudaMemcpyDeviceToHost, s));
+      MSP_CUDA_TRY(cudaStreamSynchronize(s));
+      bool changed = false;
+      any = false;
+      for (int i = 0; i < B; ++i) {
+        if (!act[i]) continue;
+        ++its[i];
+        std::vector<double>& Hi = H[i];
+        for (int k = 0; k < K; ++k) Hi[(size_t)k * m + j] = hb[(size_t)i * KM + k] + yb[(size_t)i * KM + k];
+        const double hn = std::sqrt(nb2[(size_t)i * KM]);
+        Hi[(size_t)(j + 1) * m + j] = hn;
+        for (int k = 0; k < j; ++k) {
+          const double a = Hi[(size_t)k * m + j], c = Hi[(size_t)(k + 1) * m + j];
+          Hi[(size_t)k * m + j] = cs[i][k] * a + sn[i][k] * c;
+          Hi[(size_t)(k + 1) * m + j] = -sn[i][k] * a + cs[i][k] * c;
+        }
+        const double a = Hi[(size_t)j * m + j], c = Hi[(size_t)(j + 1) * m + j];
+        const double rho = std::sqrt(a * a + c * c);
+        if (rho == 0.0) {
+          cs[i][j] = 1.0;
+          sn[i][j] = 0.0;
+        } else {
+          cs[i][j] = a / rho;
+          sn[i][j] = c / rho;
+        }
+        Hi[(size_t)j * m + j] = rho;
+        Hi[(size_t)(j + 1) * m + j] = 0.0;
+        sv[i][j + 1] = -sn[i][j] * sv[i][j];
+        sv[i][j] = cs[i][j] * sv[i][j];
+        jused[i] = j + 1;
+        est[i] = std::fabs(sv[i][j + 1]) / bnorm[i];
+        if (!std::isfinite(est[i])) {
+          status[i] = MSP_ERR_NONFINITE;
+          done[i] = 1;
+          jused[i] = 0;
+        }
+        if (hn == 0.0) brk[i] = 1;
+        if (done[i] || est[i] <= tol || its[i] >= h->cfg.max_it || brk[i]) {
+          act[i] = 0;
+          changed = true;
+        } else {
+          any = true;
+        }
+      }
+      if (changed && any) MSP_TRY(upload_act(act));
+    }
+    // x_i += Z y_i with y_i = H_i^{-1} s_i
+    std::fill(ybuf.begin(), ybuf.end(), 0.0);
+    for (int i = 0; i < B; ++i) {
+      cnt[i] = jused[i];
+      const int J = jused[i];
+      for (int r = J - 1; r >= 0; --r) {
+        double t = sv[i][r];
+        for (int k = r + 1; k < J; ++k) t -= H[i][(size_t)r * m + k] * ybuf[(size_t)i * KM + k];
+        const double d = H[i][(size_t)r * m + r];
+        ybuf[(size_t)i * KM + r] = d != 0.0 ? t / d : 0.0;
+      }
+    }
+    MSP_CUDA_TRY(cudaMemcpyAsync(h->bydev.p, ybuf.data(), (size_t)B * KM * sizeof(double),
+                                 cudaMemcpyHostToDevice, s));
+    MSP_CUDA_TRY(cudaMemcpyAsync(h->bcount.p, cnt.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+    MSP_TRY(launch_seg_update_x(sc, h->bcount.p, Z, n, h->bydev.p, x, s));
+    MSP_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  // true residuals
+  MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, x, bvec, h->rvec.p,
+                                  true, s));
+  for (int i = 0; i < B; ++i) act[i] = bnorm[i] > 0.0 && std::isfinite(bnorm[i]);
+  MSP_TRY(upload_act(act));
+  MSP_TRY(seg_norms(h->rvec.p));
+  for (int i = 0; i < B; ++i) {
+    if (act[i]) relres[i] = std::sqrt(nb2[(size_t)i * KM]) / bnorm[i];
+    if (status[i] != MSP_ERR_BREAKDOWN) relest[i] = est[i];
+    if (bnorm[i] == 0.0) relest[i] = 0.0;
+  }
+  return MSP_OK;
+}
+
 int pattern_setup(msp_handle h, const int32_t* d_rp, const int32_t* d_ci, cudaStream_t s) {
   const int nb = h->nb;
   const size_t nnzb = (size_t)h->nnzb;
@@ -1519,6 +1755,7 @@ void destroy(msp_handle h) {
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->h_flags) cudaFreeHost(h->h_flags);
   if (h->h_pin) cudaFreeHost(h->h_pin);
+  if (h->h_bpin) cudaFreeHost(h->h_bpin);
   if (h->ss) sort_scratch_destroy(h->ss);
   delete h;
 }
@@ -1806,6 +2043,147 @@ int msp_stats_get(int index, char* name, int name_len, long long* launches, doub
   if (total_ms) *total_ms = st.ms;
   if (bytes) *bytes = st.bytes;
   return MSP_OK;
+}
+
+int msp_set_instances(msp_handle h, int32_t count, const int32_t* h_row_offsets) {
+  if (!h || count < 1 || !h_row_offsets || h_row_offsets[0] != 0 || h_row_offsets[count] != h->nb)
+    return MSP_ERR_ARG;
+  for (int i = 0; i < count; ++i)
+    if (h_row_offsets[i + 1] <= h_row_offsets[i]) return MSP_ERR_ARG;
+  DevBytesScope bytes_scope(h);
+  cudaStream_t s = nullptr;
+  try {
+    const int nb = h->nb, b = h->b;
+    DevBuf<int> off;
+    MSP_TRY(off.alloc((size_t)count + 1));
+    MSP_CUDA_TRY(cudaMemcpy(off.p, h_row_offsets, sizeof(int) * ((size_t)count + 1),
+                            cudaMemcpyHostToDevice));
+    MSP_TRY(reset_flags(h, s));
+    MSP_TRY(launch_check_block_diagonal(nb, h->rp.p, h->ci.p, h->perm0.p, count, off.p,
+                                        h->flags.p, s));
+    if (sync_flags(h, s) != MSP_OK) return h->h_flags->code;
+    // (colour, instance) segments of the colour-ordered rows, cut into chunks
+    std::vector<int> perm(nb);
+    MSP_CUDA_TRY(cudaMemcpy(perm.data(), h->perm0.p, sizeof(int) * (size_t)nb,
+                            cudaMemcpyDeviceToHost));
+    std::vector<int> cstart, cend, cinst;
+    const std::vector<int> offs(h_row_offsets, h_row_offsets + count + 1);
+    auto inst_of = [&](int r) {
+      return (int)(std::upper_bound(offs.begin(), offs.end(), r) - offs.begin()) - 1;
+    };
+    for (size_t c = 0; c + 1 < h->cptr0.size(); ++c) {
+      int p = h->cptr0[c];
+      const int p1 = h->cptr0[c + 1];
+      while (p < p1) {
+        const int inst = inst_of(perm[p]);
+        int q = p + 1;
+        while (q < p1 && inst_of(perm[q]) == inst) ++q;
+        if (q < p1 && inst_of(perm[q]) < inst) return MSP_ERR_PATTERN;  // not instance-major
+        for (long long e = (long long)p * b; e < (long long)q * b; e += kSegChunk) {
+          cstart.push_back((int)e);
+          cend.push_back((int)std::min<long long>(e + kSegChunk, (long long)q * b));
+          cinst.push_back(inst);
+        }
+        p = q;
+      }
+    }
+    const int nchunks = (int)cstart.size();
+    std::vector<int> iptr(count + 1, 0), ichunks(nchunks);
+    for (int c = 0; c < nchunks; ++c) ++iptr[cinst[c] + 1];
+    for (int i = 0; i < count; ++i) iptr[i + 1] += iptr[i];
+    {
+      std::vector<int> fill(iptr.begin(), iptr.end() - 1);
+      for (int c = 0; c < nchunks; ++c) ichunks[fill[cinst[c]]++] = c;
+    }
+    MSP_TRY(h->seg_start.alloc(nchunks));
+    MSP_TRY(h->seg_end.alloc(nchunks));
+    MSP_TRY(h->seg_inst.alloc(nchunks));
+    MSP_TRY(h->seg_iptr.alloc((size_t)count + 1));
+    MSP_TRY(h->seg_ichunks.alloc(nchunks));
+    MSP_CUDA_TRY(cudaMemcpy(h->seg_start.p, cstart.data(), sizeof(int) * nchunks, cudaMemcpyHostToDevice));
+    MSP_CUDA_TRY(cudaMemcpy(h->seg_end.p, cend.data(), sizeof(int) * nchunks, cudaMemcpyHostToDevice));
+    MSP_CUDA_TRY(cudaMemcpy(h->seg_inst.p, cinst.data(), sizeof(int) * nchunks, cudaMemcpyHostToDevice));
+    MSP_CUDA_TRY(cudaMemcpy(h->seg_iptr.p, iptr.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice));
+    MSP_CUDA_TRY(cudaMemcpy(h->seg_ichunks.p, ichunks.data(), sizeof(int) * nchunks, cudaMemcpyHostToDevice));
+    const size_t per = (size_t)count * kKrylovMaxK;
+    MSP_TRY(h->bpart.alloc((size_t)nchunks * kKrylovMaxK));
+    MSP_TRY(h->bh.alloc(per));
+    MSP_TRY(h->by.alloc(per));
+    MSP_TRY(h->bn.alloc(per));
+    MSP_TRY(h->bydev.alloc(per));
+    MSP_TRY(h->bact.alloc(count));
+    MSP_TRY(h->bcount.alloc(count));
+    if (h->h_bpin) cudaFreeHost(h->h_bpin);
+    h->h_bpin = nullptr;
+    MSP_CUDA_TRY(cudaMallocHost(&h->h_bpin, 3 * per * sizeof(double)));
+    h->seg_n = nchunks;
+    h->batch = count;
+    h->batch_offsets = offs;
+    return MSP_OK;
+  } catch (...) {
+    return MSP_ERR_NOMEM;
+  }
+}
+
+int msp_solve_batch(msp_handle h, const double* d_b, double* d_x, double rel_tol,
+                    msp_solve_info* h_infos, void* stream) {
+  if (!h || !d_b || !d_x || !(rel_tol > 0.0) || h->batch < 1) return MSP_ERR_ARG;
+  if (h->cfg.restart >= kKrylovMaxK) return MSP_ERR_ARG;
+  DevBytesScope bytes_scope(h);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int B = h->batch;
+  try {
+    const size_t n = (size_t)h->nb * h->b;
+    MSP_CUDA_TRY(cudaMemsetAsync(h->ifl.p, 0, sizeof(int), s));
+    MSP_TRY(launch_check_finite(n, d_b, h->ifl.p, s));
+    int bad = 0;
+    MSP_CUDA_TRY(cudaMemcpyAsync(&bad, h->ifl.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MSP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (bad) return MSP_ERR_NONFINITE;
+    // adaptive setup (Section 3.2) on the largest iteration count of the previous batch
+    auto ts = Clock::now();
+    int setup = 0;
+    if (!h->first_solve && (h->prev_it > h->cfg.mu || !h->setup_valid)) {
+      MSP_TRY(value_setup(h, s));
+      setup = 1;
+    } else if (h->first_solve) {
+      setup = 1;
+    }
+    const double t_setup = ms_since(ts);
+    h->first_solve = false;
+    auto t0 = Clock::now();
+    MSP_TRY(launch_gather_blocks(h->nb, h->b, h->perm0.p, d_b, h->bperm.p, s));
+    std::vector<int> its, status;
+    std::vector<double> rr, est;
+    MSP_TRY(fgmres_batched(h, rel_tol, its, rr, est, status, s));
+    MSP_TRY(launch_scatter_blocks(h->nb, h->b, h->perm0.p, h->xperm.p, d_x, s));
+    MSP_CUDA_TRY(cudaStreamSynchronize(s));
+    const double t_solve = ms_since(t0);
+    int worst = MSP_OK, maxit = 0;
+    for (int i = 0; i < B; ++i) {
+      maxit = std::max(maxit, its[i]);
+      if (status[i] < 0 && worst >= 0) worst = status[i];
+      else if (status[i] == MSP_NOT_CONVERGED && worst == MSP_OK) worst = MSP_NOT_CONVERGED;
+      if (h_infos) {
+        msp_solve_info& f = h_infos[i];
+        std::memset(&f, 0, sizeof(f));
+        f.status = status[i];
+        f.iterations = its[i];
+        f.setup_performed = setup;
+        f.setup_calls = h->setup_calls;
+        f.levels = (int)h->levels.size();
+        f.colours_l0 = h->g0;
+        f.rel_residual = rr[i];
+        f.rel_residual_est = est[i];
+        f.t_setup_ms = t_setup;
+        f.t_solve_ms = t_solve;
+      }
+    }
+    h->prev_it = maxit;
+    return worst;
+  } catch (...) {
+    return MSP_ERR_NOMEM;
+  }
 }
 
 int msp_device_bytes(msp_handle h, int64_t* bytes) {

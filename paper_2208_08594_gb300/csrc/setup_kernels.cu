@@ -41,6 +41,31 @@ __global__ void check_pattern_kernel(int nb, const int* __restrict__ rp, const i
   }
 }
 
+// instance of an original row: the last i with off[i] <= r
+__device__ __forceinline__ int instance_of(int r, int B, const int* __restrict__ off) {
+  int lo = 0, hi = B - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= r) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// MSP_ERR_PATTERN where a block couples two instances (rows and columns are positions of
+// the permuted pattern; perm maps them to original rows)
+__global__ void check_block_diagonal_kernel(int nb, const int* __restrict__ rp,
+                                            const int* __restrict__ ci, const int* __restrict__ perm,
+                                            int B, const int* __restrict__ off, DevFlags* flags) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
+    const int inst = instance_of(perm[i], B, off);
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+      if (instance_of(perm[ci[p]], B, off) != inst) {
+        raise_flag(flags, MSP_ERR_PATTERN, i);
+        break;
+      }
+  }
+}
+
 __global__ void check_finite_vals_kernel(size_t n, const double* __restrict__ v, DevFlags* flags) {
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
        k += (size_t)gridDim.x * blockDim.x)
@@ -513,6 +538,14 @@ __global__ void scatter_inverse_kernel(int n, const int* __restrict__ perm, int*
 int launch_check_pattern(int nb, const int* rp, const int* ci, int* dpos, DevFlags* flags,
                          cudaStream_t s) {
   check_pattern_kernel<<<grid_for(nb, kThreads), kThreads, 0, s>>>(nb, rp, ci, dpos, flags);
+  return launch_status();
+}
+
+int launch_check_block_diagonal(int nb, const int* rp, const int* ci, const int* perm, int B,
+                                const int* off, DevFlags* flags, cudaStream_t s) {
+  if (nb <= 0) return MSP_OK;
+  check_block_diagonal_kernel<<<grid_for(nb, kThreads), kThreads, 0, s>>>(nb, rp, ci, perm, B,
+                                                                          off, flags);
   return launch_status();
 }
 

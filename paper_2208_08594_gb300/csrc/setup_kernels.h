@@ -58,6 +58,11 @@ int launch_colouring(int n, const int* srp, const int* sci, const int* tp, const
 int launch_check_pattern(int nb, const int* rp, const int* ci, int* dpos, DevFlags* flags,
                          cudaStream_t s);
 int launch_check_finite_vals(size_t n, const double* v, DevFlags* flags, cudaStream_t s);
+// MSP_ERR_PATTERN (index = permuted row) where a block couples two instances: row i of the
+// permuted pattern is original row perm[i]; instance k owns the original rows
+// [off[k], off[k+1])
+int launch_check_block_diagonal(int nb, const int* rp, const int* ci, const int* perm, int B,
+                                const int* off, DevFlags* flags, cudaStream_t s);
 int launch_gather_values(size_t nnz, int bb, const int* src, const double* in, double* out,
                          cudaStream_t s);
 int launch_extract_N(int b, size_t nnzb, const double* v, double* aN, cudaStream_t s);

@@ -672,7 +672,7 @@ __global__ void cast_f2d_kernel(size_t n, const float* __restrict__ in, double* 
 // Krylov reductions (deterministic: per-block partials, then a fixed-order sum)
 // ----------------------------------------------------------------------------------
 constexpr int kDotChunk = 8;
-constexpr int kMaxK = 72;
+constexpr int kMaxK = kKrylovMaxK;
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   v = group_sum<kWarp>(v);
@@ -829,6 +829,128 @@ __global__ void scale_kernel(size_t n, const double* __restrict__ r, double alph
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x)
     v[i] = r[i] * alpha;
+}
+
+// ---- batched Krylov: the vector of a block-diagonal system is split into chunks that each
+// lie inside one instance (chunk c covers [cs[c], ce[c]) of instance ci[c]); every chunk
+// writes its own partials and the partials of an instance are summed in chunk order, so
+// the result is deterministic and does not depend on the other instances.  Chunks of an
+// instance whose active[] flag is 0 are skipped.
+__global__ void __launch_bounds__(kThreads) seg_multi_dot_kernel(
+    int nchunks, const int* __restrict__ cs, const int* __restrict__ ce,
+    const int* __restrict__ cinst, const int* __restrict__ active, const double* __restrict__ V,
+    size_t ldv, int K, const double* __restrict__ w, double* __restrict__ partial) {
+  __shared__ double sh[kThreads / kWarp][kDotChunk];
+  const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp;
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    if (!active[cinst[c]]) continue;  // uniform over the block
+    const size_t i0 = cs[c], i1 = ce[c];
+    for (int k0 = 0; k0 < K; k0 += kDotChunk) {
+      const int kc = min(kDotChunk, K - k0);
+      double acc[kDotChunk];
+#pragma unroll
+      for (int k = 0; k < kDotChunk; ++k) acc[k] = 0.0;
+      for (size_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const double wi = w[i];
+#pragma unroll
+        for (int k = 0; k < kDotChunk; ++k)
+          if (k < kc) acc[k] = fma(__ldg(V + (size_t)(k0 + k) * ldv + i), wi, acc[k]);
+      }
+      const double r = transpose_sum8(acc, lane);
+      __syncthreads();
+      if ((lane & 3) == 0)
+        sh[wid][((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)] = r;
+      __syncthreads();
+      if (threadIdx.x < kc) {
+        double t = 0.0;
+#pragma unroll
+        for (int w2 = 0; w2 < kThreads / kWarp; ++w2) t += sh[w2][threadIdx.x];
+        partial[(size_t)c * kMaxK + k0 + threadIdx.x] = t;
+      }
+    }
+  }
+}
+
+// out[i * kMaxK + koff + k] = sum over instance i's chunks (in order) of partial[c][k];
+// one warp per (instance, k)
+__global__ void seg_reduce_kernel(int B, int K, const int* __restrict__ iptr,
+                                  const int* __restrict__ ichunks, const int* __restrict__ active,
+                                  const double* __restrict__ partial, double* __restrict__ out,
+                                  int koff) {
+  const int q = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
+  const int lane = threadIdx.x % kWarp;
+  if (q >= B * K) return;
+  const int inst = q / K, k = q % K;
+  if (!active[inst]) return;
+  double s = 0.0;
+  for (int t = iptr[inst] + lane; t < iptr[inst + 1]; t += kWarp)
+    s += partial[(size_t)ichunks[t] * kMaxK + k];
+  s = group_sum<kWarp>(s);
+  if (lane == 0) out[(size_t)inst * kMaxK + koff + k] = s;
+}
+
+// w -= sum_k coef[inst][k] V[k] on every chunk of an active instance; partial[c][0] = sum of
+// the new w^2 over the chunk
+__global__ void __launch_bounds__(kThreads) seg_multi_axpy_norm_kernel(
+    int nchunks, const int* __restrict__ cs, const int* __restrict__ ce,
+    const int* __restrict__ cinst, const int* __restrict__ active, const double* __restrict__ V,
+    size_t ldv, int K, const double* __restrict__ coef, double* __restrict__ w,
+    double* __restrict__ partial) {
+  __shared__ double sh[kThreads / kWarp];
+  __shared__ double hs[kMaxK];
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const int inst = cinst[c];
+    if (!active[inst]) continue;
+    __syncthreads();  // the previous chunk's reads of hs are done
+    for (int k = threadIdx.x; k < K; k += blockDim.x) hs[k] = coef[(size_t)inst * kMaxK + k];
+    __syncthreads();
+    double nrm = 0.0;
+    for (size_t i = cs[c] + threadIdx.x; i < (size_t)ce[c]; i += blockDim.x) {
+      double wi = w[i];
+      for (int k = 0; k < K; ++k) wi = fma(-hs[k], __ldg(V + (size_t)k * ldv + i), wi);
+      w[i] = wi;
+      nrm = fma(wi, wi, nrm);
+    }
+    const double t = block_sum(nrm, sh);
+    if (threadIdx.x == 0) partial[(size_t)c * kMaxK] = t;
+  }
+}
+
+// v = w / sqrt(nrm2[inst * kMaxK]) on the chunks of active instances (nothing where the
+// norm is zero); in place allowed
+__global__ void seg_normalize_kernel(int nchunks, const int* __restrict__ cs,
+                                     const int* __restrict__ ce, const int* __restrict__ cinst,
+                                     const int* __restrict__ active, const double* w,
+                                     const double* __restrict__ nrm2, double* v) {
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const int inst = cinst[c];
+    if (!active[inst]) continue;
+    const double h = sqrt(nrm2[(size_t)inst * kMaxK]);
+    if (h == 0.0) continue;
+    const double rh = 1.0 / h;
+    for (size_t i = cs[c] + threadIdx.x; i < (size_t)ce[c]; i += blockDim.x) v[i] = w[i] * rh;
+  }
+}
+
+// x += sum_{k < count[inst]} y[inst][k] Z[k]
+__global__ void seg_update_x_kernel(int nchunks, const int* __restrict__ cs,
+                                    const int* __restrict__ ce, const int* __restrict__ cinst,
+                                    const int* __restrict__ count, const double* __restrict__ Z,
+                                    size_t ldz, const double* __restrict__ y,
+                                    double* __restrict__ x) {
+  __shared__ double ys[kMaxK];
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const int inst = cinst[c], K = count[inst];
+    if (K <= 0) continue;
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x) ys[k] = y[(size_t)inst * kMaxK + k];
+    __syncthreads();
+    for (size_t i = cs[c] + threadIdx.x; i < (size_t)ce[c]; i += blockDim.x) {
+      double xi = x[i];
+      for (int k = 0; k < K; ++k) xi = fma(ys[k], __ldg(Z + (size_t)k * ldz + i), xi);
+      x[i] = xi;
+    }
+  }
 }
 
 __global__ void check_finite_kernel(size_t n, const double* __restrict__ x, int* flag) {
@@ -1174,6 +1296,54 @@ int launch_update_x(size_t n, const double* Z, size_t ldz, int K, const double* 
 
 int launch_scale(size_t n, const double* r, double alpha, double* v, cudaStream_t s) {
   scale_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, r, alpha, v);
+  return launch_status();
+}
+
+int seg_grid(int nchunks) { return std::max(1, std::min(nchunks, krylov_blocks())); }
+
+int launch_seg_multi_dot(const SegChunks& sc, const int* active, const double* V, size_t ldv,
+                         int K, const double* w, double* partial, cudaStream_t s) {
+  if (K > kMaxK) return MSP_ERR_ARG;
+  if (K <= 0 || sc.n <= 0) return MSP_OK;
+  seg_multi_dot_kernel<<<seg_grid(sc.n), kThreads, 0, s>>>(sc.n, sc.start, sc.end, sc.inst,
+                                                           active, V, ldv, K, w, partial);
+  return launch_status();
+}
+
+int launch_seg_reduce(const SegChunks& sc, int B, int K, const int* active,
+                      const double* partial, double* out, int koff, cudaStream_t s) {
+  if (K + koff > kMaxK) return MSP_ERR_ARG;
+  if (K <= 0 || B <= 0) return MSP_OK;
+  const int wpb = 4;
+  const long long q = (long long)B * K;
+  seg_reduce_kernel<<<(unsigned)((q + wpb - 1) / wpb), wpb * kWarp, 0, s>>>(
+      B, K, sc.iptr, sc.ichunks, active, partial, out, koff);
+  return launch_status();
+}
+
+int launch_seg_multi_axpy_norm(const SegChunks& sc, const int* active, const double* V,
+                               size_t ldv, int K, const double* coef, double* w, double* partial,
+                               cudaStream_t s) {
+  if (K > kMaxK) return MSP_ERR_ARG;
+  if (sc.n <= 0) return MSP_OK;
+  seg_multi_axpy_norm_kernel<<<seg_grid(sc.n), kThreads, 0, s>>>(
+      sc.n, sc.start, sc.end, sc.inst, active, V, ldv, K, coef, w, partial);
+  return launch_status();
+}
+
+int launch_seg_normalize(const SegChunks& sc, const int* active, const double* w,
+                         const double* nrm2, double* v, cudaStream_t s) {
+  if (sc.n <= 0) return MSP_OK;
+  seg_normalize_kernel<<<seg_grid(sc.n), kThreads, 0, s>>>(sc.n, sc.start, sc.end, sc.inst,
+                                                           active, w, nrm2, v);
+  return launch_status();
+}
+
+int launch_seg_update_x(const SegChunks& sc, const int* count, const double* Z, size_t ldz,
+                        const double* y, double* x, cudaStream_t s) {
+  if (sc.n <= 0) return MSP_OK;
+  seg_update_x_kernel<<<seg_grid(sc.n), kThreads, 0, s>>>(sc.n, sc.start, sc.end, sc.inst,
+                                                          count, Z, ldz, y, x);
   return launch_status();
 }
 
