@@ -105,6 +105,12 @@ def parse():
                         "rate divided by the mean Newton steps per reservoir)")
     p.add_argument("--serve-slots", type=int, nargs="+", default=[1, 4])
     p.add_argument("--serve-budget-gb", type=float, default=150.0)
+    p.add_argument("--batch", action="store_true",
+                   help="batched instances: many uneven systems stacked block-diagonally and "
+                        "solved together, against the same systems one at a time")
+    p.add_argument("--batch-instances", type=int, default=64)
+    p.add_argument("--batch-cells", type=float, nargs=2, default=[2e4, 5e5])
+    p.add_argument("--batch-steps", type=int, default=2)
     p.add_argument("--time-steps", type=int, default=6)
     p.add_argument("--newton-steps", type=int, default=3)
     p.add_argument("--rel-step", type=float, default=0.15)
@@ -761,8 +767,162 @@ def run_serve(args):
     print(json.dumps(out))
 
 
+def batch_workload(args):
+    """Seeded instances: cells log-uniform in --batch-cells on random boxes (nz 5-40, the
+    rest split with aspect U[1, 4]), b 4 or 6, 0-2 wells; one right-hand side each."""
+    from synthetic import box_jacobian, random_rhs
+    rng = np.random.default_rng(6464)
+    lo, hi = np.log(args.batch_cells[0]), np.log(args.batch_cells[1])
+    out = []
+    for k in range(args.batch_instances):
+        cells = float(np.exp(rng.uniform(lo, hi)))
+        nz = int(rng.integers(5, 41))
+        b = int(rng.choice([4, 6]))
+        aspect = float(rng.uniform(1.0, 4.0))
+        area = max(cells / nz, 4.0)
+        nx = max(2, int(round(np.sqrt(area / aspect))))
+        ny = max(2, int(round(area / nx)))
+        a = box_jacobian(nx, ny, nz, b, 7000 + k, layered=True, kz_ratio=0.1,
+                         n_wells=int(rng.integers(0, 3)))
+        out.append((a, random_rhs(a, 7100 + k)))
+    return out
+
+
+def run_batch(args):
+    """Every instance solved `--batch-steps` times (values fixed, preconditioner reused):
+    (a) batched: one stack per block size, msp_solve_batch; (b) one at a time: a handle
+    per instance, msp_solve.  Both timed with CUDA events on the same stream."""
+    import torch
+
+    import paper_2208_08594_gb300 as msp
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    prec = msp.MSP_PRECISION_FP32 if args.precision == "fp32" else msp.MSP_PRECISION_FP64
+    opts = dict(mu=args.mu, precision=prec, colouring=colouring_of(args, msp),
+                smoother=smoother_of(args, msp))
+    t_gen = time.perf_counter()
+    inst = batch_workload(args)
+    t_gen = time.perf_counter() - t_gen
+    cells = sum(a.nb for a, _ in inst)
+
+    def timed(fn, steps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    # (a) batched, one stack per block size
+    groups = {}
+    for k, (a, r) in enumerate(inst):
+        groups.setdefault(a.b, []).append(k)
+    stacks, t_setup_b = [], time.perf_counter()
+    for b, ks in sorted(groups.items()):
+        nb, bb, rp, ci, v, off = msp.stack_block_diagonal([inst[k][0] for k in ks])
+        rhs = np.concatenate([inst[k][1] for k in ks])
+        solver = msp.BatchSolver(nb, bb, torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev),
+                                 torch.from_numpy(v).to(dev), off, **opts)
+        stacks.append({"b": b, "ks": ks, "solver": solver, "rhs": torch.from_numpy(rhs).to(dev),
+                       "x": torch.zeros(nb * bb, dtype=torch.float64, device=dev),
+                       "nb": nb, "nnzb": int(ci.size), "levels": solver.num_levels,
+                       "colours": msp.msp_level_info(solver.h, 0)[2]})
+    torch.cuda.synchronize()
+    t_setup_b = time.perf_counter() - t_setup_b
+    its_b = {}
+
+    st_b = {}
+
+    def batched():
+        for st in stacks:
+            infos = st["solver"].solve_batch(st["rhs"], st["x"], TOL)
+            for k, i in zip(st["ks"], infos):
+                if i["status"] < 0:
+                    raise RuntimeError("instance %d: %s" % (k, i))
+                its_b[k] = i["iterations"]
+                st_b[k] = i["status"]
+
+    batched()  # warm-up
+    msp.msp_stats_reset()
+    msp.msp_stats_enable(1)
+    ms_b = timed(batched, args.batch_steps)
+    launches_b = msp.msp_stats_launches()
+    msp.msp_stats_enable(0)
+    stack_info = [dict({k: st[k] for k in ("b", "nb", "nnzb", "levels", "colours")},
+                       instances=len(st["ks"])) for st in stacks]
+    for st in stacks:
+        st["solver"].close()
+    del stacks
+
+    # (b) one at a time
+    t_setup_1 = time.perf_counter()
+    singles = []
+    for a, r in inst:
+        solver = msp.Solver(a.nb, a.b, torch.from_numpy(a.row_ptr).to(dev),
+                            torch.from_numpy(a.col_idx).to(dev),
+                            torch.from_numpy(a.values.reshape(-1)).to(dev), **opts)
+        singles.append((solver, torch.from_numpy(r).to(dev),
+                        torch.zeros(a.nb * a.b, dtype=torch.float64, device=dev)))
+    torch.cuda.synchronize()
+    t_setup_1 = time.perf_counter() - t_setup_1
+    its_1 = {}
+
+    st_1 = {}
+
+    def one_by_one():
+        for k, (solver, r, x) in enumerate(singles):
+            i = solver.solve(r, x, TOL)
+            if i["status"] < 0:
+                raise RuntimeError("instance %d: %s" % (k, i))
+            its_1[k] = i["iterations"]
+            st_1[k] = i["status"]
+
+    one_by_one()
+    msp.msp_stats_reset()
+    msp.msp_stats_enable(1)
+    ms_1 = timed(one_by_one, args.batch_steps)
+    launches_1 = msp.msp_stats_launches()
+    msp.msp_stats_enable(0)
+    for solver, _, _ in singles:
+        solver.close()
+
+    n_solves = args.batch_steps * len(inst)
+    out = {"metric": "batched instances: solves/s", "unit": "solves/s",
+           "value": round(n_solves / (ms_b / 1000.0), 3), "higher_is_better": True, "n_gpus": 1,
+           "dtype": "f64" if args.precision == "fp64" else "f32-precond/f64-krylov",
+           "data": "synthetic", "vs_baseline": None,
+           "config": {"workload": "%d instances, cells log-uniform %.0f-%.0f, b 4 or 6" % (
+                          len(inst), args.batch_cells[0], args.batch_cells[1]),
+                      "cells": cells, "steps": args.batch_steps, "mu": args.mu, "tol": TOL,
+                      "generation_s": round(t_gen, 1)},
+           "batched": {"ms_per_step": round(ms_b / args.batch_steps, 1),
+                       "solves_per_s": round(n_solves / (ms_b / 1000.0), 3),
+                       "cell_solves_per_s": round(cells * args.batch_steps / (ms_b / 1000.0), 1),
+                       "launches_per_step": round(launches_b / args.batch_steps, 1),
+                       "setup_s": round(t_setup_b, 2),
+                       "iterations_total": int(sum(its_b.values())),
+                       "iterations_max": int(max(its_b.values())),
+                       "not_converged": sorted(k for k, v in st_b.items() if v != 0)},
+           "one_at_a_time": {"ms_per_step": round(ms_1 / args.batch_steps, 1),
+                             "solves_per_s": round(n_solves / (ms_1 / 1000.0), 3),
+                             "cell_solves_per_s": round(cells * args.batch_steps / (ms_1 / 1000.0), 1),
+                             "launches_per_step": round(launches_1 / args.batch_steps, 1),
+                             "setup_s": round(t_setup_1, 2),
+                             "iterations_total": int(sum(its_1.values())),
+                             "iterations_max": int(max(its_1.values())),
+                             "not_converged": sorted(k for k, v in st_1.items() if v != 0)},
+           "stacks": stack_info}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
+    if args.batch:
+        run_batch(args)
+        return
     if args.serve:
         run_serve(args)
         return

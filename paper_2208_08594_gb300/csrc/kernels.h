@@ -8,20 +8,24 @@
 namespace msp {
 
 // ---------------- solve phase: block rows of the colour-ordered BSR matrix --------------
+// rmask (optional, one byte per row of the level-0 order): rows with rmask[i] == 0 are
+// skipped — not read, not written (instances of a batch that have left the active set).
 // y = A x (residual = false) or y = g - A x (residual = true); b = block size 1..8.
 template <typename T>
 int launch_bsr_spmv(int b, int nb, const int* rp, const int* ci, const T* v, const T* x,
-                    const T* g, T* y, bool residual, cudaStream_t s);
+                    const T* g, T* y, bool residual, cudaStream_t s,
+                    const unsigned char* rmask = nullptr);
 // rP[i] = omega_i^T (g_i - (A w)_i)   (omega == nullptr: first unknown only); r != nullptr
 // also receives g - A w
 template <typename T>
 int launch_bsr_restrict_p(int b, int nb, const int* rp, const int* ci, const T* v,
-                          const T* w, const T* g, const T* omega, T* rP, T* r, cudaStream_t s);
+                          const T* w, const T* g, const T* omega, T* rP, T* r, cudaStream_t s,
+                          const unsigned char* rmask = nullptr);
 // r_i <- r_i - sum_j A_ij[:, 0] e_j and w_i[0] += e_i (r, w: nb*b values; c0: column 0 of
 // every block, nnzb*b values; e: one value per block row)
 template <typename T>
 int launch_bsr_col0_update(int b, int nb, const int* rp, const int* ci, const T* c0, const T* e,
-                           T* r, T* w, cudaStream_t s);
+                           T* r, T* w, cudaStream_t s, const unsigned char* rmask = nullptr);
 // c0[p*b + r] = v[(p*b + r)*b]
 template <typename T>
 int launch_extract_col0(size_t nnzb, int b, const T* v, T* c0, cudaStream_t s);
@@ -31,15 +35,17 @@ int launch_extract_col0(size_t nnzb, int b, const T* v, T* c0, cudaStream_t s);
 template <typename T>
 int launch_bgs_colour(int b, int r0, int r1, const int* rp, const int* ci, const int* dpos,
                       const T* aN, const T* dNinv, const T* g, T* w, bool lower_only,
-                      bool zero_pressure, cudaStream_t s);
+                      bool zero_pressure, cudaStream_t s, const unsigned char* rmask = nullptr);
 // stage R: forward y_i = r_i - sum_{j<i} L_ij y_j and backward x_i = U_ii^-1 (y_i -
 // sum_{j>i} U_ij x_j); the backward sweep also adds x_i into w.
 template <typename T>
 int launch_bilu_fwd(int b, int r0, int r1, const int* rp, const int* ci, const int* dpos,
-                    const T* lu, const T* r, T* y, cudaStream_t s);
+                    const T* lu, const T* r, T* y, cudaStream_t s,
+                    const unsigned char* rmask = nullptr);
 template <typename T>
 int launch_bilu_bwd(int b, int r0, int r1, const int* rp, const int* ci, const int* dpos,
-                    const T* lu, const T* uinv, const T* y, T* x, T* w, cudaStream_t s);
+                    const T* lu, const T* uinv, const T* y, T* x, T* w, cudaStream_t s,
+                    const unsigned char* rmask = nullptr);
 // w[i*b] += e[i]
 template <typename T>
 int launch_prolong_p(int b, int nb, const T* e, T* w, cudaStream_t s);
@@ -51,7 +57,7 @@ int launch_prolong_p(int b, int nb, const T* e, T* w, cudaStream_t s);
 template <typename T>
 int launch_csr_gs_colour(int r0, int r1, const int* rp, const int* ci, const T* v,
                          const int* dpos, const T* rdiag, const T* b, T* x, bool lower_only,
-                         int avg_row, cudaStream_t s);
+                         int avg_row, cudaStream_t s, const unsigned char* rmask = nullptr);
 // bc[I] = sum over members i of aggregate I (ascending) of (b_i - (A x)_i)
 // the same sweep over the ELL copy of the level (K in {8, 16, 24, 32} slots per row, slot
 // k of row i at i*K + k; meta from launch_build_ell; rows with meta < 0 use rp/ci/v)
@@ -59,7 +65,7 @@ template <typename T>
 int launch_ell_gs_colour(int K, int r0, int r1, const int* ell_ci, const T* ell_v,
                          const int* meta, const int* rp, const int* ci, const T* v,
                          const int* dpos, const T* rdiag, const T* b, T* x, bool lower_only,
-                         cudaStream_t s);
+                         cudaStream_t s, const unsigned char* rmask = nullptr);
 // the same restriction over the ELL copy of the level (diag: a_ii of every row)
 template <typename T>
 int launch_ell_residual_restrict(int K, int nc, const int* mptr, const int* members,
@@ -153,6 +159,11 @@ int launch_seg_multi_axpy_norm(const SegChunks& sc, const int* active, const dou
 // v = w / sqrt(nrm2[i][0]) per instance (nothing where the norm is zero)
 int launch_seg_normalize(const SegChunks& sc, const int* active, const double* w,
                          const double* nrm2, double* v, cudaStream_t s);
+// rmask[i] = (active[row_inst[i]] != 0) for the nb level-0 rows
+int launch_expand_mask(int nb, const int* row_inst, const int* active, unsigned char* rmask,
+                       cudaStream_t s);
+// v = 0 on the instances with mask[i] != 0
+int launch_seg_zero(const SegChunks& sc, const int* mask, double* v, cudaStream_t s);
 // x += sum_{k < count[i]} y[i][k] Z[k]
 int launch_seg_update_x(const SegChunks& sc, const int* count, const double* Z, size_t ldz,
                         const double* y, double* x, cudaStream_t s);

@@ -389,9 +389,11 @@ struct msp_handle_s {
   std::vector<int> batch_offsets;             // block-row offsets (natural order)
   msp::DevBuf<int> seg_start, seg_end, seg_inst, seg_iptr, seg_ichunks;
   int seg_n = 0;
-  msp::DevBuf<int> bact, bcount;              // per instance: active flag, columns used
+  msp::DevBuf<int> bact, bcount, bzero;       // per instance: active, columns used, zero mask
   msp::DevBuf<double> bpart, bh, by, bn, bydev;  // chunk partials; per instance kKrylovMaxK
   double* h_bpin = nullptr;                   // pinned: bh, by, bn (3 * batch * kKrylovMaxK)
+  msp::DevBuf<int> row_inst;                  // instance of every level-0 (permuted) row
+  msp::DevBuf<unsigned char> rmask0;          // level-0 rows of the active instances
 };
 
 namespace msp {
@@ -888,6 +890,8 @@ struct PView {
   std::vector<const T*> lv, lrd, lev, led;
   std::vector<T*> lb, lx, lt;
   T *r, *y, *x;
+  // level-0 rows to skip (instances of a batch that left the active set), or nullptr
+  const unsigned char* m0 = nullptr;
 };
 
 PView<double> view64(msp_handle h) {
@@ -911,6 +915,7 @@ PView<double> view64(msp_handle h) {
   p.r = h->pr.p;
   p.y = h->py.p;
   p.x = h->px.p;
+  p.m0 = h->batch ? h->rmask0.p : nullptr;
   return p;
 }
 
@@ -935,6 +940,7 @@ PView<float> view32(msp_handle h) {
   p.r = h->pr32.p;
   p.y = h->py32.p;
   p.x = h->px32.p;
+  p.m0 = h->batch ? h->rmask0.p : nullptr;
   return p;
 }
 
@@ -978,9 +984,11 @@ int vcycle(msp_handle h, const PView<T>& P, int l, cudaStream_t s) {
     if (use_ell(c, lower_only))
       return launch_ell_gs_colour<T>(L.ell_k, L.cptr[c], L.cptr[c + 1], L.ell_ci.p, P.lev[l],
                                      L.ell_meta.p, L.A.rp.p, L.A.ci.p, P.lv[l], L.dpos.p,
-                                     P.lrd[l], P.lb[l], P.lx[l], lower_only, s);
+                                     P.lrd[l], P.lb[l], P.lx[l], lower_only, s,
+                                     l == 0 ? P.m0 : nullptr);
     return launch_csr_gs_colour<T>(L.cptr[c], L.cptr[c + 1], L.A.rp.p, L.A.ci.p, P.lv[l],
-                                   L.dpos.p, P.lrd[l], P.lb[l], P.lx[l], lower_only, avg_row, s);
+                                   L.dpos.p, P.lrd[l], P.lb[l], P.lx[l], lower_only, avg_row, s,
+                                   l == 0 ? P.m0 : nullptr);
   };
   // one smoothing phase: its colour launches in order, timed in runs of one kernel
   struct SweepLaunch {
@@ -1082,7 +1090,7 @@ int stage_N(msp_handle h, const PView<T>& P, const T* g, T* w, cudaStream_t s) {
   for (int sw = 0; sw < h->cfg.bgs_sweeps; ++sw)
     for (int c = 0; c < h->g0; ++c)
       MSP_TRY(launch_bgs_colour<T>(b, h->cptr0[c], h->cptr0[c + 1], h->rp.p, h->ci.p, h->dpos.p,
-                                   P.aN, P.dNinv, g, w, sw == 0, sw == 0, s));
+                                   P.aN, P.dNinv, g, w, sw == 0, sw == 0, s, P.m0));
   return MSP_OK;
 }
 
@@ -1102,7 +1110,7 @@ int stage_P(msp_handle h, const PView<T>& P, const T* g, T* w, T* r, cudaStream_
   {
     Probe pr("stageP_residual_restrict", bsr_bytes(h, sT, r ? 3 : 2) + (double)h->nb * sT, s);
     MSP_TRY(launch_bsr_restrict_p<T>(h->b, h->nb, h->rp.p, h->ci.p, P.vals, w, g, P.omega,
-                                     P.lb[0], r, s));
+                                     P.lb[0], r, s, P.m0));
   }
   MSP_TRY(vcycle<T>(h, P, 0, s));
   if (!r) {
@@ -1112,7 +1120,7 @@ int stage_P(msp_handle h, const PView<T>& P, const T* g, T* w, T* r, cudaStream_
   Probe pr("stageP_correct_residual",
            (double)h->nnzb * (b * sT + 4) + (double)(h->nb + 1) * 4 +
                (double)h->nb * sT * (1 + 2 * b + 2), s);
-  return launch_bsr_col0_update<T>(h->b, h->nb, h->rp.p, h->ci.p, P.c0, P.lx[0], r, w, s);
+  return launch_bsr_col0_update<T>(h->b, h->nb, h->rp.p, h->ci.p, P.c0, P.lx[0], r, w, s, P.m0);
 }
 
 template <typename T>
@@ -1130,12 +1138,12 @@ int stage_R(msp_handle h, const PView<T>& P, const T* r, T* w, cudaStream_t s) {
     Probe pr("stageR_bilu_fwd", fwd, s, h->g0);
     for (int c = 0; c < h->g0; ++c)
       MSP_TRY(launch_bilu_fwd<T>(b, h->cptr0[c], h->cptr0[c + 1], h->rp.p, h->ci.p, h->dpos.p,
-                                 P.lu, r, P.y, s));
+                                 P.lu, r, P.y, s, P.m0));
   }
   Probe pr("stageR_bilu_bwd", bwd, s, h->g0);
   for (int c = h->g0 - 1; c >= 0; --c)
     MSP_TRY(launch_bilu_bwd<T>(b, h->cptr0[c], h->cptr0[c + 1], h->rp.p, h->ci.p, h->dpos.p,
-                               P.lu, P.uinv, P.y, P.x, w, s));
+                               P.lu, P.uinv, P.y, P.x, w, s, P.m0));
   return MSP_OK;
 }
 
@@ -1496,8 +1504,12 @@ SegChunks seg_chunks(msp_handle h) {
 // application and one SpMV per step serve all instances (the matrix and the preconditioner
 // are block diagonal); inner products, norms, Hessenberg matrices, rotations, convergence
 // and restarts are per instance.  Each step uses classical Gram-Schmidt with a second pass
-// (always taken).  An instance that converges or stops leaves the active set; its vectors
-// are no longer read or written.
+// (always taken).  An instance that converges or stops leaves the active set: the Krylov
+// kernels, the SpMV and the level-0 kernels of the preconditioner skip its rows (a row
+// mask), so a straggling instance no longer costs the others' bandwidth there; its part
+// of the next basis vector is set to zero, so what the coarse AMG levels still compute for
+// it stays finite (the dense coarsest solve multiplies every instance's entries, zeros
+// included, into every row).
 int fgmres_batched(msp_handle h, double tol, std::vector<int>& its, std::vector<double>& relres,
                    std::vector<double>& relest, std::vector<int>& status, cudaStream_t s) {
   const int B = h->batch, m = h->cfg.restart;
@@ -1518,7 +1530,15 @@ int fgmres_batched(msp_handle h, double tol, std::vector<int>& its, std::vector<
   std::vector<int> act(B, 1), done(B, 0), stop(B, 0), jused(B, 0), brk(B, 0);
   auto upload_act = [&](const std::vector<int>& a) -> int {
     MSP_CUDA_TRY(cudaMemcpyAsync(h->bact.p, a.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+    MSP_TRY(launch_expand_mask(h->nb, h->row_inst.p, h->bact.p, h->rmask0.p, s));
     // the host vector may change before the copy runs: wait for it
+    MSP_CUDA_TRY(cudaStreamSynchronize(s));
+    return MSP_OK;
+  };
+  // zero the part of v that belongs to the instances with z[i] != 0
+  auto zero_parts = [&](const std::vector<int>& z, double* v) -> int {
+    MSP_CUDA_TRY(cudaMemcpyAsync(h->bzero.p, z.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
+    MSP_TRY(launch_seg_zero(sc, h->bzero.p, v, s));
     MSP_CUDA_TRY(cudaStreamSynchronize(s));
     return MSP_OK;
   };
@@ -1555,10 +1575,10 @@ int fgmres_batched(msp_handle h, double tol, std::vector<int>& its, std::vector<
   std::vector<double> est(B, 1.0), ybuf((size_t)B * KM, 0.0);
   std::vector<int> cnt(B, 0);
   while (true) {
-    MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, x, bvec, h->rvec.p,
-                                    true, s));
     for (int i = 0; i < B; ++i) act[i] = !done[i];
     MSP_TRY(upload_act(act));
+    MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, x, bvec, h->rvec.p,
+                                    true, s, h->rmask0.p));
     MSP_TRY(seg_norms(h->rvec.p));
     int ncycle = 0;
     for (int i = 0; i < B; ++i) {
@@ -1589,6 +1609,7 @@ int fgmres_batched(msp_handle h, double tol, std::vector<int>& its, std::vector<
     if (ncycle == 0) break;
     MSP_TRY(upload_act(act));
     MSP_TRY(launch_seg_normalize(sc, h->bact.p, h->rvec.p, h->bn.p, V, s));
+    MSP_TRY(zero_parts(done, V));  // the instances outside this cycle start from zero
     bool any = true;
     for (int j = 0; j < m && any; ++j) {
       double* vj = V + (size_t)j * n;
@@ -1598,7 +1619,7 @@ int fgmres_batched(msp_handle h, double tol, std::vector<int>& its, std::vector<
       {
         Probe pr("batch_spmv", bsr_bytes(h, 8.0, 1), s);
         MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, zj, nullptr, w,
-                                        false, s));
+                                        false, s, h->rmask0.p));
       }
       const int K = j + 1;
       {
@@ -1630,6 +1651,7 @@ int fgmres_batched(msp_handle h, double tol, std::vector<int>& its, std::vector<
       MSP_CUDA_TRY(cudaStreamSynchronize(s));
       bool changed = false;
       any = false;
+      std::vector<int> left(B, 0);
       for (int i = 0; i < B; ++i) {
         if (!act[i]) continue;
         ++its[i];
@@ -1665,12 +1687,16 @@ int fgmres_batched(msp_handle h, double tol, std::vector<int>& its, std::vector<
         if (hn == 0.0) brk[i] = 1;
         if (done[i] || est[i] <= tol || its[i] >= h->cfg.max_it || brk[i]) {
           act[i] = 0;
+          left[i] = 1;
           changed = true;
         } else {
           any = true;
         }
       }
-      if (changed && any) MSP_TRY(upload_act(act));
+      if (changed && any) {
+        MSP_TRY(upload_act(act));
+        MSP_TRY(zero_parts(left, w));  // the next preconditioner input of those instances
+      }
     }
     // x_i += Z y_i with y_i = H_i^{-1} s_i
     std::fill(ybuf.begin(), ybuf.end(), 0.0);
@@ -1691,10 +1717,10 @@ int fgmres_batched(msp_handle h, double tol, std::vector<int>& its, std::vector<
     MSP_CUDA_TRY(cudaStreamSynchronize(s));
   }
   // true residuals
-  MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, x, bvec, h->rvec.p,
-                                  true, s));
   for (int i = 0; i < B; ++i) act[i] = bnorm[i] > 0.0 && std::isfinite(bnorm[i]);
   MSP_TRY(upload_act(act));
+  MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, x, bvec, h->rvec.p,
+                                  true, s, h->rmask0.p));
   MSP_TRY(seg_norms(h->rvec.p));
   for (int i = 0; i < B; ++i) {
     if (act[i]) relres[i] = std::sqrt(nb2[(size_t)i * KM]) / bnorm[i];
@@ -1900,6 +1926,7 @@ int msp_solve(msp_handle h, const double* d_b, double* d_x, double rel_tol,
   if (!h || !d_b || !d_x || !(rel_tol > 0.0)) return MSP_ERR_ARG;
   DevBytesScope bytes_scope(h);
   cudaStream_t s = (cudaStream_t)stream;
+  if (h->batch) MSP_CUDA_TRY(cudaMemsetAsync(h->rmask0.p, 1, h->nb, s));  // every row
   msp_solve_info local{};
   msp_solve_info* inf = info ? info : &local;
   std::memset(inf, 0, sizeof(*inf));
@@ -1977,6 +2004,7 @@ int msp_apply_precond(msp_handle h, const double* d_g, double* d_w, void* stream
   if (!h || !d_g || !d_w) return MSP_ERR_ARG;
   DevBytesScope bytes_scope(h);
   cudaStream_t s = (cudaStream_t)stream;
+  if (h->batch) MSP_CUDA_TRY(cudaMemsetAsync(h->rmask0.p, 1, h->nb, s));  // every row
   try {
     MSP_TRY(launch_gather_blocks(h->nb, h->b, h->perm0.p, d_g, h->bperm.p, s));
     MSP_TRY(apply_precond(h, h->bperm.p, h->xperm.p, s));
@@ -2113,9 +2141,18 @@ int msp_set_instances(msp_handle h, int32_t count, const int32_t* h_row_offsets)
     MSP_TRY(h->bydev.alloc(per));
     MSP_TRY(h->bact.alloc(count));
     MSP_TRY(h->bcount.alloc(count));
+    MSP_TRY(h->bzero.alloc(count));
     if (h->h_bpin) cudaFreeHost(h->h_bpin);
     h->h_bpin = nullptr;
     MSP_CUDA_TRY(cudaMallocHost(&h->h_bpin, 3 * per * sizeof(double)));
+    std::vector<int> rinst(nb);
+    for (int p = 0; p < nb; ++p) rinst[p] = inst_of(perm[p]);
+    MSP_TRY(h->row_inst.alloc(nb));
+    MSP_TRY(h->rmask0.alloc(nb));
+    MSP_CUDA_TRY(cudaMemcpy(h->row_inst.p, rinst.data(), sizeof(int) * (size_t)nb,
+                            cudaMemcpyHostToDevice));
+    MSP_CUDA_TRY(cudaMemset(h->rmask0.p, 1, nb));
+    drop_graph(h);  // the preconditioner graph is captured again with the row mask
     h->seg_n = nchunks;
     h->batch = count;
     h->batch_offsets = offs;

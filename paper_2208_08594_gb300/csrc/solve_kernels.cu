@@ -92,13 +92,14 @@ __global__ void __launch_bounds__(kThreads) bsr_spmv_kernel(int nb, const int* _
                                                            const T* __restrict__ v,
                                                            const T* __restrict__ x,
                                                            const T* __restrict__ g,
-                                                           T* __restrict__ y) {
+                                                           T* __restrict__ y,
+                                                           const unsigned char* __restrict__ rmask) {
   constexpr int GP = Gp<B>::v;
   const int lane = threadIdx.x % GP;
   const int gpb = blockDim.x / GP;
   const int stride = gridDim.x * gpb;
   for (int i = blockIdx.x * gpb + threadIdx.x / GP; i < nb; i += stride) {
-    if (lane >= B) continue;
+    if (lane >= B || (rmask && !rmask[i])) continue;
     const int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
     T acc = RES ? g[(size_t)i * B + lane] : T(0);
     int p = p0;
@@ -130,7 +131,7 @@ template <int B, typename T, bool WR>
 __global__ void __launch_bounds__(kThreads) bsr_restrict_p_kernel(
     int nb, const int* __restrict__ rp, const int* __restrict__ ci, const T* __restrict__ v,
     const T* __restrict__ w, const T* __restrict__ g, const T* __restrict__ omega,
-    T* __restrict__ rP, T* __restrict__ r) {
+    T* __restrict__ rP, T* __restrict__ r, const unsigned char* __restrict__ rmask) {
   constexpr int GP = Gp<B>::v;
   const int lane = threadIdx.x % GP;
   const int gpb = blockDim.x / GP;
@@ -138,7 +139,8 @@ __global__ void __launch_bounds__(kThreads) bsr_restrict_p_kernel(
   for (int base = blockIdx.x * gpb; base < nb; base += gridDim.x * gpb) {
     const int i = base + threadIdx.x / GP;
     T res = T(0);
-    const bool active = (i < nb) && (lane < B);
+    const bool live = (i < nb) && (!rmask || rmask[i]);
+    const bool active = live && (lane < B);
     if (active) {
       const int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
       T acc = g[(size_t)i * B + lane];
@@ -164,7 +166,7 @@ __global__ void __launch_bounds__(kThreads) bsr_restrict_p_kernel(
       res = omega ? acc * omega[(size_t)i * B + lane] : (lane == 0 ? acc : T(0));
     }
     res = group_sum<GP>(res);
-    if (i < nb && lane == 0) rP[i] = res;
+    if (live && lane == 0) rP[i] = res;
   }
 }
 
@@ -178,13 +180,14 @@ __global__ void __launch_bounds__(kThreads) bsr_restrict_p_kernel(
 template <int B, typename T>
 __global__ void __launch_bounds__(kThreads) bsr_col0_update_kernel(
     int nb, const int* __restrict__ rp, const int* __restrict__ ci, const T* __restrict__ c0,
-    const T* __restrict__ e, T* __restrict__ r, T* __restrict__ w) {
+    const T* __restrict__ e, T* __restrict__ r, T* __restrict__ w,
+    const unsigned char* __restrict__ rmask) {
   constexpr int GP = Gp<B>::v;
   const int lane = threadIdx.x % GP;
   const int gpb = blockDim.x / GP;
   const int stride = gridDim.x * gpb;
   for (int i = blockIdx.x * gpb + threadIdx.x / GP; i < nb; i += stride) {
-    if (lane >= B) continue;
+    if (lane >= B || (rmask && !rmask[i])) continue;
     const int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
     T acc = r[(size_t)i * B + lane];
     int p = p0;
@@ -222,7 +225,8 @@ template <int B, typename T>
 __global__ void __launch_bounds__(kThreads) bgs_colour_kernel(
     int r0, int r1, const int* __restrict__ rp, const int* __restrict__ ci,
     const int* __restrict__ dpos, const T* __restrict__ aN, const T* __restrict__ dNinv,
-    const T* __restrict__ g, T* __restrict__ w, bool lower_only, bool zero_pressure) {
+    const T* __restrict__ g, T* __restrict__ w, bool lower_only, bool zero_pressure,
+    const unsigned char* __restrict__ rmask) {
   constexpr int BN = B - 1;
   // BN lanes per row, packed 32 / BN rows to a warp (b = 4: 10 rows, 30 lanes busy)
   constexpr int R = kWarp / BN;
@@ -233,7 +237,7 @@ __global__ void __launch_bounds__(kThreads) bgs_colour_kernel(
   for (int base = r0 + blockIdx.x * rpb; base < r1; base += gridDim.x * rpb) {
     const int i = base + first;
     T acc = T(0);
-    const bool active = (slot < R) && (i < r1);
+    const bool active = (slot < R) && (i < r1) && (!rmask || rmask[i]);
     if (active) {
       acc = g[(size_t)i * B + 1 + lane];
       const int p0 = __ldg(rp + i), pd = __ldg(dpos + i), p1 = __ldg(rp + i + 1);
@@ -292,12 +296,12 @@ template <int B, typename T>
 __global__ void __launch_bounds__(kThreads) bilu_fwd_kernel(
     int r0, int r1, const int* __restrict__ rp, const int* __restrict__ ci,
     const int* __restrict__ dpos, const T* __restrict__ lu, const T* __restrict__ r,
-    T* __restrict__ y) {
+    T* __restrict__ y, const unsigned char* __restrict__ rmask) {
   constexpr int GP = Gp<B>::v;
   const int lane = threadIdx.x % GP;
   const int gpb = blockDim.x / GP;
   for (int i = r0 + blockIdx.x * gpb + threadIdx.x / GP; i < r1; i += gridDim.x * gpb) {
-    if (lane >= B) continue;
+    if (lane >= B || (rmask && !rmask[i])) continue;
     T acc = r[(size_t)i * B + lane];
     const int p0 = __ldg(rp + i), pd = __ldg(dpos + i);
     // y rows of earlier colours: none of them is written by this launch
@@ -328,14 +332,15 @@ template <int B, typename T>
 __global__ void __launch_bounds__(kThreads) bilu_bwd_kernel(
     int r0, int r1, const int* __restrict__ rp, const int* __restrict__ ci,
     const int* __restrict__ dpos, const T* __restrict__ lu, const T* __restrict__ uinv,
-    const T* __restrict__ y, T* __restrict__ x, T* __restrict__ w) {
+    const T* __restrict__ y, T* __restrict__ x, T* __restrict__ w,
+    const unsigned char* __restrict__ rmask) {
   constexpr int GP = Gp<B>::v;
   const int lane = threadIdx.x % GP;
   const int gpb = blockDim.x / GP;
   const int grp = threadIdx.x / GP;
   for (int base = r0 + blockIdx.x * gpb; base < r1; base += gridDim.x * gpb) {
     const int i = base + grp;
-    const bool active = (i < r1) && (lane < B);
+    const bool active = (i < r1) && (lane < B) && (!rmask || rmask[i]);
     T acc = T(0);
     if (active) {
       acc = y[(size_t)i * B + lane];
@@ -388,13 +393,15 @@ template <typename T, int TPR>
 __global__ void __launch_bounds__(kThreads) csr_gs_colour_kernel(
     int r0, int r1, const int* __restrict__ rp, const int* __restrict__ ci,
     const T* __restrict__ v, const int* __restrict__ dpos, const T* __restrict__ rdiag,
-    const T* __restrict__ b, T* __restrict__ x, bool lower_only) {
+    const T* __restrict__ b, T* __restrict__ x, bool lower_only,
+    const unsigned char* __restrict__ rmask) {
   const int lane = threadIdx.x % TPR;
   const int rpb = blockDim.x / TPR;
   for (int base = r0 + blockIdx.x * rpb; base < r1; base += gridDim.x * rpb) {
     const int i = base + threadIdx.x / TPR;
     T s = T(0), bi = T(0), di = T(0);
-    if (i < r1) {
+    const bool live = (i < r1) && (!rmask || rmask[i]);
+    if (live) {
       if (lane == 0) {  // issued with the row's first loads, not after the reduction
         bi = __ldg(b + i);
         di = __ldg(rdiag + i);
@@ -407,7 +414,7 @@ __global__ void __launch_bounds__(kThreads) csr_gs_colour_kernel(
       }
     }
     s = group_sum<TPR>(s);
-    if (i < r1 && lane == 0) x[i] = (bi - s) * di;
+    if (live && lane == 0) x[i] = (bi - s) * di;
   }
 }
 
@@ -422,14 +429,16 @@ __global__ void __launch_bounds__(kThreads) ell_gs_colour_kernel(
     int r0, int r1, const int* __restrict__ ell_ci, const T* __restrict__ ell_v,
     const int* __restrict__ meta, const int* __restrict__ rp, const int* __restrict__ ci,
     const T* __restrict__ v, const int* __restrict__ dpos, const T* __restrict__ rdiag,
-    const T* __restrict__ b, T* __restrict__ x, bool lower_only) {
+    const T* __restrict__ b, T* __restrict__ x, bool lower_only,
+    const unsigned char* __restrict__ rmask) {
   constexpr int S = (K + TPR - 1) / TPR;  // slots per lane
   const int lane = threadIdx.x % TPR;
   const int rpb = blockDim.x / TPR;
   for (int base = r0 + blockIdx.x * rpb; base < r1; base += gridDim.x * rpb) {
     const int i = base + threadIdx.x / TPR;
     T s = T(0), bi = T(0), di = T(0);
-    if (i < r1) {
+    const bool live = (i < r1) && (!rmask || rmask[i]);
+    if (live) {
       const int m = __ldg(meta + i);
       if (lane == 0) {
         bi = __ldg(b + i);
@@ -460,7 +469,7 @@ __global__ void __launch_bounds__(kThreads) ell_gs_colour_kernel(
       }
     }
     s = group_sum<TPR>(s);
-    if (i < r1 && lane == 0) x[i] = (bi - s) * di;
+    if (live && lane == 0) x[i] = (bi - s) * di;
   }
 }
 
@@ -932,6 +941,23 @@ __global__ void seg_normalize_kernel(int nchunks, const int* __restrict__ cs,
   }
 }
 
+// rmask[i] = active[row_inst[i]] != 0 for every level-0 row
+__global__ void expand_mask_kernel(int nb, const int* __restrict__ row_inst,
+                                   const int* __restrict__ active, unsigned char* __restrict__ rmask) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x)
+    rmask[i] = active[row_inst[i]] != 0;
+}
+
+// v = 0 on the chunks of the instances with mask[inst] != 0
+__global__ void seg_zero_kernel(int nchunks, const int* __restrict__ cs, const int* __restrict__ ce,
+                                const int* __restrict__ cinst, const int* __restrict__ mask,
+                                double* __restrict__ v) {
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    if (!mask[cinst[c]]) continue;
+    for (size_t i = cs[c] + threadIdx.x; i < (size_t)ce[c]; i += blockDim.x) v[i] = 0.0;
+  }
+}
+
 // x += sum_{k < count[inst]} y[inst][k] Z[k]
 __global__ void seg_update_x_kernel(int nchunks, const int* __restrict__ cs,
                                     const int* __restrict__ ce, const int* __restrict__ cinst,
@@ -1006,41 +1032,43 @@ inline unsigned grid_groups(size_t groups, int gp) {
 
 template <typename T>
 int launch_bsr_spmv(int b, int nb, const int* rp, const int* ci, const T* v, const T* x,
-                    const T* g, T* y, bool residual, cudaStream_t s) {
+                    const T* g, T* y, bool residual, cudaStream_t s,
+                    const unsigned char* rmask) {
   if (nb <= 0) return MSP_OK;
   MSP_B_SWITCH(b, {
     const unsigned grid = grid_groups(nb, Gp<B_>::v);
     if (residual)
-      bsr_spmv_kernel<B_, T, true><<<grid, kThreads, 0, s>>>(nb, rp, ci, v, x, g, y);
+      bsr_spmv_kernel<B_, T, true><<<grid, kThreads, 0, s>>>(nb, rp, ci, v, x, g, y, rmask);
     else
-      bsr_spmv_kernel<B_, T, false><<<grid, kThreads, 0, s>>>(nb, rp, ci, v, x, g, y);
+      bsr_spmv_kernel<B_, T, false><<<grid, kThreads, 0, s>>>(nb, rp, ci, v, x, g, y, rmask);
   });
   return launch_status();
 }
 
 template <typename T>
 int launch_bsr_restrict_p(int b, int nb, const int* rp, const int* ci, const T* v, const T* w,
-                          const T* g, const T* omega, T* rP, T* r, cudaStream_t s) {
+                          const T* g, const T* omega, T* rP, T* r, cudaStream_t s,
+                          const unsigned char* rmask) {
   if (nb <= 0) return MSP_OK;
   MSP_B_SWITCH(b, {
     const unsigned grid = grid_groups(nb, Gp<B_>::v);
     if (r)
       bsr_restrict_p_kernel<B_, T, true><<<grid, kThreads, 0, s>>>(nb, rp, ci, v, w, g, omega,
-                                                                   rP, r);
+                                                                   rP, r, rmask);
     else
       bsr_restrict_p_kernel<B_, T, false><<<grid, kThreads, 0, s>>>(nb, rp, ci, v, w, g, omega,
-                                                                    rP, r);
+                                                                    rP, r, rmask);
   });
   return launch_status();
 }
 
 template <typename T>
 int launch_bsr_col0_update(int b, int nb, const int* rp, const int* ci, const T* c0, const T* e,
-                           T* r, T* w, cudaStream_t s) {
+                           T* r, T* w, cudaStream_t s, const unsigned char* rmask) {
   if (nb <= 0) return MSP_OK;
   MSP_B_SWITCH(b, {
     const unsigned grid = grid_groups(nb, Gp<B_>::v);
-    bsr_col0_update_kernel<B_, T><<<grid, kThreads, 0, s>>>(nb, rp, ci, c0, e, r, w);
+    bsr_col0_update_kernel<B_, T><<<grid, kThreads, 0, s>>>(nb, rp, ci, c0, e, r, w, rmask);
   });
   return launch_status();
 }
@@ -1055,14 +1083,14 @@ int launch_extract_col0(size_t nnzb, int b, const T* v, T* c0, cudaStream_t s) {
 template <typename T>
 int launch_bgs_colour(int b, int r0, int r1, const int* rp, const int* ci, const int* dpos,
                       const T* aN, const T* dNinv, const T* g, T* w, bool lower_only,
-                      bool zero_pressure, cudaStream_t s) {
+                      bool zero_pressure, cudaStream_t s, const unsigned char* rmask) {
   if (r1 <= r0 || b < 2) return MSP_OK;
   switch (b) {
 #define MSP_BGS_CASE(BB)                                                                   \
   case BB: {                                                                               \
     const unsigned grid = grid_for((size_t)(r1 - r0) * kWarp / (kWarp / (BB - 1)), kThreads); \
     bgs_colour_kernel<BB, T><<<grid, kThreads, 0, s>>>(r0, r1, rp, ci, dpos, aN, dNinv, g, \
-                                                       w, lower_only, zero_pressure);      \
+                                                       w, lower_only, zero_pressure, rmask); \
   } break;
     MSP_BGS_CASE(2)
     MSP_BGS_CASE(3)
@@ -1080,22 +1108,24 @@ int launch_bgs_colour(int b, int r0, int r1, const int* rp, const int* ci, const
 
 template <typename T>
 int launch_bilu_fwd(int b, int r0, int r1, const int* rp, const int* ci, const int* dpos,
-                    const T* lu, const T* r, T* y, cudaStream_t s) {
+                    const T* lu, const T* r, T* y, cudaStream_t s, const unsigned char* rmask) {
   if (r1 <= r0) return MSP_OK;
   MSP_B_SWITCH(b, {
     const unsigned grid = grid_groups(r1 - r0, Gp<B_>::v);
-    bilu_fwd_kernel<B_, T><<<grid, kThreads, 0, s>>>(r0, r1, rp, ci, dpos, lu, r, y);
+    bilu_fwd_kernel<B_, T><<<grid, kThreads, 0, s>>>(r0, r1, rp, ci, dpos, lu, r, y, rmask);
   });
   return launch_status();
 }
 
 template <typename T>
 int launch_bilu_bwd(int b, int r0, int r1, const int* rp, const int* ci, const int* dpos,
-                    const T* lu, const T* uinv, const T* y, T* x, T* w, cudaStream_t s) {
+                    const T* lu, const T* uinv, const T* y, T* x, T* w, cudaStream_t s,
+                    const unsigned char* rmask) {
   if (r1 <= r0) return MSP_OK;
   MSP_B_SWITCH(b, {
     const unsigned grid = grid_groups(r1 - r0, Gp<B_>::v);
-    bilu_bwd_kernel<B_, T><<<grid, kThreads, 0, s>>>(r0, r1, rp, ci, dpos, lu, uinv, y, x, w);
+    bilu_bwd_kernel<B_, T><<<grid, kThreads, 0, s>>>(r0, r1, rp, ci, dpos, lu, uinv, y, x, w,
+                                                     rmask);
   });
   return launch_status();
 }
@@ -1130,11 +1160,11 @@ int csr_lanes(int len) {
 template <typename T>
 int launch_csr_gs_colour(int r0, int r1, const int* rp, const int* ci, const T* v,
                          const int* dpos, const T* rdiag, const T* b, T* x, bool lower_only,
-                         int avg_row, cudaStream_t s) {
+                         int avg_row, cudaStream_t s, const unsigned char* rmask) {
   if (r1 <= r0) return MSP_OK;
   const int tpr = csr_lanes<T>(lower_only ? (avg_row + 1) / 2 : avg_row);
   MSP_TPR_SWITCH(tpr, csr_gs_colour_kernel<T, TPR_><<<grid_groups(r1 - r0, TPR_), kThreads, 0, s>>>(
-                          r0, r1, rp, ci, v, dpos, rdiag, b, x, lower_only));
+                          r0, r1, rp, ci, v, dpos, rdiag, b, x, lower_only, rmask));
   return launch_status();
 }
 
@@ -1142,13 +1172,13 @@ template <typename T>
 int launch_ell_gs_colour(int K, int r0, int r1, const int* ell_ci, const T* ell_v,
                          const int* meta, const int* rp, const int* ci, const T* v,
                          const int* dpos, const T* rdiag, const T* b, T* x, bool lower_only,
-                         cudaStream_t s) {
+                         cudaStream_t s, const unsigned char* rmask) {
   if (r1 <= r0) return MSP_OK;
   switch (K) {
 #define MSP_ELL_CASE(KK, TT)                                                                \
   case KK:                                                                                  \
     ell_gs_colour_kernel<T, KK, TT><<<grid_groups(r1 - r0, TT), kThreads, 0, s>>>(          \
-        r0, r1, ell_ci, ell_v, meta, rp, ci, v, dpos, rdiag, b, x, lower_only);            \
+        r0, r1, ell_ci, ell_v, meta, rp, ci, v, dpos, rdiag, b, x, lower_only, rmask);     \
     break;
     MSP_ELL_CASE(8, 2)
     MSP_ELL_CASE(16, 4)
@@ -1339,6 +1369,19 @@ int launch_seg_normalize(const SegChunks& sc, const int* active, const double* w
   return launch_status();
 }
 
+int launch_expand_mask(int nb, const int* row_inst, const int* active, unsigned char* rmask,
+                       cudaStream_t s) {
+  if (nb <= 0) return MSP_OK;
+  expand_mask_kernel<<<grid_for(nb, kThreads), kThreads, 0, s>>>(nb, row_inst, active, rmask);
+  return launch_status();
+}
+
+int launch_seg_zero(const SegChunks& sc, const int* mask, double* v, cudaStream_t s) {
+  if (sc.n <= 0) return MSP_OK;
+  seg_zero_kernel<<<seg_grid(sc.n), kThreads, 0, s>>>(sc.n, sc.start, sc.end, sc.inst, mask, v);
+  return launch_status();
+}
+
 int launch_seg_update_x(const SegChunks& sc, const int* count, const double* Z, size_t ldz,
                         const double* y, double* x, cudaStream_t s) {
   if (sc.n <= 0) return MSP_OK;
@@ -1370,26 +1413,29 @@ int launch_scatter_blocks(int nb, int b, const int* perm, const double* in, doub
 // explicit instantiations for the two value types of the preconditioner
 #define MSP_INST(T)                                                                         \
   template int launch_bsr_spmv<T>(int, int, const int*, const int*, const T*, const T*,     \
-                                  const T*, T*, bool, cudaStream_t);                        \
+                                  const T*, T*, bool, cudaStream_t, const unsigned char*);  \
   template int launch_bsr_restrict_p<T>(int, int, const int*, const int*, const T*,         \
-                                        const T*, const T*, const T*, T*, T*, cudaStream_t); \
+                                        const T*, const T*, const T*, T*, T*, cudaStream_t, \
+                                        const unsigned char*);                              \
   template int launch_bsr_col0_update<T>(int, int, const int*, const int*, const T*,        \
-                                         const T*, T*, T*, cudaStream_t);                   \
+                                         const T*, T*, T*, cudaStream_t, const unsigned char*); \
   template int launch_extract_col0<T>(size_t, int, const T*, T*, cudaStream_t);             \
   template int launch_bgs_colour<T>(int, int, int, const int*, const int*, const int*,      \
                                     const T*, const T*, const T*, T*, bool, bool,           \
-                                    cudaStream_t);                                          \
+                                    cudaStream_t, const unsigned char*);                    \
   template int launch_bilu_fwd<T>(int, int, int, const int*, const int*, const int*,        \
-                                  const T*, const T*, T*, cudaStream_t);                    \
+                                  const T*, const T*, T*, cudaStream_t, const unsigned char*); \
   template int launch_bilu_bwd<T>(int, int, int, const int*, const int*, const int*,        \
-                                  const T*, const T*, const T*, T*, T*, cudaStream_t);      \
+                                  const T*, const T*, const T*, T*, T*, cudaStream_t,       \
+                                  const unsigned char*);                                    \
   template int launch_prolong_p<T>(int, int, const T*, T*, cudaStream_t);                   \
   template int launch_csr_gs_colour<T>(int, int, const int*, const int*, const T*,          \
                                        const int*, const T*, const T*, T*, bool, int,       \
-                                       cudaStream_t);                                       \
+                                       cudaStream_t, const unsigned char*);                 \
   template int launch_ell_gs_colour<T>(int, int, int, const int*, const T*, const int*,      \
                                        const int*, const int*, const T*, const int*,      \
-                                       const T*, const T*, T*, bool, cudaStream_t);       \
+                                       const T*, const T*, T*, bool, cudaStream_t,        \
+                                       const unsigned char*);                             \
   template int launch_ell_residual_restrict<T>(int, int, const int*, const int*, const int*, \
                                                const T*, const int*, const T*, const int*,  \
                                                const int*, const T*, const T*, const T*, T*, \
