@@ -60,12 +60,14 @@ int launch_csr_gs_colour(int r0, int r1, const int* rp, const int* ci, const T* 
                          int avg_row, cudaStream_t s, const unsigned char* rmask = nullptr);
 // bc[I] = sum over members i of aggregate I (ascending) of (b_i - (A x)_i)
 // the same sweep over the ELL copy of the level (K in {8, 16, 24, 32} slots per row, slot
-// k of row i at i*K + k; meta from launch_build_ell; rows with meta < 0 use rp/ci/v)
+// k of row i at i*K + k; meta from launch_build_ell; rows with meta < 0 use rp/ci/v);
+// pdl: launched as a programmatic dependent of the previous kernel (constant operands are
+// loaded before it waits for that kernel)
 template <typename T>
 int launch_ell_gs_colour(int K, int r0, int r1, const int* ell_ci, const T* ell_v,
                          const int* meta, const int* rp, const int* ci, const T* v,
                          const int* dpos, const T* rdiag, const T* b, T* x, bool lower_only,
-                         cudaStream_t s, const unsigned char* rmask = nullptr);
+                         cudaStream_t s, const unsigned char* rmask = nullptr, bool pdl = false);
 // the same restriction over the ELL copy of the level (diag: a_ii of every row)
 template <typename T>
 int launch_ell_residual_restrict(int K, int nc, const int* mptr, const int* members,

@@ -980,12 +980,15 @@ int vcycle(msp_handle h, const PView<T>& P, int l, cudaStream_t s) {
   auto use_ell = [&](int c, bool lower_only) {
     return L.ell_k > 0 && !(lower_only && L.cptr[c + 1] - L.cptr[c] > 16384);
   };
+  // classes of the coarse levels small enough to run beside the previous colour's launch:
+  // launched as its programmatic dependents, they load their slots while it runs
+  auto overlap = [&](int c) { return l >= 1 && L.cptr[c + 1] - L.cptr[c] <= 32768; };
   auto sweep = [&](int c, bool lower_only) {
     if (use_ell(c, lower_only))
       return launch_ell_gs_colour<T>(L.ell_k, L.cptr[c], L.cptr[c + 1], L.ell_ci.p, P.lev[l],
                                      L.ell_meta.p, L.A.rp.p, L.A.ci.p, P.lv[l], L.dpos.p,
                                      P.lrd[l], P.lb[l], P.lx[l], lower_only, s,
-                                     l == 0 ? P.m0 : nullptr);
+                                     l == 0 ? P.m0 : nullptr, overlap(c));
     return launch_csr_gs_colour<T>(L.cptr[c], L.cptr[c + 1], L.A.rp.p, L.A.ci.p, P.lv[l],
                                    L.dpos.p, P.lrd[l], P.lb[l], P.lx[l], lower_only, avg_row, s,
                                    l == 0 ? P.m0 : nullptr);

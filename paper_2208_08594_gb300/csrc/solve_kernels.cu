@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <utility>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -424,7 +425,11 @@ __global__ void __launch_bounds__(kThreads) csr_gs_colour_kernel(
 // the only load that waits for another is the gather of x: two dependent trips to memory
 // instead of three (row pointer, then entries, then x).  Rows longer than K (meta < 0)
 // walk their CSR row instead.
-template <typename T, int K, int TPR>
+// PDL: launched as a programmatic dependent of the previous kernel; the grid lets the next
+// colour launch at once and loads what no kernel of the sweep writes (the slots, meta,
+// 1/diagonal) before it waits for the previous colour, so only the gather of x and b
+// remain after the dependency resolves.
+template <typename T, int K, int TPR, bool PDL>
 __global__ void __launch_bounds__(kThreads) ell_gs_colour_kernel(
     int r0, int r1, const int* __restrict__ ell_ci, const T* __restrict__ ell_v,
     const int* __restrict__ meta, const int* __restrict__ rp, const int* __restrict__ ci,
@@ -434,24 +439,27 @@ __global__ void __launch_bounds__(kThreads) ell_gs_colour_kernel(
   constexpr int S = (K + TPR - 1) / TPR;  // slots per lane
   const int lane = threadIdx.x % TPR;
   const int rpb = blockDim.x / TPR;
+  if constexpr (PDL) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   for (int base = r0 + blockIdx.x * rpb; base < r1; base += gridDim.x * rpb) {
     const int i = base + threadIdx.x / TPR;
     T s = T(0), bi = T(0), di = T(0);
     const bool live = (i < r1) && (!rmask || rmask[i]);
+    int m = 0;
+    int j[S];
+    T a[S], xj[S];
     if (live) {
-      const int m = __ldg(meta + i);
-      if (lane == 0) {
-        bi = __ldg(b + i);
-        di = __ldg(rdiag + i);
-      }
-      int j[S];
-      T a[S], xj[S];
+      m = __ldg(meta + i);
+      if (lane == 0) di = __ldg(rdiag + i);
 #pragma unroll
       for (int q = 0; q < S; ++q) {
         const int k = lane + q * TPR;
         j[q] = k < K ? __ldg(ell_ci + (size_t)i * K + k) : i;
         a[q] = k < K ? __ldg(ell_v + (size_t)i * K + k) : T(0);
       }
+    }
+    if constexpr (PDL) asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (live) {
+      if (lane == 0) bi = b[i];
 #pragma unroll
       for (int q = 0; q < S; ++q) xj[q] = x[j[q]];
       // lower_only: x of the later colours is stale, only the entries left of the diagonal
@@ -1168,17 +1176,43 @@ int launch_csr_gs_colour(int r0, int r1, const int* rp, const int* ci, const T* 
   return launch_status();
 }
 
+// a launch as a programmatic dependent of the previous kernel in the stream
+template <typename... Args, typename... Act>
+int launch_programmatic(void (*kern)(Args...), unsigned grid, cudaStream_t s, Act&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, std::forward<Act>(args)...);
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, "cudaLaunchKernelEx", __FILE__, __LINE__);
+    return MSP_ERR_CUDA;
+  }
+  return MSP_OK;
+}
+
 template <typename T>
 int launch_ell_gs_colour(int K, int r0, int r1, const int* ell_ci, const T* ell_v,
                          const int* meta, const int* rp, const int* ci, const T* v,
                          const int* dpos, const T* rdiag, const T* b, T* x, bool lower_only,
-                         cudaStream_t s, const unsigned char* rmask) {
+                         cudaStream_t s, const unsigned char* rmask, bool pdl) {
   if (r1 <= r0) return MSP_OK;
   switch (K) {
 #define MSP_ELL_CASE(KK, TT)                                                                \
   case KK:                                                                                  \
-    ell_gs_colour_kernel<T, KK, TT><<<grid_groups(r1 - r0, TT), kThreads, 0, s>>>(          \
-        r0, r1, ell_ci, ell_v, meta, rp, ci, v, dpos, rdiag, b, x, lower_only, rmask);     \
+    if (pdl) {                                                                              \
+      MSP_TRY(launch_programmatic(ell_gs_colour_kernel<T, KK, TT, true>,                    \
+                                  grid_groups(r1 - r0, TT), s, r0, r1, ell_ci, ell_v, meta, \
+                                  rp, ci, v, dpos, rdiag, b, x, lower_only, rmask));        \
+    } else {                                                                                \
+      ell_gs_colour_kernel<T, KK, TT, false><<<grid_groups(r1 - r0, TT), kThreads, 0, s>>>( \
+          r0, r1, ell_ci, ell_v, meta, rp, ci, v, dpos, rdiag, b, x, lower_only, rmask);   \
+    }                                                                                       \
     break;
     MSP_ELL_CASE(8, 2)
     MSP_ELL_CASE(16, 4)
@@ -1435,7 +1469,7 @@ int launch_scatter_blocks(int nb, int b, const int* perm, const double* in, doub
   template int launch_ell_gs_colour<T>(int, int, int, const int*, const T*, const int*,      \
                                        const int*, const int*, const T*, const int*,      \
                                        const T*, const T*, T*, bool, cudaStream_t,        \
-                                       const unsigned char*);                             \
+                                       const unsigned char*, bool);                       \
   template int launch_ell_residual_restrict<T>(int, int, const int*, const int*, const int*, \
                                                const T*, const int*, const T*, const int*,  \
                                                const int*, const T*, const T*, const T*, T*, \
