@@ -982,7 +982,7 @@ int vcycle(msp_handle h, const PView<T>& P, int l, cudaStream_t s) {
   };
   // classes of the coarse levels small enough to run beside the previous colour's launch:
   // launched as its programmatic dependents, they load their slots while it runs
-  auto overlap = [&](int c) { return l >= 1 && L.cptr[c + 1] - L.cptr[c] <= 32768; };
+  auto overlap = [&](int c) { return l >= 1 && L.cptr[c + 1] - L.cptr[c] <= 262144; };
   auto sweep = [&](int c, bool lower_only) {
     if (use_ell(c, lower_only))
       return launch_ell_gs_colour<T>(L.ell_k, L.cptr[c], L.cptr[c + 1], L.ell_ci.p, P.lev[l],
