@@ -322,8 +322,8 @@ int msp_wells_free(msp_wells W);
  * device; a request is admitted as soon as a slot is free, its key is not busy and its
  * system fits the device-memory budget (idle resident systems are released, least
  * recently used first, to make room).  Requests of one key run one at a time in submit
- * order; requests that wait for memory keep their order among themselves, while requests
- * of resident systems may pass them.  Results do not depend on the mix: every system is
+ * order; requests that wait for memory for a new system keep their order among
+ * themselves, while requests of resident systems (new patterns included) may pass them.  Results do not depend on the mix: every system is
  * solved by the same deterministic kernels on its own buffers. */
 typedef struct msp_server_s* msp_server;
 

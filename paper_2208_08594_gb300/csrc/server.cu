@@ -10,8 +10,8 @@
 //   * a request that needs a new system is charged its estimated footprint against the
 //     device-memory budget; idle resident systems (no request running or queued) are
 //     released least recently used first to make room; if it still does not fit, it waits,
-//     and so do the later requests that need memory (they keep their order), while later
-//     requests of resident systems may still start;
+//     and so do the later requests that need a new system (they keep their order), while
+//     later requests of resident systems, replacements included, may still start;
 //   * once a system is set up its measured footprint replaces the estimate.
 #include <cuda_runtime.h>
 
@@ -100,8 +100,11 @@ bool pick_job(msp_server_s* S, Pick& out) {
       S->queue.erase(it);
       return true;
     }
-    // needs memory for a new system (or for the replacement of its resident one)
-    if (memory_blocked) {
+    // needs memory for a new system (or for the replacement of its resident one).  Once a
+    // request waits for memory, later new systems wait behind it; replacements of resident
+    // systems may still go: a system with a queued request cannot be released to make room,
+    // so holding its replacement back could leave both waiting for ever.
+    if (memory_blocked && !sy.ready) {
       blocked_keys.insert(key);
       continue;
     }

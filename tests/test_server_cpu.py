@@ -145,6 +145,20 @@ def test_release_and_new_pattern():
     assert stats["resident_systems"] == 1
 
 
+def test_replacement_passes_a_memory_waiter():
+    """Two resident systems fill the budget and each has a new-pattern request queued
+    behind a third key that needs room: the replacements go first (their systems cannot be
+    released while they have requests queued), then the third key evicts one of them."""
+    rec = Recorder(run_s=0.005)
+    N = _native.MSP_REQ_NEW_PATTERN
+    results, stats = _run(1, int(2.5 * EST), [(0, 0), (1, 0), (2, 0), (0, N), (1, N)], rec)
+    assert all(r is not None and r["status"] == 0 for r in results)
+    starts = [k for e, k, *_ in rec.before_free if e == "start"]
+    assert starts[:2] == [0, 1] and sorted(starts[2:]) == [0, 1, 2]
+    assert starts.index(2, 2) > 2  # key 2 started after a replacement
+    assert rec.max_alive <= 2.5 * EST
+
+
 def test_oversized_request_rejected_and_bad_arguments():
     rec = Recorder()
     S = _native.msp_server_create(2, EST // 2, None, 0, rec.fn)
