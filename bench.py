@@ -478,6 +478,10 @@ def run_native(args):
                    "level_sizes": [li[0] for li in level_info],
                    "level_nnz": [li[1] for li in level_info],
                    "level_colours": [li[2] for li in level_info],
+                   "amg_operator_complexity": round(sum(li[1] for li in level_info)
+                                                    / max(1, level_info[0][1]), 3),
+                   "amg_grid_complexity": round(sum(li[0] for li in level_info)
+                                                / max(1, level_info[0][0]), 3),
                    "iterations": its, "setups_in_timed_steps": setups,
                    "setup_s_first": round(setup_s, 3),
                    "l2": "inputs larger than L2 (1 GB of values), no flush",

@@ -9,6 +9,7 @@
 // FP64 on the host, and Algorithm 3.1 as the preconditioner.  ASMSP (Section 3.2): a
 // solve regenerates B iff the previous solve took more than mu iterations.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <chrono>
@@ -34,6 +35,17 @@ thread_local int t_bytes_scope_depth = 0;
 }
 
 thread_local long long t_dev_bytes = 0;
+
+namespace {
+// NVTX range over a host scope (setup phases, solves, Krylov cycles, preconditioner
+// applications), visible in a timeline profiler; a no-op when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace
 
 void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
   char buf[512];
@@ -722,6 +734,7 @@ int coarse_inverse(msp_handle h, const DCsr& C, cudaStream_t s) {
 // value setup: decoupling, AMG hierarchy, stage N, BILU(0)
 // ---------------------------------------------------------------------------------
 int value_setup(msp_handle h, cudaStream_t s) {
+  NvtxRange nvtx("msp:value_setup");
   const int nb = h->nb, b = h->b, bb = b * b, bn = b - 1;
   const size_t nnzb = (size_t)h->nnzb;
   const msp_config& cfg = h->cfg;
@@ -1247,6 +1260,7 @@ int capture_graph(msp_handle h) {
 // w = B g on FP64 colour-ordered vectors, in the configured precision.  Replays the
 // captured graph, except while every launch is timed (stats mode 2).
 int apply_precond(msp_handle h, const double* g, double* w, cudaStream_t s) {
+  NvtxRange nvtx("msp:precond");
   const size_t n = (size_t)h->nb * h->b;
   const bool fp32 = h->cfg.precision == MSP_PRECISION_FP32;
   if (g_stats_mode == 2) {
@@ -1343,6 +1357,7 @@ int refresh_values(msp_handle h, const double* d_user_values, cudaStream_t s) {
 // ---------------------------------------------------------------------------------
 int fgmres(msp_handle h, double tol, int* iters, double* relres, double* relres_est,
            cudaStream_t s) {
+  NvtxRange nvtx("msp:fgmres");
   const size_t n = (size_t)h->nb * h->b;
   const int m = h->cfg.restart;
   const int nbk = krylov_blocks();
@@ -1515,6 +1530,7 @@ SegChunks seg_chunks(msp_handle h) {
 // included, into every row).
 int fgmres_batched(msp_handle h, double tol, std::vector<int>& its, std::vector<double>& relres,
                    std::vector<double>& relest, std::vector<int>& status, cudaStream_t s) {
+  NvtxRange nvtx("msp:fgmres_batched");
   const int B = h->batch, m = h->cfg.restart;
   const size_t n = (size_t)h->nb * h->b;
   const int KM = kKrylovMaxK;
@@ -1734,6 +1750,7 @@ int fgmres_batched(msp_handle h, double tol, std::vector<int>& its, std::vector<
 }
 
 int pattern_setup(msp_handle h, const int32_t* d_rp, const int32_t* d_ci, cudaStream_t s) {
+  NvtxRange nvtx("msp:pattern_setup");
   const int nb = h->nb;
   const size_t nnzb = (size_t)h->nnzb;
   DevBuf<int> urp, uci, udpos;
