@@ -46,3 +46,9 @@ def test_preconditioner_of_a_stack_is_block_diagonal():
         r = g - S.to_scipy() @ x
         assert np.linalg.norm(r) <= 1e-8 * np.linalg.norm(g) * 1.001
     o.close()
+
+
+def test_stack_rejects_mixed_block_sizes():
+    import pytest
+    with pytest.raises(ValueError):
+        msp.stack_block_diagonal([box_jacobian(3, 3, 2, 3, 1), box_jacobian(3, 3, 2, 4, 2)])
