@@ -171,7 +171,6 @@ class Server:
     here until :meth:`wait` returns their ticket."""
 
     def __init__(self, slots=4, hbm_budget=150 * 10**9, device=0, exec_fn=None, **config):
-        import numpy as np  # noqa: F401
         self.cfg = msp_config_default(**config)
         self._exec = exec_fn
         self.S = msp_server_create(slots, int(hbm_budget), self.cfg, device, exec_fn)
