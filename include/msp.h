@@ -138,6 +138,17 @@ int msp_update_values(msp_handle h, const double* d_values, void* stream);
 /* msp_update_values with a HOST array (pinned memory gives the fastest copy). */
 int msp_update_values_host(msp_handle h, const double* h_values, void* stream);
 
+/* Values copied ahead (pipelining the host-to-device copy of the next Newton step's matrix
+ * with the current solve): msp_stage_values_host enqueues the copy of h_values (HOST,
+ * nnzb*b*b doubles; pinned memory makes it asynchronous; keep it valid and unchanged until
+ * the copy has run) on `stream`, typically a second stream, and returns at once;
+ * msp_update_values_staged then makes its own stream wait for that copy and applies the
+ * values as msp_update_values does.  One staged copy at a time: staging again waits (on
+ * the copy stream) until the previous staged values have been applied.
+ * msp_update_values_staged without a staged copy returns MSP_ERR_ARG. */
+int msp_stage_values_host(msp_handle h, const double* h_values, void* stream);
+int msp_update_values_staged(msp_handle h, void* stream);
+
 /* Solve A x = b to ||b - A x|| / ||b|| <= rel_tol with x0 = 0.  d_b, d_x: device
  * arrays of nb*b doubles (natural order; may not alias).  Runs SETUP first when the
  * adaptive rule asks for it (previous It > mu).  info may be NULL.  Returns MSP_OK,

@@ -23,10 +23,12 @@ from ._native import (MSP_NOT_CONVERGED, MSP_OK, MSP_PREC_MSP, MSP_PREC_N_ONLY, 
                       msp_server_create, msp_server_submit, msp_server_wait,
                       msp_server_get_stats, msp_server_free, MspRequest, MSP_REQ_NEW_PATTERN,
                       MSP_REQ_RELEASE, MSP_EXEC_RUN, MSP_EXEC_RELEASE, MSP_SERVER_EXEC_FN,
-                      msp_set_instances, msp_solve_batch)
+                      msp_set_instances, msp_solve_batch, msp_stage_values_host,
+                      msp_update_values_staged)
 
 __all__ = ["Solver", "Wells", "WellEliminatedSolver", "Server", "BatchSolver",
            "stack_block_diagonal", "msp_set_instances", "msp_solve_batch", "MspError",
+           "msp_stage_values_host", "msp_update_values_staged",
            "msp_wells_setup",
            "msp_device_bytes", "msp_estimate_device_bytes", "msp_server_create",
            "msp_server_submit", "msp_server_wait", "msp_server_get_stats", "msp_server_free",
@@ -62,6 +64,14 @@ class Solver:
 
     def update_values_host(self, values, stream=None):
         msp_update_values_host(self.h, values, stream)
+
+    def stage_values_host(self, values, stream=None):
+        """Enqueue the copy of the next values (host array) on `stream` and return."""
+        msp_stage_values_host(self.h, values, stream)
+
+    def update_values_staged(self, stream=None):
+        """Apply the values of the last stage_values_host once their copy has landed."""
+        msp_update_values_staged(self.h, stream)
 
     def solve(self, rhs, x, rel_tol=1e-6, stream=None):
         return msp_solve(self.h, rhs, x, rel_tol, stream)

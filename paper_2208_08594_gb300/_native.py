@@ -34,7 +34,8 @@ EXPORTS = ("msp_config_default", "msp_setup", "msp_update_values", "msp_update_v
            "msp_wells_update_values", "msp_wells_reduce_rhs", "msp_wells_recover",
            "msp_wells_free", "msp_device_bytes", "msp_estimate_device_bytes",
            "msp_server_create", "msp_server_submit", "msp_server_wait", "msp_server_get_stats",
-           "msp_server_free", "msp_set_instances", "msp_solve_batch")
+           "msp_server_free", "msp_set_instances", "msp_solve_batch",
+           "msp_stage_values_host", "msp_update_values_staged")
 
 # largest n accepted by msp_vertices_grouping_noalloc (size of its fixed scratch)
 NOALLOC_MAX_VERTICES = 1 << 16
@@ -153,6 +154,8 @@ def lib(build_if_missing: bool = True):
     L.msp_wells_free.argtypes = [P]
     L.msp_device_bytes.argtypes = [P, C.POINTER(C.c_int64)]
     L.msp_set_instances.argtypes = [P, C.c_int32, P]
+    L.msp_stage_values_host.argtypes = [P, P, P]
+    L.msp_update_values_staged.argtypes = [P, P]
     L.msp_solve_batch.argtypes = [P, P, P, D, P, P]
     L.msp_estimate_device_bytes.argtypes = [C.c_int32, C.c_int32, C.c_int64, C.POINTER(MspConfig)]
     L.msp_estimate_device_bytes.restype = C.c_int64
@@ -495,3 +498,16 @@ def msp_solve_batch(h, count: int, b, x, rel_tol=1e-6, stream=None):
     if st < 0 and st != MSP_ERR_BREAKDOWN and not any(i.status for i in infos):
         raise MspError(st, "msp_solve_batch")
     return [_info_dict(i) for i in infos]
+
+
+def msp_stage_values_host(h, values: np.ndarray, stream=None):
+    assert values.dtype == np.float64 and values.flags.c_contiguous
+    st = lib().msp_stage_values_host(h, _ptr(values), _stream(stream))
+    if st != MSP_OK:
+        raise MspError(st, "msp_stage_values_host")
+
+
+def msp_update_values_staged(h, stream=None):
+    st = lib().msp_update_values_staged(h, _stream(stream))
+    if st != MSP_OK:
+        raise MspError(st, "msp_update_values_staged")

@@ -370,6 +370,12 @@ struct msp_handle_s {
   msp::DevBuf<double> vals;            // colour-ordered current values
   msp::DevBuf<double> c0;              // column 0 of every block of vals (FP64 preconditioner)
   msp::DevBuf<double> staging;         // user values before the gather
+  // values copied ahead of their update (msp_stage_values_host / msp_update_values_staged)
+  msp::DevBuf<double> staged;
+  cudaEvent_t staged_ev = nullptr;     // the staged copy has landed
+  cudaEvent_t consumed_ev = nullptr;   // the staged values have been gathered
+  bool staged_pending = false;
+  bool consumed_recorded = false;
   // setup products
   msp::DevBuf<double> omega, dNinv, aN, lu, uinv, cinv;
   int ncoarse = 0;
@@ -1802,6 +1808,8 @@ void destroy(msp_handle h) {
   if (h->h_flags) cudaFreeHost(h->h_flags);
   if (h->h_pin) cudaFreeHost(h->h_pin);
   if (h->h_bpin) cudaFreeHost(h->h_bpin);
+  if (h->staged_ev) cudaEventDestroy(h->staged_ev);
+  if (h->consumed_ev) cudaEventDestroy(h->consumed_ev);
   if (h->ss) sort_scratch_destroy(h->ss);
   delete h;
 }
@@ -1939,6 +1947,35 @@ int msp_update_values_host(msp_handle h, const double* h_values, void* stream) {
   MSP_CUDA_TRY(cudaMemcpyAsync(h->staging.p, h_values, cnt * sizeof(double),
                                cudaMemcpyHostToDevice, s));
   return msp_update_values(h, h->staging.p, stream);
+}
+
+int msp_stage_values_host(msp_handle h, const double* h_values, void* stream) {
+  if (!h || !h_values) return MSP_ERR_ARG;
+  DevBytesScope bytes_scope(h);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t cnt = (size_t)h->nnzb * h->b * h->b;
+  if (!h->staged.p) MSP_TRY(h->staged.alloc(cnt));
+  if (!h->staged_ev) MSP_CUDA_TRY(cudaEventCreateWithFlags(&h->staged_ev, cudaEventDisableTiming));
+  if (!h->consumed_ev)
+    MSP_CUDA_TRY(cudaEventCreateWithFlags(&h->consumed_ev, cudaEventDisableTiming));
+  // the buffer is free again once the previous staged values have been gathered
+  if (h->consumed_recorded) MSP_CUDA_TRY(cudaStreamWaitEvent(s, h->consumed_ev, 0));
+  MSP_CUDA_TRY(cudaMemcpyAsync(h->staged.p, h_values, cnt * sizeof(double),
+                               cudaMemcpyHostToDevice, s));
+  MSP_CUDA_TRY(cudaEventRecord(h->staged_ev, s));
+  h->staged_pending = true;
+  return MSP_OK;
+}
+
+int msp_update_values_staged(msp_handle h, void* stream) {
+  if (!h || !h->staged_pending) return MSP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  MSP_CUDA_TRY(cudaStreamWaitEvent(s, h->staged_ev, 0));
+  const int st = msp_update_values(h, h->staged.p, stream);
+  MSP_CUDA_TRY(cudaEventRecord(h->consumed_ev, s));
+  h->consumed_recorded = true;
+  h->staged_pending = false;
+  return st;
 }
 
 int msp_solve(msp_handle h, const double* d_b, double* d_x, double rel_tol,

@@ -324,3 +324,28 @@ def test_fp32_preconditioner_converges_to_fp64_accuracy():
     # conditioning of A times that tolerance; the measured gap is far smaller
     assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-3
     g.close()
+
+
+def test_staged_values_equal_direct_update():
+    a = grid_small()
+    cfg = dict(coarse_max=100, mu=10**6)
+    rp, ci, v = _dev(a)
+    g1 = msp.Solver(a.nb, a.b, rp, ci, v, **cfg)
+    g2 = msp.Solver(a.nb, a.b, rp, ci, v, **cfg)
+    copy = torch.cuda.Stream()
+    rhs = _vec(random_rhs(a, 3))
+    with pytest.raises(msp.MspError):
+        g2.update_values_staged()  # nothing staged
+    for k in range(3):
+        vals = torch.from_numpy(perturb_values(a, 40 + k).reshape(-1)).pin_memory().numpy()
+        g1.update_values_host(vals)
+        g2.stage_values_host(vals, copy)
+        g2.update_values_staged()
+        x1 = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+        x2 = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+        i1 = g1.solve(rhs, x1, 1e-6)
+        i2 = g2.solve(rhs, x2, 1e-6)
+        assert i1["iterations"] == i2["iterations"]
+        assert torch.equal(x1, x2)
+    g1.close()
+    g2.close()
