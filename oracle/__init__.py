@@ -7,6 +7,7 @@ the seeded inputs of ``synthetic``.
 from __future__ import annotations
 
 import ctypes as C
+import os
 
 import numpy as np
 
@@ -39,7 +40,9 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
+        # MSP_ORACLE_LIB: a library built from a modified copy of the oracle's source (the
+        # test that plants mistakes in the oracle checks that its pins catch them)
+        _lib = C.CDLL(os.environ.get("MSP_ORACLE_LIB") or build())
         P = C.c_void_p
         _lib.orc_create.restype = P
         _lib.orc_create.argtypes = [C.POINTER(OrcConfig), C.c_int, C.c_int, P, P, P,

@@ -36,6 +36,29 @@ def test_msp_equals_product_form(case):
     assert np.allclose(lhs, e, rtol=1e-10, atol=1e-10 * np.abs(e).max())
 
 
+@pytest.mark.parametrize("b,wells", [(3, 1), (4, 2)])
+def test_stage_p_with_exact_coarse_solve_is_the_decoupled_pressure_inverse(b, wells):
+    """Stage P alone with one AMG level (coarse_max >= n, a direct solve) is
+    Pi_P A_P^-1 Pi_P^T: restriction r_P[i] = omega_i . r_i with omega_i^T = e_0^T D_i^-1,
+    A_P[i,j] = omega_i . A_ij e_0, and the correction added to unknown 0 of every block."""
+    a = box_jacobian(4, 3, 3, b, 61, layered=True, kz_ratio=0.1, n_wells=wells)
+    o = oracle.Oracle(a, precond=oracle.PREC_P_ONLY, coarse_max=10**6)
+    nb = a.nb
+    rows = np.repeat(np.arange(nb), np.diff(a.row_ptr))
+    diag = {i: a.values[p] for p, (i, j) in enumerate(zip(rows, a.col_idx)) if i == j}
+    omega = np.array([np.linalg.inv(diag[i])[0] for i in range(nb)])
+    AP = np.zeros((nb, nb))
+    for p, (i, j) in enumerate(zip(rows, a.col_idx)):
+        AP[i, j] = omega[i] @ a.values[p][:, 0]
+    r = np.random.default_rng(7).normal(size=a.n)
+    e = np.linalg.solve(AP, np.einsum("ik,ik->i", omega, r.reshape(nb, b)))
+    want = np.zeros((nb, b))
+    want[:, 0] = e
+    got = o.apply_precond(r)
+    assert np.allclose(got, want.reshape(-1), rtol=1e-10, atol=1e-10 * np.abs(e).max())
+    o.close()
+
+
 @pytest.mark.parametrize("case", [
     dict(dims=(2, 2, 2), b=2, wells=0), dict(dims=(3, 3, 2), b=3, wells=1),
     dict(dims=(4, 4, 3), b=4, wells=1), dict(dims=(6, 6, 4), b=4, wells=2),

@@ -1,0 +1,68 @@
+"""The oracle's pins are strong enough to catch plausible mistakes: each case below plants
+one (a dropped term, a wrong sign, a wrong index, a transposed operand, a skipped step) in
+a copy of the oracle's source, builds it with the oracle's own flags, and runs the CPU
+pins against that library (through MSP_ORACLE_LIB in a child process); at least one pin
+must fail.  The product oracle is never modified."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "msp_oracle.cpp")
+PINS = ["tests/test_oracle_amg.py", "tests/test_oracle_colouring.py",
+        "tests/test_oracle_krylov.py", "tests/test_oracle_smoothers.py",
+        "tests/test_oracle_wells.py", "tests/test_batch_cpu.py"]
+
+# name: (exact source text, planted mistake)
+MUTANTS = {
+    "gauss_jordan_elimination_sign": (
+        "a[r * b + k] = a[r * b + k] - f * a[c * b + k];",
+        "a[r * b + k] = a[r * b + k] + f * a[c * b + k];"),
+    "colouring_second_circle_ignored": (
+        "int vi = !Wh.empty() ? Wh.begin()->second : Vq.begin()->second;",
+        "int vi = Vq.begin()->second;"),
+    "strength_of_connection_sign": (
+        "s[p - S.rp[i]] = -0.5 * t;", "s[p - S.rp[i]] = 0.5 * t;"),
+    "galerkin_term_dropped": (
+        "it->second = it->second + a.v[p];", "it->second = it->second;"),
+    "gauss_seidel_sign": (
+        "          acc -= a.v[p] * x[j];\n      }\n      x[i] = acc / d;",
+        "          acc += a.v[p] * x[j];\n      }\n      x[i] = acc / d;"),
+    "bilu_operands_transposed": (
+        "blk_mul(b, &h.lu[(size_t)p * bb], &h.u_inv[(size_t)k * bb], L.data());",
+        "blk_mul(b, &h.u_inv[(size_t)k * bb], &h.lu[(size_t)p * bb], L.data());"),
+    "stage_n_reads_the_pressure_slot": (
+        "for (int k = 0; k < bn; ++k) acc[k] = r[(size_t)i * b + k + 1];",
+        "for (int k = 0; k < bn; ++k) acc[k] = r[(size_t)i * b + k];"),
+    "decoupled_restriction_terms_dropped": (
+        "for (int k = 0; k < b; ++k) s = s + h.omega[(size_t)i * b + k] * r[(size_t)i * b + k];",
+        "for (int k = 0; k < 1; ++k) s = s + h.omega[(size_t)i * b + k] * r[(size_t)i * b + k];"),
+    "givens_sign": (
+        "s[j + 1] = -sn[j] * s[j];", "s[j + 1] = sn[j] * s[j];"),
+    "gram_schmidt_sign": (
+        "V[j + 1][k] -= hij * V[i][k];", "V[j + 1][k] += hij * V[i][k];"),
+    "schur_complement_sign": (
+        "out[r * b + c] -= acc;", "out[r * b + c] += acc;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, "the oracle's source changed: update %s" % name
+    mutant = tmp_path / "mutant.cpp"
+    mutant.write_text(src.replace(old, new))
+    lib = tmp_path / "libmutant.so"
+    subprocess.run(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                    "-shared", "-o", str(lib), str(mutant)], check=True)
+    env = dict(os.environ, MSP_ORACLE_LIB=str(lib))
+    try:
+        out = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p",
+                              "no:cacheprovider", "-m", "not gpu"] + PINS, cwd=ROOT, env=env,
+                             capture_output=True, text=True, timeout=300)
+    except subprocess.TimeoutExpired:
+        return  # the mistake stopped a pin from finishing: caught
+    assert out.returncode != 0, "mistake %s passed every pin:\n%s" % (name, out.stdout[-2000:])
