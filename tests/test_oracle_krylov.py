@@ -150,6 +150,17 @@ def test_adaptive_setup_trace():
     assert setups == expect and calls == sum(expect)
 
 
+def test_adaptive_setup_boundary():
+    """It^(iota-1) equal to mu keeps B; one more than mu regenerates it (the rule is a
+    strict inequality).  The first solve's count does not depend on mu."""
+    its, _, _ = _sequence(10 ** 6, nsolves=2)
+    first = its[0]
+    _, setups, calls = _sequence(first, nsolves=2)
+    assert setups == [1, 0] and calls == 1
+    _, setups, calls = _sequence(first - 1, nsolves=2)
+    assert setups == [1, 1] and calls == 2
+
+
 def test_reuse_keeps_stage_operators_but_uses_current_matrix():
     """On reuse (Section 3.2) the residual steps of Algorithm 3.1 use the
     current A while B_N, B_P and R stay those of the last setup."""

@@ -1,5 +1,6 @@
 """The oracle's pins are strong enough to catch plausible mistakes: each case below plants
-one (a dropped term, a wrong sign, a wrong index, a transposed operand, a skipped step) in
+one (a dropped term, a wrong sign, a wrong index or bound, a transposed operand, a skipped
+step, an off-by-one in a rule, a wrong constant) in
 a copy of the oracle's source, builds it with the oracle's own flags, and runs the CPU
 pins against that library (through MSP_ORACLE_LIB in a child process); at least one pin
 must fail.  The product oracle is never modified."""
@@ -45,6 +46,25 @@ MUTANTS = {
         "V[j + 1][k] -= hij * V[i][k];", "V[j + 1][k] += hij * V[i][k];"),
     "schur_complement_sign": (
         "out[r * b + c] -= acc;", "out[r * b + c] += acc;"),
+    "well_recovery_sign": (
+        "        r[i] -= acc;\n", "        r[i] += acc;\n"),
+    "adaptive_setup_rule_off_by_one": (
+        "if (!h->first_solve && h->prev_it > h->cfg.mu) {",
+        "if (!h->first_solve && h->prev_it >= h->cfg.mu) {"),
+    "restriction_not_summed": (
+        "for (int i = 0; i < n; ++i) bc[L.agg[i]] += r[i];  // restriction P^T r",
+        "for (int i = 0; i < n; ++i) bc[L.agg[i]] = r[i];  // restriction P^T r"),
+    "prolongation_dropped": (
+        "for (int i = 0; i < n; ++i) x[i] += xc[L.agg[i]];  // prolongation by injection",
+        "for (int i = 0; i < n; ++i) x[i] += 0.0 * xc[L.agg[i]];"),
+    "bilu_backward_skips_the_upper_part": (
+        "if (pos[j] > t) blk_gemv_sub(b, &h.lu[(size_t)p * bb], &x[(size_t)j * b], acc.data());",
+        "if (pos[j] > t + nb) blk_gemv_sub(b, &h.lu[(size_t)p * bb], &x[(size_t)j * b], acc.data());"),
+    "jp_priority_reversed": (
+        "order[v] = {-(S.rp[v + 1] - S.rp[v]), (uint32_t)(splitmix64((uint64_t)v ^ kJpSeed) >> 32),",
+        "order[v] = {(S.rp[v + 1] - S.rp[v]), (uint32_t)(splitmix64((uint64_t)v ^ kJpSeed) >> 32),"),
+    "pgs_no_chunk_size": (
+        "constexpr int kPgsNoChunk = 16;", "constexpr int kPgsNoChunk = 8;"),
 }
 
 
