@@ -8,6 +8,10 @@
 // classical Gram-Schmidt and one re-orthogonalisation, the Hessenberg least squares in
 // FP64 on the host, and Algorithm 3.1 as the preconditioner.  ASMSP (Section 3.2): a
 // solve regenerates B iff the previous solve took more than mu iterations.
+// Also here: the batched solve of the instances of a block-diagonal matrix (one FGMRES
+// per instance, shared launches, a row mask for the instances that have converged), the
+// pipelined value update (the copy of the next values on another stream), launch and
+// per-site timing statistics, and the device-memory count of a handle.
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
