@@ -49,3 +49,24 @@ def test_invalid_arguments_rejected_without_gpu_work():
     cfg.restart = 1000
     assert L.msp_setup(ctypes.byref(h), ctypes.byref(cfg), 10, 4, None, None, None, 10, None) == -1
     assert L.msp_free(None) == 0
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """No CPU fallback: without the compiled library the binding raises instead of
+    computing anything (the solver exists only as CUDA kernels)."""
+    from paper_2208_08594_gb300 import _native, build
+    monkeypatch.setattr(build, "LIB", str(tmp_path / "missing_libmsp.so"))
+    monkeypatch.setattr(_native, "_lib", None)
+    with pytest.raises(ImportError):
+        _native.lib(build_if_missing=False)
+
+
+def test_estimate_grows_with_the_system():
+    from paper_2208_08594_gb300 import _native
+    small = _native.msp_estimate_device_bytes(1000, 4, 7000)
+    big = _native.msp_estimate_device_bytes(100000, 4, 700000)
+    wider = _native.msp_estimate_device_bytes(1000, 6, 7000)
+    assert 0 < small < big and small < wider
+    # at least the values, the ILU factors and the Krylov bases
+    n = 100000 * 4
+    assert big >= 700000 * 16 * 8 * 2 + n * 8 * 2 * 30
