@@ -52,3 +52,28 @@ def test_stack_rejects_mixed_block_sizes():
     import pytest
     with pytest.raises(ValueError):
         msp.stack_block_diagonal([box_jacobian(3, 3, 2, 3, 1), box_jacobian(3, 3, 2, 4, 2)])
+
+
+def test_colour_classes_of_a_stack_are_instance_major():
+    """The batched Krylov kernels cut the colour-ordered vector into (colour, instance)
+    segments: within every level-0 colour class (rows in original order, Algorithm 4.3
+    step 3) the rows of one instance must be contiguous and the instances in order.  The
+    colouring here is the oracle's, which the library's equals bit for bit."""
+    ms = _instances() + [box_jacobian(3, 3, 3, 3, 14, n_wells=1)]
+    nb, b, rp, ci, v, off = msp.stack_block_diagonal(ms)
+    S = BSRMatrix(nb=nb, b=b, row_ptr=rp, col_idx=ci, values=v.reshape(-1, b, b))
+    o = oracle.Oracle(S, coarse_max=20, mu=10**6)
+    colour, g = o.colour0()
+    perm = np.lexsort((np.arange(nb), colour))  # colour order, original order inside
+    inst = np.searchsorted(off, perm, side="right") - 1
+    cls = colour[perm]
+    segments = 0
+    for c in np.unique(cls):
+        ids = inst[cls == c]
+        assert np.all(np.diff(ids) >= 0), c
+        segments += len(np.unique(ids))
+    assert segments <= g * len(ms)
+    # every instance appears in at least one class, and a class never mixes rows of two
+    # instances inside one segment
+    assert set(np.unique(inst)) == set(range(len(ms)))
+    o.close()
