@@ -182,8 +182,10 @@ int msp_set_instances(msp_handle h, int32_t count, const int32_t* h_row_offsets)
  * d_x device arrays of nb*b doubles (natural order, may not alias); h_infos (host, may be
  * NULL) receives one msp_solve_info per instance.  The adaptive rule of Section 3.2
  * regenerates the preconditioner when the largest iteration count of the previous batch
- * exceeded mu.  Returns MSP_OK if every instance converged, else the first error status or
- * MSP_NOT_CONVERGED.  Synchronises the stream. */
+ * exceeded mu.  Each instance's FGMRES is that of msp_solve (restart m < 72) except that
+ * the second Gram-Schmidt pass is always taken.  Returns MSP_OK if every instance
+ * converged, else the first error status or MSP_NOT_CONVERGED; MSP_ERR_ARG if no
+ * instances were declared.  Synchronises the stream. */
 int msp_solve_batch(msp_handle h, const double* d_b, double* d_x, double rel_tol,
                     msp_solve_info* h_infos, void* stream);
 
