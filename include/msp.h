@@ -100,6 +100,12 @@ typedef struct {
   int precision;               /* MSP_PRECISION_* */
   int colouring;               /* MSP_COLOURING_* */
   int smoother;                /* MSP_SMOOTHER_* */
+  int loop_limit; /* 0 (default): every bounded SETUP loop runs to the bound its sizes
+                   * give (a colouring needs at most n passes of Algorithm 4.2, the
+                   * Jones-Plassmann colouring and the pairwise matching at most n
+                   * rounds).  > 0: caps each of those loops at this many passes or
+                   * rounds; a loop still unfinished then returns MSP_ERR_TIMEOUT.
+                   * For tests of the MSP_ERR_TIMEOUT path. */
 } msp_config;
 
 typedef struct {
@@ -123,8 +129,9 @@ int msp_config_default(msp_config* cfg);
  * adjacency matrix (Eq. adjacency-matrix), VerticesGrouping (Algorithms 4.1/4.2) and
  * the colour permutation (Algorithm 4.3 step 3) of the block graph, then the value
  * setup (decoupling, AMG hierarchy, stage-N blocks, BILU(0)).  nb >= 1, 1 <= b <= 8,
- * nnzb = row_ptr[nb].  Errors: MSP_ERR_ARG (sizes/config), MSP_ERR_PATTERN (unsorted
- * or out-of-range columns, missing diagonal), MSP_ERR_NONFINITE, MSP_ERR_SINGULAR_BLOCK
+ * nnzb = row_ptr[nb].  Errors: MSP_ERR_ARG (sizes/config), MSP_ERR_PATTERN (row
+ * pointers outside [0, nnzb] or decreasing, unsorted or out-of-range columns, missing
+ * diagonal; col_idx is never read outside [0, nnzb)), MSP_ERR_NONFINITE, MSP_ERR_SINGULAR_BLOCK
  * (a diagonal block, its concentration sub-block, a BILU pivot or the coarsest matrix
  * is singular), MSP_ERR_NOMEM, MSP_ERR_CUDA.  On error *out is NULL. */
 int msp_setup(msp_handle* out, const msp_config* cfg, int32_t nb, int32_t b,
@@ -265,9 +272,12 @@ int msp_stats_get(int index, char* name, int name_len, long long* launches, doub
  *                   (otherwise MSP_ERR_PATTERN / MSP_ERR_ARG)
  *   d_colour        int32[n], device, output: colour 1..g of every row
  *   h_ncolours      host, output: g
+ *                   Row pointers outside [0, row_ptr[n]] or decreasing give
+ *                   MSP_ERR_PATTERN; col_idx is never read outside [0, row_ptr[n]).
  * Calls no cudaMalloc, cudaFree or allocating library routine.  The first call on a
- * device looks up the device address of the scratch array (cudaGetSymbolAddress), so
- * make that first call before any stream capture.  Every call reuses the same array,
+ * device looks up the device address of the scratch array (cudaGetSymbolAddress), and
+ * so does the first call after the device's context changed (cudaDeviceReset), so make
+ * those calls before any stream capture.  Every call reuses the same array,
  * which keeps the previous call's contents: calls that overlap on the GPU (other
  * streams, other host threads) race on it and must be serialised by the caller.
  * Synchronises `stream`.  msp_noalloc_error() describes the last rejection of this

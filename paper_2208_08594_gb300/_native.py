@@ -48,7 +48,7 @@ class MspConfig(C.Structure):
                 ("bilu_order", C.c_int), ("precond", C.c_int), ("max_levels", C.c_int),
                 ("beta", C.c_double), ("agg_seed", C.c_ulonglong),
                 ("coarse_hard_max", C.c_int), ("precision", C.c_int), ("colouring", C.c_int),
-                ("smoother", C.c_int)]
+                ("smoother", C.c_int), ("loop_limit", C.c_int)]
 
 
 class MspSolveInfo(C.Structure):

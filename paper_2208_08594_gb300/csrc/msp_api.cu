@@ -481,7 +481,8 @@ int vertices_grouping_gpu(msp_handle h, int n, const DevBuf<int>& srp, const Dev
     MSP_TRY(launch_twohop_fill(n, rrp.p, rci.p, tp.p, tl.p, s));
   }
   MSP_TRY(launch_colouring(n, rrp.p, rci.p, twohop ? tp.p : nullptr, twohop ? tl.p : nullptr,
-                           inV.p, wbar.p, bitmap.p, words, colour_r.p, meta.p, s));
+                           inV.p, wbar.p, bitmap.p, words, colour_r.p, meta.p,
+                           h->cfg.loop_limit > 0 ? h->cfg.loop_limit : n, s));
   map_kernel<<<grid1(n), kThreads, 0, s>>>(n, colour_r.p, rank.p, colour.p);  // colour[v] = colour_r[rank[v]]
   MSP_TRY(launch_status());
   int hm[2] = {0, 0};
@@ -510,13 +511,15 @@ int jp_colouring_gpu(msp_handle h, int n, const int* srp, const int* sci, DevBuf
   MSP_CUDA_TRY(cudaMemsetAsync(colour.p, 0, (size_t)n * sizeof(int), s));
   MSP_CUDA_TRY(cudaMemsetAsync(counters.p, 0, 2 * sizeof(int), s));
   // every round colours at least the first uncoloured vertex in priority order
-  const long long max_rounds = (long long)n + 8;
+  const long long max_rounds =
+      h->cfg.loop_limit > 0 ? (long long)h->cfg.loop_limit : (long long)n + 8;
   int hc[2] = {0, 0};
   for (long long rounds = 0; hc[0] < n;) {
-    if (rounds > max_rounds) return MSP_ERR_TIMEOUT;
-    for (int r = 0; r < 8; ++r)
+    if (rounds >= max_rounds) return MSP_ERR_TIMEOUT;
+    const long long batch = std::min<long long>(8, max_rounds - rounds);
+    for (long long r = 0; r < batch; ++r)
       MSP_TRY(launch_jp_round(n, srp, sci, rank.p, colour.p, counters.p, s));
-    rounds += 8;
+    rounds += batch;
     MSP_CUDA_TRY(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, s));
     MSP_CUDA_TRY(cudaStreamSynchronize(s));
   }
@@ -640,7 +643,8 @@ int pairwise_pass(msp_handle h, const DCsr& A, double beta, unsigned long long s
     MSP_CUDA_TRY(cudaMemcpyAsync(h->h_flags, h->flags.p, sizeof(DevFlags), cudaMemcpyDeviceToHost, s));
     MSP_CUDA_TRY(cudaStreamSynchronize(s));
     if (h->h_flags->count == 0) break;
-    if (++rounds > n + 8) return MSP_ERR_TIMEOUT;  // at least one node decides per round
+    // at least one node decides per round, so n rounds decide every node
+    if (++rounds >= (h->cfg.loop_limit > 0 ? h->cfg.loop_limit : n + 8)) return MSP_ERR_TIMEOUT;
   }
   MSP_TRY(rep.alloc(n));
   MSP_TRY(id.alloc(n));
@@ -1775,7 +1779,7 @@ int pattern_setup(msp_handle h, const int32_t* d_rp, const int32_t* d_ci, cudaSt
   MSP_CUDA_TRY(cudaStreamSynchronize(s));
   if (hr[0] != 0 || (int64_t)hr[1] != h->nnzb) return MSP_ERR_PATTERN;
   MSP_TRY(reset_flags(h, s));
-  MSP_TRY(launch_check_pattern(nb, urp.p, uci.p, udpos.p, h->flags.p, s));
+  MSP_TRY(launch_check_pattern(nb, (int)nnzb, urp.p, uci.p, udpos.p, h->flags.p, s));
   if (sync_flags(h, s) != MSP_OK) return h->h_flags->code;
   // colouring of the block graph (Algorithms 4.1/4.2) and the colour permutation
   MSP_TRY(colour_graph(h, nb, urp.p, uci.p, (int)nnzb, h->colour0, h->perm0, h->cptr0, &h->g0, s));
@@ -1825,7 +1829,8 @@ bool config_ok(const msp_config& c, int b) {
          c.max_levels >= 1 && c.beta >= 0.0 && c.coarse_hard_max >= 1 &&
          (c.precision == MSP_PRECISION_FP64 || c.precision == MSP_PRECISION_FP32) &&
          (c.colouring == MSP_COLOURING_ALG41 || c.colouring == MSP_COLOURING_JP) &&
-         c.smoother >= MSP_SMOOTHER_PGS_MC && c.smoother <= MSP_SMOOTHER_PGS_NO && b >= 1 &&
+         c.smoother >= MSP_SMOOTHER_PGS_MC && c.smoother <= MSP_SMOOTHER_PGS_NO &&
+         c.loop_limit >= 0 && b >= 1 &&
          b <= 8;
 }
 
@@ -1856,6 +1861,7 @@ int msp_config_default(msp_config* c) {
   c->precision = MSP_PRECISION_FP64;
   c->colouring = MSP_COLOURING_ALG41;
   c->smoother = MSP_SMOOTHER_PGS_MC;
+  c->loop_limit = 0;
   return MSP_OK;
 }
 

@@ -49,12 +49,14 @@ __device__ void na_fail(int* meta, int code, int row) {
 }
 
 // validate the pattern (sorted, in range, diagonal present, off-diagonal part
-// symmetric) and count the off-diagonal entries of every row
-__global__ void na_degree_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                                 int* __restrict__ deg, int* meta) {
+// symmetric) and count the off-diagonal entries of every row.  Every read of ci stays
+// inside [0, nnz): a row (or the row of a neighbour searched for symmetry) whose
+// pointers leave that range or decrease is rejected before its columns are read.
+__global__ void na_degree_kernel(int n, int nnz, const int* __restrict__ rp,
+                                 const int* __restrict__ ci, int* __restrict__ deg, int* meta) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int p0 = rp[i], p1 = rp[i + 1];
-    if (p1 < p0) {
+    if (p0 < 0 || p1 < p0 || p1 > nnz) {
       na_fail(meta, MSP_ERR_PATTERN, i);
       deg[i] = 0;
       continue;
@@ -70,7 +72,12 @@ __global__ void na_degree_kernel(int n, const int* __restrict__ rp, const int* _
         diag = true;
         continue;
       }
-      int lo = rp[j], hi = rp[j + 1];  // (j, i) must be stored too
+      const int q0 = rp[j], q1 = rp[j + 1];  // (j, i) must be stored too
+      if (q0 < 0 || q1 < q0 || q1 > nnz) {
+        bad = true;
+        break;
+      }
+      int lo = q0, hi = q1;
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         if (ci[mid] < i)
@@ -78,7 +85,7 @@ __global__ void na_degree_kernel(int n, const int* __restrict__ rp, const int* _
         else
           hi = mid;
       }
-      if (lo >= rp[j + 1] || ci[lo] != i) {
+      if (lo >= q1 || ci[lo] != i) {
         bad = true;
         break;
       }
@@ -188,18 +195,56 @@ __global__ void na_map_kernel(int n, const int* __restrict__ colour_r, const int
 
 std::mutex g_na_mu;
 int* g_na_addr[64] = {nullptr};
+unsigned long long g_na_ctx[64] = {0};
 
-// Device address of the scratch array on the current device (looked up once per
-// device; the array's name in host code is only a host-side stand-in).
+// Unique id of the calling thread's current CUDA context (0 if it cannot be read): the
+// driver's cuCtxGetCurrent and cuCtxGetId, reached through the runtime so that the
+// library does not link the driver library itself.
+unsigned long long na_context_id() {
+  typedef int (*GetCurrentFn)(void**);
+  typedef int (*GetIdFn)(void*, unsigned long long*);
+  static GetCurrentFn get_current = nullptr;
+  static GetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault,
+                                         &q1) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) ==
+            cudaSuccess &&
+        q2 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<GetCurrentFn>(f1);
+      get_id = reinterpret_cast<GetIdFn>(f2);
+    }
+    cudaGetLastError();
+    looked_up = true;
+  }
+  if (!get_current || !get_id) return 0;
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of the scratch array on the current device.  The array's name in host
+// code is only a host-side stand-in; its address is looked up with cudaGetSymbolAddress
+// on the first call on a device (that device current) and again whenever the device's
+// context has changed since (after cudaDeviceReset, say), since a new context loads the
+// module, and the array, afresh.
 int na_scratch(int** out) {
   int dev = 0;
   MSP_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return MSP_ERR_ARG;
   std::lock_guard<std::mutex> lk(g_na_mu);
-  if (!g_na_addr[dev]) {
+  const unsigned long long ctx = na_context_id();  // 0 before any context is current
+  if (!g_na_addr[dev] || ctx == 0 || ctx != g_na_ctx[dev]) {
     void* p = nullptr;
-    MSP_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    MSP_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));  // makes the context current
     g_na_addr[dev] = static_cast<int*>(p);
+    g_na_ctx[dev] = na_context_id();
   }
   *out = g_na_addr[dev];
   return MSP_OK;
@@ -257,7 +302,7 @@ int msp_vertices_grouping_noalloc(int32_t n, const int32_t* d_row_ptr, const int
   // the array keeps the previous call's contents: clear what must start at zero
   MSP_CUDA_TRY(cudaMemsetAsync(meta, 0, 8 * sizeof(int), s));
   const unsigned grid = grid_for(n, 256);
-  na_degree_kernel<<<grid, 256, 0, s>>>(n, d_row_ptr, d_col_idx, deg, meta);
+  na_degree_kernel<<<grid, 256, 0, s>>>(n, rp_end[1], d_row_ptr, d_col_idx, deg, meta);
   MSP_TRY(launch_status());
   int h_meta[4] = {0, 0, 0, 0};
   MSP_CUDA_TRY(cudaMemcpyAsync(h_meta, meta, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -277,7 +322,7 @@ int msp_vertices_grouping_noalloc(int32_t n, const int32_t* d_row_ptr, const int
   na_relabel_fill_kernel<<<grid, 256, 0, s>>>(n, d_row_ptr, d_col_idx, rank, vor, rp2, ci2);
   MSP_TRY(launch_status());
   MSP_TRY(launch_colouring(n, rp2, ci2, nullptr, nullptr, inV, wbar, bits, kNaBitWords,
-                           colour_r, meta + 2, s));
+                           colour_r, meta + 2, n, s));
   na_map_kernel<<<grid, 256, 0, s>>>(n, colour_r, rank, d_colour);
   MSP_TRY(launch_status());
   MSP_CUDA_TRY(cudaMemcpyAsync(h_meta + 2, meta + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));

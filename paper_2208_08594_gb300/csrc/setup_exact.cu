@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(64) colouring_kernel(int n, const int* __restr
                                                        const int* __restrict__ tl,
                                                        unsigned* ginV, int* wbar,
                                                        unsigned* gbitmap, int layout,
-                                                       int* colour, int* meta) {
+                                                       int* colour, int* meta, int max_passes) {
   extern __shared__ unsigned smem_bits[];
   __shared__ int s_kb[32], s_off[33];
   __shared__ volatile int s_hint, s_done, s_sink;
@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(64) colouring_kernel(int n, const int* __restr
   int coloured = 0, g = 0;
   while (coloured < n) {
     ++g;
-    if (g > n) {  // every pass colours at least one vertex
+    if (g > n || g > max_passes) {  // every pass colours at least one vertex
       if (lane == 0) {
         meta[1] = 1;
         s_done = 1;
@@ -762,7 +762,7 @@ int launch_segment_sums(int nseg, const int* seg_start, const int* src, const do
 
 int launch_colouring(int n, const int* srp, const int* sci, const int* tp, const int* tl,
                      unsigned* inV, int* wbar, unsigned* bitmap, size_t bitmap_words,
-                     int* colour, int* meta, cudaStream_t s) {
+                     int* colour, int* meta, int max_passes, cudaStream_t s) {
   if (n <= 0) return MSP_OK;
   const int n0 = (n + 31) / 32, n1 = (n0 + 31) / 32, n2 = (n1 + 31) / 32;
   const size_t fwords = (size_t)n0 + n1 + n2;
@@ -790,7 +790,7 @@ int launch_colouring(int n, const int* srp, const int* sci, const int* tp, const
     }
   }
   colouring_kernel<<<1, 64, smem, s>>>(n, srp, sci, tp, tl, inV, wbar, bitmap, layout, colour,
-                                       meta);
+                                       meta, max_passes);
   return launch_status();
 }
 

@@ -18,11 +18,15 @@ __device__ void raise_flag(DevFlags* f, int code, int index) {
   if (atomicCAS(&f->code, MSP_OK, code) == MSP_OK) f->index = index;
 }
 
-__global__ void check_pattern_kernel(int nb, const int* __restrict__ rp, const int* __restrict__ ci,
-                                     int* __restrict__ dpos, DevFlags* flags) {
+// Every read of ci stays inside [0, nnz): a row whose pointers leave that range or
+// decrease is rejected before its columns are read (nnz = rp[nb], checked by the host).
+__global__ void check_pattern_kernel(int nb, int nnz, const int* __restrict__ rp,
+                                     const int* __restrict__ ci, int* __restrict__ dpos,
+                                     DevFlags* flags) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
     const int p0 = rp[i], p1 = rp[i + 1];
-    if (p1 < p0) {
+    if (p0 < 0 || p1 < p0 || p1 > nnz) {
+      dpos[i] = -2;
       raise_flag(flags, MSP_ERR_PATTERN, i);
       continue;
     }
@@ -535,9 +539,9 @@ __global__ void scatter_inverse_kernel(int n, const int* __restrict__ perm, int*
 
 }  // namespace
 
-int launch_check_pattern(int nb, const int* rp, const int* ci, int* dpos, DevFlags* flags,
+int launch_check_pattern(int nb, int nnz, const int* rp, const int* ci, int* dpos, DevFlags* flags,
                          cudaStream_t s) {
-  check_pattern_kernel<<<grid_for(nb, kThreads), kThreads, 0, s>>>(nb, rp, ci, dpos, flags);
+  check_pattern_kernel<<<grid_for(nb, kThreads), kThreads, 0, s>>>(nb, nnz, rp, ci, dpos, flags);
   return launch_status();
 }
 

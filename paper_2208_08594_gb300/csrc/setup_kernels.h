@@ -49,14 +49,17 @@ int launch_segment_sums(int nseg, const int* seg_start, const int* src, const do
 // bitmap of ceil(n/32) words, n ints Wbar list, frontier bitmap words.  On return
 // colour[r] in 1..g (by label), meta[0] = g, meta[1] = error flag (a bounded loop ran
 // out).  tp/tl: the graph's two-hop lists (launch_twohop_*), or both nullptr.
+// max_passes: passes of Algorithm 4.2 (colours) before the loop gives up (n always
+// suffices: every pass colours at least one vertex).
 int launch_colouring(int n, const int* srp, const int* sci, const int* tp, const int* tl,
                      unsigned* inV, int* wbar, unsigned* bitmap, size_t bitmap_words,
-                     int* colour, int* meta, cudaStream_t s);
+                     int* colour, int* meta, int max_passes, cudaStream_t s);
 
 // ---- other setup kernels (setup_kernels.cu) ----
-// errors in the BSR pattern: unsorted / out of range columns, missing diagonal
-int launch_check_pattern(int nb, const int* rp, const int* ci, int* dpos, DevFlags* flags,
-                         cudaStream_t s);
+// errors in the BSR pattern: row pointers outside [0, nnz] or decreasing, unsorted / out
+// of range columns, missing diagonal; ci is read only inside [0, nnz)
+int launch_check_pattern(int nb, int nnz, const int* rp, const int* ci, int* dpos,
+                         DevFlags* flags, cudaStream_t s);
 int launch_check_finite_vals(size_t n, const double* v, DevFlags* flags, cudaStream_t s);
 // MSP_ERR_PATTERN (index = permuted row) where a block couples two instances: row i of the
 // permuted pattern is original row perm[i]; instance k owns the original rows

@@ -336,7 +336,8 @@ int wells_build(msp_wells_s* W, const int* rp, const int* ci, const double* v, c
   MSP_CUDA_TRY(cudaMallocHost(&W->h_flags, sizeof(DevFlags)));
   MSP_CUDA_TRY(cudaMemsetAsync(W->flags.p, 0, sizeof(DevFlags), s));
   MSP_TRY(W->dpos.alloc(nb));
-  MSP_TRY(launch_check_pattern(nb, rp, ci, W->dpos.p, W->flags.p, s));
+  // reads ci only inside [0, nnzb), so a bad row_ptr is reported, never followed
+  MSP_TRY(launch_check_pattern(nb, (int)W->nnzb, rp, ci, W->dpos.p, W->flags.p, s));
   MSP_TRY(sync_wflags(W, s));
   if (W->h_flags->code != MSP_OK) return W->h_flags->code;
   int rp_nb = 0, rp_nr = 0;

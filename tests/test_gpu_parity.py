@@ -349,3 +349,75 @@ def test_staged_values_equal_direct_update():
         assert torch.equal(x1, x2)
     g1.close()
     g2.close()
+
+
+def _bad_row_ptr_inputs(a):
+    """A row_ptr whose middle entry lies past nnzb, with col_idx padded so that even a
+    scan that followed the bad pointer would stay inside the buffer."""
+    rp = a.row_ptr.copy()
+    k = a.nb // 2
+    rp[k] = a.nnzb + 5  # row k-1 would end past nnzb, row k would run backwards
+    ci = np.concatenate([a.col_idx, np.arange(2 * a.nnzb + 16, dtype=np.int32) % a.nb])
+    return _vec(rp), _vec(ci.astype(np.int32))
+
+
+def test_row_pointer_outside_the_column_array_rejected():
+    import ctypes as C
+    a = grid_spe10(nx=6, ny=5, nz=4)
+    rp, ci = _bad_row_ptr_inputs(a)
+    v = _vec(a.values.reshape(-1))
+    L = msp._native.lib()
+    cfg = msp.msp_config_default(coarse_max=20)
+    h = C.c_void_p()
+    st = L.msp_setup(C.byref(h), C.byref(cfg), a.nb, a.b, C.c_void_p(rp.data_ptr()),
+                     C.c_void_p(ci.data_ptr()), C.c_void_p(v.data_ptr()), a.nnzb, None)
+    torch.cuda.synchronize()
+    assert st == -2 and not h.value
+    W = C.c_void_p()
+    st = L.msp_wells_setup(C.byref(W), a.nb, a.b, a.n_wells, C.c_void_p(rp.data_ptr()),
+                           C.c_void_p(ci.data_ptr()), C.c_void_p(v.data_ptr()), a.nnzb, None)
+    torch.cuda.synchronize()
+    assert st == -2 and not W.value
+    # a decreasing pointer that stays inside [0, nnzb]
+    rp2 = a.row_ptr.copy()
+    rp2[a.nb // 2] = rp2[a.nb // 2 - 1] - 1
+    rpd, cid, _ = _dev(a)
+    with pytest.raises(msp.MspError) as e:
+        msp.Solver(a.nb, a.b, _vec(rp2), cid, v)
+    assert e.value.status == -2
+
+
+def test_bounded_setup_loops_return_timeout():
+    """loop_limit caps the colouring passes (Algorithm 4.2), the Jones-Plassmann rounds and
+    the matching rounds; a loop that needs more returns MSP_ERR_TIMEOUT (-7) and leaves
+    nothing behind that msp_free cannot release."""
+    a = box_jacobian(8, 8, 6, 2, 21)  # 7-point grid, no wells: Algorithm 4.1 gives 2 colours
+    rp, ci, v = _dev(a)
+    # Algorithm 4.2 needs two passes on the grid
+    with pytest.raises(msp.MspError) as e:
+        msp.Solver(a.nb, a.b, rp, ci, v, loop_limit=1, coarse_max=20)
+    assert e.value.status == -7
+    # one Jones-Plassmann round colours only the vertices without a higher-priority neighbour
+    with pytest.raises(msp.MspError) as e:
+        msp.Solver(a.nb, a.b, rp, ci, v, loop_limit=1, coarse_max=20,
+                   colouring=msp.MSP_COLOURING_JP)
+    assert e.value.status == -7
+    # with the off-diagonal blocks zero, every node is a singleton after one matching round
+    # (a second confirms it) and the hierarchy stops at one level: SETUP fits in two rounds
+    vals = a.values.copy()
+    rows = np.repeat(np.arange(a.nb), np.diff(a.row_ptr))
+    vals[rows != a.col_idx] = 0.0
+    s = msp.Solver(a.nb, a.b, rp, ci, _vec(vals.reshape(-1)), loop_limit=2, coarse_max=20,
+                   mu=0, max_it=40)
+    s.update_values(v)
+    rhs = _vec(random_rhs(a, 5))
+    x = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+    info = s.solve(rhs, x, 1e-6)  # the B of msp_setup, stale for the new values
+    assert info["status"] in (0, 1) and info["iterations"] > 0
+    # mu = 0: this solve regenerates B, and the grid's matching needs more than two rounds
+    with pytest.raises(msp.MspError) as e:
+        s.solve(rhs, x, 1e-6)
+    assert e.value.status == -7
+    assert msp._native.lib().msp_free(s.h) == 0
+    s.h = None
+    torch.cuda.synchronize()  # the context is still usable

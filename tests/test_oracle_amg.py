@@ -51,6 +51,46 @@ def test_splitmix64_reference_values():
     assert oracle.splitmix64(0x9E3779B97F4A7C15) == 0x6E789E6AA1B965F4
 
 
+def _golden_pairwise():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "pairwise_hand_traces.json")
+    with open(path) as f:
+        return json.load(f)
+
+
+def test_splitmix64_published_outputs():
+    ref = _golden_pairwise()["splitmix64_reference"]
+    for x, y in zip(ref["inputs"], ref["outputs"]):
+        assert oracle.splitmix64(int(x, 16)) == int(y, 16)
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_pairwise_hand_traces(k):
+    """One matching pass on a 7-node graph traced by hand (tests/golden): exact-threshold
+    candidates, a negative strength, a tie, an asymmetric pair whose row-only strength
+    would choose differently, taken candidates and singletons."""
+    d = _golden_pairwise()
+    gr, case = d["graph"], d["cases"][k]
+    n = gr["n"]
+    ent = {(i, i): gr["diagonal"] for i in range(n)}
+    for i, j, v in gr["entries"]:
+        ent[(i, j)] = v
+    keys = sorted(ent)
+    rp = np.zeros(n + 1, np.int32)
+    for i, _ in keys:
+        rp[i + 1] += 1
+    rp = np.cumsum(rp).astype(np.int32)
+    ci = np.array([j for _, j in keys], np.int32)
+    v = np.array([ent[key] for key in keys])
+    order = sorted(range(n), key=lambda i: (oracle.splitmix64(i ^ case["seed"]), i))
+    assert order == case["visit_order"]  # the premise of the trace
+    agg, nc = oracle.pairwise(rp, ci, v, 0.25, case["seed"])
+    assert nc == case["nagg"]
+    assert agg.tolist() == case["agg"]
+    assert [sorted(np.nonzero(agg == c)[0].tolist()) for c in range(nc)] == case["aggregates"]
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_pairwise_matches_brute_force(seed):
     a = box_jacobian(5, 4, 3, 1, 100 + seed, layered=True, n_wells=1)

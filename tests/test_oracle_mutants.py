@@ -63,6 +63,15 @@ MUTANTS = {
     "jp_priority_reversed": (
         "order[v] = {-(S.rp[v + 1] - S.rp[v]), (uint32_t)(splitmix64((uint64_t)v ^ kJpSeed) >> 32),",
         "order[v] = {(S.rp[v + 1] - S.rp[v]), (uint32_t)(splitmix64((uint64_t)v ^ kJpSeed) >> 32),"),
+    "matching_threshold_strict": (
+        "if (s[p - S.rp[i]] >= thr) {", "if (s[p - S.rp[i]] > thr) {"),
+    "matching_visit_order_reversed": (
+        "std::sort(order.begin(), order.end());\n  std::vector<int> partner(n, -1);",
+        "std::sort(order.rbegin(), order.rend());\n  std::vector<int> partner(n, -1);"),
+    "matching_tie_to_larger_index": (
+        "(cand_s[p] == sbest && j < best)", "(cand_s[p] == sbest && j > best)"),
+    "matching_row_only_strength": (
+        "double t = entry(a, i, j) + entry(a, j, i);", "double t = 2.0 * entry(a, i, j);"),
     "pgs_no_chunk_size": (
         "constexpr int kPgsNoChunk = 16;", "constexpr int kPgsNoChunk = 8;"),
 }

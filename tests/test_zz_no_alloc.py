@@ -61,3 +61,22 @@ def test_noalloc_rejects_sizes_beyond_the_maximum():
                                          ctypes.c_void_p(out.data_ptr()), ctypes.byref(g), None)
     assert st == -1
     assert b"exceeds the maximum" in L.msp_noalloc_error()
+
+
+def test_noalloc_rejects_row_pointers_outside_the_column_array():
+    """A row pointer past row_ptr[n] is reported (MSP_ERR_PATTERN), never followed; col_idx
+    is padded so that even a scan that followed it would stay inside the buffer."""
+    a = grid_spe10(nx=8, ny=6, nz=4)
+    rp = a.row_ptr.copy()
+    rp[a.nb // 2] = a.nnzb + 5
+    ci = np.concatenate([a.col_idx, np.arange(2 * a.nnzb + 16, dtype=np.int32) % a.nb])
+    drp = torch.from_numpy(rp).to(DEV)
+    dci = torch.from_numpy(ci.astype(np.int32)).to(DEV)
+    out = torch.zeros(a.nb, dtype=torch.int32, device=DEV)
+    L = msp._native.lib()
+    g = ctypes.c_int32()
+    st = L.msp_vertices_grouping_noalloc(a.nb, ctypes.c_void_p(drp.data_ptr()),
+                                         ctypes.c_void_p(dci.data_ptr()),
+                                         ctypes.c_void_p(out.data_ptr()), ctypes.byref(g), None)
+    torch.cuda.synchronize()
+    assert st == -2
