@@ -44,9 +44,8 @@ METRIC = "solves/s to 1e-6 rel. residual (1.1M cells x4)"
 # timing call sites of the library (msp_stats_*) -> the kernel each one launches
 SITE_KERNELS = {
     "krylov_spmv": "bsr_spmv_kernel", "api_spmv": "bsr_spmv_kernel",
-    "krylov_multi_dot": "multi_dot_kernel", "krylov_reorth_dot": "multi_dot_kernel",
+    "krylov_multi_dot": "multi_dot2_kernel", "krylov_finalize_dot": "multi_dot_kernel",
     "krylov_multi_axpy": "multi_axpy_norm_kernel",
-    "krylov_reorth_axpy": "multi_axpy_norm_kernel",
     "stageN_bgs_sweep": "bgs_colour_kernel",
     "stageP_residual_restrict": "bsr_restrict_p_kernel",
     "stageP_correct_residual": "bsr_col0_update_kernel",
@@ -66,9 +65,6 @@ SITE_PREFIX_KERNELS = {"amg_gs_pre_l": "ell_gs_colour_kernel",
                        "amg_pjac_l": "jacobi_sweep_kernel",
                        "amg_pgs_no_l": "pgs_no_sweep_kernel",
                        "amg_residual_restrict_csr_l": "csr_residual_restrict_kernel"}
-# FP64 block kernels do one FMA per 8-byte value: at the measured 1.19 TFLOP/s FP64 FMA
-# rate they cannot move more than 1.19e12 / 2 * 8 bytes/s
-FP64_FMA_CEILING_GBPS = 1.19e12 / 2 * 8 / 1e9
 TOL = 1e-6
 
 
@@ -94,6 +90,8 @@ def parse():
     p.add_argument("--nz", type=int, default=85)
     p.add_argument("--value-sets", type=int, default=4)
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--mu0-steps", type=int, default=4,
+                   help="solves timed with mu = 0 (plain MSP: SETUP before every solve)")
     p.add_argument("--profile-steps", type=int, default=0)
     p.add_argument("--mu-sweep", action="store_true",
                    help="SetupCalls / SetupRatio / Iter / Time against mu on a drifting "
@@ -123,7 +121,9 @@ def parse():
 
 
 def workload_name(args):
-    return "spe10-shaped %dx%dx%d + 4 wells, 4x4 BSR, %s%s" % (
+    return ("spe10-shaped %dx%dx%d + 4 wells, 4x4 BSR, coupling blocks -T_ij (R_ij + 3 I) "
+            "(R_ij ~ U[0.1,1]), Newton steps: couplings x U[0.95,1.05] with rebalanced "
+            "diagonal blocks, %s%s") % (
         args.nx, args.ny, args.nz, "FP64" if args.precision == "fp64" else
         "FP32 preconditioner / FP64 Krylov",
         ", Jones-Plassmann-order colouring" if args.colouring == "jp" else "") + (
@@ -142,20 +142,64 @@ def smoother_of(args, msp):
 
 
 def kernels_from_sites(sites):
-    """{kernel: [launches, ms, bytes]} summed over the call sites that launch it
+    """{kernel: [launches, ms, bytes, flops]} summed over the call sites that launch it
     (containers such as the whole graph replay are left out)."""
     out = {}
-    for site, (n, ms, by) in sites.items():
+    for site, rec in sites.items():
+        n, ms, by = rec[:3]
+        fl = rec[3] if len(rec) > 3 else 0.0
         k = SITE_KERNELS.get(site)
         if k is None:
             k = next((v for p, v in SITE_PREFIX_KERNELS.items() if site.startswith(p)), None)
         if k is None:
             continue
-        acc = out.setdefault(k, [0, 0.0, 0.0])
+        acc = out.setdefault(k, [0, 0.0, 0.0, 0.0])
         acc[0] += n
         acc[1] += ms
         acc[2] += by
+        acc[3] += fl
     return out
+
+
+# FP64 FMA units: 152 SMs x 2 FMA per clock (the nominal 1.25 TFLOP/s FP64 of this part at
+# 2070 MHz); the peak of a kernel bound by FP64 arithmetic, at the SM clock measured under load
+FP64_FMA_PER_CLOCK_PER_SM = 2
+
+
+def roofline_of(name, rec, peak_gbs, peak_kind, sms, sm_mhz, fma64_measured, live_ms, steps):
+    """The binding roof of one kernel: HBM (algorithmic bytes / time against the measured
+    copy bandwidth) or, where its algorithmic FP64 flops need longer at the FP64 FMA rate
+    than its bytes need at the HBM rate, the FP64 ALU (flops / time against the derived FP64
+    peak)."""
+    n_l, tot_ms, tot_b, tot_f = rec
+    t = (tot_ms / n_l) / 1000.0
+    by, fl = tot_b / n_l, tot_f / n_l
+    fp64_peak = sms * FP64_FMA_PER_CLOCK_PER_SM * 2 * sm_mhz * 1e6
+    out = {"kernel": name, "algorithmic_bytes_per_launch": round(by, 1),
+           "algorithmic_flops_per_launch": round(fl, 1), "avg_launch_ms": round(t * 1000, 5),
+           "launches": n_l, "share_of_step": round(tot_ms / live_ms, 4),
+           "hbm_GBps": round(by / t / 1e9, 1), "hbm_frac": round(by / t / 1e9 / peak_gbs, 4)}
+    if fl > 0 and fl / fp64_peak > by / (peak_gbs * 1e9):
+        out.update({"bound": "alu", "achieved": round(fl / t / 1e12, 4),
+                    "peak": round(fp64_peak / 1e12, 4), "unit": "TFLOP/s",
+                    "frac": round(fl / t / fp64_peak, 4),
+                    "peak_kind": "derived: %d SMs x %d FP64 FMA/clock x 2 flops x %.0f MHz "
+                                 "(measured FMA-chain kernel: %.4f TFLOP/s)" % (
+                                     sms, FP64_FMA_PER_CLOCK_PER_SM, sm_mhz,
+                                     fma64_measured / 1e12)})
+    else:
+        out.update({"bound": "hbm", "achieved": round(by / t / 1e9, 1), "peak": peak_gbs,
+                    "unit": "GB/s", "frac": round(by / t / 1e9 / peak_gbs, 4),
+                    "peak_kind": peak_kind})
+    return out
+
+
+def static_config(args, a):
+    """The workload's configuration, the same in the native and the reference line."""
+    return {"workload": workload_name(args), "cells": args.nx * args.ny * args.nz,
+            "block_rows": a.nb, "nnzb": a.nnzb, "mu": args.mu, "restart": 30, "tol": TOL,
+            "l2": "inputs larger than L2 (1 GB of values), no flush",
+            "parallelism": "single GPU or independent replicas (one per GPU)"}
 
 
 def load_peaks():
@@ -369,6 +413,47 @@ def run_native(args):
     live_ms = i0.elapsed_time(i1)
     live = msp.msp_stats_get()
 
+    # plain MSP (mu = 0, the first CUDA rows of Tables 3, 5 and 7): every solve regenerates
+    # the preconditioner (SETUP) before FGMRES; the same value sets, one solver per pass
+    mu0 = None
+    if args.mu0_steps > 0:
+        mu0_solver = msp.Solver(a.nb, a.b, d_rp, d_ci, d_v0, mu=0, precision=prec,
+                                colouring=colouring_of(args, msp),
+                                smoother=smoother_of(args, msp))
+        mu0_infos = []
+
+        def mu0_step(k):
+            mu0_solver.update_values(d_sets[k % nsets])
+            info = mu0_solver.solve(d_rhs[k % nsets], x, TOL)
+            if info["status"] != 0:
+                raise RuntimeError("solve failed: %s" % info)
+            mu0_infos.append(info)
+
+        mu0_step(1)  # the first solve uses msp_setup's preconditioner: not timed
+        mu0_infos.clear()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.mu0_steps):
+            mu0_step(args.warmup + k)
+        torch.cuda.synchronize()
+        mu0_s = time.perf_counter() - t0
+        mu0_solver.close()
+        t_set = sum(i["t_setup_ms"] for i in mu0_infos) / 1000.0
+        mu0 = {"mu": 0, "solves": len(mu0_infos),
+               "solves_per_s": round(len(mu0_infos) / mu0_s, 4),
+               "ms_per_solve": round(1000.0 * mu0_s / len(mu0_infos), 1),
+               "setup_calls": int(sum(i["setup_performed"] for i in mu0_infos)),
+               "setup_ratio": round(t_set / mu0_s, 4),
+               "setup_ms_mean": round(1000.0 * t_set / len(mu0_infos), 1),
+               "iterations": [i["iterations"] for i in mu0_infos],
+               "timed": "host wall clock around update_values + solve (SETUP inside the "
+                        "solve, timed by the library as SetupRatio's numerator)"}
+
+    # FMA ceilings of this GPU, measured now (the FP64 block kernels do one FMA per
+    # 8-byte value and can be bound by the FP64 rate, not by HBM)
+    fma64 = msp.msp_fma_rate(msp.MSP_PRECISION_FP64)
+    fma32 = msp.msp_fma_rate(msp.MSP_PRECISION_FP32)
+
     # optional: the steps launched eagerly (no graph), every launch timed
     stats, prof_ms = {}, None
     if args.profile_steps > 0:
@@ -450,25 +535,24 @@ def run_native(args):
     # ranking as the shares of the ncu launch list under profiles/).
     kern = kernels_from_sites(live)
     roofline = None
+    sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     if kern:
-        name, (n_l, tot_ms, tot_b) = max(kern.items(), key=lambda kv: kv[1][1])
-        achieved = (tot_b / n_l) / ((tot_ms / n_l) / 1000.0) / 1e9
-        roofline = {"bound": "hbm", "kernel": name,
-                    "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind,
-                    "unit": "GB/s", "frac": round(achieved / peak, 4),
-                    "traffic": traffic_for(name),
-                    "algorithmic_bytes_per_launch": round(tot_b / n_l, 1),
-                    "avg_launch_ms": round(tot_ms / n_l, 5), "launches": n_l,
-                    "share_of_step": round(tot_ms / live_ms, 4),
+        name, rec = max(kern.items(), key=lambda kv: kv[1][1])
+        roofline = roofline_of(name, rec, peak, peak_kind, sms, sm_mhz, fma64, live_ms,
+                               args.steps)
+        roofline.update({"traffic": traffic_for(name),
                     "measured": "CUDA event pairs around every call site (one launch, or "
                                 "the consecutive launches of one kernel over the colours of "
                                 "a sweep), as event nodes inside the preconditioner's CUDA "
                                 "graph and event records on the solver stream outside it, "
-                                "over a second timed pass of the same steps"}
+                                "over a second timed pass of the same steps"})
     kernels = {k: {"launches_per_step": round(v[0] / args.steps, 1),
                    "ms_per_step": round(v[1] / args.steps, 3),
                    "GBps": round(v[2] / (v[1] / 1000.0) / 1e9, 1) if v[1] > 0 else None,
-                   "frac": round(v[2] / (v[1] / 1000.0) / 1e9 / peak, 4) if v[1] > 0 else None}
+                   "frac": round(v[2] / (v[1] / 1000.0) / 1e9 / peak, 4) if v[1] > 0 else None,
+                   "TFLOPs": round(v[3] / (v[1] / 1000.0) / 1e12, 4)
+                   if v[1] > 0 and v[3] > 0 else None}
                for k, v in sorted(kern.items(), key=lambda kv: -kv[1][1])}
     sites = {k: {"launches_per_step": round(v[0] / args.steps, 1),
                  "ms_per_step": round(v[1] / args.steps, 3),
@@ -483,9 +567,8 @@ def run_native(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32-precond/f64-krylov",
         "data": "synthetic (seeded SPE10-shaped Jacobian; SPE10 data not available)",
-        "config": {"workload": workload_name(args), "cells": args.nx * args.ny * args.nz,
-                   "block_rows": a.nb, "nnzb": a.nnzb, **reduced, "mu": args.mu,
-                   "restart": 30, "tol": TOL, "levels": solver_levels,
+        "config": static_config(args, a),
+        "run": {**reduced, "levels": solver_levels,
                    "level_sizes": [li[0] for li in level_info],
                    "level_nnz": [li[1] for li in level_info],
                    "level_colours": [li[2] for li in level_info],
@@ -494,12 +577,16 @@ def run_native(args):
                    "amg_grid_complexity": round(sum(li[0] for li in level_info)
                                                 / max(1, level_info[0][0]), 3),
                    "iterations": its, "setups_in_timed_steps": setups,
-                   "setup_s_first": round(setup_s, 3),
-                   "l2": "inputs larger than L2 (1 GB of values), no flush",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "setup_s_first": round(setup_s, 3)},
         "gpu_launches": launches,
         "roofline": roofline,
-        "fp64_fma_ceiling_GBps": round(FP64_FMA_CEILING_GBPS, 1),
+        "fma_rates": {"fp64_tflops": round(fma64 / 1e12, 4), "fp32_tflops": round(fma32 / 1e12, 3),
+                      "fp64_fma_ceiling_GBps": round(fma64 / 2 * 8 / 1e9, 1),
+                      "how": "msp_fma_rate: 8 blocks of 256 threads per SM, 8 independent FMA "
+                             "chains of 2048 steps per thread, best of 5 launches, CUDA events; "
+                             "ceiling = the bytes/s of kernels doing one FP64 FMA per 8-byte "
+                             "value"},
+        "plain_msp_mu0": mu0,
         "kernels": kernels,
         "sites": sites,
         "instrumented_ms_per_step": round(live_ms / args.steps, 3),
@@ -520,11 +607,13 @@ def run_native(args):
     return out
 
 
-def oracle_sample(args, its_mean, setup_frac, steps, warmup):
+def oracle_sample(args, its_mean, setup_frac, steps, warmup, full_solve=False):
     """Time the oracle (single thread) on the full workload: SETUP once, then per step one
     Arnoldi iteration, measured as (solve capped at 2 iterations) - (capped at 1);
     returns (solves/s extrapolated to `its_mean` iterations and a `setup_frac` share of
-    setups, seconds per iteration, setup seconds)."""
+    setups, seconds per iteration, setup seconds, its_mean).  With `full_solve`, the
+    oracle first solves the system to the tolerance once and its own iteration count
+    replaces `its_mean`."""
     import oracle
     from synthetic import grid_spe10, random_rhs
     from synthetic import BSRMatrix
@@ -539,6 +628,9 @@ def oracle_sample(args, its_mean, setup_frac, steps, warmup):
                       n_cells=W.nr)
     o = oracle.Oracle(a, mu=10 ** 9)
     setup_s = time.perf_counter() - t0
+    if full_solve:
+        _, info = o.solve(rhs, TOL)
+        its_mean = float(info["iterations"])
     per = []
     for k in range(warmup + steps):
         o.set_max_it(1)
@@ -553,32 +645,37 @@ def oracle_sample(args, its_mean, setup_frac, steps, warmup):
             per.append(max(t2 - t1, 1e-9))
     t_it = float(np.median(per))
     value = 1.0 / (setup_frac * setup_s + its_mean * t_it)
-    return value, t_it, setup_s
+    return value, t_it, setup_s, its_mean
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
-    # iterations per solve and setup share of the GPU arm on this workload (138 iterations,
-    # no setup in the timed steps at mu = 180; the GPU and oracle iteration counts agree
-    # within one in the parity tests); plain MSP (mu = 0) sets up for every solve
-    its_mean = 138.0
-    setup_frac = 1.0 if args.mu < its_mean else 0.0
+    # the oracle's own iteration count comes from one full solve of the first system; the
+    # timed steps are single Arnoldi iterations.  SETUP counts in every solve at mu = 0
+    # (plain MSP) and in none when mu is above the iteration count (the GPU arm's timed
+    # solves reuse their first SETUP)
     t0 = time.perf_counter()
-    value, t_it, setup_s = oracle_sample(args, its_mean, setup_frac, args.steps, args.warmup)
+    value, t_it, setup_s, its_mean = oracle_sample(args, 0.0, 0.0, args.steps, args.warmup,
+                                                   full_solve=True)
+    setup_frac = 1.0 if args.mu < its_mean else 0.0
+    value = 1.0 / (setup_frac * setup_s + its_mean * t_it)
     wall = time.perf_counter() - t0
-    sample = ("oracle on the full %dx%dx%d matrix: SETUP once (%.1f s) and %d timed single "
-              "Arnoldi iterations (median %.3f s, solve capped at 2 minus capped at 1); "
-              "solves/s = 1 / (%.2f * setup + %.1f iterations)" % (
-                  args.nx, args.ny, args.nz, setup_s, args.steps, t_it, setup_frac, its_mean))
+    sample = ("oracle on the full %dx%dx%d matrix: SETUP once (%.1f s), one full solve to "
+              "1e-6 (%d iterations), then %d timed single Arnoldi iterations (median %.3f s, "
+              "solve capped at 2 minus capped at 1); solves/s = 1 / (%.2f * setup + %d "
+              "iterations)" % (args.nx, args.ny, args.nz, setup_s, its_mean, args.steps, t_it,
+                               setup_frac, its_mean))
+    from synthetic import grid_spe10
+    a = grid_spe10(seed=2209, nx=args.nx, ny=args.ny, nz=args.nz)
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "solves/s",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(t_it * 1000, 3), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": workload_name(args), "mu": args.mu},
+           "config": static_config(args, a),
            "cpu_baseline": {"value": round(value, 6), "unit": "solves/s", "cores": 1,
-                            "kind": "oracle", "sample": sample},
+                            "host_cores": os.cpu_count(), "kind": "oracle", "sample": sample},
            "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0},
            "wall_s": round(wall, 1)}
@@ -958,9 +1055,10 @@ def main():
         return
     # CPU baseline: the oracle, bounded sample (rank 0, N = 1 only)
     if out["n_gpus"] == 1 and os.environ.get("MSP_BENCH_NO_CPU") != "1":
-        value, t_it, setup_s = oracle_sample(args, out["_its_mean"], out["_setup_frac"], 2, 1)
+        value, t_it, setup_s, _ = oracle_sample(args, out["_its_mean"], out["_setup_frac"], 2, 1)
         out["cpu_baseline"] = {
-            "value": round(value, 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "value": round(value, 6), "unit": "solves/s", "cores": 1,
+            "host_cores": os.cpu_count(), "kind": "oracle",
             "sample": "oracle on the full matrix: SETUP once (%.1f s) + 2 timed single Arnoldi "
                       "iterations (median %.3f s), extrapolated to %.1f iterations and a setup "
                       "share of %.2f" % (setup_s, t_it, out["_its_mean"], out["_setup_frac"])}

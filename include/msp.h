@@ -89,7 +89,8 @@ typedef struct {
   int npass;       /* pairwise matching passes per AMG level (2: aggregates <= 4) */
   int pre_sweeps;  /* PGS-MC sweeps before the coarse correction (forward colours) */
   int post_sweeps; /* PGS-MC sweeps after it (backward colours) */
-  int bgs_sweeps;  /* block GS sweeps of stage N */
+  int bgs_sweeps;  /* block GS sweeps of stage N, each forward in level-0 colour order,
+                   * the first from zero (6; the paper fixes no count) */
   int decoupling;  /* 1 = quasi-IMPES weights omega_i = D_i^-T e_0, 0 = none */
   int bilu_order;  /* must be 0: ILU(0) in level-0 colour order */
   int precond;     /* MSP_PREC_* */
@@ -251,9 +252,20 @@ long long msp_stats_launches(void);
  * pending timings). */
 int msp_stats_count(void);
 /* Call site `index`: its name (NUL-terminated, truncated to name_len), launches, summed
- * CUDA-event milliseconds and summed algorithmic bytes.  Any output may be NULL. */
+ * CUDA-event milliseconds, summed algorithmic bytes and summed algorithmic floating-point
+ * operations (2 per FMA; recorded only at sites whose kernels can be bound by the FP64
+ * rate, 0 elsewhere).  Any output may be NULL. */
 int msp_stats_get(int index, char* name, int name_len, long long* launches, double* total_ms,
-                  double* bytes);
+                  double* bytes, double* flops);
+
+/* Measured FMA throughput of the current device (the paper has no counterpart: the
+ * benchmark states the ALU ceiling of the FP64 kernels with it).  precision =
+ * MSP_PRECISION_FP64 or MSP_PRECISION_FP32; *flops_per_s receives 2 x FMAs per second
+ * of a kernel of independent FMA chains (8 blocks of 256 threads per SM, 8 chains of
+ * 2048 steps per thread), the best of 5 launches timed with CUDA events on `stream`.
+ * Allocates a small output buffer; synchronises `stream`.  MSP_ERR_ARG for another
+ * precision or a NULL output. */
+int msp_fma_rate(int precision, double* flops_per_s, void* stream);
 
 
 /* ---- allocation-free entry point ----

@@ -56,7 +56,7 @@ typedef struct {
   int npass;         // pairwise matching passes per level (2: aggregates of up to 4)
   int pre_sweeps;    // PGS-MC sweeps before coarse correction (1, forward)
   int post_sweeps;   // PGS-MC sweeps after coarse correction (1, backward)
-  int bgs_sweeps;    // block GS sweeps of stage N (1, forward from zero)
+  int bgs_sweeps;    // block GS sweeps of stage N (6, each forward, from zero)
   int decoupling;    // 1 = quasi-IMPES weights (Pi_P^T unspecified), 0 = literal Pi_P^T A Pi_P
   int bilu_order;    // 0 = level-0 colour order, 1 = natural order
   int precond;       // PREC_*; 0 = MSP (Alg 3.1)
@@ -901,7 +901,11 @@ void vcycle(const Handle& h, int l, const double* b, double* x) {
   for (int s = 0; s < h.cfg.post_sweeps; ++s) smooth(false);
 }
 
-// w += Pi_N B_N Pi_N^T r : block GS on the (b-1)x(b-1) sub-blocks, colour order, x0 = 0
+// w += Pi_N B_N Pi_N^T r : block GS on the (b-1)x(b-1) sub-blocks, colour order, x0 = 0.
+// Eq. MSP names block Gauss-Seidel for B_N without a number of sweeps; bgs_sweeps forward
+// sweeps are taken (default 6: B_N is then close enough to the inverse of the
+// concentration block that stage N stops limiting the convergence on elliptic-like
+// concentration couplings)
 void stage_N(const Handle& h, const double* r, double* w) {
   const int nb = h.nb, b = h.b, bn = b - 1;
   if (bn <= 0) return;
@@ -1250,7 +1254,7 @@ void orc_config_default(orc_config* c) {
   c->npass = 2;
   c->pre_sweeps = 1;
   c->post_sweeps = 1;
-  c->bgs_sweeps = 1;
+  c->bgs_sweeps = 6;
   c->decoupling = 1;
   c->bilu_order = 0;
   c->precond = PREC_MSP;

@@ -17,7 +17,7 @@ from ._native import (MSP_NOT_CONVERGED, MSP_OK, MSP_PREC_MSP, MSP_PREC_N_ONLY, 
                       msp_solve_host, msp_spmv, msp_status_string, msp_update_values,
                       msp_update_values_host, msp_stats_enable, msp_stats_reset,
                       msp_stats_launches, msp_stats_get, msp_vertices_grouping_noalloc,
-                      NOALLOC_MAX_VERTICES, msp_wells_setup, msp_wells_reduced,
+                      NOALLOC_MAX_VERTICES, msp_fma_rate, msp_wells_setup, msp_wells_reduced,
                       msp_wells_update_values, msp_wells_reduce_rhs, msp_wells_recover,
                       msp_wells_free, msp_device_bytes, msp_estimate_device_bytes,
                       msp_server_create, msp_server_submit, msp_server_wait,
@@ -37,7 +37,7 @@ __all__ = ["Solver", "Wells", "WellEliminatedSolver", "Server", "BatchSolver",
            "msp_wells_reduced", "msp_wells_update_values", "msp_wells_reduce_rhs",
            "msp_wells_recover", "msp_wells_free", "msp_setup", "msp_update_values", "msp_update_values_host",
            "msp_stats_enable", "msp_stats_reset", "msp_stats_launches", "msp_stats_get",
-           "msp_vertices_grouping_noalloc", "NOALLOC_MAX_VERTICES",
+           "msp_vertices_grouping_noalloc", "NOALLOC_MAX_VERTICES", "msp_fma_rate",
            "msp_solve",
            "msp_solve_host", "msp_free", "msp_apply_precond", "msp_spmv", "msp_num_levels",
            "msp_level_info", "msp_level_get", "msp_colour0", "msp_config_default",

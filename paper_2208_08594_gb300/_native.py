@@ -35,7 +35,7 @@ EXPORTS = ("msp_config_default", "msp_setup", "msp_update_values", "msp_update_v
            "msp_wells_free", "msp_device_bytes", "msp_estimate_device_bytes",
            "msp_server_create", "msp_server_submit", "msp_server_wait", "msp_server_get_stats",
            "msp_server_free", "msp_set_instances", "msp_solve_batch",
-           "msp_stage_values_host", "msp_update_values_staged")
+           "msp_stage_values_host", "msp_update_values_staged", "msp_fma_rate")
 
 # largest n accepted by msp_vertices_grouping_noalloc (size of its fixed scratch)
 NOALLOC_MAX_VERTICES = 1 << 16
@@ -140,7 +140,7 @@ def lib(build_if_missing: bool = True):
     L.msp_stats_launches.argtypes = []
     L.msp_stats_launches.restype = C.c_longlong
     L.msp_stats_count.argtypes = []
-    L.msp_stats_get.argtypes = [I, C.c_char_p, I, P, P, P]
+    L.msp_stats_get.argtypes = [I, C.c_char_p, I, P, P, P, P]
     L.msp_vertices_grouping_noalloc.argtypes = [C.c_int32, P, P, P, C.POINTER(C.c_int32), P]
     L.msp_noalloc_error.argtypes = []
     L.msp_noalloc_error.restype = C.c_char_p
@@ -156,6 +156,7 @@ def lib(build_if_missing: bool = True):
     L.msp_set_instances.argtypes = [P, C.c_int32, P]
     L.msp_stage_values_host.argtypes = [P, P, P]
     L.msp_update_values_staged.argtypes = [P, P]
+    L.msp_fma_rate.argtypes = [I, C.POINTER(D), P]
     L.msp_solve_batch.argtypes = [P, P, P, D, P, P]
     L.msp_estimate_device_bytes.argtypes = [C.c_int32, C.c_int32, C.c_int64, C.POINTER(MspConfig)]
     L.msp_estimate_device_bytes.restype = C.c_int64
@@ -335,15 +336,16 @@ def msp_stats_launches() -> int:
 
 
 def msp_stats_get():
-    """{site: (launches, total_ms, bytes)} of the call sites timed since the last reset."""
+    """{site: (launches, total_ms, bytes, flops)} of the call sites timed since the last
+    reset."""
     L = lib()
     out = {}
     for k in range(L.msp_stats_count()):
         name = C.create_string_buffer(64)
-        n, ms, by = C.c_longlong(), C.c_double(), C.c_double()
-        if L.msp_stats_get(k, name, 64, C.byref(n), C.byref(ms), C.byref(by)) == MSP_OK \
-                and n.value > 0:
-            out[name.value.decode()] = (n.value, ms.value, by.value)
+        n, ms, by, fl = C.c_longlong(), C.c_double(), C.c_double(), C.c_double()
+        if L.msp_stats_get(k, name, 64, C.byref(n), C.byref(ms), C.byref(by),
+                           C.byref(fl)) == MSP_OK and n.value > 0:
+            out[name.value.decode()] = (n.value, ms.value, by.value, fl.value)
     return out
 
 
@@ -511,3 +513,12 @@ def msp_update_values_staged(h, stream=None):
     st = lib().msp_update_values_staged(h, _stream(stream))
     if st != MSP_OK:
         raise MspError(st, "msp_update_values_staged")
+
+
+def msp_fma_rate(precision: int, stream=None) -> float:
+    """Measured FLOP/s (2 x FMAs) of the current device in FP64 or FP32."""
+    out = C.c_double()
+    st = lib().msp_fma_rate(int(precision), C.byref(out), _stream(stream))
+    if st != MSP_OK:
+        raise MspError(st, "msp_fma_rate")
+    return out.value

@@ -45,7 +45,9 @@ class Probe {
  public:
   // `launches`: kernel launches the probe brackets (consecutive launches of one kernel
   // are timed as a group: an event pair per launch would cost more than a small launch)
-  Probe(const char* site, double bytes, cudaStream_t s, int launches = 1);
+  // `flops`: algorithmic floating-point operations of the launches (2 per FMA), where the
+  // kernel's ceiling may be its arithmetic rate rather than memory
+  Probe(const char* site, double bytes, cudaStream_t s, int launches = 1, double flops = 0.0);
   ~Probe();
   Probe(const Probe&) = delete;
   Probe& operator=(const Probe&) = delete;
@@ -55,6 +57,7 @@ class Probe {
   cudaEvent_t e0_ = nullptr, e1_ = nullptr;
   cudaStream_t s_ = nullptr;
   double bytes_ = 0.0;
+  double flops_ = 0.0;
   int launches_ = 1;
   bool in_graph_ = false;  // recorded as event nodes of a graph being captured
 };

@@ -104,15 +104,23 @@ int launch_cast_f2d(size_t n, const float* in, double* out, cudaStream_t s);
 int launch_multi_dot(size_t n, const double* V, size_t ldv, int K, const double* w,
                      double* partial, int nblocks, cudaStream_t s, const int* gate = nullptr);
 // out[k] = sum_b partial[b * kmax + k] (fixed order), k < K;  accumulate: out[k] += ...
+// one-pass Gram-Schmidt of FGMRES: dots of V[0..K) with two vectors (partials of block b at
+// b * 2 * kKrylovMaxK: [0, K) against x0, [K, 2K) against x1), strided reduction, and the
+// small triangular solves of one step (kernel comments in solve_kernels.cu)
+int launch_multi_dot2(size_t n, const double* V, size_t ldv, int K, const double* x0,
+                      const double* x1, double* partial, int nblocks, cudaStream_t s);
+int launch_reduce_partials_strided(int K, int nblocks, int stride, const double* partial,
+                                   double* out, cudaStream_t s);
+int launch_dcgs_coef(int j, const double* d, double* T, int ldt, double* g, double* out,
+                     cudaStream_t s);
+int launch_dcgs_finalize(int j1, const double* d, double* T, int ldt, double* out,
+                         cudaStream_t s);
 int launch_reduce_partials(int K, int nblocks, const double* partial, double* out,
                            bool accumulate, cudaStream_t s, const int* gate = nullptr);
 // w -= sum_k h[k] V[k]; partial[blk] = sum of w_new^2 over the block
 int launch_multi_axpy_norm(size_t n, const double* V, size_t ldv, int K, const double* h,
                            double* w, double* partial, int nblocks, cudaStream_t s,
                            const int* gate = nullptr);
-// gate[0] = 1 iff nrm_after[0] < nrm_before[0] / 2 (re-orthogonalisation test)
-int launch_reorth_gate(const double* nrm_after, const double* nrm_before, int* gate,
-                       cudaStream_t s);
 // v = w / sqrt(nrm2[0]) (nothing when the norm is zero); hn[0] = sqrt(nrm2[0])
 int launch_normalize(size_t n, const double* w, const double* nrm2, double* v, double* hn,
                      cudaStream_t s);

@@ -64,7 +64,7 @@ namespace {
 struct StatSite {
   std::string name;
   long long launches = 0;
-  double ms = 0.0, bytes = 0.0;
+  double ms = 0.0, bytes = 0.0, flops = 0.0;
 };
 struct PendingTiming {
   int site;
@@ -77,6 +77,7 @@ struct GraphProbe {
   cudaEvent_t e0, e1;
   double bytes;
   int launches;
+  double flops;
 };
 std::mutex g_stats_mu;
 int g_stats_mode = 0;
@@ -150,8 +151,8 @@ int launch_check(const char* file, int line) {
   return MSP_OK;
 }
 
-Probe::Probe(const char* site, double bytes, cudaStream_t s, int launches)
-    : s_(s), bytes_(bytes), launches_(launches) {
+Probe::Probe(const char* site, double bytes, cudaStream_t s, int launches, double flops)
+    : s_(s), bytes_(bytes), launches_(launches), flops_(flops) {
   if (t_capturing) {
     t_cap_bytes += bytes;
     if (!t_cap_timed) return;
@@ -171,6 +172,7 @@ Probe::Probe(const char* site, double bytes, cudaStream_t s, int launches)
   if (!e0_ || !e1_) return;
   site_ = site_index(site);
   g_sites[site_].bytes += bytes;
+  g_sites[site_].flops += flops;
   g_sites[site_].launches += launches;
   cudaEventRecord(e0_, s_);
 }
@@ -179,7 +181,7 @@ Probe::~Probe() {
   if (site_ < 0) return;
   if (in_graph_) {
     cudaEventRecordWithFlags(e1_, s_, cudaEventRecordExternal);
-    t_cap_probes.push_back(GraphProbe{site_, e0_, e1_, bytes_, launches_});
+    t_cap_probes.push_back(GraphProbe{site_, e0_, e1_, bytes_, launches_, flops_});
     return;
   }
   cudaEventRecord(e1_, s_);
@@ -392,6 +394,9 @@ struct msp_handle_s {
   // Krylov work
   msp::DevBuf<double> V, Z, bperm, xperm, rvec, partial, hdev, nrm, ydev;
   msp::DevBuf<int> ifl;
+  // one-pass Gram-Schmidt of the single solve: triangular factor T of the stored basis
+  // ((m + 2)^2, by column), the step's dot products, axpy coefficients and host-bound results
+  msp::DevBuf<double> gs_T, gs_d, gs_g, gs_out;
   msp::DevBuf<double> e2e_b, e2e_x;  // staging of msp_solve_host
   // the preconditioner as a CUDA graph on fixed input/output buffers
   cudaStream_t cap_stream = nullptr;
@@ -1126,6 +1131,9 @@ int stage_N(msp_handle h, const PView<T>& P, const T* g, T* w, cudaStream_t s) {
 
 // algorithmic bytes of a BSR row sweep over all block rows (values, columns, row
 // pointers, the input vector once, `vecs` further vectors of nb*b values)
+// FMAs of a BSR product over all blocks
+inline double bsr_fmas(msp_handle h) { return (double)h->nnzb * h->b * h->b; }
+
 inline double bsr_bytes(msp_handle h, double sT, double vecs) {
   const double b = h->b;
   return (double)h->nnzb * (b * b * sT + 4) + (double)(h->nb + 1) * 4 +
@@ -1306,6 +1314,7 @@ int apply_precond(msp_handle h, const double* g, double* w, cudaStream_t s) {
     for (const auto& gp : h->graph_probes) {
       g_sites[gp.site].launches += gp.launches;
       g_sites[gp.site].bytes += gp.bytes;
+      g_sites[gp.site].flops += gp.flops;
       g_pending.push_back(PendingTiming{gp.site, gp.e0, gp.e1, true});
     }
   }
@@ -1337,7 +1346,11 @@ int alloc_work(msp_handle h) {
   MSP_TRY(h->bperm.alloc(n));
   MSP_TRY(h->xperm.alloc(n));
   MSP_TRY(h->rvec.alloc(n));
-  MSP_TRY(h->partial.alloc((size_t)krylov_blocks() * 72));
+  MSP_TRY(h->partial.alloc((size_t)krylov_blocks() * 2 * kKrylovMaxK));
+  MSP_TRY(h->gs_T.alloc((size_t)(m + 2) * (m + 2)));
+  MSP_TRY(h->gs_d.alloc(2 * kKrylovMaxK));
+  MSP_TRY(h->gs_g.alloc(kKrylovMaxK));
+  MSP_TRY(h->gs_out.alloc(160));
   MSP_TRY(h->hdev.alloc(72));
   MSP_TRY(h->nrm.alloc(72));
   MSP_TRY(h->ydev.alloc(72));
@@ -1404,85 +1417,152 @@ int fgmres(msp_handle h, double tol, int* iters, double* relres, double* relres_
     if (it >= h->cfg.max_it) break;
     MSP_TRY(launch_scale(n, h->rvec.p, 1.0 / beta, V, s));
     std::fill(sv.begin(), sv.end(), 0.0);
-    sv[0] = beta;
     int j_used = 0;
     bool breakdown = false;
+    // One-pass classical Gram-Schmidt with the reorthogonalisation carried by a triangular
+    // factor (reading D17).  The stored basis u_0..u_j is orthogonalised once; the
+    // orthonormal Arnoldi basis is Q = U T^-1, T upper triangular, whose column k (c_k above
+    // the diagonal, nu_k on it) is the projection of u_k on the earlier q's and the norm of
+    // the rest: the second pass of CGS2, applied to coefficients instead of vectors.  Step
+    // j reads the basis twice: one pass of dot products against u_j and against the new
+    // vector w = A z_j (which gives column j of T and h = Q^T w), one update w <- w - U g
+    // with g = T^-1 h.  Then A z_j = Q h + |w'| u_{j+1}, so column j of the Hessenberg
+    // matrix is final once column j + 1 of T is known: h + |w'| c_{j+1} above the
+    // diagonal, |w'| nu_{j+1} below it.  It is made final at the next step, or at once
+    // (one more pass of dot products, no preconditioner) when the provisional estimate
+    // (c_{j+1} = 0, nu_{j+1} = 1) says the tolerance is met, at MaxIt and at the end of
+    // the cycle.  Convergence is decided on final columns only.
+    std::vector<double> Hraw((size_t)(m + 1) * m, 0.0), hprov(m + 1), col(m + 1);
+    const int ldt = m + 2;
+    double* T = h->gs_T.p;
+    double* out = h->gs_out.p;
+    double* hp = h->h_pin;  // host copy of out[0..147]
+    double hn_prev = 0.0;   // |w'| of the pending column
+    int committed = 0;      // columns 0..committed-1 are final and rotated
+    // rotate final column k (Hraw) into H and update the least-squares right-hand side
+    auto commit = [&](int k) {
+      for (int i = 0; i <= k + 1; ++i) H[(size_t)i * m + k] = Hraw[(size_t)i * m + k];
+      for (int i = 0; i < k; ++i) {
+        const double a = H[(size_t)i * m + k], c = H[(size_t)(i + 1) * m + k];
+        H[(size_t)i * m + k] = cs[i] * a + sn[i] * c;
+        H[(size_t)(i + 1) * m + k] = -sn[i] * a + cs[i] * c;
+      }
+      const double a = H[(size_t)k * m + k], c = H[(size_t)(k + 1) * m + k];
+      const double rho = std::sqrt(a * a + c * c);
+      if (rho == 0.0) {
+        cs[k] = 1.0;
+        sn[k] = 0.0;
+      } else {
+        cs[k] = a / rho;
+        sn[k] = c / rho;
+      }
+      H[(size_t)k * m + k] = rho;
+      H[(size_t)(k + 1) * m + k] = 0.0;
+      sv[k + 1] = -sn[k] * sv[k];
+      sv[k] = cs[k] * sv[k];
+      committed = k + 1;
+    };
+    // residual estimate of column k taken with c_{k+1} = 0, nu_{k+1} = 1 (rotations 0..k-1
+    // are final), without changing the committed state
+    auto provisional_estimate = [&](int k, double hn) {
+      for (int i = 0; i <= k; ++i) col[i] = hprov[i];
+      col[k + 1] = hn;
+      for (int i = 0; i < k; ++i) {
+        const double a = col[i], c = col[i + 1];
+        col[i] = cs[i] * a + sn[i] * c;
+        col[i + 1] = -sn[i] * a + cs[i] * c;
+      }
+      const double a = col[k], c = col[k + 1];
+      const double rho = std::sqrt(a * a + c * c);
+      const double snk = rho == 0.0 ? 0.0 : c / rho;
+      return std::fabs(snk * sv[k]) / bnorm;
+    };
+    auto fetch_out = [&]() -> int {
+      MSP_CUDA_TRY(cudaMemcpyAsync(hp, out, 148 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      MSP_CUDA_TRY(cudaMemcpyAsync(hp + 150, h->nrm.p + 1, sizeof(double),
+                                   cudaMemcpyDeviceToHost, s));
+      MSP_CUDA_TRY(cudaStreamSynchronize(s));
+      return MSP_OK;
+    };
     for (int j = 0; j < m; ++j) {
       double* vj = V + (size_t)j * n;
       double* zj = Z + (size_t)j * n;
       double* w = V + (size_t)(j + 1) * n;
       MSP_TRY(apply_precond(h, vj, zj, s));
       {
-        Probe pr("krylov_spmv", bsr_bytes(h, 8.0, 1), s);
+        Probe pr("krylov_spmv", bsr_bytes(h, 8.0, 1), s, 1, 2.0 * bsr_fmas(h));
         MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, zj, nullptr, w,
                                         false, s));
       }
       ++it;
-      // classical Gram-Schmidt with a conditional second pass (DGKS: repeat the pass
-      // iff it shrank w below 1/sqrt(2) of its norm; the test runs on the device).
-      // w is stored right after V_j, so one multi-dot over K+1 vectors gives the
-      // projections h and ||w||^2.
-      const int K = j + 1;
+      const int K = j + 2;  // u_0 .. u_j and w
       {
-        Probe pr("krylov_multi_dot", (double)(K + 1) * n * 8.0, s);
-        MSP_TRY(launch_multi_dot(n, V, n, K + 1, w, h->partial.p, nbk, s));
+        Probe pr("krylov_multi_dot", (double)K * n * 8.0, s, 1, 4.0 * K * n);
+        MSP_TRY(launch_multi_dot2(n, V, n, K, vj, w, h->partial.p, nbk, s));
       }
-      MSP_TRY(launch_reduce_partials(K + 1, nbk, h->partial.p, h->hdev.p, false, s));
+      MSP_TRY(launch_reduce_partials_strided(2 * K, nbk, 2 * kKrylovMaxK, h->partial.p,
+                                             h->gs_d.p, s));
+      MSP_TRY(launch_dcgs_coef(j, h->gs_d.p, T, ldt, h->gs_g.p, out, s));
       {
-        Probe pr("krylov_multi_axpy", (double)(K + 2) * n * 8.0, s);
-        MSP_TRY(launch_multi_axpy_norm(n, V, n, K, h->hdev.p, w, h->partial.p, nbk, s));
+        Probe pr("krylov_multi_axpy", (double)(K + 1) * n * 8.0, s, 1, 2.0 * K * n);
+        MSP_TRY(launch_multi_axpy_norm(n, V, n, j + 1, h->gs_g.p, w, h->partial.p, nbk, s));
       }
       MSP_TRY(launch_reduce_partials(1, nbk, h->partial.p, h->nrm.p, false, s));
-      int* gate = h->ifl.p + 1;
-      MSP_TRY(launch_reorth_gate(h->nrm.p, h->hdev.p + K, gate, s));
-      {
-        Probe pr("krylov_reorth_dot", 0.0, s);
-        MSP_TRY(launch_multi_dot(n, V, n, K, w, h->partial.p, nbk, s, gate));
-      }
-      MSP_TRY(launch_reduce_partials(K, nbk, h->partial.p, h->ydev.p, false, s, gate));
-      {
-        Probe pr("krylov_reorth_axpy", 0.0, s);
-        MSP_TRY(launch_multi_axpy_norm(n, V, n, K, h->ydev.p, w, h->partial.p, nbk, s, gate));
-      }
-      MSP_TRY(launch_reduce_partials(K, 1, h->ydev.p, h->hdev.p, true, s, gate));  // h += h2
-      MSP_TRY(launch_reduce_partials(1, nbk, h->partial.p, h->nrm.p, false, s, gate));
       MSP_TRY(launch_normalize(n, w, h->nrm.p, w, h->nrm.p + 1, s));
-      MSP_CUDA_TRY(cudaMemcpyAsync(h->h_pin, h->hdev.p, K * sizeof(double), cudaMemcpyDeviceToHost, s));
-      MSP_CUDA_TRY(cudaMemcpyAsync(h->h_pin + 64, h->nrm.p + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
-      MSP_CUDA_TRY(cudaMemcpyAsync(h->h_pin + 65, gate, sizeof(int), cudaMemcpyDeviceToHost, s));
-      MSP_CUDA_TRY(cudaStreamSynchronize(s));
-      int reorth = 0;
-      std::memcpy(&reorth, h->h_pin + 65, sizeof(int));
-      if (reorth) {  // the second pass ran: credit its bytes to its timed sites
-        stats_add_bytes("krylov_reorth_dot", (double)(K + 1) * n * 8.0);
-        stats_add_bytes("krylov_reorth_axpy", (double)(K + 2) * n * 8.0);
+      MSP_TRY(fetch_out());
+      const double hn = hp[150];
+      if (!std::isfinite(hn) || !std::isfinite(hp[145])) return MSP_ERR_NONFINITE;
+      if (hp[147] != 0.0) {
+        // u_j lies in the span of the earlier vectors: the Krylov space is invariant, and
+        // the pending column j - 1 ends the cycle with a zero subdiagonal
+        if (j == 0) return MSP_ERR_NONFINITE;  // u_0 = r / |r| cannot be degenerate
+        for (int i = 0; i < j; ++i) Hraw[(size_t)i * m + (j - 1)] += hn_prev * hp[72 + i];
+        Hraw[(size_t)j * m + (j - 1)] = 0.0;
+        commit(j - 1);
+        j_used = j;
+        breakdown = true;
+        est = std::fabs(sv[j]) / bnorm;
+        break;
       }
-      for (int i = 0; i < K; ++i) H[(size_t)i * m + j] = h->h_pin[i];
-      const double hn = h->h_pin[64];
-      H[(size_t)(j + 1) * m + j] = hn;
-      for (int i = 0; i < j; ++i) {
-        const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
-        H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
-        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+      if (j == 0) {
+        sv[0] = beta * hp[144];  // r = beta u_0 = beta nu_0 q_0
+      } else if (committed < j) {  // column j - 1 becomes final
+        for (int i = 0; i < j; ++i) Hraw[(size_t)i * m + (j - 1)] += hn_prev * hp[72 + i];
+        Hraw[(size_t)j * m + (j - 1)] = hn_prev * hp[144];
+        commit(j - 1);
       }
-      const double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
-      const double rho = std::sqrt(a * a + c * c);
-      if (rho == 0.0) {
-        cs[j] = 1.0;
-        sn[j] = 0.0;
-      } else {
-        cs[j] = a / rho;
-        sn[j] = c / rho;
-      }
-      H[(size_t)j * m + j] = rho;
-      H[(size_t)(j + 1) * m + j] = 0.0;
-      sv[j + 1] = -sn[j] * sv[j];
-      sv[j] = cs[j] * sv[j];
+      for (int i = 0; i <= j; ++i) hprov[i] = hp[i];
+      for (int i = 0; i <= j; ++i) Hraw[(size_t)i * m + j] = hp[i];
+      hn_prev = hn;
       j_used = j + 1;
-      est = std::fabs(sv[j + 1]) / bnorm;
+      if (hn == 0.0) {  // exact breakdown: w lies in the span of the basis
+        Hraw[(size_t)(j + 1) * m + j] = 0.0;
+        commit(j);
+        est = std::fabs(sv[j + 1]) / bnorm;
+        breakdown = true;
+        break;
+      }
+      const bool last = (j == m - 1) || it >= h->cfg.max_it;
+      est = provisional_estimate(j, hn);
       if (!std::isfinite(est)) return MSP_ERR_NONFINITE;
-      if (hn == 0.0) breakdown = true;
-      if (est <= tol || it >= h->cfg.max_it || breakdown) break;
+      if (last || est <= tol * (1.0 + 1e-6)) {
+        // column j final now: column j + 1 of T from the dot products of u_{j+1}
+        {
+          Probe pr("krylov_finalize_dot", (double)(j + 2) * n * 8.0, s, 1, 2.0 * (j + 2) * n);
+          MSP_TRY(launch_multi_dot(n, V, n, j + 2, w, h->partial.p, nbk, s));
+        }
+        MSP_TRY(launch_reduce_partials(j + 2, nbk, h->partial.p, h->gs_d.p, false, s));
+        MSP_TRY(launch_dcgs_finalize(j + 1, h->gs_d.p, T, ldt, out, s));
+        MSP_TRY(fetch_out());
+        if (!std::isfinite(hp[145])) return MSP_ERR_NONFINITE;
+        for (int i = 0; i <= j; ++i) Hraw[(size_t)i * m + j] += hn * hp[72 + i];
+        Hraw[(size_t)(j + 1) * m + j] = hn * hp[144];  // 0 if u_{j+1} is degenerate
+        commit(j);
+        est = std::fabs(sv[j + 1]) / bnorm;
+        if (!std::isfinite(est)) return MSP_ERR_NONFINITE;
+        if (hp[147] != 0.0) breakdown = true;
+        if (est <= tol || last || breakdown) break;
+      }
     }
     for (int i = j_used - 1; i >= 0; --i) {
       double t = sv[i];
@@ -1850,7 +1930,7 @@ int msp_config_default(msp_config* c) {
   c->npass = 2;
   c->pre_sweeps = 1;
   c->post_sweeps = 1;
-  c->bgs_sweeps = 1;
+  c->bgs_sweeps = 6;
   c->decoupling = 1;
   c->bilu_order = 0;
   c->precond = MSP_PREC_MSP;
@@ -1905,7 +1985,7 @@ int msp_setup(msp_handle* out, const msp_config* cfg, int32_t nb, int32_t b,
     h->ss = sort_scratch_create();
     int st = h->flags.alloc(1);
     if (st == MSP_OK && cudaMallocHost(&h->h_flags, sizeof(DevFlags)) != cudaSuccess) st = MSP_ERR_NOMEM;
-    if (st == MSP_OK && cudaMallocHost(&h->h_pin, 128 * sizeof(double)) != cudaSuccess) st = MSP_ERR_NOMEM;
+    if (st == MSP_OK && cudaMallocHost(&h->h_pin, 256 * sizeof(double)) != cudaSuccess) st = MSP_ERR_NOMEM;
     if (st == MSP_OK) {
       auto t0 = Clock::now();
       st = pattern_setup(h, d_row_ptr, d_col_idx, s);
@@ -2125,7 +2205,7 @@ int msp_stats_count(void) {
 }
 
 int msp_stats_get(int index, char* name, int name_len, long long* launches, double* total_ms,
-                  double* bytes) {
+                  double* bytes, double* flops) {
   std::lock_guard<std::mutex> lk(g_stats_mu);
   resolve_pending();
   if (index < 0 || index >= (int)g_sites.size()) return MSP_ERR_ARG;
@@ -2137,6 +2217,7 @@ int msp_stats_get(int index, char* name, int name_len, long long* launches, doub
   if (launches) *launches = st.launches;
   if (total_ms) *total_ms = st.ms;
   if (bytes) *bytes = st.bytes;
+  if (flops) *flops = st.flops;
   return MSP_OK;
 }
 

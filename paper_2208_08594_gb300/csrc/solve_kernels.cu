@@ -764,6 +764,140 @@ __global__ void __launch_bounds__(kThreads) multi_dot_kernel(size_t n, const dou
   }
 }
 
+// Two right-hand vectors at once: partial[b][k] = V_k . x0 and partial[b][K + k] = V_k . x1
+// for k < K (block b's share; row stride 2 * kMaxK).  The one-pass Gram-Schmidt of FGMRES
+// needs the basis against the newest basis vector and against the new Krylov vector: one
+// read of the basis serves both (two FMAs per element of V read).
+__global__ void __launch_bounds__(kThreads) multi_dot2_kernel(size_t n, const double* __restrict__ V,
+                                                             size_t ldv, int K,
+                                                             const double* __restrict__ x0,
+                                                             const double* __restrict__ x1,
+                                                             double* __restrict__ partial) {
+  static_assert(kDotChunk == 8 && kThreads == 256, "the reduction below is for 8 x 8 warps");
+  __shared__ double sh[2][kThreads / kWarp][kDotChunk];
+  const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp;
+  const int slot = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+  for (int k0 = 0; k0 < K; k0 += kDotChunk) {
+    const int kc = min(kDotChunk, K - k0);
+    double a0[kDotChunk], a1[kDotChunk];
+#pragma unroll
+    for (int k = 0; k < kDotChunk; ++k) a0[k] = a1[k] = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+      const double u = x0[i], w = x1[i];
+#pragma unroll
+      for (int k = 0; k < kDotChunk; ++k)
+        if (k < kc) {
+          const double vk = __ldg(V + (size_t)(k0 + k) * ldv + i);
+          a0[k] = fma(vk, u, a0[k]);
+          a1[k] = fma(vk, w, a1[k]);
+        }
+    }
+    const double r0 = transpose_sum8(a0, lane);
+    const double r1 = transpose_sum8(a1, lane);
+    __syncthreads();  // the previous chunk's reads of sh are done
+    if ((lane & 3) == 0) {
+      sh[0][wid][slot] = r0;
+      sh[1][wid][slot] = r1;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * kc) {  // fixed order over the warps
+      const int r = threadIdx.x / kc, k = threadIdx.x % kc;
+      double t = 0.0;
+#pragma unroll
+      for (int w2 = 0; w2 < kThreads / kWarp; ++w2) t += sh[r][w2][k];
+      partial[(size_t)blockIdx.x * (2 * kMaxK) + r * K + k0 + k] = t;
+    }
+  }
+}
+
+// out[k] = sum over blocks of partial[b * stride + k], k < K (one warp per output)
+__global__ void reduce_partials_strided_kernel(int K, int nblocks, int stride,
+                                               const double* __restrict__ partial,
+                                               double* __restrict__ out) {
+  const int k = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
+  const int lane = threadIdx.x % kWarp;
+  if (k >= K) return;
+  double s = 0.0;
+  for (int b = lane; b < nblocks; b += kWarp) s += partial[(size_t)b * stride + k];
+  s = group_sum<kWarp>(s);
+  if (lane == 0) out[k] = s;
+}
+
+// One-pass Gram-Schmidt of FGMRES step j (one thread: j <= 64, a few microseconds).  The
+// stored basis U = [u_0 .. u_j] is orthogonalised once; the orthonormal basis it stands for
+// is Q = U T^-1 with T upper triangular (column k of T holds c_k = Q_k^T u_k above the
+// diagonal and nu_k = ||u_k - Q_k c_k|| on it), so Q is never formed.  Inputs: d[k] = u_k .
+// u_j and d[K + k] = u_k . w for k < K = j + 2 (u_{j+1} stands for w).  Computes
+//   c_j = T_j^-T d[0..j-1], nu_j^2 = d[j] - |c_j|^2           (column j of T)
+//   h = T_{j+1}^-T d[K .. K+j]                                (h = Q^T w, Arnoldi column)
+//   g = T_{j+1}^-1 h                                          (w - Q h = w - U g)
+// out[0..j] = h, out[72 + k] = c_j[k], out[144] = nu_j, out[145] = nu_j^2, out[146] = w.w,
+// out[147] = 1 if nu_j^2 <= 0 (u_j lies in span Q: the previous step broke down).
+__global__ void dcgs_coef_kernel(int j, const double* __restrict__ d, double* __restrict__ T,
+                                 int ldt, double* __restrict__ g, double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  const int K = j + 2;
+  double c2 = 0.0;
+  for (int k = 0; k < j; ++k) {  // forward substitution with T_j^T
+    double t = d[k];
+    for (int i = 0; i < k; ++i) t -= T[(size_t)k * ldt + i] * out[72 + i];
+    const double ck = t / T[(size_t)k * ldt + k];
+    out[72 + k] = ck;
+    c2 += ck * ck;
+  }
+  const double nu2 = d[j] - c2;
+  out[145] = nu2;
+  out[146] = d[K + j + 1];
+  if (!(nu2 > 0.0)) {
+    out[144] = 0.0;
+    out[147] = 1.0;
+    for (int k = 0; k <= j; ++k) g[k] = 0.0;
+    return;
+  }
+  const double nu = sqrt(nu2);
+  out[144] = nu;
+  out[147] = 0.0;
+  for (int k = 0; k < j; ++k) T[(size_t)j * ldt + k] = out[72 + k];  // column j, stored by column
+  T[(size_t)j * ldt + j] = nu;
+  for (int k = 0; k <= j; ++k) {  // h = T^-T (U^T w)
+    double t = d[K + k];
+    for (int i = 0; i < k; ++i) t -= T[(size_t)k * ldt + i] * out[i];
+    out[k] = t / T[(size_t)k * ldt + k];
+  }
+  for (int k = j; k >= 0; --k) {  // g = T^-1 h
+    double t = out[k];
+    for (int i = k + 1; i <= j; ++i) t -= T[(size_t)i * ldt + k] * g[i];
+    g[k] = t / T[(size_t)k * ldt + k];
+  }
+}
+
+// Column j + 1 of T from d[k] = u_k . u_{j+1}, k <= j + 1 (the last vector's own
+// correction, computed when the Arnoldi column of step j must be final: at convergence, at
+// MaxIt and at the end of a restart cycle).  out[72 + k] = c_{j+1}[k], out[144] = nu_{j+1},
+// out[145] = nu_{j+1}^2, out[147] = 1 if nu_{j+1}^2 <= 0.
+__global__ void dcgs_finalize_kernel(int j1, const double* __restrict__ d, double* __restrict__ T,
+                                     int ldt, double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double c2 = 0.0;
+  for (int k = 0; k < j1; ++k) {
+    double t = d[k];
+    for (int i = 0; i < k; ++i) t -= T[(size_t)k * ldt + i] * out[72 + i];
+    const double ck = t / T[(size_t)k * ldt + k];
+    out[72 + k] = ck;
+    c2 += ck * ck;
+  }
+  const double nu2 = d[j1] - c2;
+  out[145] = nu2;
+  const bool ok = nu2 > 0.0;
+  out[144] = ok ? sqrt(nu2) : 0.0;
+  out[147] = ok ? 0.0 : 1.0;
+  if (ok) {
+    for (int k = 0; k < j1; ++k) T[(size_t)j1 * ldt + k] = out[72 + k];
+    T[(size_t)j1 * ldt + j1] = out[144];
+  }
+}
+
 // one warp per output k: lanes sum strided partials, then a fixed-order shuffle tree
 __global__ void reduce_partials_kernel(int K, int nblocks, const double* __restrict__ partial,
                                        double* __restrict__ out, bool accumulate,
@@ -823,10 +957,6 @@ __global__ void normalize_kernel(size_t n, const double* w, const double* __rest
 }
 
 // DGKS test after one Gram-Schmidt pass: gate = 1 iff ||w_after||^2 < ||w_before||^2 / 2
-__global__ void reorth_gate_kernel(const double* __restrict__ nrm_after,
-                                   const double* __restrict__ nrm_before, int* gate) {
-  gate[0] = nrm_after[0] < 0.5 * nrm_before[0] ? 1 : 0;
-}
 
 __global__ void update_x_kernel(size_t n, const double* __restrict__ Z, size_t ldz, int K,
                                 const double* __restrict__ y, double* __restrict__ x) {
@@ -1314,6 +1444,37 @@ int launch_multi_dot(size_t n, const double* V, size_t ldv, int K, const double*
   return launch_status();
 }
 
+int launch_multi_dot2(size_t n, const double* V, size_t ldv, int K, const double* x0,
+                      const double* x1, double* partial, int nblocks, cudaStream_t s) {
+  if (K > kMaxK) return MSP_ERR_ARG;
+  multi_dot2_kernel<<<nblocks, kThreads, 0, s>>>(n, V, ldv, K, x0, x1, partial);
+  return launch_status();
+}
+
+int launch_reduce_partials_strided(int K, int nblocks, int stride, const double* partial,
+                                   double* out, cudaStream_t s) {
+  if (K <= 0) return MSP_OK;
+  if (K > stride) return MSP_ERR_ARG;
+  const int wpb = 4;
+  reduce_partials_strided_kernel<<<(K + wpb - 1) / wpb, wpb * kWarp, 0, s>>>(K, nblocks, stride,
+                                                                             partial, out);
+  return launch_status();
+}
+
+int launch_dcgs_coef(int j, const double* d, double* T, int ldt, double* g, double* out,
+                     cudaStream_t s) {
+  if (j < 0 || j + 2 > kMaxK || j + 1 > ldt) return MSP_ERR_ARG;
+  dcgs_coef_kernel<<<1, kWarp, 0, s>>>(j, d, T, ldt, g, out);
+  return launch_status();
+}
+
+int launch_dcgs_finalize(int j1, const double* d, double* T, int ldt, double* out,
+                         cudaStream_t s) {
+  if (j1 < 1 || j1 + 1 > kMaxK || j1 + 1 > ldt) return MSP_ERR_ARG;
+  dcgs_finalize_kernel<<<1, kWarp, 0, s>>>(j1, d, T, ldt, out);
+  return launch_status();
+}
+
 int launch_reduce_partials(int K, int nblocks, const double* partial, double* out,
                            bool accumulate, cudaStream_t s, const int* gate) {
   if (K > kMaxK) return MSP_ERR_ARG;
@@ -1341,12 +1502,6 @@ int launch_norm2_partial(size_t n, const double* x, double* partial, int nblocks
 int launch_normalize(size_t n, const double* w, const double* nrm2, double* v, double* hn,
                      cudaStream_t s) {
   normalize_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, w, nrm2, v, hn);
-  return launch_status();
-}
-
-int launch_reorth_gate(const double* nrm_after, const double* nrm_before, int* gate,
-                       cudaStream_t s) {
-  reorth_gate_kernel<<<1, 1, 0, s>>>(nrm_after, nrm_before, gate);
   return launch_status();
 }
 

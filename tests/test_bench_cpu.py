@@ -1,6 +1,6 @@
 """Host-side checks of the benchmark's bookkeeping: every timing site the library records
 maps to a kernel the library defines (so the per-kernel table and the roofline see every
-launch), the grouping of sites into kernels, and the FP64 ceiling arithmetic."""
+launch), the grouping of sites into kernels, and the configuration both arms report."""
 import glob
 import os
 import re
@@ -44,15 +44,34 @@ def test_every_timed_site_maps_to_a_defined_kernel():
 
 
 def test_kernels_from_sites_groups_by_kernel():
-    sites = {"krylov_multi_dot": (139, 20.0, 1e9), "krylov_reorth_dot": (139, 22.0, 1e9),
-             "amg_gs_pre_l1": (417, 2.0, 1e8), "amg_gs_post_l3": (1390, 5.0, 2e8),
-             "precond_graph": (139, 200.0, 5e9), "setup:galerkin": (1, 30.0, 0.0)}
+    sites = {"krylov_multi_dot": (139, 20.0, 1e9, 4e9), "krylov_finalize_dot": (5, 1.0, 1e8, 2e8),
+             "amg_gs_pre_l1": (417, 2.0, 1e8, 0.0), "amg_gs_post_l3": (1390, 5.0, 2e8, 0.0),
+             "precond_graph": (139, 200.0, 5e9, 0.0), "setup:galerkin": (1, 30.0, 0.0, 0.0)}
     out = bench.kernels_from_sites(sites)
-    assert out["multi_dot_kernel"] == [278, 42.0, 2e9]
-    assert out["ell_gs_colour_kernel"] == [1807, 7.0, 3e8]
-    assert "precond_graph" not in out and len(out) == 2
+    assert out["multi_dot2_kernel"] == [139, 20.0, 1e9, 4e9]
+    assert out["multi_dot_kernel"] == [5, 1.0, 1e8, 2e8]
+    assert out["ell_gs_colour_kernel"] == [1807, 7.0, 3e8, 0.0]
+    assert "precond_graph" not in out and len(out) == 3
 
 
-def test_fp64_fma_ceiling():
-    # one FMA per 8-byte value at 1.19 TFLOP/s (two flops per FMA)
-    assert abs(bench.FP64_FMA_CEILING_GBPS - 4760.0) < 1e-6
+def test_roofline_picks_the_binding_roof():
+    # 1 GB and 0.25 TFLOP in 1 ms: 1 TB/s of 6.7 TB/s HBM, but 250 TFLOP/s-equivalent work
+    # at the FP64 rate: the ALU binds (its time at peak is the longer)
+    r = bench.roofline_of("k", [10, 10.0, 1e10, 2.5e12 * 1e-3 * 10], 6763.3, "measured", 152,
+                          2070.0, 1.25e12, 100.0, 1)
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert abs(r["peak"] - 152 * 2 * 2 * 2070e6 / 1e12) < 1e-3
+    r = bench.roofline_of("k", [10, 10.0, 1e10, 0.0], 6763.3, "measured", 152, 2070.0, 1.25e12,
+                          100.0, 1)
+    assert r["bound"] == "hbm" and r["achieved"] == 1000.0
+
+
+def test_static_config_is_shared_by_both_arms():
+    import argparse
+    from synthetic import grid_spe10
+    args = argparse.Namespace(nx=6, ny=5, nz=4, mu=180, precision="fp64", colouring="alg41",
+                              smoother="pgs_mc", wells="rows")
+    a = grid_spe10(nx=6, ny=5, nz=4)
+    c = bench.static_config(args, a)
+    assert c["cells"] == 120 and c["block_rows"] == 124 and c["nnzb"] == a.nnzb
+    assert "R_ij + 3 I" in c["workload"] and "rebalanced" in c["workload"]

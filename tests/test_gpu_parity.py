@@ -319,10 +319,11 @@ def test_fp32_preconditioner_converges_to_fp64_accuracy():
     xg = x.cpu().numpy()
     assert info["status"] == 0
     assert np.linalg.norm(rhs - A @ xg) / np.linalg.norm(rhs) <= 1e-6 * 1.001
-    assert abs(info["iterations"] - io["iterations"]) <= max(2, io["iterations"] // 10)
-    # both iterates meet the same residual tolerance, so they agree to the
-    # conditioning of A times that tolerance; the measured gap is far smaller
-    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-3
+    err = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
+    print("\nFP32 preconditioner, 23x17x9: GPU it=%d, oracle it=%d, |x-x_o|/|x_o| = %.3e"
+          % (info["iterations"], io["iterations"], err))
+    assert abs(info["iterations"] - io["iterations"]) <= 1
+    assert err <= 1e-9, err
     g.close()
 
 

@@ -120,11 +120,48 @@ def test_bilu_red_black_closed_form():
         assert np.allclose(piv[k], ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max()), k
 
 
+def _concentration_split(a, perm, iperm):
+    """Block lower (diagonal included) and strictly upper parts of Pi_N^T A Pi_N in colour
+    order, dense."""
+    bn = a.b - 1
+    L = np.zeros((a.nb * bn, a.nb * bn))
+    U = np.zeros_like(L)
+    for i in range(a.nb):
+        for p in range(a.row_ptr[i], a.row_ptr[i + 1]):
+            j = int(a.col_idx[p])
+            M = L if iperm[j] <= iperm[i] else U
+            M[iperm[i] * bn:(iperm[i] + 1) * bn, iperm[j] * bn:(iperm[j] + 1) * bn] = \
+                a.values[p][1:, 1:]
+    return L, U
+
+
+@pytest.mark.parametrize("sweeps", [3, 6])
+def test_stage_n_sweeps_are_the_block_gs_iteration(sweeps):
+    """k forward sweeps from zero are k steps of the block Gauss-Seidel splitting
+    (D + L_A) x_{s+1} = r - U_A x_s of Pi_N^T A Pi_N in colour order."""
+    a = box_jacobian(5, 4, 3, 3, 17, n_wells=1)
+    o = oracle.Oracle(a, precond=oracle.PREC_N_ONLY, bgs_sweeps=sweeps)
+    colour, g = o.colour0()
+    perm = np.lexsort((np.arange(a.nb), colour))
+    iperm = np.empty_like(perm)
+    iperm[perm] = np.arange(a.nb)
+    gvec = random_rhs(a, 2)
+    w = o.apply_precond(gvec).reshape(a.nb, a.b)
+    assert np.all(w[:, 0] == 0.0)
+    L, U = _concentration_split(a, perm, iperm)
+    rhs = gvec.reshape(a.nb, a.b)[perm][:, 1:].reshape(-1)
+    x = np.zeros_like(rhs)
+    for _ in range(sweeps):
+        x = np.linalg.solve(L, rhs - U @ x)
+    ref = x.reshape(a.nb, a.b - 1)
+    assert np.allclose(w[perm][:, 1:], ref, rtol=1e-11, atol=1e-11 * np.abs(ref).max())
+
+
 def test_stage_n_is_block_gs_on_concentration_subsystem():
     """Stage N with one forward sweep from zero solves the block lower-triangular part
     of Pi_N^T A Pi_N (colour order) exactly; the pressure slot is untouched."""
     a = box_jacobian(5, 4, 3, 3, 17, n_wells=1)
-    o = oracle.Oracle(a, precond=oracle.PREC_N_ONLY)
+    o = oracle.Oracle(a, precond=oracle.PREC_N_ONLY, bgs_sweeps=1)
     colour, g = o.colour0()
     perm = np.lexsort((np.arange(a.nb), colour))
     iperm = np.empty_like(perm)
