@@ -437,6 +437,17 @@ def run_native(args):
             mu0_step(args.warmup + k)
         torch.cuda.synchronize()
         mu0_s = time.perf_counter() - t0
+        # one more plain-MSP solve with every setup phase timed by CUDA events (not part of
+        # the timed solves above): where a SETUP's time goes
+        msp.msp_stats_reset()
+        msp.msp_stats_enable(2)
+        mu0_step(args.warmup + args.mu0_steps)
+        mu0_infos.pop()
+        msp.msp_stats_enable(0)
+        setup_sites = {k: round(v[1], 2) for k, v in sorted(msp.msp_stats_get().items(),
+                                                            key=lambda kv: -kv[1][1])
+                       if k.startswith("setup:")}
+        msp.msp_stats_reset()
         mu0_solver.close()
         t_set = sum(i["t_setup_ms"] for i in mu0_infos) / 1000.0
         mu0 = {"mu": 0, "solves": len(mu0_infos),
@@ -446,6 +457,7 @@ def run_native(args):
                "setup_ratio": round(t_set / mu0_s, 4),
                "setup_ms_mean": round(1000.0 * t_set / len(mu0_infos), 1),
                "iterations": [i["iterations"] for i in mu0_infos],
+               "setup_phases_ms": setup_sites,
                "timed": "host wall clock around update_values + solve (SETUP inside the "
                         "solve, timed by the library as SetupRatio's numerator)"}
 

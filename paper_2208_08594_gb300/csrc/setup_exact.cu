@@ -378,6 +378,14 @@ __device__ __forceinline__ bool in_v(const unsigned* inV, int v) {
 
 constexpr int kSecondU = 8;  // second-circle entries gathered per lane per round
 
+// Fetch the row pointers and two-hop pointers of vertex x into L1 without waiting: the
+// next picks come from the second circles just added to the frontier, so their first
+// trip to memory is then an L1 hit.
+__device__ __forceinline__ void prefetch_rows(const int* srp, const int* tp, int x) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(__cvta_generic_to_global(srp + x)));
+  if (tp) asm volatile("prefetch.global.L1 [%0];" ::"l"(__cvta_generic_to_global(tp + x)));
+}
+
 // Warp 1 of the colouring CTA: while warp 0 processes its pick, load the two-hop
 // neighbourhood of the frontier's current first vertex (the likely next pick) so warp
 // 0 finds it in L1.  It only reads; the bitmap it reads is being changed by warp 0, so
@@ -423,6 +431,8 @@ __device__ void colouring_prefetcher(int n, const int* __restrict__ srp, const i
     if (tp) {
       const int e1 = __ldg(tp + c + 1);
       for (int e = __ldg(tp + c) + 8 * lane; e < e1; e += 256) acc += __ldg(tl + e);
+      const int r1 = __ldg(srp + c + 1);
+      for (int q = __ldg(srp + c) + 8 * lane; q < r1; q += 256) acc += __ldg(sci + q);
       continue;
     }
     const int q0 = __ldg(srp + c), q1 = __ldg(srp + c + 1);
@@ -571,7 +581,10 @@ __global__ void __launch_bounds__(64) colouring_kernel(int n, const int* __restr
       if (tp) {
 #pragma unroll
         for (int u = 0; u < kSecondU; ++u)
-          if (xs0[u] >= 0 && in_v(inV, xs0[u])) bm_set(bm, xs0[u]);
+          if (xs0[u] >= 0 && in_v(inV, xs0[u])) {
+            bm_set(bm, xs0[u]);
+            prefetch_rows(srp, tp, xs0[u]);
+          }
         for (int t = t0 + 32 * kSecondU; t < t1; t += 32 * kSecondU) {
           int xs[kSecondU];
 #pragma unroll
@@ -581,7 +594,10 @@ __global__ void __launch_bounds__(64) colouring_kernel(int n, const int* __restr
           }
 #pragma unroll
           for (int u = 0; u < kSecondU; ++u)
-            if (xs[u] >= 0 && in_v(inV, xs[u])) bm_set(bm, xs[u]);
+            if (xs[u] >= 0 && in_v(inV, xs[u])) {
+              bm_set(bm, xs[u]);
+              prefetch_rows(srp, tp, xs[u]);
+            }
         }
         __syncwarp();
         continue;

@@ -111,7 +111,7 @@ def test_full_size_solve_matches_oracle_iterations(full):
     assert abs(info["iterations"] - io["iterations"]) <= 1, (info, io)
     # both stop at the first iteration whose residual estimate is <= 1e-6, and the two
     # iterates differ only by the rounding of the two orthogonalisations (measured
-    # 5.3e-16 at 143 iterations; the bound leaves 20x)
+    # 6.1e-16 at 64 iterations; the bound leaves 15x)
     assert err <= 1e-14, err
 
 
@@ -127,7 +127,7 @@ def test_full_size_fp32_preconditioner_against_fp64_oracle(full):
     g32.close()
     assert info["status"] == 0
     assert rel <= 1e-6 * 1.001
-    # measured: the same 143 iterations, error 1.55e-12 against the FP64 oracle
+    # measured: the same 64 iterations, error 3.4e-12 against the FP64 oracle
     assert abs(info["iterations"] - io["iterations"]) <= 1
     assert err <= 5e-11, err
 
@@ -165,7 +165,7 @@ def test_mid_size_solve_matches_oracle_iterations(mid):
     assert info["status"] == 0 and io["status"] == 0
     assert rel <= 1e-6 * 1.001
     assert abs(info["iterations"] - io["iterations"]) <= 1, (info, io)
-    assert err <= 1e-14, err  # measured 1.65e-15 at 176 iterations
+    assert err <= 1e-14, err  # measured 2.6e-15 at 71 iterations
 
 
 def test_mid_size_fp32_preconditioner_against_fp64_oracle(mid):
@@ -178,6 +178,6 @@ def test_mid_size_fp32_preconditioner_against_fp64_oracle(mid):
     g32.close()
     assert info["status"] == 0
     assert rel <= 1e-6 * 1.001
-    # measured: the same 176 iterations, error 5.9e-12 against the FP64 oracle
+    # measured: the same 71 iterations, error 1.0e-11 against the FP64 oracle
     assert abs(info["iterations"] - io["iterations"]) <= 1
     assert err <= 5e-11, err
