@@ -113,6 +113,8 @@ def parse():
     p.add_argument("--batch-instances", type=int, default=64)
     p.add_argument("--batch-cells", type=float, nargs=2, default=[2e4, 5e5])
     p.add_argument("--batch-steps", type=int, default=2)
+    p.add_argument("--batch-profile", action="store_true",
+                   help="time every call site of one more batched step (stats mode 3)")
     p.add_argument("--time-steps", type=int, default=6)
     p.add_argument("--newton-steps", type=int, default=3)
     p.add_argument("--rel-step", type=float, default=0.15)
@@ -979,6 +981,15 @@ def run_batch(args):
     ms_b = timed(batched, args.batch_steps)
     launches_b = msp.msp_stats_launches()
     msp.msp_stats_enable(0)
+    profile_b = None
+    if args.batch_profile:  # one more step with every call site timed: where the time goes
+        msp.msp_stats_reset()
+        msp.msp_stats_enable(3)
+        batched()
+        msp.msp_stats_enable(0)
+        profile_b = {k: {"launches": v[0], "ms": round(v[1], 2)}
+                     for k, v in sorted(msp.msp_stats_get().items(), key=lambda kv: -kv[1][1])[:25]}
+        msp.msp_stats_reset()
     stack_info = [dict({k: st[k] for k in ("b", "nb", "nnzb", "levels", "colours")},
                        instances=len(st["ks"])) for st in stacks]
     for st in stacks:
@@ -1043,6 +1054,8 @@ def run_batch(args):
                              "iterations_max": int(max(its_1.values())),
                              "not_converged": sorted(k for k, v in st_1.items() if v != 0)},
            "stacks": stack_info}
+    if profile_b:
+        out["batched_sites_one_step"] = profile_b
     print(json.dumps(out))
 
 

@@ -348,6 +348,41 @@ int msp_wells_recover(msp_wells W, const double* d_g, const double* d_xs, double
 /* Release W (NULL is accepted); waits for the device to finish its work. */
 int msp_wells_free(msp_wells W);
 
+/* Wells with one unknown each, as Eq. Jacobian-system has them: the bottom-hole pressure
+ * of well w and its one equation.  The cell part is an ordinary BSR matrix A_RR (nr block
+ * rows, b x b blocks, pattern as for msp_setup, nnzb = row_ptr[nr]); well w perforates the
+ * cells well_cells[k], k in [well_ptr[w], well_ptr[w+1]) (ascending, each cell at most
+ * once over all wells), with
+ *   arw[k*b + r]  = A_RW: cell equation r of that cell w.r.t. the well's pressure,
+ *   awr[k*b + c]  = A_WR: the well equation w.r.t. unknown c of that cell,
+ *   aww[w]        = A_WW: the well equation w.r.t. its own pressure.
+ * The library pads each well to a b x b block row (identity rows and columns 1..b-1, a
+ * zero right-hand side there), which decouples exactly, and eliminates it as
+ * msp_wells_setup does: the reduced matrix is the Schur complement of the scalar A_WW,
+ * A_S[c, c'] = A_RR[c, c'] - A_RW[c] A_WR[c'] / A_WW.  All arrays are device arrays; the
+ * caller keeps them.  The other msp_wells_* calls then take vectors in the padded layout
+ * of nb = nr + nw block rows (msp_wells_pack_rhs / msp_wells_unpack convert).  Errors as
+ * msp_wells_setup; MSP_ERR_ARG also for well_ptr not starting at 0 or decreasing, a cell
+ * out of range, repeated or not ascending within its well.  Synchronises the stream. */
+int msp_wells_setup_scalar(msp_wells* out, int32_t nr, int32_t b, int32_t nw,
+                           const int32_t* d_row_ptr, const int32_t* d_col_idx,
+                           const double* d_values, int64_t nnzb, const int32_t* d_well_ptr,
+                           const int32_t* d_well_cells, const double* d_arw,
+                           const double* d_awr, const double* d_aww, void* stream);
+
+/* New values for a handle of msp_wells_setup_scalar (same pattern and perforations). */
+int msp_wells_update_values_scalar(msp_wells W, const double* d_values, const double* d_arw,
+                                   const double* d_awr, const double* d_aww, void* stream);
+
+/* d_g[(nr+nw)*b] = [g_R; g_W padded with zeros] from d_gr[nr*b] and d_gw[nw] (device). */
+int msp_wells_pack_rhs(msp_wells W, const double* d_gr, const double* d_gw, double* d_g,
+                       void* stream);
+
+/* d_xr[nr*b] = x_R and d_xw[nw] = the wells' pressures from a padded d_x[(nr+nw)*b]
+ * (either output may be NULL). */
+int msp_wells_unpack(msp_wells W, const double* d_x, double* d_xr, double* d_xw,
+                     void* stream);
+
 /* ---- Request loop (serving) -----------------------------------------------------------
  * Solves of many systems arriving over time.  A system (key) is one matrix pattern; its
  * solver handle (matrix, AMG hierarchy, stage operators) stays resident on the device

@@ -8,7 +8,8 @@ ctypes binding (``_native``) plus a small convenience wrapper (``Solver``).
 from __future__ import annotations
 
 from . import _native
-from ._native import (MSP_NOT_CONVERGED, MSP_OK, MSP_PREC_MSP, MSP_PREC_N_ONLY, MSP_PREC_NONE,
+from ._native import (msp_wells_setup_scalar, msp_wells_update_values_scalar,
+                      msp_wells_pack_rhs, msp_wells_unpack,MSP_NOT_CONVERGED, MSP_OK, MSP_PREC_MSP, MSP_PREC_N_ONLY, MSP_PREC_NONE,
                       MSP_PREC_P_ONLY, MSP_PREC_R_ONLY, MSP_PRECISION_FP32, MSP_PRECISION_FP64,
                       MSP_COLOURING_ALG41, MSP_COLOURING_JP, MSP_SMOOTHER_PGS_MC,
                       MSP_SMOOTHER_PJAC, MSP_SMOOTHER_PGS_NO,
@@ -26,7 +27,9 @@ from ._native import (MSP_NOT_CONVERGED, MSP_OK, MSP_PREC_MSP, MSP_PREC_N_ONLY, 
                       msp_set_instances, msp_solve_batch, msp_stage_values_host,
                       msp_update_values_staged)
 
-__all__ = ["Solver", "Wells", "WellEliminatedSolver", "Server", "BatchSolver",
+__all__ = ["Solver", "Wells", "ScalarWells", "WellEliminatedSolver",
+           "msp_wells_setup_scalar", "msp_wells_update_values_scalar", "msp_wells_pack_rhs",
+           "msp_wells_unpack", "Server", "BatchSolver",
            "stack_block_diagonal", "msp_set_instances", "msp_solve_batch", "MspError",
            "msp_stage_values_host", "msp_update_values_staged",
            "msp_wells_setup",
@@ -141,6 +144,30 @@ class Wells:
             self.close()
         except Exception:
             pass
+
+
+class ScalarWells(Wells):
+    """Elimination of wells with one unknown each (bottom-hole pressure): the cell matrix
+    A_RR (``nr`` block rows) plus, per well, its perforated cells (``well_ptr``,
+    ``well_cells``), ``arw``/``awr`` (b values per perforation) and ``aww`` (one per
+    well).  Vectors of ``reduce_rhs``/``recover`` are in the padded layout of ``nr + nw``
+    block rows; ``pack_rhs``/``unpack`` convert."""
+
+    def __init__(self, nr, b, nw, row_ptr, col_idx, values, well_ptr, well_cells, arw, awr,
+                 aww, stream=None):
+        self.nb, self.b, self.nw = int(nr) + int(nw), int(b), int(nw)
+        self.W = msp_wells_setup_scalar(int(nr), self.b, self.nw, row_ptr, col_idx, values,
+                                        well_ptr, well_cells, arw, awr, aww, stream)
+        self.nr, self.row_ptr, self.col_idx, self.values = msp_wells_reduced(self.W, self.b)
+
+    def update_values(self, values, arw=None, awr=None, aww=None, stream=None):
+        msp_wells_update_values_scalar(self.W, values, arw, awr, aww, stream)
+
+    def pack_rhs(self, gr, gw, g, stream=None):
+        msp_wells_pack_rhs(self.W, gr, gw, g, stream)
+
+    def unpack(self, x, xr, xw, stream=None):
+        msp_wells_unpack(self.W, x, xr, xw, stream)
 
 
 class WellEliminatedSolver:

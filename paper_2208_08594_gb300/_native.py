@@ -35,7 +35,9 @@ EXPORTS = ("msp_config_default", "msp_setup", "msp_update_values", "msp_update_v
            "msp_wells_free", "msp_device_bytes", "msp_estimate_device_bytes",
            "msp_server_create", "msp_server_submit", "msp_server_wait", "msp_server_get_stats",
            "msp_server_free", "msp_set_instances", "msp_solve_batch",
-           "msp_stage_values_host", "msp_update_values_staged", "msp_fma_rate")
+           "msp_stage_values_host", "msp_update_values_staged", "msp_fma_rate",
+           "msp_wells_setup_scalar", "msp_wells_update_values_scalar", "msp_wells_pack_rhs",
+           "msp_wells_unpack")
 
 # largest n accepted by msp_vertices_grouping_noalloc (size of its fixed scratch)
 NOALLOC_MAX_VERTICES = 1 << 16
@@ -152,6 +154,11 @@ def lib(build_if_missing: bool = True):
     L.msp_wells_reduce_rhs.argtypes = [P, P, P, P]
     L.msp_wells_recover.argtypes = [P, P, P, P, P]
     L.msp_wells_free.argtypes = [P]
+    L.msp_wells_setup_scalar.argtypes = [C.POINTER(P), C.c_int32, C.c_int32, C.c_int32, P, P, P,
+                                         C.c_int64, P, P, P, P, P, P]
+    L.msp_wells_update_values_scalar.argtypes = [P, P, P, P, P, P]
+    L.msp_wells_pack_rhs.argtypes = [P, P, P, P, P]
+    L.msp_wells_unpack.argtypes = [P, P, P, P, P]
     L.msp_device_bytes.argtypes = [P, C.POINTER(C.c_int64)]
     L.msp_set_instances.argtypes = [P, C.c_int32, P]
     L.msp_stage_values_host.argtypes = [P, P, P]
@@ -382,6 +389,50 @@ def msp_wells_setup(nb: int, b: int, nw: int, row_ptr, col_idx, values, stream=N
     if st != MSP_OK:
         raise MspError(st, "msp_wells_setup")
     return W
+
+
+def msp_wells_setup_scalar(nr: int, b: int, nw: int, row_ptr, col_idx, values, well_ptr,
+                           well_cells, arw, awr, aww, stream=None):
+    """Wells with one unknown each (see include/msp.h): cell matrix A_RR, the perforations
+    of every well, A_RW (b per perforation), A_WR (b per perforation) and A_WW (one per
+    well), all CUDA tensors."""
+    import torch
+    _check_dev(row_ptr, torch.int32, nr + 1, "row_ptr")
+    _check_dev(col_idx, torch.int32, None, "col_idx")
+    nnzb = col_idx.numel()
+    _check_dev(values, torch.float64, nnzb * b * b, "values")
+    _check_dev(well_ptr, torch.int32, nw + 1, "well_ptr")
+    _check_dev(well_cells, torch.int32, None, "well_cells")
+    nperf = well_cells.numel()
+    _check_dev(arw, torch.float64, nperf * b, "arw")
+    _check_dev(awr, torch.float64, nperf * b, "awr")
+    _check_dev(aww, torch.float64, nw, "aww")
+    W = C.c_void_p()
+    st = lib().msp_wells_setup_scalar(C.byref(W), nr, b, nw, _ptr(row_ptr), _ptr(col_idx),
+                                      _ptr(values), nnzb, _ptr(well_ptr), _ptr(well_cells),
+                                      _ptr(arw), _ptr(awr), _ptr(aww), _stream(stream))
+    if st != MSP_OK:
+        raise MspError(st, "msp_wells_setup_scalar")
+    return W
+
+
+def msp_wells_update_values_scalar(W, values, arw, awr, aww, stream=None):
+    st = lib().msp_wells_update_values_scalar(W, _ptr(values), _ptr(arw), _ptr(awr), _ptr(aww),
+                                              _stream(stream))
+    if st != MSP_OK:
+        raise MspError(st, "msp_wells_update_values_scalar")
+
+
+def msp_wells_pack_rhs(W, gr, gw, g, stream=None):
+    st = lib().msp_wells_pack_rhs(W, _ptr(gr), _ptr(gw), _ptr(g), _stream(stream))
+    if st != MSP_OK:
+        raise MspError(st, "msp_wells_pack_rhs")
+
+
+def msp_wells_unpack(W, x, xr, xw, stream=None):
+    st = lib().msp_wells_unpack(W, _ptr(x), _ptr(xr), _ptr(xw), _stream(stream))
+    if st != MSP_OK:
+        raise MspError(st, "msp_wells_unpack")
 
 
 def msp_wells_reduced(W, b: int):

@@ -107,6 +107,7 @@ int launch_multi_dot(size_t n, const double* V, size_t ldv, int K, const double*
 // one-pass Gram-Schmidt of FGMRES: dots of V[0..K) with two vectors (partials of block b at
 // b * 2 * kKrylovMaxK: [0, K) against x0, [K, 2K) against x1), strided reduction, and the
 // small triangular solves of one step (kernel comments in solve_kernels.cu)
+int krylov_dot2_blocks();
 int launch_multi_dot2(size_t n, const double* V, size_t ldv, int K, const double* x0,
                       const double* x1, double* partial, int nblocks, cudaStream_t s);
 int launch_reduce_partials_strided(int K, int nblocks, int stride, const double* partial,

@@ -1115,13 +1115,16 @@ int stage_N(msp_handle h, const PView<T>& P, const T* g, T* w, cudaStream_t s) {
     return MSP_OK;
   }
   const double sT = sizeof(T), bn = b - 1;
-  double bytes = 0.0;
+  double bytes = 0.0, fmas = 0.0;
   for (int sw = 0; sw < h->cfg.bgs_sweeps; ++sw)
-    for (int c = 0; c < h->g0; ++c)
-      bytes += sweep_bytes(h->cptr0[c], h->cptr0[c + 1],
-                           h->cc0.lower[c] + (sw == 0 ? 0 : h->cc0.upper[c]), bn * bn * sT + 4,
+    for (int c = 0; c < h->g0; ++c) {
+      const long long used = h->cc0.lower[c] + (sw == 0 ? 0 : h->cc0.upper[c]);
+      bytes += sweep_bytes(h->cptr0[c], h->cptr0[c + 1], used, bn * bn * sT + 4,
                            (2 * bn + 1 + bn * bn) * sT + 12);
-  Probe pr("stageN_bgs_sweep", bytes, s, h->cfg.bgs_sweeps * h->g0);
+      fmas += (double)(used + (h->cptr0[c + 1] - h->cptr0[c])) * bn * bn;
+    }
+  // FP64 flops are recorded: the FP64 FMA rate can bind these kernels, the FP32 one cannot
+  Probe pr("stageN_bgs_sweep", bytes, s, h->cfg.bgs_sweeps * h->g0, sT == 8 ? 2.0 * fmas : 0.0);
   for (int sw = 0; sw < h->cfg.bgs_sweeps; ++sw)
     for (int c = 0; c < h->g0; ++c)
       MSP_TRY(launch_bgs_colour<T>(b, h->cptr0[c], h->cptr0[c + 1], h->rp.p, h->ci.p, h->dpos.p,
@@ -1129,11 +1132,11 @@ int stage_N(msp_handle h, const PView<T>& P, const T* g, T* w, cudaStream_t s) {
   return MSP_OK;
 }
 
-// algorithmic bytes of a BSR row sweep over all block rows (values, columns, row
-// pointers, the input vector once, `vecs` further vectors of nb*b values)
 // FMAs of a BSR product over all blocks
 inline double bsr_fmas(msp_handle h) { return (double)h->nnzb * h->b * h->b; }
 
+// algorithmic bytes of a BSR row sweep over all block rows (values, columns, row
+// pointers, the input vector once, `vecs` further vectors of nb*b values)
 inline double bsr_bytes(msp_handle h, double sT, double vecs) {
   const double b = h->b;
   return (double)h->nnzb * (b * b * sT + 4) + (double)(h->nb + 1) * 4 +
@@ -1146,7 +1149,8 @@ int stage_P(msp_handle h, const PView<T>& P, const T* g, T* w, T* r, cudaStream_
   // as (g - A w_before) - A Pi_P e instead of a second pass over the whole matrix
   const double sT = sizeof(T), b = h->b;
   {
-    Probe pr("stageP_residual_restrict", bsr_bytes(h, sT, r ? 3 : 2) + (double)h->nb * sT, s);
+    Probe pr("stageP_residual_restrict", bsr_bytes(h, sT, r ? 3 : 2) + (double)h->nb * sT, s,
+             1, sT == 8 ? 2.0 * (bsr_fmas(h) + (double)h->nb * b) : 0.0);
     MSP_TRY(launch_bsr_restrict_p<T>(h->b, h->nb, h->rp.p, h->ci.p, P.vals, w, g, P.omega,
                                      P.lb[0], r, s, P.m0));
   }
@@ -1157,7 +1161,8 @@ int stage_P(msp_handle h, const PView<T>& P, const T* g, T* w, T* r, cudaStream_
   }
   Probe pr("stageP_correct_residual",
            (double)h->nnzb * (b * sT + 4) + (double)(h->nb + 1) * 4 +
-               (double)h->nb * sT * (1 + 2 * b + 2), s);
+               (double)h->nb * sT * (1 + 2 * b + 2), s, 1,
+           sT == 8 ? 2.0 * (double)h->nnzb * b : 0.0);
   return launch_bsr_col0_update<T>(h->b, h->nb, h->rp.p, h->ci.p, P.c0, P.lx[0], r, w, s, P.m0);
 }
 
@@ -1165,20 +1170,23 @@ template <typename T>
 int stage_R(msp_handle h, const PView<T>& P, const T* r, T* w, cudaStream_t s) {
   const int b = h->b;
   const double sT = sizeof(T), bb = (double)b * b;
-  double fwd = 0.0, bwd = 0.0;
+  double fwd = 0.0, bwd = 0.0, ffwd = 0.0, fbwd = 0.0;
   for (int c = 0; c < h->g0; ++c) {
     fwd += sweep_bytes(h->cptr0[c], h->cptr0[c + 1], h->cc0.lower[c], bb * sT + 4,
                        3.0 * b * sT + 12);
     bwd += sweep_bytes(h->cptr0[c], h->cptr0[c + 1], h->cc0.upper[c], bb * sT + 4,
                        (5.0 * b + bb) * sT + 12);
+    ffwd += 2.0 * (double)h->cc0.lower[c] * bb;
+    fbwd += 2.0 * ((double)h->cc0.upper[c] + (h->cptr0[c + 1] - h->cptr0[c])) * bb;
   }
+  if (sT != 8) ffwd = fbwd = 0.0;
   {
-    Probe pr("stageR_bilu_fwd", fwd, s, h->g0);
+    Probe pr("stageR_bilu_fwd", fwd, s, h->g0, ffwd);
     for (int c = 0; c < h->g0; ++c)
       MSP_TRY(launch_bilu_fwd<T>(b, h->cptr0[c], h->cptr0[c + 1], h->rp.p, h->ci.p, h->dpos.p,
                                  P.lu, r, P.y, s, P.m0));
   }
-  Probe pr("stageR_bilu_bwd", bwd, s, h->g0);
+  Probe pr("stageR_bilu_bwd", bwd, s, h->g0, fbwd);
   for (int c = h->g0 - 1; c >= 0; --c)
     MSP_TRY(launch_bilu_bwd<T>(b, h->cptr0[c], h->cptr0[c + 1], h->rp.p, h->ci.p, h->dpos.p,
                                P.lu, P.uinv, P.y, P.x, w, s, P.m0));
@@ -1388,6 +1396,7 @@ int fgmres(msp_handle h, double tol, int* iters, double* relres, double* relres_
   const size_t n = (size_t)h->nb * h->b;
   const int m = h->cfg.restart;
   const int nbk = krylov_blocks();
+  const int nbk2 = krylov_dot2_blocks();
   const double* bvec = h->bperm.p;
   double* x = h->xperm.p;
   double* V = h->V.p;
@@ -1498,9 +1507,9 @@ int fgmres(msp_handle h, double tol, int* iters, double* relres, double* relres_
       const int K = j + 2;  // u_0 .. u_j and w
       {
         Probe pr("krylov_multi_dot", (double)K * n * 8.0, s, 1, 4.0 * K * n);
-        MSP_TRY(launch_multi_dot2(n, V, n, K, vj, w, h->partial.p, nbk, s));
+        MSP_TRY(launch_multi_dot2(n, V, n, K, vj, w, h->partial.p, nbk2, s));
       }
-      MSP_TRY(launch_reduce_partials_strided(2 * K, nbk, 2 * kKrylovMaxK, h->partial.p,
+      MSP_TRY(launch_reduce_partials_strided(2 * K, nbk2, 2 * kKrylovMaxK, h->partial.p,
                                              h->gs_d.p, s));
       MSP_TRY(launch_dcgs_coef(j, h->gs_d.p, T, ldt, h->gs_g.p, out, s));
       {

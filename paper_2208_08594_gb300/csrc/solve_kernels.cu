@@ -1460,6 +1460,21 @@ int launch_cast_f2d(size_t n, const float* in, double* out, cudaStream_t s) {
 
 int krylov_blocks() { return sm_count() * 4; }
 
+// Blocks of the two-vector multi-dot: as many as fit on the SMs at once (its 16
+// accumulators and four elements in flight per thread take more registers than four
+// blocks of 256 threads per SM leave; a fourth block per SM would run as a second wave).
+int krylov_dot2_blocks() {
+  static const int cached = [] {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, multi_dot2_kernel, kThreads, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+      per_sm = 2;
+    return sm_count() * std::min(per_sm, 4);
+  }();
+  return cached;
+}
+
 int launch_multi_dot(size_t n, const double* V, size_t ldv, int K, const double* w,
                      double* partial, int nblocks, cudaStream_t s, const int* gate) {
   if (K > kMaxK) return MSP_ERR_ARG;

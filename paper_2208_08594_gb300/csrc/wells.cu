@@ -40,6 +40,14 @@ struct msp_wells_s {
   msp::DevBuf<double> acw;        // nperf blocks A_cw
   msp::DevBuf<double> wv;         // values of the well rows
   msp::DevBuf<double> omega;      // scratch of the block inverse (first rows)
+  // wells with one unknown each (msp_wells_setup_scalar): the identity-padded full matrix
+  // the elimination above works on, rebuilt from the compact arrays at every value update
+  bool scalar = false;
+  msp::DevBuf<int> c_rp;          // the cell rows' row pointers as given (nr + 1)
+  msp::DevBuf<int> p_rp;          // padded row pointers (nb + 1)
+  msp::DevBuf<int> c_perf;        // cell row -> its perforation index, or -1
+  msp::DevBuf<int> w_ptr;         // perforations of every well (nw + 1)
+  msp::DevBuf<double> p_vals;     // padded values (nnzb * b * b)
 };
 
 namespace msp {
@@ -279,6 +287,128 @@ __global__ void wells_rebase_kernel(int n, const int* __restrict__ in, int base,
     out[i] = in[i] - base;
 }
 
+// ---- wells with one unknown each: the padded layout -------------------------------
+// A well of Eq. Jacobian-system has one unknown (its bottom-hole pressure) and one
+// equation.  Padded to a b x b block row with identity rows/columns 1..b-1 (zero
+// right-hand side there), A_RW becomes column 0 of a block, A_WR row 0 and A_WW the (0, 0)
+// entry of an otherwise identity block; the padded unknowns then decouple exactly, and
+// eliminating the padded blocks gives the Schur complement of the scalar A_WW.
+
+// per perforation k of well w: cell row -> (well, perforation); rejects cells out of
+// range, a cell perforated twice, and cells not ascending within a well
+__global__ void pad_map_kernel(int nw, int nr, const int* __restrict__ wptr,
+                               const int* __restrict__ cells, int* __restrict__ perf_of_cell,
+                               DevFlags* flags) {
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += gridDim.x * blockDim.x) {
+    for (int k = wptr[w]; k < wptr[w + 1]; ++k) {
+      const int c = cells[k];
+      if (c < 0 || c >= nr || (k > wptr[w] && c <= cells[k - 1])) {
+        raise_flag_w(flags, MSP_ERR_ARG, w);
+        break;
+      }
+      if (atomicCAS(perf_of_cell + c, -1, k) != -1) raise_flag_w(flags, MSP_ERR_ARG, w);
+    }
+  }
+}
+
+// blocks of every padded row: a cell row keeps its blocks plus one for its well, a well
+// row has one block per perforation plus its diagonal
+__global__ void pad_count_kernel(int nr, int nw, const int* __restrict__ rp,
+                                 const int* __restrict__ perf_of_cell,
+                                 const int* __restrict__ wptr, int* __restrict__ cnt) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr + nw; i += gridDim.x * blockDim.x)
+    cnt[i] = i < nr ? rp[i + 1] - rp[i] + (perf_of_cell[i] >= 0)
+                    : wptr[i - nr + 1] - wptr[i - nr] + 1;
+}
+
+// padded columns (pattern only)
+__global__ void pad_pattern_kernel(int nr, int nw, const int* __restrict__ rp,
+                                   const int* __restrict__ ci, const int* __restrict__ perf_of_cell,
+                                   const int* __restrict__ wptr, const int* __restrict__ cells,
+                                   const int* __restrict__ prp, int* __restrict__ pci) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr + nw; i += gridDim.x * blockDim.x) {
+    int q = prp[i];
+    if (i < nr) {
+      for (int p = rp[i]; p < rp[i + 1]; ++p) pci[q++] = ci[p];
+      const int k = perf_of_cell[i];
+      if (k >= 0) {  // the well's column comes after every cell column
+        int w = 0;
+        while (wptr[w + 1] <= k) ++w;
+        pci[q] = nr + w;
+      }
+    } else {
+      const int w = i - nr;
+      for (int k = wptr[w]; k < wptr[w + 1]; ++k) pci[q++] = cells[k];
+      pci[q] = i;
+    }
+  }
+}
+
+// padded values, one thread per padded block
+template <int B>
+__global__ void pad_values_kernel(int nr, int nw, const int* __restrict__ rp,
+                                  const int* __restrict__ perf_of_cell,
+                                  const int* __restrict__ wptr, const int* __restrict__ prp,
+                                  const double* __restrict__ v, const double* __restrict__ arw,
+                                  const double* __restrict__ awr, const double* __restrict__ aww,
+                                  double* __restrict__ pv) {
+  constexpr int BB = B * B;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr + nw; i += gridDim.x * blockDim.x) {
+    double* out = pv + (size_t)prp[i] * BB;
+    if (i < nr) {
+      const int n = rp[i + 1] - rp[i];
+      const double* in = v + (size_t)rp[i] * BB;
+      for (int e = 0; e < n * BB; ++e) out[e] = in[e];
+      const int k = perf_of_cell[i];
+      if (k >= 0) {  // A_RW: column 0
+        double* blk = out + (size_t)n * BB;
+        for (int e = 0; e < BB; ++e) blk[e] = 0.0;
+        for (int r = 0; r < B; ++r) blk[r * B] = arw[(size_t)k * B + r];
+      }
+    } else {
+      const int w = i - nr;
+      const int k0 = wptr[w], k1 = wptr[w + 1];
+      for (int k = k0; k < k1; ++k) {  // A_WR: row 0
+        double* blk = out + (size_t)(k - k0) * BB;
+        for (int e = 0; e < BB; ++e) blk[e] = 0.0;
+        for (int c = 0; c < B; ++c) blk[c] = awr[(size_t)k * B + c];
+      }
+      double* d = out + (size_t)(k1 - k0) * BB;  // A_WW and the identity padding
+      for (int e = 0; e < BB; ++e) d[e] = (e % (B + 1) == 0) ? 1.0 : 0.0;
+      d[0] = aww[w];
+    }
+  }
+}
+
+// g = [g_R; g_W padded with zeros]
+__global__ void pad_rhs_kernel(int nr, int nw, int b, const double* __restrict__ gr,
+                               const double* __restrict__ gw, double* __restrict__ g) {
+  const size_t nrb = (size_t)nr * b, total = nrb + (size_t)nw * b;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    if (e < nrb) {
+      g[e] = gr[e];
+    } else {
+      const size_t q = e - nrb;
+      g[e] = (q % b == 0) ? gw[q / b] : 0.0;
+    }
+  }
+}
+
+// x_R = x[0 .. nr*b), x_W[w] = x[(nr + w) * b]
+__global__ void unpad_kernel(int nr, int nw, int b, const double* __restrict__ x,
+                             double* __restrict__ xr, double* __restrict__ xw) {
+  const size_t nrb = (size_t)nr * b;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nrb + nw;
+       e += (size_t)gridDim.x * blockDim.x) {
+    if (e < nrb) {
+      if (xr) xr[e] = x[e];
+    } else if (xw) {
+      xw[e - nrb] = x[nrb + (e - nrb) * b];
+    }
+  }
+}
+
 #define MSP_WB_SWITCH(b, ...)                              \
   switch (b) {                                             \
     case 1: { constexpr int B_ = 1; __VA_ARGS__; } break;  \
@@ -332,8 +462,8 @@ int wells_values(msp_wells_s* W, const double* v, cudaStream_t s) {
 
 int wells_build(msp_wells_s* W, const int* rp, const int* ci, const double* v, cudaStream_t s) {
   const int nb = W->nb, nr = W->nr;
-  MSP_TRY(W->flags.alloc(1));
-  MSP_CUDA_TRY(cudaMallocHost(&W->h_flags, sizeof(DevFlags)));
+  if (!W->flags.p) MSP_TRY(W->flags.alloc(1));
+  if (!W->h_flags) MSP_CUDA_TRY(cudaMallocHost(&W->h_flags, sizeof(DevFlags)));
   MSP_CUDA_TRY(cudaMemsetAsync(W->flags.p, 0, sizeof(DevFlags), s));
   MSP_TRY(W->dpos.alloc(nb));
   // reads ci only inside [0, nnzb), so a bad row_ptr is reported, never followed
@@ -505,6 +635,141 @@ int msp_wells_free(msp_wells W) {
     destroy_wells(W);
   }
   return MSP_OK;
+}
+
+// ---- wells with one unknown each ----------------------------------------------------
+int msp_wells_setup_scalar(msp_wells* out, int32_t nr, int32_t b, int32_t nw,
+                           const int32_t* d_row_ptr, const int32_t* d_col_idx,
+                           const double* d_values, int64_t nnzb, const int32_t* d_well_ptr,
+                           const int32_t* d_well_cells, const double* d_arw, const double* d_awr,
+                           const double* d_aww, void* stream) {
+  if (!out) return MSP_ERR_ARG;
+  *out = nullptr;
+  if (nr < 1 || b < 1 || b > 8 || nw < 1 || nnzb < nr || nnzb > 0x3fffffffLL || !d_row_ptr ||
+      !d_col_idx || !d_values || !d_well_ptr || !d_aww)
+    return MSP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  msp_wells_s* W = nullptr;
+  try {
+    // the perforation ranges, checked on the host before anything reads them
+    std::vector<int> wp(nw + 1);
+    MSP_CUDA_TRY(cudaMemcpyAsync(wp.data(), d_well_ptr, sizeof(int) * (nw + 1),
+                                 cudaMemcpyDeviceToHost, s));
+    int rp_ends[2] = {0, 0};
+    MSP_CUDA_TRY(cudaMemcpyAsync(&rp_ends[0], d_row_ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MSP_CUDA_TRY(cudaMemcpyAsync(&rp_ends[1], d_row_ptr + nr, sizeof(int), cudaMemcpyDeviceToHost,
+                                 s));
+    MSP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (rp_ends[0] != 0 || (int64_t)rp_ends[1] != nnzb) return MSP_ERR_PATTERN;
+    if (wp[0] != 0) return MSP_ERR_ARG;
+    for (int w = 0; w < nw; ++w)
+      if (wp[w + 1] < wp[w]) return MSP_ERR_ARG;
+    const int nperf = wp[nw];
+    if (nperf > nr || (nperf > 0 && (!d_well_cells || !d_arw || !d_awr))) return MSP_ERR_ARG;
+    W = new msp_wells_s();
+    W->scalar = true;
+    W->b = b;
+    W->nw = nw;
+    W->nr = nr;
+    W->nb = nr + nw;
+    W->nnzb = nnzb + 2LL * nperf + nw;
+    W->ss = sort_scratch_create();
+    int st = W->ss ? MSP_OK : MSP_ERR_NOMEM;
+    auto fail = [&](int code) {
+      cudaStreamSynchronize(s);
+      destroy_wells(W);
+      return code;
+    };
+    if (st != MSP_OK) return fail(st);
+    // the cell matrix's own pattern first (reads its columns only inside [0, nnzb))
+    st = W->flags.alloc(1);
+    if (st == MSP_OK && cudaMallocHost(&W->h_flags, sizeof(DevFlags)) != cudaSuccess)
+      st = MSP_ERR_NOMEM;
+    if (st != MSP_OK) return fail(st);
+    {
+      DevBuf<int> cdpos;
+      if ((st = cdpos.alloc(nr)) != MSP_OK) return fail(st);
+      cudaMemsetAsync(W->flags.p, 0, sizeof(DevFlags), s);
+      if ((st = launch_check_pattern(nr, (int)nnzb, d_row_ptr, d_col_idx, cdpos.p, W->flags.p, s)) !=
+              MSP_OK ||
+          (st = sync_wflags(W, s)) != MSP_OK)
+        return fail(st);
+      if (W->h_flags->code != MSP_OK) return fail(W->h_flags->code);
+    }
+    if ((st = W->c_rp.alloc(nr + 1)) != MSP_OK || (st = W->c_perf.alloc(nr)) != MSP_OK ||
+        (st = W->w_ptr.alloc(nw + 1)) != MSP_OK || (st = W->p_rp.alloc(W->nb + 1)) != MSP_OK ||
+        (st = W->p_vals.alloc((size_t)W->nnzb * b * b)) != MSP_OK)
+      return fail(st);
+    cudaMemcpyAsync(W->c_rp.p, d_row_ptr, sizeof(int) * (nr + 1), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(W->w_ptr.p, d_well_ptr, sizeof(int) * (nw + 1), cudaMemcpyDeviceToDevice, s);
+    if ((st = launch_fill_int(nr, -1, W->c_perf.p, s)) != MSP_OK) return fail(st);
+    cudaMemsetAsync(W->flags.p, 0, sizeof(DevFlags), s);
+    pad_map_kernel<<<grid_for(nw, 64), 64, 0, s>>>(nw, nr, W->w_ptr.p, d_well_cells,
+                                                     W->c_perf.p, W->flags.p);
+    if ((st = launch_status()) != MSP_OK || (st = sync_wflags(W, s)) != MSP_OK) return fail(st);
+    if (W->h_flags->code != MSP_OK) return fail(W->h_flags->code);
+    // padded pattern and values
+    DevBuf<int> cnt, pci;
+    if ((st = cnt.alloc(W->nb)) != MSP_OK || (st = pci.alloc((size_t)W->nnzb)) != MSP_OK)
+      return fail(st);
+    pad_count_kernel<<<grid_for(W->nb, kThreads), kThreads, 0, s>>>(nr, nw, W->c_rp.p,
+                                                                    W->c_perf.p, W->w_ptr.p,
+                                                                    cnt.p);
+    if ((st = launch_status()) != MSP_OK ||
+        (st = exclusive_scan_int(W->ss, (size_t)W->nb, cnt.p, W->p_rp.p, s)) != MSP_OK)
+      return fail(st);
+    const int total = (int)W->nnzb;
+    cudaMemcpyAsync(W->p_rp.p + W->nb, &total, sizeof(int), cudaMemcpyHostToDevice, s);
+    pad_pattern_kernel<<<grid_for(W->nb, kThreads), kThreads, 0, s>>>(
+        nr, nw, W->c_rp.p, d_col_idx, W->c_perf.p, W->w_ptr.p, d_well_cells, W->p_rp.p, pci.p);
+    if ((st = launch_status()) != MSP_OK) return fail(st);
+    MSP_WB_SWITCH(b, pad_values_kernel<B_><<<grid_for(W->nb, kThreads), kThreads, 0, s>>>(
+                         nr, nw, W->c_rp.p, W->c_perf.p, W->w_ptr.p, W->p_rp.p, d_values, d_arw,
+                         d_awr, d_aww, W->p_vals.p));
+    if ((st = launch_status()) != MSP_OK) return fail(st);
+    // `total` is read by the copy above: wait before it goes out of scope
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(MSP_ERR_CUDA);
+    if ((st = wells_build(W, W->p_rp.p, pci.p, W->p_vals.p, s)) != MSP_OK) return fail(st);
+  } catch (...) {
+    destroy_wells(W);
+    return MSP_ERR_NOMEM;
+  }
+  *out = W;
+  return MSP_OK;
+}
+
+int msp_wells_update_values_scalar(msp_wells W, const double* d_values, const double* d_arw,
+                                   const double* d_awr, const double* d_aww, void* stream) {
+  if (!W || !W->scalar || !d_values || !d_aww) return MSP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    MSP_WB_SWITCH(W->b, pad_values_kernel<B_><<<grid_for(W->nb, kThreads), kThreads, 0, s>>>(
+                            W->nr, W->nw, W->c_rp.p, W->c_perf.p, W->w_ptr.p, W->p_rp.p,
+                            d_values, d_arw, d_awr, d_aww, W->p_vals.p));
+    MSP_TRY(launch_status());
+    return wells_values(W, W->p_vals.p, s);
+  } catch (...) {
+    return MSP_ERR_NOMEM;
+  }
+}
+
+int msp_wells_pack_rhs(msp_wells W, const double* d_gr, const double* d_gw, double* d_g,
+                       void* stream) {
+  if (!W || !d_gr || !d_gw || !d_g) return MSP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t total = (size_t)W->nb * W->b;
+  pad_rhs_kernel<<<grid_for(total, kThreads), kThreads, 0, s>>>(W->nr, W->nw, W->b, d_gr, d_gw,
+                                                                d_g);
+  return launch_status();
+}
+
+int msp_wells_unpack(msp_wells W, const double* d_x, double* d_xr, double* d_xw, void* stream) {
+  if (!W || !d_x || (!d_xr && !d_xw)) return MSP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t total = (size_t)W->nr * W->b + W->nw;
+  unpad_kernel<<<grid_for(total, kThreads), kThreads, 0, s>>>(W->nr, W->nw, W->b, d_x, d_xr,
+                                                              d_xw);
+  return launch_status();
 }
 
 }  // extern "C"

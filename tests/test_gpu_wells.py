@@ -170,3 +170,158 @@ def test_full_size_reduction_and_solve():
     assert np.linalg.norm(r) <= 1e-6 * np.linalg.norm(gs) * 1.001
     S.close()
     O.close()
+
+
+def _compact_wells(a):
+    """The one-unknown form of a matrix whose wells are identity-padded block rows: the
+    cell matrix A_RR, the perforated cells of every well (ascending), A_RW (column 0 of
+    the cell-well blocks), A_WR (row 0 of the well-cell blocks) and A_WW (entry (0, 0) of
+    the well's diagonal block)."""
+    nr, nw, b = a.n_cells, a.n_wells, a.b
+    rp, ci, v = [0], [], []
+    arw_of = {}
+    for c in range(nr):
+        for p in range(a.row_ptr[c], a.row_ptr[c + 1]):
+            j = int(a.col_idx[p])
+            if j < nr:
+                ci.append(j)
+                v.append(a.values[p])
+            else:
+                arw_of[c] = a.values[p][:, 0].copy()
+        rp.append(len(ci))
+    wptr, cells, arw, awr, aww = [0], [], [], [], []
+    for w in range(nw):
+        i = nr + w
+        for p in range(a.row_ptr[i], a.row_ptr[i + 1]):
+            j = int(a.col_idx[p])
+            if j < nr:
+                cells.append(j)
+                awr.append(a.values[p][0, :].copy())
+                arw.append(arw_of[j])
+            elif j == i:
+                aww.append(a.values[p][0, 0])
+        wptr.append(len(cells))
+    return (np.array(rp, np.int32), np.array(ci, np.int32), np.array(v).reshape(-1, b, b),
+            np.array(wptr, np.int32), np.array(cells, np.int32),
+            np.array(arw).reshape(-1, b), np.array(awr).reshape(-1, b), np.array(aww))
+
+
+def _padded(nr, b, rp, ci, v, wptr, cells, arw, awr, aww):
+    """The same system with every well padded to a b x b block row: A_RW in column 0,
+    A_WR in row 0, A_WW at (0, 0) of an identity block (Eq. Jacobian-system with the
+    well's extra unknowns decoupled)."""
+    nw = len(aww)
+    perf = {int(c): k for k, c in enumerate(cells)}
+    well = {int(c): w for w in range(nw) for c in cells[wptr[w]:wptr[w + 1]]}
+    prp, pci, pv = [0], [], []
+    for c in range(nr):
+        for p in range(rp[c], rp[c + 1]):
+            pci.append(int(ci[p]))
+            pv.append(v[p])
+        if c in perf:
+            blk = np.zeros((b, b))
+            blk[:, 0] = arw[perf[c]]
+            pci.append(nr + well[c])
+            pv.append(blk)
+        prp.append(len(pci))
+    for w in range(nw):
+        for k in range(wptr[w], wptr[w + 1]):
+            blk = np.zeros((b, b))
+            blk[0, :] = awr[k]
+            pci.append(int(cells[k]))
+            pv.append(blk)
+        d = np.eye(b)
+        d[0, 0] = aww[w]
+        pci.append(nr + w)
+        pv.append(d)
+        prp.append(len(pci))
+    return BSRMatrix(nb=nr + nw, b=b, row_ptr=np.array(prp, np.int32),
+                     col_idx=np.array(pci, np.int32), values=np.array(pv).reshape(-1, b, b),
+                     n_cells=nr, n_wells=nw)
+
+
+@pytest.mark.parametrize("name", ["b3_two_wells", "spe10_like_b4", "b2_three_wells"])
+def test_one_unknown_wells_match_the_oracle(name):
+    """msp_wells_setup_scalar: the compact form (A_RR, perforations, A_RW, A_WR, scalar
+    A_WW) gives the reduced matrix, right-hand side and recovered unknowns of the oracle's
+    elimination of the padded system bit for bit, and A_S equals the scalar Schur
+    complement A_RR - A_RW A_WR / A_WW."""
+    a = CASES[name]()
+    nr, nw, b = a.n_cells, a.n_wells, a.b
+    rp, ci, v, wptr, cells, arw, awr, aww = _compact_wells(a)
+    W = msp.ScalarWells(nr, b, nw, _t(rp), _t(ci), _t(v.reshape(-1)), _t(wptr), _t(cells),
+                        _t(arw.reshape(-1)), _t(awr.reshape(-1)), _t(aww))
+    ap = _padded(nr, b, rp, ci, v, wptr, cells, arw, awr, aww)
+    O = oracle.Wells(ap, nw)
+    srp, sci, sv = W.reduced()
+    orp, oci, ov = O.reduced()
+    assert np.array_equal(srp.cpu().numpy(), orp) and np.array_equal(sci.cpu().numpy(), oci)
+    assert np.array_equal(_bits(sv.cpu().numpy()), _bits(ov))
+    # closed form of the scalar Schur complement
+    dense = np.zeros((nr * b, nr * b))
+    for c in range(nr):
+        for p in range(rp[c], rp[c + 1]):
+            dense[c * b:(c + 1) * b, ci[p] * b:(ci[p] + 1) * b] = v[p]
+    for w in range(nw):
+        for k in range(wptr[w], wptr[w + 1]):
+            for k2 in range(wptr[w], wptr[w + 1]):
+                c, c2 = cells[k], cells[k2]
+                dense[c * b:(c + 1) * b, c2 * b:(c2 + 1) * b] -= np.outer(arw[k], awr[k2]) / aww[w]
+    got = np.zeros_like(dense)
+    svh = sv.cpu().numpy().reshape(-1, b, b)
+    for c in range(nr):
+        for p in range(orp[c], orp[c + 1]):
+            got[c * b:(c + 1) * b, oci[p] * b:(oci[p] + 1) * b] = svh[p]
+    assert np.allclose(got, dense, rtol=1e-13, atol=1e-13 * np.abs(dense).max())
+    # right-hand side and recovery through the padded layout
+    rng = np.random.default_rng(5)
+    gr, gw = rng.normal(size=nr * b), rng.normal(size=nw)
+    g = torch.empty((nr + nw) * b, dtype=torch.float64, device=DEV)
+    W.pack_rhs(_t(gr), _t(gw), g)
+    gpad = np.concatenate([gr, np.concatenate([[gw[w]] + [0.0] * (b - 1) for w in range(nw)])])
+    assert np.array_equal(g.cpu().numpy(), gpad)
+    gs = torch.empty(nr * b, dtype=torch.float64, device=DEV)
+    W.reduce_rhs(g, gs)
+    assert np.array_equal(_bits(gs.cpu().numpy()), _bits(O.reduce_rhs(gpad)))
+    xs = rng.normal(size=nr * b)
+    x = torch.empty((nr + nw) * b, dtype=torch.float64, device=DEV)
+    W.recover(g, _t(xs), x)
+    ox = O.recover(gpad, xs)
+    assert np.array_equal(_bits(x.cpu().numpy()), _bits(ox))
+    xr = torch.empty(nr * b, dtype=torch.float64, device=DEV)
+    xw = torch.empty(nw, dtype=torch.float64, device=DEV)
+    W.unpack(x, xr, xw)
+    assert np.array_equal(xr.cpu().numpy(), xs)
+    assert np.array_equal(xw.cpu().numpy(), ox.reshape(-1, b)[nr:, 0])
+    # x_W = (g_W - A_WR x_R) / A_WW
+    for w in range(nw):
+        ref = gw[w] - sum(awr[k] @ xs[cells[k] * b:(cells[k] + 1) * b]
+                          for k in range(wptr[w], wptr[w + 1]))
+        assert np.isclose(xw[w].item(), ref / aww[w], rtol=1e-12)
+    # new values
+    v2 = v * 1.01
+    W.update_values(_t(v2.reshape(-1)), _t(arw.reshape(-1) * 0.9), _t(awr.reshape(-1)), _t(aww * 1.1))
+    O2 = oracle.Wells(_padded(nr, b, rp, ci, v2, wptr, cells, arw * 0.9, awr, aww * 1.1), nw)
+    assert np.array_equal(_bits(W.reduced()[2].cpu().numpy()), _bits(O2.reduced()[2]))
+    W.close()
+    O.close()
+    O2.close()
+
+
+def test_one_unknown_wells_rejected_layouts():
+    a = CASES["b3_two_wells"]()
+    nr, nw, b = a.n_cells, a.n_wells, a.b
+    rp, ci, v, wptr, cells, arw, awr, aww = _compact_wells(a)
+    bad = cells.copy()
+    bad[1], bad[0] = bad[0], bad[1]  # not ascending within the well
+    with pytest.raises(msp.MspError) as e:
+        msp.ScalarWells(nr, b, nw, _t(rp), _t(ci), _t(v.reshape(-1)), _t(wptr), _t(bad),
+                        _t(arw.reshape(-1)), _t(awr.reshape(-1)), _t(aww))
+    assert e.value.status == -1
+    twice = cells.copy()
+    twice[wptr[1]] = cells[0]  # a cell perforated by two wells
+    twice[wptr[1]:wptr[2]] = np.sort(twice[wptr[1]:wptr[2]])
+    with pytest.raises(msp.MspError) as e:
+        msp.ScalarWells(nr, b, nw, _t(rp), _t(ci), _t(v.reshape(-1)), _t(wptr), _t(twice),
+                        _t(arw.reshape(-1)), _t(awr.reshape(-1)), _t(aww))
+    assert e.value.status == -1
