@@ -690,6 +690,7 @@ __global__ void cast_f2d_kernel(size_t n, const float* __restrict__ in, double* 
 // ----------------------------------------------------------------------------------
 constexpr int kDotChunk = 8;
 constexpr int kMaxK = kKrylovMaxK;
+constexpr int kMaxRestart = 64;  // msp_config.restart <= 64
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   v = group_sum<kWarp>(v);
@@ -859,19 +860,30 @@ __global__ void reduce_partials_strided_kernel(int K, int nblocks, int stride,
 // out[147] = 1 if nu_j^2 <= 0 (u_j lies in span Q: the previous step broke down).
 __global__ void dcgs_coef_kernel(int j, const double* __restrict__ d, double* __restrict__ T,
                                  int ldt, double* __restrict__ g, double* __restrict__ out) {
+  // the warp stages the triangle of T and the dot products in shared memory (coalesced),
+  // then one thread runs the three substitutions from there
+  __shared__ double sT[(kMaxRestart + 2) * (kMaxRestart + 2)];
+  __shared__ double sd[2 * kMaxK], sc[kMaxK], sh[kMaxK];
+  const int K = j + 2, ld = kMaxRestart + 2;
+  for (int q = threadIdx.x; q < j * j; q += blockDim.x) {
+    const int col = q / j, row = q % j;
+    if (row <= col) sT[col * ld + row] = T[(size_t)col * ldt + row];
+  }
+  for (int q = threadIdx.x; q < 2 * K; q += blockDim.x) sd[q] = d[q];
+  __syncthreads();
   if (threadIdx.x != 0) return;
-  const int K = j + 2;
   double c2 = 0.0;
   for (int k = 0; k < j; ++k) {  // forward substitution with T_j^T
-    double t = d[k];
-    for (int i = 0; i < k; ++i) t -= T[(size_t)k * ldt + i] * out[72 + i];
-    const double ck = t / T[(size_t)k * ldt + k];
+    double t = sd[k];
+    for (int i = 0; i < k; ++i) t -= sT[k * ld + i] * sc[i];
+    const double ck = t / sT[k * ld + k];
+    sc[k] = ck;
     out[72 + k] = ck;
     c2 += ck * ck;
   }
-  const double nu2 = d[j] - c2;
+  const double nu2 = sd[j] - c2;
   out[145] = nu2;
-  out[146] = d[K + j + 1];
+  out[146] = sd[K + j + 1];
   if (!(nu2 > 0.0)) {
     out[144] = 0.0;
     out[147] = 1.0;
@@ -881,17 +893,23 @@ __global__ void dcgs_coef_kernel(int j, const double* __restrict__ d, double* __
   const double nu = sqrt(nu2);
   out[144] = nu;
   out[147] = 0.0;
-  for (int k = 0; k < j; ++k) T[(size_t)j * ldt + k] = out[72 + k];  // column j, stored by column
-  T[(size_t)j * ldt + j] = nu;
-  for (int k = 0; k <= j; ++k) {  // h = T^-T (U^T w)
-    double t = d[K + k];
-    for (int i = 0; i < k; ++i) t -= T[(size_t)k * ldt + i] * out[i];
-    out[k] = t / T[(size_t)k * ldt + k];
+  for (int k = 0; k < j; ++k) {  // column j of T, stored by column
+    T[(size_t)j * ldt + k] = sc[k];
+    sT[j * ld + k] = sc[k];
   }
-  for (int k = j; k >= 0; --k) {  // g = T^-1 h
-    double t = out[k];
-    for (int i = k + 1; i <= j; ++i) t -= T[(size_t)i * ldt + k] * g[i];
-    g[k] = t / T[(size_t)k * ldt + k];
+  T[(size_t)j * ldt + j] = nu;
+  sT[j * ld + j] = nu;
+  for (int k = 0; k <= j; ++k) {  // h = T^-T (U^T w)
+    double t = sd[K + k];
+    for (int i = 0; i < k; ++i) t -= sT[k * ld + i] * sh[i];
+    sh[k] = t / sT[k * ld + k];
+    out[k] = sh[k];
+  }
+  for (int k = j; k >= 0; --k) {  // g = T^-1 h; the computed g_i are kept in sd[0..j]
+    double t = sh[k];
+    for (int i = k + 1; i <= j; ++i) t -= sT[i * ld + k] * sd[i];
+    sd[k] = t / sT[k * ld + k];
+    g[k] = sd[k];
   }
 }
 
