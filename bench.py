@@ -46,7 +46,7 @@ SITE_KERNELS = {
     "krylov_spmv": "bsr_spmv_kernel", "api_spmv": "bsr_spmv_kernel",
     "krylov_multi_dot": "multi_dot2_kernel", "krylov_finalize_dot": "multi_dot_kernel",
     "krylov_multi_axpy": "multi_axpy_norm_kernel",
-    "stageN_bgs_sweep": "bgs_colour_kernel",
+    "stageN_bgs_sweep": "bgs_colour_kernel", "stageN_scale": "nscale_kernel",
     "stageP_residual_restrict": "bsr_restrict_p_kernel",
     "stageP_correct_residual": "bsr_col0_update_kernel",
     "stageP_prolong": "prolong_p_kernel",
@@ -85,6 +85,9 @@ def parse():
                    help="wells as ordinary block rows of the solved system (default), or "
                         "eliminated by the Schur complement of A_WW before the solve")
     p.add_argument("--mu", type=int, default=180)
+    p.add_argument("--autotune", action="store_true",
+                   help="time the lanes per row of the AMG levels' ELL kernels at SETUP and "
+                        "keep the fastest (msp_config.autotune)")
     p.add_argument("--nx", type=int, default=60)
     p.add_argument("--ny", type=int, default=220)
     p.add_argument("--nz", type=int, default=85)
@@ -350,7 +353,7 @@ def run_native(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     opts = dict(mu=args.mu, precision=prec, colouring=colouring_of(args, msp),
-                smoother=smoother_of(args, msp))
+                smoother=smoother_of(args, msp), autotune=int(args.autotune))
     if args.wells == "eliminate":
         solver = msp.WellEliminatedSolver(a.nb, a.b, a.n_wells, d_rp, d_ci, d_v0, **opts)
         inner = solver.solver
@@ -533,6 +536,7 @@ def run_native(args):
         e2e["ms"] = e2e_ms
     solver_levels = inner.num_levels
     level_info = [msp.msp_level_info(inner.h, l) for l in range(solver_levels)]
+    level_tiles = [msp.msp_level_tiles(inner.h, l) for l in range(solver_levels)]
     solver.close()
     if world > 1:
         dist.destroy_process_group()
@@ -586,6 +590,8 @@ def run_native(args):
                    "level_sizes": [li[0] for li in level_info],
                    "level_nnz": [li[1] for li in level_info],
                    "level_colours": [li[2] for li in level_info],
+                   "level_tiles": [list(t) for t in level_tiles],
+                   "autotune": bool(args.autotune),
                    "amg_operator_complexity": round(sum(li[1] for li in level_info)
                                                     / max(1, level_info[0][1]), 3),
                    "amg_grid_complexity": round(sum(li[0] for li in level_info)
@@ -929,7 +935,7 @@ def run_batch(args):
     stream = torch.cuda.current_stream()
     prec = msp.MSP_PRECISION_FP32 if args.precision == "fp32" else msp.MSP_PRECISION_FP64
     opts = dict(mu=args.mu, precision=prec, colouring=colouring_of(args, msp),
-                smoother=smoother_of(args, msp))
+                smoother=smoother_of(args, msp), autotune=int(args.autotune))
     t_gen = time.perf_counter()
     inst = batch_workload(args)
     t_gen = time.perf_counter() - t_gen
@@ -959,7 +965,9 @@ def run_batch(args):
         stacks.append({"b": b, "ks": ks, "solver": solver, "rhs": torch.from_numpy(rhs).to(dev),
                        "x": torch.zeros(nb * bb, dtype=torch.float64, device=dev),
                        "nb": nb, "nnzb": int(ci.size), "levels": solver.num_levels,
-                       "colours": msp.msp_level_info(solver.h, 0)[2]})
+                       "colours": msp.msp_level_info(solver.h, 0)[2],
+                       "tiles": [msp.msp_level_tiles(solver.h, l)
+                                 for l in range(solver.num_levels)]})
     torch.cuda.synchronize()
     t_setup_b = time.perf_counter() - t_setup_b
     its_b = {}
@@ -990,7 +998,7 @@ def run_batch(args):
         profile_b = {k: {"launches": v[0], "ms": round(v[1], 2)}
                      for k, v in sorted(msp.msp_stats_get().items(), key=lambda kv: -kv[1][1])[:25]}
         msp.msp_stats_reset()
-    stack_info = [dict({k: st[k] for k in ("b", "nb", "nnzb", "levels", "colours")},
+    stack_info = [dict({k: st[k] for k in ("b", "nb", "nnzb", "levels", "colours", "tiles")},
                        instances=len(st["ks"])) for st in stacks]
     for st in stacks:
         st["solver"].close()

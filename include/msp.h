@@ -107,6 +107,12 @@ typedef struct {
                    * rounds).  > 0: caps each of those loops at this many passes or
                    * rounds; a loop still unfinished then returns MSP_ERR_TIMEOUT.
                    * For tests of the MSP_ERR_TIMEOUT path. */
+  int autotune;   /* 1: at SETUP, time the lanes per row of the AMG levels' ELL colour
+                   * sweeps and restrictions (2, 4 or 8) on the level's own data and keep
+                   * the fastest; the choice is kept per (level, slots per row) for the
+                   * handle's life, so later SETUPs round the same way.  0 (default): the
+                   * fixed choice (one lane per 4 slots).  Changes the rounding of the
+                   * sweeps' row sums, not the operator. */
 } msp_config;
 
 typedef struct {
@@ -222,6 +228,11 @@ int msp_num_levels(msp_handle h);
 
 /* Size, stored nonzeros and colour count of level l (0 colours: level not coloured). */
 int msp_level_info(msp_handle h, int level, int32_t* n, int32_t* nnz, int32_t* ncolours);
+/* Tiles of AMG level `level`: slots per row of its ELL copy (0: swept in CSR form) and the
+ * lanes per row its colour sweeps and its residual restriction use (the autotuner's
+ * choice with msp_config.autotune, else the fixed default).  Any output may be NULL. */
+int msp_level_tiles(msp_handle h, int level, int32_t* ell_slots, int32_t* sweep_lanes,
+                    int32_t* restrict_lanes);
 
 /* Copy level l to HOST arrays (any may be NULL): perm[n] (colour-ordered index ->
  * index before colouring: the natural block row for l = 0, the aggregate number for

@@ -8,7 +8,7 @@ ctypes binding (``_native``) plus a small convenience wrapper (``Solver``).
 from __future__ import annotations
 
 from . import _native
-from ._native import (msp_wells_setup_scalar, msp_wells_update_values_scalar,
+from ._native import (msp_level_tiles, msp_wells_setup_scalar, msp_wells_update_values_scalar,
                       msp_wells_pack_rhs, msp_wells_unpack,MSP_NOT_CONVERGED, MSP_OK, MSP_PREC_MSP, MSP_PREC_N_ONLY, MSP_PREC_NONE,
                       MSP_PREC_P_ONLY, MSP_PREC_R_ONLY, MSP_PRECISION_FP32, MSP_PRECISION_FP64,
                       MSP_COLOURING_ALG41, MSP_COLOURING_JP, MSP_SMOOTHER_PGS_MC,
@@ -27,7 +27,7 @@ from ._native import (msp_wells_setup_scalar, msp_wells_update_values_scalar,
                       msp_set_instances, msp_solve_batch, msp_stage_values_host,
                       msp_update_values_staged)
 
-__all__ = ["Solver", "Wells", "ScalarWells", "WellEliminatedSolver",
+__all__ = ["msp_level_tiles", "Solver", "Wells", "ScalarWells", "WellEliminatedSolver",
            "msp_wells_setup_scalar", "msp_wells_update_values_scalar", "msp_wells_pack_rhs",
            "msp_wells_unpack", "Server", "BatchSolver",
            "stack_block_diagonal", "msp_set_instances", "msp_solve_batch", "MspError",

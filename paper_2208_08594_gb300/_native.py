@@ -37,7 +37,7 @@ EXPORTS = ("msp_config_default", "msp_setup", "msp_update_values", "msp_update_v
            "msp_server_free", "msp_set_instances", "msp_solve_batch",
            "msp_stage_values_host", "msp_update_values_staged", "msp_fma_rate",
            "msp_wells_setup_scalar", "msp_wells_update_values_scalar", "msp_wells_pack_rhs",
-           "msp_wells_unpack")
+           "msp_wells_unpack", "msp_level_tiles")
 
 # largest n accepted by msp_vertices_grouping_noalloc (size of its fixed scratch)
 NOALLOC_MAX_VERTICES = 1 << 16
@@ -50,7 +50,7 @@ class MspConfig(C.Structure):
                 ("bilu_order", C.c_int), ("precond", C.c_int), ("max_levels", C.c_int),
                 ("beta", C.c_double), ("agg_seed", C.c_ulonglong),
                 ("coarse_hard_max", C.c_int), ("precision", C.c_int), ("colouring", C.c_int),
-                ("smoother", C.c_int), ("loop_limit", C.c_int)]
+                ("smoother", C.c_int), ("loop_limit", C.c_int), ("autotune", C.c_int)]
 
 
 class MspSolveInfo(C.Structure):
@@ -133,6 +133,7 @@ def lib(build_if_missing: bool = True):
     L.msp_spmv.argtypes = [P, P, P, P]
     L.msp_num_levels.argtypes = [P]
     L.msp_level_info.argtypes = [P, I, P, P, P]
+    L.msp_level_tiles.argtypes = [P, I, P, P, P]
     L.msp_level_get.argtypes = [P, I, P, P, P, P, P, P]
     L.msp_colour0.argtypes = [P, P]
     L.msp_last_error.argtypes = []
@@ -301,6 +302,15 @@ def msp_level_info(h, level):
     if st != MSP_OK:
         raise MspError(st, "msp_level_info")
     return n.value, nnz.value, nc.value
+
+
+def msp_level_tiles(h, level):
+    """(ELL slots per row, sweep lanes per row, restriction lanes per row) of a level."""
+    k, g, r = C.c_int32(), C.c_int32(), C.c_int32()
+    st = lib().msp_level_tiles(h, level, C.byref(k), C.byref(g), C.byref(r))
+    if st != MSP_OK:
+        raise MspError(st, "msp_level_tiles")
+    return k.value, g.value, r.value
 
 
 def msp_level_get(h, level):

@@ -30,12 +30,16 @@ int launch_bsr_col0_update(int b, int nb, const int* rp, const int* ci, const T*
 template <typename T>
 int launch_extract_col0(size_t nnzb, int b, const T* v, T* c0, cudaStream_t s);
 // stage N: one block-GS sweep over the rows [r0, r1) of one colour on the (b-1)x(b-1)
-// sub-blocks aN; reads/writes the concentration slots of w (stride b); lower_only for
-// the first sweep from zero (later colours still hold zero).
+// sub-blocks aN, pre-scaled by their row's D_N,i^-1, from y = D_N^-1 g (launch_nscale);
+// reads/writes the concentration slots of w (stride b); lower_only for the first sweep
+// from zero (later colours still hold zero).
 template <typename T>
 int launch_bgs_colour(int b, int r0, int r1, const int* rp, const int* ci, const int* dpos,
-                      const T* aN, const T* dNinv, const T* g, T* w, bool lower_only,
-                      bool zero_pressure, cudaStream_t s, const unsigned char* rmask = nullptr);
+                      const T* aN, const T* y, T* w, bool lower_only, bool zero_pressure,
+                      cudaStream_t s, const unsigned char* rmask = nullptr);
+// y[i*(b-1) + r] = (D_N,i^-1 g_i)[r] over the concentration unknowns of every block row
+template <typename T>
+int launch_nscale(int b, int nb, const T* dNinv, const T* g, T* y, cudaStream_t s);
 // stage R: forward y_i = r_i - sum_{j<i} L_ij y_j and backward x_i = U_ii^-1 (y_i -
 // sum_{j>i} U_ij x_j); the backward sweep also adds x_i into w.
 template <typename T>
@@ -62,18 +66,23 @@ int launch_csr_gs_colour(int r0, int r1, const int* rp, const int* ci, const T* 
 // the same sweep over the ELL copy of the level (K in {8, 16, 24, 32} slots per row, slot
 // k of row i at i*K + k; meta from launch_build_ell; rows with meta < 0 use rp/ci/v);
 // pdl: launched as a programmatic dependent of the previous kernel (constant operands are
-// loaded before it waits for that kernel)
+// loaded before it waits for that kernel); tpr: lanes per row (2, 4 or 8 with at most 8
+// slots per lane; 0: the default for K, ell_default_tpr)
 template <typename T>
 int launch_ell_gs_colour(int K, int r0, int r1, const int* ell_ci, const T* ell_v,
                          const int* meta, const int* rp, const int* ci, const T* v,
                          const int* dpos, const T* rdiag, const T* b, T* x, bool lower_only,
-                         cudaStream_t s, const unsigned char* rmask = nullptr, bool pdl = false);
+                         cudaStream_t s, const unsigned char* rmask = nullptr, bool pdl = false,
+                         int tpr = 0);
 // the same restriction over the ELL copy of the level (diag: a_ii of every row)
 template <typename T>
 int launch_ell_residual_restrict(int K, int nc, const int* mptr, const int* members,
                                  const int* ell_ci, const T* ell_v, const int* meta,
                                  const T* diag, const int* rp, const int* ci, const T* v,
-                                 const T* b, const T* x, T* bc, cudaStream_t s);
+                                 const T* b, const T* x, T* bc, cudaStream_t s,
+                                 const unsigned char* cmask = nullptr, int tpr = 0);
+int ell_default_tpr(int K);
+bool ell_tpr_ok(int K, int tpr);
 // PJAC-NO and PGS-NO sweeps in storage order (x0: the values at the start of the sweep,
 // a separate copy; PGS-NO sweeps chunks of 16 consecutive rows)
 template <typename T>
@@ -86,10 +95,11 @@ int launch_pgs_no_sweep(int n, const int* rp, const int* ci, const T* v, const i
 template <typename T>
 int launch_csr_residual_restrict(int nc, const int* mptr, const int* members, const int* rp,
                                  const int* ci, const T* v, const T* b, const T* x, T* bc,
-                                 int avg_row, cudaStream_t s);
-// x_i += xc[agg[i]]
+                                 int avg_row, cudaStream_t s, const unsigned char* cmask = nullptr);
+// x_i += xc[agg[i]] (fmask: only the rows with fmask[i] != 0)
 template <typename T>
-int launch_prolong_add(int n, const int* agg, const T* xc, T* x, cudaStream_t s);
+int launch_prolong_add(int n, const int* agg, const T* xc, T* x, cudaStream_t s,
+                       const unsigned char* fmask = nullptr);
 // x = Ainv b (dense row-major n x n, FP64); b, x in the level's value type
 template <typename T>
 int launch_dense_gemv(int n, const double* Ainv, const T* b, T* x, cudaStream_t s);

@@ -275,6 +275,14 @@ __global__ void map_kernel(int n, const int* __restrict__ m, const int* __restri
     out[i] = m[in[i]];
 }
 
+// inst_c[agg[i]] = inst_f[i]: an aggregate's members all belong to one instance (the
+// matrix is block diagonal over the instances, so no pair crosses two of them)
+__global__ void inst_scatter_kernel(int n, const int* __restrict__ agg,
+                                    const int* __restrict__ inst_f, int* __restrict__ inst_c) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    inst_c[agg[i]] = inst_f[i];
+}
+
 __global__ void member_keys_kernel(int n, const int* __restrict__ agg, unsigned long long* keys) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     keys[i] = ((unsigned long long)(unsigned)agg[i] << 32) | (unsigned)i;
@@ -345,6 +353,7 @@ struct Level {
   // ELL copy of the off-diagonal entries for the colour sweeps (ell_k slots per row; 0:
   // the level is swept in CSR form)
   int ell_k = 0;
+  int gs_tpr = 0, rr_tpr = 0;  // lanes per row of the ELL sweep / restriction (0: default)
   DevBuf<int> ell_ci, ell_meta;
   DevBuf<double> ell_v, ell_diag;
   // FP32 copies (mixed precision)
@@ -352,6 +361,10 @@ struct Level {
   // work vectors (t: the start values of a PJAC-NO / PGS-NO sweep)
   DevBuf<double> b64, x64, t64;
   DevBuf<float> b32, x32, t32;
+  // batched instances (levels >= 1): the instance of every row and the rows of the
+  // instances still iterating
+  DevBuf<int> row_inst;
+  DevBuf<unsigned char> rmask;
 };
 
 }  // namespace
@@ -391,6 +404,8 @@ struct msp_handle_s {
   // preconditioner work vectors
   msp::DevBuf<double> pr, py, px;
   msp::DevBuf<float> g32, w32, pr32, py32, px32;
+  msp::DevBuf<double> ny;    // stage N: D_N^-1 g, nb * (b - 1)
+  msp::DevBuf<float> ny32;
   // Krylov work
   msp::DevBuf<double> V, Z, bperm, xperm, rvec, partial, hdev, nrm, ydev;
   msp::DevBuf<int> ifl;
@@ -406,6 +421,8 @@ struct msp_handle_s {
   bool graph_timed = false;      // captured with event nodes around every site
   std::vector<msp::GraphProbe> graph_probes;
   msp::DevBuf<double> pg64, pw64;
+  // autotuned lanes per row of the ELL kernels, per (level, slots per row)
+  std::map<std::pair<int, int>, std::pair<int, int>> tuned;
   // adaptive setup
   int setup_calls = 0;
   int prev_it = -1;
@@ -689,6 +706,11 @@ int level_extras(msp_handle h, Level& L, bool smoothed, bool ell, cudaStream_t s
   }
   MSP_TRY(L.b64.alloc(L.A.n));
   MSP_TRY(L.x64.alloc(L.A.n));
+  // zero from the start: with batched instances the rows of an instance that never
+  // iterates are never written, and the coarsest level's dense product reads every row
+  // (times exact zeros in the inverse, which must not meet a NaN bit pattern)
+  MSP_CUDA_TRY(cudaMemsetAsync(L.b64.p, 0, sizeof(double) * L.A.n, s));
+  MSP_CUDA_TRY(cudaMemsetAsync(L.x64.p, 0, sizeof(double) * L.A.n, s));
   const bool copies = smoothed && h->cfg.smoother != MSP_SMOOTHER_PGS_MC;
   if (copies) MSP_TRY(L.t64.alloc(L.A.n));
   if (h->cfg.precision == MSP_PRECISION_FP32) {
@@ -704,6 +726,8 @@ int level_extras(msp_handle h, Level& L, bool smoothed, bool ell, cudaStream_t s
     }
     MSP_TRY(L.b32.alloc(L.A.n));
     MSP_TRY(L.x32.alloc(L.A.n));
+    MSP_CUDA_TRY(cudaMemsetAsync(L.b32.p, 0, sizeof(float) * L.A.n, s));
+    MSP_CUDA_TRY(cudaMemsetAsync(L.x32.p, 0, sizeof(float) * L.A.n, s));
     if (copies) MSP_TRY(L.t32.alloc(L.A.n));
   }
   return MSP_OK;
@@ -752,6 +776,28 @@ int coarse_inverse(msp_handle h, const DCsr& C, cudaStream_t s) {
 // ---------------------------------------------------------------------------------
 // value setup: decoupling, AMG hierarchy, stage N, BILU(0)
 // ---------------------------------------------------------------------------------
+int autotune_levels(msp_handle h, cudaStream_t s);
+
+// Batched instances: the instance of every row of the AMG levels below level 0 and their
+// row masks (all rows on), so that the coarse levels too skip the instances that have left
+// the active set.
+int batch_level_masks(msp_handle h, cudaStream_t s) {
+  if (!h->batch || !h->row_inst.p) return MSP_OK;
+  const int* inst = h->row_inst.p;
+  for (size_t l = 0; l + 1 < h->levels.size(); ++l) {
+    Level& F = h->levels[l];
+    Level& C = h->levels[l + 1];
+    MSP_TRY(C.row_inst.alloc(C.A.n));
+    MSP_TRY(C.rmask.alloc(C.A.n));
+    inst_scatter_kernel<<<grid1(F.A.n), kThreads, 0, s>>>(F.A.n, F.agg.p, inst, C.row_inst.p);
+    MSP_TRY(launch_status());
+    MSP_CUDA_TRY(cudaMemsetAsync(C.rmask.p, 1, C.A.n, s));
+    inst = C.row_inst.p;
+  }
+  MSP_CUDA_TRY(cudaStreamSynchronize(s));
+  return MSP_OK;
+}
+
 int value_setup(msp_handle h, cudaStream_t s) {
   NvtxRange nvtx("msp:value_setup");
   const int nb = h->nb, b = h->b, bb = b * b, bn = b - 1;
@@ -881,6 +927,9 @@ int value_setup(msp_handle h, cudaStream_t s) {
     MSP_TRY(h->dNinv.alloc((size_t)nb * bn * bn));
     MSP_TRY(launch_extract_N(b, nnzb, h->vals.p, h->aN.p, s));
     MSP_TRY(launch_diagN_inverse(b, nb, h->dpos.p, h->vals.p, h->dNinv.p, h->flags.p, s));
+    // the sweeps read D_N,i^-1 A_ij (the row's diagonal inverse applied once here, not in
+    // every sweep); a singular diagonal sub-block stops the setup at the flag check below
+    MSP_TRY(launch_scale_N_rows(b, nb, h->rp.p, h->dpos.p, h->dNinv.p, h->aN.p, s));
   }
   // stage R: BILU(0) in colour order
   Probe pr_bilu("setup:bilu_factor", 0.0, s);
@@ -908,6 +957,8 @@ int value_setup(msp_handle h, cudaStream_t s) {
   }
   MSP_CUDA_TRY(cudaStreamSynchronize(s));
   h->setup_calls++;
+  MSP_TRY(batch_level_masks(h, s));
+  if (cfg.autotune) MSP_TRY(autotune_levels(h, s));
   h->setup_valid = true;
   return MSP_OK;
 }
@@ -922,8 +973,11 @@ struct PView {
   std::vector<const T*> lv, lrd, lev, led;
   std::vector<T*> lb, lx, lt;
   T *r, *y, *x;
+  T* ny;  // stage N: D_N^-1 g
   // level-0 rows to skip (instances of a batch that left the active set), or nullptr
   const unsigned char* m0 = nullptr;
+  // the same per AMG level (lm[0] = m0), or nullptrs
+  std::vector<const unsigned char*> lm;
 };
 
 PView<double> view64(msp_handle h) {
@@ -947,7 +1001,10 @@ PView<double> view64(msp_handle h) {
   p.r = h->pr.p;
   p.y = h->py.p;
   p.x = h->px.p;
+  p.ny = h->ny.p;
   p.m0 = h->batch ? h->rmask0.p : nullptr;
+  for (size_t l = 0; l < h->levels.size(); ++l)
+    p.lm.push_back(l == 0 ? p.m0 : (h->batch && h->levels[l].rmask.p ? h->levels[l].rmask.p : nullptr));
   return p;
 }
 
@@ -972,12 +1029,102 @@ PView<float> view32(msp_handle h) {
   p.r = h->pr32.p;
   p.y = h->py32.p;
   p.x = h->px32.p;
+  p.ny = h->ny32.p;
   p.m0 = h->batch ? h->rmask0.p : nullptr;
+  for (size_t l = 0; l < h->levels.size(); ++l)
+    p.lm.push_back(l == 0 ? p.m0 : (h->batch && h->levels[l].rmask.p ? h->levels[l].rmask.p : nullptr));
   return p;
 }
 
 // algorithmic bytes of one colour sweep launch over rows [r0, r1) reading `entries`
 // nonzeros of `eb` bytes each (value + column index) plus `rowb` bytes per row
+// The tile autotuner (msp_config.autotune): for every AMG level swept over its ELL copy,
+// time a full colour sweep and the residual restriction with 2, 4 and 8 lanes per row
+// (those with at most 8 slots per lane) on the level's own matrix, with CUDA events on the
+// solver stream (best of three), and keep the fastest.  A choice is made once per (level,
+// slots per row) and kept for the handle's life, so later SETUPs round the same way.  The
+// level's work vectors are zeroed before and after.
+template <typename T>
+int autotune_levels_t(msp_handle h, const PView<T>& P, cudaStream_t s) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  MSP_CUDA_TRY(cudaEventCreate(&e0));
+  MSP_CUDA_TRY(cudaEventCreate(&e1));
+  int st = MSP_OK;
+  auto time_it = [&](auto&& launch, float* best) -> int {
+    *best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, s);
+      MSP_TRY(launch());
+      cudaEventRecord(e1, s);
+      MSP_CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      MSP_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep > 0 && ms < *best) *best = ms;  // the first run warms the caches
+    }
+    return MSP_OK;
+  };
+  for (size_t l = 0; l + 1 < h->levels.size() && st == MSP_OK; ++l) {
+    Level& L = h->levels[l];
+    if (L.ell_k <= 0 || L.cptr.size() < 2) continue;
+    const auto key = std::make_pair((int)l, L.ell_k);
+    auto it = h->tuned.find(key);
+    if (it != h->tuned.end()) {
+      L.gs_tpr = it->second.first;
+      L.rr_tpr = it->second.second;
+      continue;
+    }
+    const int n = L.A.n, g = (int)L.cptr.size() - 1;
+    int best_gs = ell_default_tpr(L.ell_k), best_rr = best_gs;
+    float t_gs = 1e30f, t_rr = 1e30f;
+    for (int tpr : {2, 4, 8}) {
+      if (!ell_tpr_ok(L.ell_k, tpr)) continue;
+      MSP_CUDA_TRY(cudaMemsetAsync(P.lx[l], 0, sizeof(T) * n, s));
+      MSP_CUDA_TRY(cudaMemsetAsync(P.lb[l], 0, sizeof(T) * n, s));
+      float t = 0.0f;
+      st = time_it([&]() -> int {
+        for (int c = 0; c < g; ++c)
+          MSP_TRY(launch_ell_gs_colour<T>(L.ell_k, L.cptr[c], L.cptr[c + 1], L.ell_ci.p,
+                                          P.lev[l], L.ell_meta.p, L.A.rp.p, L.A.ci.p, P.lv[l],
+                                          L.dpos.p, P.lrd[l], P.lb[l], P.lx[l], false, s,
+                                          nullptr, false, tpr));
+        return MSP_OK;
+      }, &t);
+      if (st != MSP_OK) break;
+      if (t < t_gs) {
+        t_gs = t;
+        best_gs = tpr;
+      }
+      st = time_it([&]() -> int {
+        return launch_ell_residual_restrict<T>(L.ell_k, L.nc, L.mptr.p, L.members.p, L.ell_ci.p,
+                                               P.lev[l], L.ell_meta.p, P.led[l], L.A.rp.p,
+                                               L.A.ci.p, P.lv[l], P.lb[l], P.lx[l],
+                                               P.lb[l + 1], s, nullptr, tpr);
+      }, &t);
+      if (st != MSP_OK) break;
+      if (t < t_rr) {
+        t_rr = t;
+        best_rr = tpr;
+      }
+    }
+    cudaMemsetAsync(P.lx[l], 0, sizeof(T) * n, s);
+    cudaMemsetAsync(P.lb[l], 0, sizeof(T) * n, s);
+    cudaMemsetAsync(P.lb[l + 1], 0, sizeof(T) * h->levels[l + 1].A.n, s);
+    if (st != MSP_OK) break;
+    L.gs_tpr = best_gs;
+    L.rr_tpr = best_rr;
+    h->tuned[key] = {best_gs, best_rr};
+  }
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
+
+int autotune_levels(msp_handle h, cudaStream_t s) {
+  if (h->cfg.precision == MSP_PRECISION_FP32) return autotune_levels_t<float>(h, view32(h), s);
+  return autotune_levels_t<double>(h, view64(h), s);
+}
+
 inline double sweep_bytes(int r0, int r1, long long entries, double eb, double rowb) {
   return (double)entries * eb + (double)(r1 - r0) * rowb;
 }
@@ -1019,11 +1166,11 @@ int vcycle(msp_handle h, const PView<T>& P, int l, cudaStream_t s) {
     if (use_ell(c, lower_only))
       return launch_ell_gs_colour<T>(L.ell_k, L.cptr[c], L.cptr[c + 1], L.ell_ci.p, P.lev[l],
                                      L.ell_meta.p, L.A.rp.p, L.A.ci.p, P.lv[l], L.dpos.p,
-                                     P.lrd[l], P.lb[l], P.lx[l], lower_only, s,
-                                     l == 0 ? P.m0 : nullptr, overlap(c));
+                                     P.lrd[l], P.lb[l], P.lx[l], lower_only, s, P.lm[l],
+                                     overlap(c), L.gs_tpr);
     return launch_csr_gs_colour<T>(L.cptr[c], L.cptr[c + 1], L.A.rp.p, L.A.ci.p, P.lv[l],
                                    L.dpos.p, P.lrd[l], P.lb[l], P.lx[l], lower_only, avg_row, s,
-                                   l == 0 ? P.m0 : nullptr);
+                                   P.lm[l]);
   };
   // one smoothing phase: its colour launches in order, timed in runs of one kernel
   struct SweepLaunch {
@@ -1083,18 +1230,18 @@ int vcycle(msp_handle h, const PView<T>& P, int l, cudaStream_t s) {
       MSP_TRY(launch_ell_residual_restrict<T>(L.ell_k, L.nc, L.mptr.p, L.members.p, L.ell_ci.p,
                                               P.lev[l], L.ell_meta.p, P.led[l], L.A.rp.p,
                                               L.A.ci.p, P.lv[l], P.lb[l], P.lx[l], P.lb[l + 1],
-                                              s));
+                                              s, P.lm[l + 1], L.rr_tpr));
     } else {
       Probe pr(level_site("amg_residual_restrict_csr_l", l), bytes, s);
       MSP_TRY(launch_csr_residual_restrict<T>(L.nc, L.mptr.p, L.members.p, L.A.rp.p,
                                               L.A.ci.p, P.lv[l], P.lb[l], P.lx[l], P.lb[l + 1],
-                                              avg_row, s));
+                                              avg_row, s, P.lm[l + 1]));
     }
   }
   MSP_TRY(vcycle<T>(h, P, l + 1, s));
   {
     Probe pr("amg_prolong", (double)n * (3 * sT + 4), s);
-    MSP_TRY(launch_prolong_add<T>(n, L.agg.p, P.lx[l + 1], P.lx[l], s));
+    MSP_TRY(launch_prolong_add<T>(n, L.agg.p, P.lx[l + 1], P.lx[l], s, P.lm[l]));
   }
   if (natural) {
     for (int sw = 0; sw < h->cfg.post_sweeps; ++sw) MSP_TRY(natural_sweep(false, false));
@@ -1115,20 +1262,25 @@ int stage_N(msp_handle h, const PView<T>& P, const T* g, T* w, cudaStream_t s) {
     return MSP_OK;
   }
   const double sT = sizeof(T), bn = b - 1;
+  // FP64 flops are recorded: the FP64 FMA rate can bind these kernels, the FP32 one cannot
+  {
+    Probe pr("stageN_scale", (double)h->nb * (bn * bn + 2 * bn) * sT, s, 1,
+             sT == 8 ? 2.0 * (double)h->nb * bn * bn : 0.0);
+    MSP_TRY(launch_nscale<T>(b, h->nb, P.dNinv, g, P.ny, s));
+  }
   double bytes = 0.0, fmas = 0.0;
   for (int sw = 0; sw < h->cfg.bgs_sweeps; ++sw)
     for (int c = 0; c < h->g0; ++c) {
       const long long used = h->cc0.lower[c] + (sw == 0 ? 0 : h->cc0.upper[c]);
       bytes += sweep_bytes(h->cptr0[c], h->cptr0[c + 1], used, bn * bn * sT + 4,
-                           (2 * bn + 1 + bn * bn) * sT + 12);
-      fmas += (double)(used + (h->cptr0[c + 1] - h->cptr0[c])) * bn * bn;
+                           (2 * bn + 1) * sT + 12);
+      fmas += (double)used * bn * bn;
     }
-  // FP64 flops are recorded: the FP64 FMA rate can bind these kernels, the FP32 one cannot
   Probe pr("stageN_bgs_sweep", bytes, s, h->cfg.bgs_sweeps * h->g0, sT == 8 ? 2.0 * fmas : 0.0);
   for (int sw = 0; sw < h->cfg.bgs_sweeps; ++sw)
     for (int c = 0; c < h->g0; ++c)
       MSP_TRY(launch_bgs_colour<T>(b, h->cptr0[c], h->cptr0[c + 1], h->rp.p, h->ci.p, h->dpos.p,
-                                   P.aN, P.dNinv, g, w, sw == 0, sw == 0, s, P.m0));
+                                   P.aN, P.ny, w, sw == 0, sw == 0, s, P.m0));
   return MSP_OK;
 }
 
@@ -1339,7 +1491,11 @@ int alloc_work(msp_handle h) {
   MSP_TRY(h->px.alloc(n));
   MSP_TRY(h->pg64.alloc(n));
   MSP_TRY(h->pw64.alloc(n));
-  if (h->cfg.precision == MSP_PRECISION_FP64) MSP_TRY(h->c0.alloc((size_t)h->nnzb * h->b));
+  const size_t nN = (size_t)h->nb * std::max(1, h->b - 1);
+  if (h->cfg.precision == MSP_PRECISION_FP64) {
+    MSP_TRY(h->c0.alloc((size_t)h->nnzb * h->b));
+    MSP_TRY(h->ny.alloc(nN));
+  }
   if (h->cfg.precision == MSP_PRECISION_FP32) {
     MSP_TRY(h->c0_32.alloc((size_t)h->nnzb * h->b));
     MSP_TRY(h->g32.alloc(n));
@@ -1347,6 +1503,7 @@ int alloc_work(msp_handle h) {
     MSP_TRY(h->pr32.alloc(n));
     MSP_TRY(h->py32.alloc(n));
     MSP_TRY(h->px32.alloc(n));
+    MSP_TRY(h->ny32.alloc(nN));
     MSP_TRY(h->vals32.alloc((size_t)h->nnzb * h->b * h->b));
   }
   MSP_TRY(h->V.alloc((size_t)(m + 1) * n));
@@ -1653,6 +1810,10 @@ int fgmres_batched(msp_handle h, double tol, std::vector<int>& its, std::vector<
   auto upload_act = [&](const std::vector<int>& a) -> int {
     MSP_CUDA_TRY(cudaMemcpyAsync(h->bact.p, a.data(), B * sizeof(int), cudaMemcpyHostToDevice, s));
     MSP_TRY(launch_expand_mask(h->nb, h->row_inst.p, h->bact.p, h->rmask0.p, s));
+    for (size_t l = 1; l < h->levels.size(); ++l) {
+      Level& L = h->levels[l];
+      if (L.rmask.p) MSP_TRY(launch_expand_mask(L.A.n, L.row_inst.p, h->bact.p, L.rmask.p, s));
+    }
     // the host vector may change before the copy runs: wait for it
     MSP_CUDA_TRY(cudaStreamSynchronize(s));
     return MSP_OK;
@@ -1919,7 +2080,7 @@ bool config_ok(const msp_config& c, int b) {
          (c.precision == MSP_PRECISION_FP64 || c.precision == MSP_PRECISION_FP32) &&
          (c.colouring == MSP_COLOURING_ALG41 || c.colouring == MSP_COLOURING_JP) &&
          c.smoother >= MSP_SMOOTHER_PGS_MC && c.smoother <= MSP_SMOOTHER_PGS_NO &&
-         c.loop_limit >= 0 && b >= 1 &&
+         c.loop_limit >= 0 && (c.autotune == 0 || c.autotune == 1) && b >= 1 &&
          b <= 8;
 }
 
@@ -1951,6 +2112,7 @@ int msp_config_default(msp_config* c) {
   c->colouring = MSP_COLOURING_ALG41;
   c->smoother = MSP_SMOOTHER_PGS_MC;
   c->loop_limit = 0;
+  c->autotune = 0;
   return MSP_OK;
 }
 
@@ -2309,9 +2471,10 @@ int msp_set_instances(msp_handle h, int32_t count, const int32_t* h_row_offsets)
     MSP_CUDA_TRY(cudaMemcpy(h->row_inst.p, rinst.data(), sizeof(int) * (size_t)nb,
                             cudaMemcpyHostToDevice));
     MSP_CUDA_TRY(cudaMemset(h->rmask0.p, 1, nb));
-    drop_graph(h);  // the preconditioner graph is captured again with the row mask
+    drop_graph(h);  // the preconditioner graph is captured again with the row masks
     h->seg_n = nchunks;
     h->batch = count;
+    MSP_TRY(batch_level_masks(h, s));
     h->batch_offsets = offs;
     return MSP_OK;
   } catch (...) {
@@ -2394,6 +2557,17 @@ int msp_level_info(msp_handle h, int level, int32_t* n, int32_t* nnz, int32_t* n
   if (n) *n = L.A.n;
   if (nnz) *nnz = L.A.nnz;
   if (ncolours) *ncolours = L.cptr.empty() ? 0 : (int)L.cptr.size() - 1;
+  return MSP_OK;
+}
+
+int msp_level_tiles(msp_handle h, int level, int32_t* ell_slots, int32_t* sweep_lanes,
+                    int32_t* restrict_lanes) {
+  if (!h || level < 0 || level >= (int)h->levels.size()) return MSP_ERR_ARG;
+  const Level& L = h->levels[level];
+  if (ell_slots) *ell_slots = L.ell_k;
+  const int def = L.ell_k > 0 ? ell_default_tpr(L.ell_k) : 0;
+  if (sweep_lanes) *sweep_lanes = L.gs_tpr ? L.gs_tpr : def;
+  if (restrict_lanes) *restrict_lanes = L.rr_tpr ? L.rr_tpr : def;
   return MSP_OK;
 }
 

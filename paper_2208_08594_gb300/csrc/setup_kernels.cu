@@ -101,6 +101,36 @@ __global__ void extract_N_kernel(int b, size_t nnzb, const double* __restrict__ 
   }
 }
 
+// Stage N works with the concentration sub-blocks scaled by the inverse of their row's
+// diagonal sub-block: aN[p] <- D_N,i^-1 aN[p] for the off-diagonal blocks p of row i (the
+// diagonal block is left as it is and never read by the sweeps).  One thread per row.
+template <int BN>
+__global__ void scale_N_rows_kernel(int nb, const int* __restrict__ rp, const int* __restrict__ dpos,
+                                    const double* __restrict__ dNinv, double* __restrict__ aN) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
+    double D[BN * BN];
+#pragma unroll
+    for (int e = 0; e < BN * BN; ++e) D[e] = dNinv[(size_t)i * BN * BN + e];
+    const int pd = dpos[i];
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      if (p == pd) continue;
+      double* a = aN + (size_t)p * BN * BN;
+      double in[BN * BN];
+#pragma unroll
+      for (int e = 0; e < BN * BN; ++e) in[e] = a[e];
+#pragma unroll
+      for (int r = 0; r < BN; ++r)
+#pragma unroll
+        for (int c = 0; c < BN; ++c) {
+          double t = 0.0;
+#pragma unroll
+          for (int k = 0; k < BN; ++k) t = fma(D[r * BN + k], in[k * BN + c], t);
+          a[r * BN + c] = t;
+        }
+    }
+  }
+}
+
 __global__ void diag_pos_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                 int* __restrict__ dpos) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -570,6 +600,23 @@ int launch_extract_N(int b, size_t nnzb, const double* v, double* aN, cudaStream
   if (b < 2 || !nnzb) return MSP_OK;
   extract_N_kernel<<<grid_for(nnzb * (b - 1) * (b - 1), kThreads), kThreads, 0, s>>>(b, nnzb, v,
                                                                                      aN);
+  return launch_status();
+}
+
+int launch_scale_N_rows(int b, int nb, const int* rp, const int* dpos, const double* dNinv,
+                        double* aN, cudaStream_t s) {
+  if (nb <= 0 || b < 2) return MSP_OK;
+  const unsigned grid = grid_for(nb, kThreads);
+  switch (b - 1) {
+    case 1: scale_N_rows_kernel<1><<<grid, kThreads, 0, s>>>(nb, rp, dpos, dNinv, aN); break;
+    case 2: scale_N_rows_kernel<2><<<grid, kThreads, 0, s>>>(nb, rp, dpos, dNinv, aN); break;
+    case 3: scale_N_rows_kernel<3><<<grid, kThreads, 0, s>>>(nb, rp, dpos, dNinv, aN); break;
+    case 4: scale_N_rows_kernel<4><<<grid, kThreads, 0, s>>>(nb, rp, dpos, dNinv, aN); break;
+    case 5: scale_N_rows_kernel<5><<<grid, kThreads, 0, s>>>(nb, rp, dpos, dNinv, aN); break;
+    case 6: scale_N_rows_kernel<6><<<grid, kThreads, 0, s>>>(nb, rp, dpos, dNinv, aN); break;
+    case 7: scale_N_rows_kernel<7><<<grid, kThreads, 0, s>>>(nb, rp, dpos, dNinv, aN); break;
+    default: return MSP_ERR_ARG;
+  }
   return launch_status();
 }
 

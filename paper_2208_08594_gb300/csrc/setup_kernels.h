@@ -69,6 +69,9 @@ int launch_check_block_diagonal(int nb, const int* rp, const int* ci, const int*
 int launch_gather_values(size_t nnz, int bb, const int* src, const double* in, double* out,
                          cudaStream_t s);
 int launch_extract_N(int b, size_t nnzb, const double* v, double* aN, cudaStream_t s);
+// aN[p] <- D_N,i^-1 aN[p] for every off-diagonal block p of row i (stage N pre-scaling)
+int launch_scale_N_rows(int b, int nb, const int* rp, const int* dpos, const double* dNinv,
+                        double* aN, cudaStream_t s);
 int launch_diag_pos(int n, const int* rp, const int* ci, int* dpos, cudaStream_t s);
 // Jones-Plassmann priority keys of a symmetric graph (larger degree first, then the high
 // word of SplitMix64(v ^ seed)); idx[v] = v for a stable key-value sort

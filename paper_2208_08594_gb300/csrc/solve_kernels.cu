@@ -225,8 +225,8 @@ __global__ void extract_col0_kernel(size_t nnzb, int b, const T* __restrict__ v,
 template <int B, typename T>
 __global__ void __launch_bounds__(kThreads) bgs_colour_kernel(
     int r0, int r1, const int* __restrict__ rp, const int* __restrict__ ci,
-    const int* __restrict__ dpos, const T* __restrict__ aN, const T* __restrict__ dNinv,
-    const T* __restrict__ g, T* __restrict__ w, bool lower_only, bool zero_pressure,
+    const int* __restrict__ dpos, const T* __restrict__ aN, const T* __restrict__ y,
+    T* __restrict__ w, bool lower_only, bool zero_pressure,
     const unsigned char* __restrict__ rmask) {
   constexpr int BN = B - 1;
   // BN lanes per row, packed 32 / BN rows to a warp (b = 4: 10 rows, 30 lanes busy)
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kThreads) bgs_colour_kernel(
     T acc = T(0);
     const bool active = (slot < R) && (i < r1) && (!rmask || rmask[i]);
     if (active) {
-      acc = g[(size_t)i * B + 1 + lane];
+      acc = y[(size_t)i * BN + lane];
       const int p0 = __ldg(rp + i), pd = __ldg(dpos + i), p1 = __ldg(rp + i + 1);
       const int pend = lower_only ? pd : p1;
       // w rows of other colours: none of them is written by this launch
@@ -274,19 +274,31 @@ __global__ void __launch_bounds__(kThreads) bgs_colour_kernel(
         for (int c = 0; c < BN; ++c) acc = fma(-a0[c], x0[c], acc);
       }
     }
-    // x_i = D_N,i^{-1} acc : gather the BN partial results of the row's lanes
-    T out = T(0);
-    const T* di = dNinv + ((size_t)(active ? i : 0) * BN + lane) * BN;
-    const int src = slot * BN;
-#pragma unroll
-    for (int c = 0; c < BN; ++c) {
-      const T ac = __shfl_sync(0xffffffffu, acc, (src + c) & (kWarp - 1));
-      if (active) out = fma(__ldg(di + c), ac, out);
-    }
+    // the blocks are D_N,i^-1 A_ij and y_i = D_N,i^-1 g_i: acc is x_i itself
     if (active) {
-      w[(size_t)i * B + 1 + lane] = out;
+      w[(size_t)i * B + 1 + lane] = acc;
       if (zero_pressure && lane == 0) w[(size_t)i * B] = T(0);
     }
+  }
+}
+
+// y_i = D_N,i^-1 g_i (concentration part of g), once per stage-N application: the sweeps
+// then start every row from y_i and use the pre-scaled blocks
+template <int BN, typename T>
+__global__ void nscale_kernel(int nb, const T* __restrict__ dNinv, const T* __restrict__ g,
+                              T* __restrict__ y) {
+  constexpr int B = BN + 1;
+  const size_t total = (size_t)nb * BN;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = t / BN;
+    const int r = (int)(t % BN);
+    const T* d = dNinv + t * BN;
+    const T* gi = g + i * B + 1;
+    T acc = T(0);
+#pragma unroll
+    for (int c = 0; c < BN; ++c) acc = fma(__ldg(d + c), gi[c], acc);
+    y[t] = acc;
   }
 }
 
@@ -492,7 +504,7 @@ __global__ void __launch_bounds__(kThreads) ell_residual_restrict_kernel(
     const int* __restrict__ ell_ci, const T* __restrict__ ell_v, const int* __restrict__ meta,
     const T* __restrict__ diag, const int* __restrict__ rp, const int* __restrict__ ci,
     const T* __restrict__ v, const T* __restrict__ b, const T* __restrict__ x,
-    T* __restrict__ bc) {
+    T* __restrict__ bc, const unsigned char* __restrict__ cmask) {
   constexpr int kMembers = 4, G = kMembers * TPR, S = (K + TPR - 1) / TPR;
   const int lane = threadIdx.x % G;
   const int ms = lane / TPR, t = lane % TPR;
@@ -500,7 +512,10 @@ __global__ void __launch_bounds__(kThreads) ell_residual_restrict_kernel(
   for (int base = blockIdx.x * gpb; base < nc; base += gridDim.x * gpb) {
     const int I = base + threadIdx.x / G;
     T total = T(0);
-    if (I < nc) {
+    // cmask: aggregates of the batched instances still iterating (the others keep stale
+    // values that no active row reads)
+    const bool live = I < nc && (!cmask || cmask[I]);
+    if (live) {
       const int m0 = __ldg(mptr + I), m1 = __ldg(mptr + I + 1);
       for (int mb = m0 + ms; mb < m1; mb += kMembers) {
         const int i = __ldg(members + mb);
@@ -530,7 +545,7 @@ __global__ void __launch_bounds__(kThreads) ell_residual_restrict_kernel(
       }
     }
     total = group_sum<G>(total);
-    if (I < nc && lane == 0) bc[I] = total;
+    if (live && lane == 0) bc[I] = total;
   }
 }
 
@@ -606,13 +621,15 @@ template <typename T, int TPR>
 __global__ void __launch_bounds__(kThreads) csr_residual_restrict_kernel(
     int nc, const int* __restrict__ mptr, const int* __restrict__ members,
     const int* __restrict__ rp, const int* __restrict__ ci, const T* __restrict__ v,
-    const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ bc) {
+    const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ bc,
+    const unsigned char* __restrict__ cmask) {
   const int lane = threadIdx.x % TPR;
   const int rpb = blockDim.x / TPR;
   for (int base = blockIdx.x * rpb; base < nc; base += gridDim.x * rpb) {
     const int I = base + threadIdx.x / TPR;
     T total = T(0);
-    if (I < nc) {
+    const bool live = I < nc && (!cmask || cmask[I]);
+    if (live) {
       const int m0 = __ldg(mptr + I), m1 = __ldg(mptr + I + 1);
       for (int m = m0; m < m1; ++m) {
         const int i = __ldg(members + m);
@@ -623,15 +640,15 @@ __global__ void __launch_bounds__(kThreads) csr_residual_restrict_kernel(
       }
     }
     total = group_sum<TPR>(total);
-    if (I < nc && lane == 0) bc[I] = total;
+    if (live && lane == 0) bc[I] = total;
   }
 }
 
 template <typename T>
 __global__ void prolong_add_kernel(int n, const int* __restrict__ agg, const T* __restrict__ xc,
-                                   T* __restrict__ x) {
+                                   T* __restrict__ x, const unsigned char* __restrict__ fmask) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    x[i] += xc[agg[i]];
+    if (!fmask || fmask[i]) x[i] += xc[agg[i]];
 }
 
 // x = Ainv b: four warps per row (interleaved 32-column slices, four accumulators per
@@ -1261,15 +1278,15 @@ int launch_extract_col0(size_t nnzb, int b, const T* v, T* c0, cudaStream_t s) {
 
 template <typename T>
 int launch_bgs_colour(int b, int r0, int r1, const int* rp, const int* ci, const int* dpos,
-                      const T* aN, const T* dNinv, const T* g, T* w, bool lower_only,
-                      bool zero_pressure, cudaStream_t s, const unsigned char* rmask) {
+                      const T* aN, const T* y, T* w, bool lower_only, bool zero_pressure,
+                      cudaStream_t s, const unsigned char* rmask) {
   if (r1 <= r0 || b < 2) return MSP_OK;
   switch (b) {
 #define MSP_BGS_CASE(BB)                                                                   \
   case BB: {                                                                               \
     const unsigned grid = grid_for((size_t)(r1 - r0) * kWarp / (kWarp / (BB - 1)), kThreads); \
-    bgs_colour_kernel<BB, T><<<grid, kThreads, 0, s>>>(r0, r1, rp, ci, dpos, aN, dNinv, g, \
-                                                       w, lower_only, zero_pressure, rmask); \
+    bgs_colour_kernel<BB, T><<<grid, kThreads, 0, s>>>(r0, r1, rp, ci, dpos, aN, y, w,      \
+                                                       lower_only, zero_pressure, rmask);   \
   } break;
     MSP_BGS_CASE(2)
     MSP_BGS_CASE(3)
@@ -1281,6 +1298,23 @@ int launch_bgs_colour(int b, int r0, int r1, const int* rp, const int* ci, const
 #undef MSP_BGS_CASE
     default:
       return MSP_ERR_ARG;
+  }
+  return launch_status();
+}
+
+template <typename T>
+int launch_nscale(int b, int nb, const T* dNinv, const T* g, T* y, cudaStream_t s) {
+  if (nb <= 0 || b < 2) return MSP_OK;
+  const unsigned grid = grid_for((size_t)nb * (b - 1), kThreads);
+  switch (b - 1) {
+    case 1: nscale_kernel<1, T><<<grid, kThreads, 0, s>>>(nb, dNinv, g, y); break;
+    case 2: nscale_kernel<2, T><<<grid, kThreads, 0, s>>>(nb, dNinv, g, y); break;
+    case 3: nscale_kernel<3, T><<<grid, kThreads, 0, s>>>(nb, dNinv, g, y); break;
+    case 4: nscale_kernel<4, T><<<grid, kThreads, 0, s>>>(nb, dNinv, g, y); break;
+    case 5: nscale_kernel<5, T><<<grid, kThreads, 0, s>>>(nb, dNinv, g, y); break;
+    case 6: nscale_kernel<6, T><<<grid, kThreads, 0, s>>>(nb, dNinv, g, y); break;
+    case 7: nscale_kernel<7, T><<<grid, kThreads, 0, s>>>(nb, dNinv, g, y); break;
+    default: return MSP_ERR_ARG;
   }
   return launch_status();
 }
@@ -1367,15 +1401,28 @@ int launch_programmatic(void (*kern)(Args...), unsigned grid, cudaStream_t s, Ac
   return MSP_OK;
 }
 
+// lanes per row of the ELL kernels by default (measured: one lane per 4 slots, 8 at most)
+int ell_default_tpr(int K) { return K <= 8 ? 2 : (K <= 16 ? 4 : 8); }
+
+// the (K, TPR) pairs the ELL kernels are built for: at most 8 slots per lane
+bool ell_tpr_ok(int K, int tpr) {
+  if (tpr != 2 && tpr != 4 && tpr != 8) return false;
+  if (K != 8 && K != 16 && K != 24 && K != 32) return false;
+  return K / tpr <= 8 && tpr <= K;
+}
+
 template <typename T>
 int launch_ell_gs_colour(int K, int r0, int r1, const int* ell_ci, const T* ell_v,
                          const int* meta, const int* rp, const int* ci, const T* v,
                          const int* dpos, const T* rdiag, const T* b, T* x, bool lower_only,
-                         cudaStream_t s, const unsigned char* rmask, bool pdl) {
+                         cudaStream_t s, const unsigned char* rmask, bool pdl, int tpr) {
   if (r1 <= r0) return MSP_OK;
-  switch (K) {
+  if (tpr == 0) tpr = ell_default_tpr(K);
+  if (!ell_tpr_ok(K, tpr)) return MSP_ERR_ARG;
+  const int key = K * 16 + tpr;
+  switch (key) {
 #define MSP_ELL_CASE(KK, TT)                                                                \
-  case KK:                                                                                  \
+  case KK * 16 + TT:                                                                        \
     if (pdl) {                                                                              \
       MSP_TRY(launch_programmatic(ell_gs_colour_kernel<T, KK, TT, true>,                    \
                                   grid_groups(r1 - r0, TT), s, r0, r1, ell_ci, ell_v, meta, \
@@ -1386,8 +1433,14 @@ int launch_ell_gs_colour(int K, int r0, int r1, const int* ell_ci, const T* ell_
     }                                                                                       \
     break;
     MSP_ELL_CASE(8, 2)
+    MSP_ELL_CASE(8, 4)
+    MSP_ELL_CASE(8, 8)
+    MSP_ELL_CASE(16, 2)
     MSP_ELL_CASE(16, 4)
+    MSP_ELL_CASE(16, 8)
+    MSP_ELL_CASE(24, 4)
     MSP_ELL_CASE(24, 8)
+    MSP_ELL_CASE(32, 4)
     MSP_ELL_CASE(32, 8)
 #undef MSP_ELL_CASE
     default:
@@ -1399,11 +1452,11 @@ int launch_ell_gs_colour(int K, int r0, int r1, const int* ell_ci, const T* ell_
 template <typename T>
 int launch_csr_residual_restrict(int nc, const int* mptr, const int* members, const int* rp,
                                  const int* ci, const T* v, const T* b, const T* x, T* bc,
-                                 int avg_row, cudaStream_t s) {
+                                 int avg_row, cudaStream_t s, const unsigned char* cmask) {
   if (nc <= 0) return MSP_OK;
   const int tpr = std::min(8, csr_lanes<T>(avg_row));
   MSP_TPR_SWITCH(tpr, csr_residual_restrict_kernel<T, TPR_><<<grid_groups(nc, TPR_), kThreads, 0, s>>>(
-                          nc, mptr, members, rp, ci, v, b, x, bc));
+                          nc, mptr, members, rp, ci, v, b, x, bc, cmask));
   return launch_status();
 }
 
@@ -1431,17 +1484,26 @@ template <typename T>
 int launch_ell_residual_restrict(int K, int nc, const int* mptr, const int* members,
                                  const int* ell_ci, const T* ell_v, const int* meta,
                                  const T* diag, const int* rp, const int* ci, const T* v,
-                                 const T* b, const T* x, T* bc, cudaStream_t s) {
+                                 const T* b, const T* x, T* bc, cudaStream_t s,
+                                 const unsigned char* cmask, int tpr) {
   if (nc <= 0) return MSP_OK;
-  switch (K) {
+  if (tpr == 0) tpr = ell_default_tpr(K);
+  if (!ell_tpr_ok(K, tpr)) return MSP_ERR_ARG;
+  switch (K * 16 + tpr) {
 #define MSP_ELLR_CASE(KK, TT)                                                               \
-  case KK:                                                                                  \
+  case KK * 16 + TT:                                                                        \
     ell_residual_restrict_kernel<T, KK, TT><<<grid_groups(nc, 4 * TT), kThreads, 0, s>>>(   \
-        nc, mptr, members, ell_ci, ell_v, meta, diag, rp, ci, v, b, x, bc);                \
+        nc, mptr, members, ell_ci, ell_v, meta, diag, rp, ci, v, b, x, bc, cmask);         \
     break;
     MSP_ELLR_CASE(8, 2)
+    MSP_ELLR_CASE(8, 4)
+    MSP_ELLR_CASE(8, 8)
+    MSP_ELLR_CASE(16, 2)
     MSP_ELLR_CASE(16, 4)
+    MSP_ELLR_CASE(16, 8)
+    MSP_ELLR_CASE(24, 4)
     MSP_ELLR_CASE(24, 8)
+    MSP_ELLR_CASE(32, 4)
     MSP_ELLR_CASE(32, 8)
 #undef MSP_ELLR_CASE
     default:
@@ -1451,9 +1513,10 @@ int launch_ell_residual_restrict(int K, int nc, const int* mptr, const int* memb
 }
 
 template <typename T>
-int launch_prolong_add(int n, const int* agg, const T* xc, T* x, cudaStream_t s) {
+int launch_prolong_add(int n, const int* agg, const T* xc, T* x, cudaStream_t s,
+                       const unsigned char* fmask) {
   if (n <= 0) return MSP_OK;
-  prolong_add_kernel<T><<<grid_for(n, kThreads), kThreads, 0, s>>>(n, agg, xc, x);
+  prolong_add_kernel<T><<<grid_for(n, kThreads), kThreads, 0, s>>>(n, agg, xc, x, fmask);
   return launch_status();
 }
 
@@ -1666,8 +1729,9 @@ int launch_scatter_blocks(int nb, int b, const int* perm, const double* in, doub
                                          const T*, T*, T*, cudaStream_t, const unsigned char*); \
   template int launch_extract_col0<T>(size_t, int, const T*, T*, cudaStream_t);             \
   template int launch_bgs_colour<T>(int, int, int, const int*, const int*, const int*,      \
-                                    const T*, const T*, const T*, T*, bool, bool,           \
-                                    cudaStream_t, const unsigned char*);                    \
+                                    const T*, const T*, T*, bool, bool, cudaStream_t,       \
+                                    const unsigned char*);                                  \
+  template int launch_nscale<T>(int, int, const T*, const T*, T*, cudaStream_t);            \
   template int launch_bilu_fwd<T>(int, int, int, const int*, const int*, const int*,        \
                                   const T*, const T*, T*, cudaStream_t, const unsigned char*); \
   template int launch_bilu_bwd<T>(int, int, int, const int*, const int*, const int*,        \
@@ -1680,19 +1744,20 @@ int launch_scatter_blocks(int nb, int b, const int* perm, const double* in, doub
   template int launch_ell_gs_colour<T>(int, int, int, const int*, const T*, const int*,      \
                                        const int*, const int*, const T*, const int*,      \
                                        const T*, const T*, T*, bool, cudaStream_t,        \
-                                       const unsigned char*, bool);                       \
+                                       const unsigned char*, bool, int);                  \
   template int launch_ell_residual_restrict<T>(int, int, const int*, const int*, const int*, \
                                                const T*, const int*, const T*, const int*,  \
                                                const int*, const T*, const T*, const T*, T*, \
-                                               cudaStream_t);                               \
+                                               cudaStream_t, const unsigned char*, int);                               \
   template int launch_jacobi_sweep<T>(int, const int*, const int*, const T*, const int*,    \
                                       const T*, const T*, const T*, T*, cudaStream_t);      \
   template int launch_pgs_no_sweep<T>(int, const int*, const int*, const T*, const int*,    \
                                       const T*, const T*, const T*, T*, bool, cudaStream_t); \
   template int launch_csr_residual_restrict<T>(int, const int*, const int*, const int*,     \
                                                const int*, const T*, const T*, const T*,    \
-                                               T*, int, cudaStream_t);                      \
-  template int launch_prolong_add<T>(int, const int*, const T*, T*, cudaStream_t);          \
+                                               T*, int, cudaStream_t, const unsigned char*);                       \
+  template int launch_prolong_add<T>(int, const int*, const T*, T*, cudaStream_t,             \
+                                     const unsigned char*);          \
   template int launch_dense_gemv<T>(int, const double*, const T*, T*, cudaStream_t);
 MSP_INST(double)
 MSP_INST(float)

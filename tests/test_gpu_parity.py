@@ -422,3 +422,39 @@ def test_bounded_setup_loops_return_timeout():
     assert msp._native.lib().msp_free(s.h) == 0
     s.h = None
     torch.cuda.synchronize()  # the context is still usable
+
+
+def test_autotuned_tiles_match_oracle_and_persist():
+    """msp_config.autotune: the lanes per row of the ELL sweeps and restrictions are timed
+    at SETUP and kept; the operator is unchanged (one application within 1e-10 of the
+    oracle, the solve within one iteration), and a regenerated preconditioner reuses the
+    handle's choice, so it rounds exactly as before."""
+    a = grid_spe10(nx=23, ny=17, nz=9)
+    cfg = dict(coarse_max=120)
+    rp, ci, v = _dev(a)
+    g = msp.Solver(a.nb, a.b, rp, ci, v, autotune=1, mu=0, **cfg)
+    o = oracle.Oracle(a, **cfg)
+    tuned = 0
+    for l in range(g.num_levels - 1):
+        k, gl, rl = msp.msp_level_tiles(g.h, l)
+        if k:
+            tuned += 1
+            assert gl in (2, 4, 8) and rl in (2, 4, 8) and k // gl <= 8 and k // rl <= 8
+    assert tuned >= 1
+    gvec = random_rhs(a, 3)
+    w = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+    g.apply_precond(_vec(gvec), w)
+    ref = o.apply_precond(gvec)
+    assert np.abs(w.cpu().numpy() - ref).max() / np.abs(ref).max() <= TOL_APPLY
+    rhs = random_rhs(a, 4)
+    x1 = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+    i1 = g.solve(_vec(rhs), x1, 1e-6)
+    _, io = o.solve(rhs, 1e-6)
+    assert abs(i1["iterations"] - io["iterations"]) <= 1
+    tiles = [msp.msp_level_tiles(g.h, l) for l in range(g.num_levels)]
+    x2 = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+    i2 = g.solve(_vec(rhs), x2, 1e-6)  # mu = 0: SETUP runs again
+    assert i2["setup_performed"] == 1
+    assert [msp.msp_level_tiles(g.h, l) for l in range(g.num_levels)] == tiles
+    assert i2["iterations"] == i1["iterations"] and torch.equal(x1, x2)
+    g.close()
