@@ -53,9 +53,8 @@ SITE_KERNELS = {
     "stageR_bilu_fwd": "bilu_fwd_kernel", "stageR_bilu_bwd": "bilu_bwd_kernel",
     "amg_prolong": "prolong_add_kernel", "coarse_gemv": "dense_gemv_kernel",
     "batch_spmv": "bsr_spmv_kernel",
-    "batch_multi_dot": "seg_multi_dot_kernel", "batch_reorth_dot": "seg_multi_dot_kernel",
+    "batch_multi_dot": "seg_multi_dot2_kernel", "batch_finalize_dot": "seg_multi_dot_kernel",
     "batch_multi_axpy": "seg_multi_axpy_norm_kernel",
-    "batch_reorth_axpy": "seg_multi_axpy_norm_kernel",
 }
 SITE_PREFIX_KERNELS = {"amg_gs_pre_l": "ell_gs_colour_kernel",
                        "amg_gs_post_l": "ell_gs_colour_kernel",

@@ -10,22 +10,36 @@ namespace msp {
 // ---------------- solve phase: block rows of the colour-ordered BSR matrix --------------
 // rmask (optional, one byte per row of the level-0 order): rows with rmask[i] == 0 are
 // skipped — not read, not written (instances of a batch that have left the active set).
+//
+// Long rows (a well row couples to every perforated cell: ~nz blocks against <= 8 for a
+// cell) would make one lane group walk a long dependent chain of loads while the rest of
+// the launch waits for it.  Rows with more than `thr` blocks are taken by one warp each,
+// the row's blocks dealt round-robin over the lanes and the partial sums combined by a
+// fixed butterfly (deterministic); `rows` lists exactly the rows of the launch's range
+// with more than `thr` blocks, ascending.  The default (no list, thr = INT_MAX) leaves
+// every row to its lane group.
+struct LongRows {
+  const int* rows = nullptr;
+  int n = 0;
+  int thr = 0x7fffffff;
+};
 // y = A x (residual = false) or y = g - A x (residual = true); b = block size 1..8.
 template <typename T>
 int launch_bsr_spmv(int b, int nb, const int* rp, const int* ci, const T* v, const T* x,
                     const T* g, T* y, bool residual, cudaStream_t s,
-                    const unsigned char* rmask = nullptr);
+                    const unsigned char* rmask = nullptr, LongRows lr = LongRows());
 // rP[i] = omega_i^T (g_i - (A w)_i)   (omega == nullptr: first unknown only); r != nullptr
 // also receives g - A w
 template <typename T>
 int launch_bsr_restrict_p(int b, int nb, const int* rp, const int* ci, const T* v,
                           const T* w, const T* g, const T* omega, T* rP, T* r, cudaStream_t s,
-                          const unsigned char* rmask = nullptr);
+                          const unsigned char* rmask = nullptr, LongRows lr = LongRows());
 // r_i <- r_i - sum_j A_ij[:, 0] e_j and w_i[0] += e_i (r, w: nb*b values; c0: column 0 of
 // every block, nnzb*b values; e: one value per block row)
 template <typename T>
 int launch_bsr_col0_update(int b, int nb, const int* rp, const int* ci, const T* c0, const T* e,
-                           T* r, T* w, cudaStream_t s, const unsigned char* rmask = nullptr);
+                           T* r, T* w, cudaStream_t s, const unsigned char* rmask = nullptr,
+                           LongRows lr = LongRows());
 // c0[p*b + r] = v[(p*b + r)*b]
 template <typename T>
 int launch_extract_col0(size_t nnzb, int b, const T* v, T* c0, cudaStream_t s);
@@ -36,7 +50,8 @@ int launch_extract_col0(size_t nnzb, int b, const T* v, T* c0, cudaStream_t s);
 template <typename T>
 int launch_bgs_colour(int b, int r0, int r1, const int* rp, const int* ci, const int* dpos,
                       const T* aN, const T* y, T* w, bool lower_only, bool zero_pressure,
-                      cudaStream_t s, const unsigned char* rmask = nullptr);
+                      cudaStream_t s, const unsigned char* rmask = nullptr,
+                      LongRows lr = LongRows());
 // y[i*(b-1) + r] = (D_N,i^-1 g_i)[r] over the concentration unknowns of every block row
 template <typename T>
 int launch_nscale(int b, int nb, const T* dNinv, const T* g, T* y, cudaStream_t s);
@@ -45,11 +60,11 @@ int launch_nscale(int b, int nb, const T* dNinv, const T* g, T* y, cudaStream_t 
 template <typename T>
 int launch_bilu_fwd(int b, int r0, int r1, const int* rp, const int* ci, const int* dpos,
                     const T* lu, const T* r, T* y, cudaStream_t s,
-                    const unsigned char* rmask = nullptr);
+                    const unsigned char* rmask = nullptr, LongRows lr = LongRows());
 template <typename T>
 int launch_bilu_bwd(int b, int r0, int r1, const int* rp, const int* ci, const int* dpos,
                     const T* lu, const T* uinv, const T* y, T* x, T* w, cudaStream_t s,
-                    const unsigned char* rmask = nullptr);
+                    const unsigned char* rmask = nullptr, LongRows lr = LongRows());
 // w[i*b] += e[i]
 template <typename T>
 int launch_prolong_p(int b, int nb, const T* e, T* w, cudaStream_t s);
@@ -173,6 +188,21 @@ int launch_seg_multi_dot(const SegChunks& sc, const int* active, const double* V
 // out[i][koff + k] = sum over instance i's chunks of partial[c][k] (active instances)
 int launch_seg_reduce(const SegChunks& sc, int B, int K, const int* active,
                       const double* partial, double* out, int koff, cudaStream_t s);
+// one-pass Gram-Schmidt of the batched solve: partial[c][k] = V[k] . x0 and
+// partial[c][K + k] = V[k] . x1 over chunk c (stride 2 * kKrylovMaxK); a reduction with
+// explicit strides; the per-instance triangular solves of a step (one block per instance)
+int launch_seg_multi_dot2(const SegChunks& sc, const int* active, const double* V, size_t ldv,
+                          int K, const double* x0, const double* x1, double* partial,
+                          cudaStream_t s);
+int launch_seg_reduce_strided(const SegChunks& sc, int B, int K, const int* active,
+                              const double* partial, int pstride, double* out, int ostride,
+                              cudaStream_t s);
+int launch_dcgs_coef_batch(int B, int j, const int* active, const double* d, int dstride,
+                           double* T, int tstride, int ldt, double* g, int gstride, double* out,
+                           int ostride, cudaStream_t s);
+int launch_dcgs_finalize_batch(int B, int j1, const int* active, const double* d, int dstride,
+                               double* T, int tstride, int ldt, double* out, int ostride,
+                               cudaStream_t s);
 // w -= sum_k coef[i][k] V[k]; partial[c][0] = sum of the new w^2 over chunk c
 int launch_seg_multi_axpy_norm(const SegChunks& sc, const int* active, const double* V,
                                size_t ldv, int K, const double* coef, double* w, double* partial,

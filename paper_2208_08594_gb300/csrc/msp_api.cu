@@ -203,6 +203,11 @@ int sm_count() {
 namespace {
 
 constexpr int kThreads = 256;
+// Block rows with more blocks than this are walked by a warp in the level-0 block-row
+// kernels (the lane-group walk of a row is a chain of dependent loads two blocks long per
+// step: a well row perforating 85 layers alone would outlast a colour sweep of a million
+// cells).
+constexpr int kLongRowBlocks = 16;
 using Clock = std::chrono::steady_clock;
 double ms_since(Clock::time_point t0) {
   return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
@@ -386,6 +391,10 @@ struct msp_handle_s {
   msp::ColourCounts cc0;
   int g0 = 0;
   msp::DevBuf<int> rp, ci, dpos, src;  // colour-ordered BSR pattern, source nonzero
+  // rows with more than kLongRowBlocks blocks (the well rows), ascending: the block-row
+  // kernels give each of them a warp instead of one lane group
+  std::vector<int> long_h;
+  msp::DevBuf<int> long_d;
   msp::DevBuf<double> vals;            // colour-ordered current values
   msp::DevBuf<double> c0;              // column 0 of every block of vals (FP64 preconditioner)
   msp::DevBuf<double> staging;         // user values before the gather
@@ -437,6 +446,12 @@ struct msp_handle_s {
   msp::DevBuf<double> bpart, bh, by, bn, bydev;  // chunk partials; per instance kKrylovMaxK
   double* h_bpin = nullptr;                   // pinned: bh, by, bn (3 * batch * kKrylovMaxK)
   msp::DevBuf<int> row_inst;                  // instance of every level-0 (permuted) row
+  // one-pass Gram-Schmidt of the batched solve, per instance: the triangular factor
+  // ((m + 2)^2), the step's dot products (2 * kKrylovMaxK), the results (kBatchOut), and a
+  // mask of the instances whose column is made final at this step
+  msp::DevBuf<double> gs_bT, gs_bD, gs_bout;
+  msp::DevBuf<int> gs_bfin;
+  double* h_bout = nullptr;                   // pinned copy of gs_bout
   msp::DevBuf<unsigned char> rmask0;          // level-0 rows of the active instances
 };
 
@@ -1254,6 +1269,17 @@ int vcycle(msp_handle h, const PView<T>& P, int l, cudaStream_t s) {
   return MSP_OK;
 }
 
+// the long rows of level-0 rows [r0, r1) (a contiguous piece of the ascending list)
+inline LongRows long_rows(msp_handle h, int r0, int r1) {
+  LongRows lr;
+  lr.thr = kLongRowBlocks;
+  const auto lo = std::lower_bound(h->long_h.begin(), h->long_h.end(), r0);
+  const auto hi = std::lower_bound(h->long_h.begin(), h->long_h.end(), r1);
+  lr.n = (int)(hi - lo);
+  lr.rows = lr.n ? h->long_d.p + (lo - h->long_h.begin()) : nullptr;
+  return lr;
+}
+
 template <typename T>
 int stage_N(msp_handle h, const PView<T>& P, const T* g, T* w, cudaStream_t s) {
   const int b = h->b;
@@ -1280,7 +1306,8 @@ int stage_N(msp_handle h, const PView<T>& P, const T* g, T* w, cudaStream_t s) {
   for (int sw = 0; sw < h->cfg.bgs_sweeps; ++sw)
     for (int c = 0; c < h->g0; ++c)
       MSP_TRY(launch_bgs_colour<T>(b, h->cptr0[c], h->cptr0[c + 1], h->rp.p, h->ci.p, h->dpos.p,
-                                   P.aN, P.ny, w, sw == 0, sw == 0, s, P.m0));
+                                   P.aN, P.ny, w, sw == 0, sw == 0, s, P.m0,
+                                   long_rows(h, h->cptr0[c], h->cptr0[c + 1])));
   return MSP_OK;
 }
 
@@ -1304,7 +1331,7 @@ int stage_P(msp_handle h, const PView<T>& P, const T* g, T* w, T* r, cudaStream_
     Probe pr("stageP_residual_restrict", bsr_bytes(h, sT, r ? 3 : 2) + (double)h->nb * sT, s,
              1, sT == 8 ? 2.0 * (bsr_fmas(h) + (double)h->nb * b) : 0.0);
     MSP_TRY(launch_bsr_restrict_p<T>(h->b, h->nb, h->rp.p, h->ci.p, P.vals, w, g, P.omega,
-                                     P.lb[0], r, s, P.m0));
+                                     P.lb[0], r, s, P.m0, long_rows(h, 0, h->nb)));
   }
   MSP_TRY(vcycle<T>(h, P, 0, s));
   if (!r) {
@@ -1315,7 +1342,8 @@ int stage_P(msp_handle h, const PView<T>& P, const T* g, T* w, T* r, cudaStream_
            (double)h->nnzb * (b * sT + 4) + (double)(h->nb + 1) * 4 +
                (double)h->nb * sT * (1 + 2 * b + 2), s, 1,
            sT == 8 ? 2.0 * (double)h->nnzb * b : 0.0);
-  return launch_bsr_col0_update<T>(h->b, h->nb, h->rp.p, h->ci.p, P.c0, P.lx[0], r, w, s, P.m0);
+  return launch_bsr_col0_update<T>(h->b, h->nb, h->rp.p, h->ci.p, P.c0, P.lx[0], r, w, s, P.m0,
+                                   long_rows(h, 0, h->nb));
 }
 
 template <typename T>
@@ -1336,12 +1364,14 @@ int stage_R(msp_handle h, const PView<T>& P, const T* r, T* w, cudaStream_t s) {
     Probe pr("stageR_bilu_fwd", fwd, s, h->g0, ffwd);
     for (int c = 0; c < h->g0; ++c)
       MSP_TRY(launch_bilu_fwd<T>(b, h->cptr0[c], h->cptr0[c + 1], h->rp.p, h->ci.p, h->dpos.p,
-                                 P.lu, r, P.y, s, P.m0));
+                                 P.lu, r, P.y, s, P.m0,
+                                 long_rows(h, h->cptr0[c], h->cptr0[c + 1])));
   }
   Probe pr("stageR_bilu_bwd", bwd, s, h->g0, fbwd);
   for (int c = h->g0 - 1; c >= 0; --c)
     MSP_TRY(launch_bilu_bwd<T>(b, h->cptr0[c], h->cptr0[c + 1], h->rp.p, h->ci.p, h->dpos.p,
-                               P.lu, P.uinv, P.y, P.x, w, s, P.m0));
+                               P.lu, P.uinv, P.y, P.x, w, s, P.m0,
+                               long_rows(h, h->cptr0[c], h->cptr0[c + 1])));
   return MSP_OK;
 }
 
@@ -1571,7 +1601,8 @@ int fgmres(msp_handle h, double tol, int* iters, double* relres, double* relres_
   double est = 1.0;
   while (true) {
     MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, x, bvec, h->rvec.p,
-                                    true, s));
+                                    true, s, nullptr,
+                                    long_rows(h, 0, h->nb)));
     double beta = 0.0;
     MSP_TRY(norm2(h, h->rvec.p, n, &beta, s));
     if (!std::isfinite(beta)) return MSP_ERR_NONFINITE;
@@ -1658,7 +1689,8 @@ int fgmres(msp_handle h, double tol, int* iters, double* relres, double* relres_
       {
         Probe pr("krylov_spmv", bsr_bytes(h, 8.0, 1), s, 1, 2.0 * bsr_fmas(h));
         MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, zj, nullptr, w,
-                                        false, s));
+                                        false, s, nullptr,
+                                        long_rows(h, 0, h->nb)));
       }
       ++it;
       const int K = j + 2;  // u_0 .. u_j and w
@@ -1740,7 +1772,8 @@ int fgmres(msp_handle h, double tol, int* iters, double* relres, double* relres_
     MSP_CUDA_TRY(cudaStreamSynchronize(s));
     if (breakdown) {
       MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, x, bvec,
-                                      h->rvec.p, true, s));
+                                      h->rvec.p, true, s, nullptr,
+                                      long_rows(h, 0, h->nb)));
       double rr = 0.0;
       MSP_TRY(norm2(h, h->rvec.p, n, &rr, s));
       rr /= bnorm;
@@ -1753,7 +1786,8 @@ int fgmres(msp_handle h, double tol, int* iters, double* relres, double* relres_
     }
   }
   MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, x, bvec, h->rvec.p,
-                                  true, s));
+                                  true, s, nullptr,
+                                  long_rows(h, 0, h->nb)));
   double rr = 0.0;
   MSP_TRY(norm2(h, h->rvec.p, n, &rr, s));
   *relres = rr / bnorm;
@@ -1766,6 +1800,7 @@ int fgmres(msp_handle h, double tol, int* iters, double* relres, double* relres_
 // instance in increasing original index, i.e. instance by instance, so the vector splits
 // into (colour, instance) segments, cut into chunks of at most kSegChunk elements.
 constexpr int kSegChunk = 8192;
+constexpr int kBatchOut = 160;  // per-instance results of a Gram-Schmidt step (see dcgs_coef_kernel)
 
 SegChunks seg_chunks(msp_handle h) {
   SegChunks sc;
@@ -1799,8 +1834,6 @@ int fgmres_batched(msp_handle h, double tol, std::vector<int>& its, std::vector<
   double* x = h->xperm.p;
   double* V = h->V.p;
   double* Z = h->Z.p;
-  double* hb = h->h_bpin;                 // B * KM: first-pass coefficients
-  double* yb = h->h_bpin + (size_t)B * KM;  // second-pass coefficients
   double* nb2 = h->h_bpin + (size_t)2 * B * KM;  // squared norms
   its.assign(B, 0);
   relres.assign(B, 0.0);
@@ -1856,12 +1889,16 @@ int fgmres_batched(msp_handle h, double tol, std::vector<int>& its, std::vector<
     sv[i].assign(m + 1, 0.0);
   }
   std::vector<double> est(B, 1.0), ybuf((size_t)B * KM, 0.0);
+  std::vector<std::vector<double>> Hraw(B, std::vector<double>((size_t)(m + 1) * m, 0.0));
+  std::vector<int> committed(B, 0);
+  std::vector<double> hn_prev(B, 0.0), beta0(B, 0.0);
   std::vector<int> cnt(B, 0);
   while (true) {
     for (int i = 0; i < B; ++i) act[i] = !done[i];
     MSP_TRY(upload_act(act));
     MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, x, bvec, h->rvec.p,
-                                    true, s, h->rmask0.p));
+                                    true, s, h->rmask0.p,
+                                    long_rows(h, 0, h->nb)));
     MSP_TRY(seg_norms(h->rvec.p));
     int ncycle = 0;
     for (int i = 0; i < B; ++i) {
@@ -1893,6 +1930,54 @@ int fgmres_batched(msp_handle h, double tol, std::vector<int>& its, std::vector<
     MSP_TRY(upload_act(act));
     MSP_TRY(launch_seg_normalize(sc, h->bact.p, h->rvec.p, h->bn.p, V, s));
     MSP_TRY(zero_parts(done, V));  // the instances outside this cycle start from zero
+    // one-pass Gram-Schmidt per instance, as in the single solve (reading D17): the basis
+    // is orthogonalised once, the second pass is carried by each instance's triangular
+    // factor T_i, and column j of H_i becomes final once column j + 1 of T_i is known
+    const int m2 = m + 2;
+    for (int i = 0; i < B; ++i) {
+      if (!act[i]) continue;
+      std::fill(Hraw[i].begin(), Hraw[i].end(), 0.0);
+      committed[i] = 0;
+      hn_prev[i] = 0.0;
+      beta0[i] = sv[i][0];
+    }
+    // rotate final column k of instance i into H_i, update its least-squares right side
+    auto commit = [&](int i, int k) {
+      std::vector<double>& Hi = H[i];
+      const std::vector<double>& Ri = Hraw[i];
+      for (int r = 0; r <= k + 1; ++r) Hi[(size_t)r * m + k] = Ri[(size_t)r * m + k];
+      for (int r = 0; r < k; ++r) {
+        const double a = Hi[(size_t)r * m + k], c = Hi[(size_t)(r + 1) * m + k];
+        Hi[(size_t)r * m + k] = cs[i][r] * a + sn[i][r] * c;
+        Hi[(size_t)(r + 1) * m + k] = -sn[i][r] * a + cs[i][r] * c;
+      }
+      const double a = Hi[(size_t)k * m + k], c = Hi[(size_t)(k + 1) * m + k];
+      const double rho = std::sqrt(a * a + c * c);
+      if (rho == 0.0) {
+        cs[i][k] = 1.0;
+        sn[i][k] = 0.0;
+      } else {
+        cs[i][k] = a / rho;
+        sn[i][k] = c / rho;
+      }
+      Hi[(size_t)k * m + k] = rho;
+      Hi[(size_t)(k + 1) * m + k] = 0.0;
+      sv[i][k + 1] = -sn[i][k] * sv[i][k];
+      sv[i][k] = cs[i][k] * sv[i][k];
+      committed[i] = k + 1;
+    };
+    auto provisional = [&](int i, int k, const double* h, double hn) {
+      std::vector<double> col(k + 2);
+      for (int r = 0; r <= k; ++r) col[r] = h[r];
+      col[k + 1] = hn;
+      for (int r = 0; r < k; ++r) {
+        const double a = col[r], c = col[r + 1];
+        col[r] = cs[i][r] * a + sn[i][r] * c;
+        col[r + 1] = -sn[i][r] * a + cs[i][r] * c;
+      }
+      const double rho = std::sqrt(col[k] * col[k] + col[k + 1] * col[k + 1]);
+      return std::fabs((rho == 0.0 ? 0.0 : col[k + 1] / rho) * sv[i][k]) / bnorm[i];
+    };
     bool any = true;
     for (int j = 0; j < m && any; ++j) {
       double* vj = V + (size_t)j * n;
@@ -1902,78 +1987,138 @@ int fgmres_batched(msp_handle h, double tol, std::vector<int>& its, std::vector<
       {
         Probe pr("batch_spmv", bsr_bytes(h, 8.0, 1), s);
         MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, zj, nullptr, w,
-                                        false, s, h->rmask0.p));
+                                        false, s, h->rmask0.p,
+                                        long_rows(h, 0, h->nb)));
       }
-      const int K = j + 1;
+      const int K = j + 2;
       {
-        Probe pr("batch_multi_dot", (double)(K + 1) * n * 8.0, s);
-        MSP_TRY(launch_seg_multi_dot(sc, h->bact.p, V, n, K + 1, w, h->bpart.p, s));
+        Probe pr("batch_multi_dot", (double)K * n * 8.0, s);
+        MSP_TRY(launch_seg_multi_dot2(sc, h->bact.p, V, n, K, vj, w, h->bpart.p, s));
       }
-      MSP_TRY(launch_seg_reduce(sc, B, K + 1, h->bact.p, h->bpart.p, h->bh.p, 0, s));
+      MSP_TRY(launch_seg_reduce_strided(sc, B, 2 * K, h->bact.p, h->bpart.p, 2 * KM,
+                                        h->gs_bD.p, 2 * KM, s));
+      MSP_TRY(launch_dcgs_coef_batch(B, j, h->bact.p, h->gs_bD.p, 2 * KM, h->gs_bT.p, m2 * m2, m2,
+                                     h->by.p, KM, h->gs_bout.p, kBatchOut, s));
       {
-        Probe pr("batch_multi_axpy", (double)(K + 2) * n * 8.0, s);
-        MSP_TRY(launch_seg_multi_axpy_norm(sc, h->bact.p, V, n, K, h->bh.p, w, h->bpart.p, s));
-      }
-      {
-        Probe pr("batch_reorth_dot", (double)(K + 1) * n * 8.0, s);
-        MSP_TRY(launch_seg_multi_dot(sc, h->bact.p, V, n, K, w, h->bpart.p, s));
-      }
-      MSP_TRY(launch_seg_reduce(sc, B, K, h->bact.p, h->bpart.p, h->by.p, 0, s));
-      {
-        Probe pr("batch_reorth_axpy", (double)(K + 2) * n * 8.0, s);
-        MSP_TRY(launch_seg_multi_axpy_norm(sc, h->bact.p, V, n, K, h->by.p, w, h->bpart.p, s));
+        Probe pr("batch_multi_axpy", (double)(K + 1) * n * 8.0, s);
+        MSP_TRY(launch_seg_multi_axpy_norm(sc, h->bact.p, V, n, j + 1, h->by.p, w, h->bpart.p, s));
       }
       MSP_TRY(launch_seg_reduce(sc, B, 1, h->bact.p, h->bpart.p, h->bn.p, 0, s));
       MSP_TRY(launch_seg_normalize(sc, h->bact.p, w, h->bn.p, w, s));
-      MSP_CUDA_TRY(cudaMemcpyAsync(hb, h->bh.p, (size_t)B * KM * sizeof(double),
-                                   cudaMemcpyDeviceToHost, s));
-      MSP_CUDA_TRY(cudaMemcpyAsync(yb, h->by.p, (size_t)B * KM * sizeof(double),
+      MSP_CUDA_TRY(cudaMemcpyAsync(h->h_bout, h->gs_bout.p, (size_t)B * kBatchOut * sizeof(double),
                                    cudaMemcpyDeviceToHost, s));
       MSP_CUDA_TRY(cudaMemcpyAsync(nb2, h->bn.p, (size_t)B * KM * sizeof(double),
                                    cudaMemcpyDeviceToHost, s));
       MSP_CUDA_TRY(cudaStreamSynchronize(s));
       bool changed = false;
       any = false;
-      std::vector<int> left(B, 0);
+      std::vector<int> left(B, 0), fin(B, 0);
+      std::vector<double> hn_now(B, 0.0);
+      bool any_fin = false;
+      auto leave = [&](int i) {
+        act[i] = 0;
+        left[i] = 1;
+        changed = true;
+      };
       for (int i = 0; i < B; ++i) {
         if (!act[i]) continue;
         ++its[i];
-        std::vector<double>& Hi = H[i];
-        for (int k = 0; k < K; ++k) Hi[(size_t)k * m + j] = hb[(size_t)i * KM + k] + yb[(size_t)i * KM + k];
+        const double* o = h->h_bout + (size_t)i * kBatchOut;
         const double hn = std::sqrt(nb2[(size_t)i * KM]);
-        Hi[(size_t)(j + 1) * m + j] = hn;
-        for (int k = 0; k < j; ++k) {
-          const double a = Hi[(size_t)k * m + j], c = Hi[(size_t)(k + 1) * m + j];
-          Hi[(size_t)k * m + j] = cs[i][k] * a + sn[i][k] * c;
-          Hi[(size_t)(k + 1) * m + j] = -sn[i][k] * a + cs[i][k] * c;
+        hn_now[i] = hn;
+        if (!std::isfinite(hn) || !std::isfinite(o[145])) {
+          status[i] = MSP_ERR_NONFINITE;
+          done[i] = 1;
+          jused[i] = 0;
+          leave(i);
+          continue;
         }
-        const double a = Hi[(size_t)j * m + j], c = Hi[(size_t)(j + 1) * m + j];
-        const double rho = std::sqrt(a * a + c * c);
-        if (rho == 0.0) {
-          cs[i][j] = 1.0;
-          sn[i][j] = 0.0;
-        } else {
-          cs[i][j] = a / rho;
-          sn[i][j] = c / rho;
+        std::vector<double>& Ri = Hraw[i];
+        if (o[147] != 0.0) {  // u_j lies in the span of the earlier vectors: breakdown
+          if (j == 0) {
+            status[i] = MSP_ERR_NONFINITE;
+            done[i] = 1;
+            jused[i] = 0;
+          } else {
+            for (int k = 0; k < j; ++k) Ri[(size_t)k * m + (j - 1)] += hn_prev[i] * o[72 + k];
+            Ri[(size_t)j * m + (j - 1)] = 0.0;
+            commit(i, j - 1);
+            jused[i] = j;
+            est[i] = std::fabs(sv[i][j]) / bnorm[i];
+            brk[i] = 1;
+          }
+          leave(i);
+          continue;
         }
-        Hi[(size_t)j * m + j] = rho;
-        Hi[(size_t)(j + 1) * m + j] = 0.0;
-        sv[i][j + 1] = -sn[i][j] * sv[i][j];
-        sv[i][j] = cs[i][j] * sv[i][j];
+        if (j == 0) {
+          sv[i][0] = beta0[i] * o[144];
+        } else if (committed[i] < j) {
+          for (int k = 0; k < j; ++k) Ri[(size_t)k * m + (j - 1)] += hn_prev[i] * o[72 + k];
+          Ri[(size_t)j * m + (j - 1)] = hn_prev[i] * o[144];
+          commit(i, j - 1);
+        }
+        for (int k = 0; k <= j; ++k) Ri[(size_t)k * m + j] = o[k];
+        hn_prev[i] = hn;
         jused[i] = j + 1;
-        est[i] = std::fabs(sv[i][j + 1]) / bnorm[i];
+        if (hn == 0.0) {  // exact breakdown
+          Ri[(size_t)(j + 1) * m + j] = 0.0;
+          commit(i, j);
+          est[i] = std::fabs(sv[i][j + 1]) / bnorm[i];
+          brk[i] = 1;
+          leave(i);
+          continue;
+        }
+        const bool last = (j == m - 1) || its[i] >= h->cfg.max_it;
+        est[i] = provisional(i, j, o, hn);
         if (!std::isfinite(est[i])) {
           status[i] = MSP_ERR_NONFINITE;
           done[i] = 1;
           jused[i] = 0;
+          leave(i);
+          continue;
         }
-        if (hn == 0.0) brk[i] = 1;
-        if (done[i] || est[i] <= tol || its[i] >= h->cfg.max_it || brk[i]) {
-          act[i] = 0;
-          left[i] = 1;
-          changed = true;
+        if (last || est[i] <= tol * (1.0 + 1e-6)) {
+          fin[i] = 1;
+          any_fin = true;
         } else {
           any = true;
+        }
+      }
+      if (any_fin) {  // make column j final for those instances (no preconditioner)
+        MSP_CUDA_TRY(cudaMemcpyAsync(h->gs_bfin.p, fin.data(), B * sizeof(int),
+                                     cudaMemcpyHostToDevice, s));
+        {
+          Probe pr("batch_finalize_dot", (double)(j + 2) * n * 8.0, s);
+          MSP_TRY(launch_seg_multi_dot(sc, h->gs_bfin.p, V, n, j + 2, w, h->bpart.p, s));
+        }
+        MSP_TRY(launch_seg_reduce(sc, B, j + 2, h->gs_bfin.p, h->bpart.p, h->bh.p, 0, s));
+        MSP_TRY(launch_dcgs_finalize_batch(B, j + 1, h->gs_bfin.p, h->bh.p, KM, h->gs_bT.p,
+                                           m2 * m2, m2, h->gs_bout.p, kBatchOut, s));
+        MSP_CUDA_TRY(cudaMemcpyAsync(h->h_bout, h->gs_bout.p,
+                                     (size_t)B * kBatchOut * sizeof(double),
+                                     cudaMemcpyDeviceToHost, s));
+        MSP_CUDA_TRY(cudaStreamSynchronize(s));  // fin is read by the copy above
+        for (int i = 0; i < B; ++i) {
+          if (!fin[i]) continue;
+          const double* o = h->h_bout + (size_t)i * kBatchOut;
+          std::vector<double>& Ri = Hraw[i];
+          const double hn = hn_now[i];
+          for (int k = 0; k <= j; ++k) Ri[(size_t)k * m + j] += hn * o[72 + k];
+          Ri[(size_t)(j + 1) * m + j] = hn * o[144];
+          commit(i, j);
+          est[i] = std::fabs(sv[i][j + 1]) / bnorm[i];
+          if (o[147] != 0.0) brk[i] = 1;
+          const bool last = (j == m - 1) || its[i] >= h->cfg.max_it;
+          if (!std::isfinite(est[i])) {
+            status[i] = MSP_ERR_NONFINITE;
+            done[i] = 1;
+            jused[i] = 0;
+            leave(i);
+          } else if (est[i] <= tol || last || brk[i]) {
+            leave(i);
+          } else {
+            any = true;
+          }
         }
       }
       if (changed && any) {
@@ -2003,7 +2148,8 @@ int fgmres_batched(msp_handle h, double tol, std::vector<int>& its, std::vector<
   for (int i = 0; i < B; ++i) act[i] = bnorm[i] > 0.0 && std::isfinite(bnorm[i]);
   MSP_TRY(upload_act(act));
   MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, x, bvec, h->rvec.p,
-                                  true, s, h->rmask0.p));
+                                  true, s, h->rmask0.p,
+                                  long_rows(h, 0, h->nb)));
   MSP_TRY(seg_norms(h->rvec.p));
   for (int i = 0; i < B; ++i) {
     if (act[i]) relres[i] = std::sqrt(nb2[(size_t)i * KM]) / bnorm[i];
@@ -2039,6 +2185,22 @@ int pattern_setup(msp_handle h, const int32_t* d_rp, const int32_t* d_ci, cudaSt
   MSP_TRY(h->dpos.alloc(nb));
   MSP_TRY(launch_diag_pos(nb, h->rp.p, h->ci.p, h->dpos.p, s));
   MSP_TRY(colour_counts(h->rp.p, h->dpos.p, nb, h->cptr0, h->cc0, s));
+  // rows longer than kLongRowBlocks blocks, in the colour order
+  {
+    std::vector<int> hrp(nb + 1);
+    MSP_CUDA_TRY(cudaMemcpyAsync(hrp.data(), h->rp.p, (nb + 1) * sizeof(int),
+                                 cudaMemcpyDeviceToHost, s));
+    MSP_CUDA_TRY(cudaStreamSynchronize(s));
+    h->long_h.clear();
+    for (int i = 0; i < nb; ++i)
+      if (hrp[i + 1] - hrp[i] > kLongRowBlocks) h->long_h.push_back(i);
+    h->long_d.release();
+    if (!h->long_h.empty()) {
+      MSP_TRY(h->long_d.alloc(h->long_h.size()));
+      MSP_CUDA_TRY(cudaMemcpyAsync(h->long_d.p, h->long_h.data(), h->long_h.size() * sizeof(int),
+                                   cudaMemcpyHostToDevice, s));
+    }
+  }
   MSP_CUDA_TRY(cudaStreamSynchronize(s));
   return MSP_OK;
 }
@@ -2066,6 +2228,7 @@ void destroy(msp_handle h) {
   if (h->h_flags) cudaFreeHost(h->h_flags);
   if (h->h_pin) cudaFreeHost(h->h_pin);
   if (h->h_bpin) cudaFreeHost(h->h_bpin);
+  if (h->h_bout) cudaFreeHost(h->h_bout);
   if (h->staged_ev) cudaEventDestroy(h->staged_ev);
   if (h->consumed_ev) cudaEventDestroy(h->consumed_ev);
   if (h->ss) sort_scratch_destroy(h->ss);
@@ -2341,7 +2504,8 @@ int msp_spmv(msp_handle h, const double* d_x, double* d_y, void* stream) {
   {
     Probe pr("api_spmv", bsr_bytes(h, 8.0, 1), s);
     MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, h->bperm.p,
-                                    nullptr, h->xperm.p, false, s));
+                                    nullptr, h->xperm.p, false, s, nullptr,
+                                    long_rows(h, 0, h->nb)));
   }
   MSP_TRY(launch_scatter_blocks(h->nb, h->b, h->perm0.p, h->xperm.p, d_y, s));
   MSP_CUDA_TRY(cudaStreamSynchronize(s));
@@ -2453,7 +2617,17 @@ int msp_set_instances(msp_handle h, int32_t count, const int32_t* h_row_offsets)
     MSP_CUDA_TRY(cudaMemcpy(h->seg_iptr.p, iptr.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice));
     MSP_CUDA_TRY(cudaMemcpy(h->seg_ichunks.p, ichunks.data(), sizeof(int) * nchunks, cudaMemcpyHostToDevice));
     const size_t per = (size_t)count * kKrylovMaxK;
-    MSP_TRY(h->bpart.alloc((size_t)nchunks * kKrylovMaxK));
+    MSP_TRY(h->bpart.alloc((size_t)nchunks * 2 * kKrylovMaxK));
+    {
+      const int m2 = h->cfg.restart + 2;
+      MSP_TRY(h->gs_bT.alloc((size_t)count * m2 * m2));
+      MSP_TRY(h->gs_bD.alloc((size_t)count * 2 * kKrylovMaxK));
+      MSP_TRY(h->gs_bout.alloc((size_t)count * kBatchOut));
+      MSP_TRY(h->gs_bfin.alloc(count));
+      if (h->h_bout) cudaFreeHost(h->h_bout);
+      h->h_bout = nullptr;
+      MSP_CUDA_TRY(cudaMallocHost(&h->h_bout, (size_t)count * kBatchOut * sizeof(double)));
+    }
     MSP_TRY(h->bh.alloc(per));
     MSP_TRY(h->by.alloc(per));
     MSP_TRY(h->bn.alloc(per));

@@ -84,6 +84,42 @@ __device__ __forceinline__ T group_sum(T v) {
   return v;
 }
 
+// One long row by one warp: S_r = sum over the blocks q in [q0, q1), q != skip, of
+// sum_c A_q[r][c] x_{ci[q]}[c], with A_q the R x C values at vals + q * R * C (row-major)
+// and x_j the C values at x + j * xs + xo.  The warp holds NB = 32 / R blocks at a time,
+// R lanes each (lane l: row l % R of blocks q0 + l / R, q0 + l / R + NB, ...), the same
+// few registers per lane as the lane-group kernels; lane r < R returns S_r, summed over
+// its NB partners in a fixed order.  x rows are never written by the launch.
+template <int R, int C, typename T>
+__device__ __forceinline__ T warp_row_sum(int q0, int q1, int skip, const int* __restrict__ ci,
+                                          const T* __restrict__ vals, const T* x, int xs,
+                                          int xo) {
+  constexpr int NB = kWarp / R;
+  const int l = threadIdx.x % kWarp;
+  const int r = l % R, k0 = l / R;
+  T part = T(0);
+  if (k0 < NB) {
+#pragma unroll 1
+    for (int q = q0 + k0; q < q1; q += NB) {
+      if (q == skip) continue;
+      const T* xr = x + (size_t)__ldg(ci + q) * xs + xo;
+      const T* a = vals + ((size_t)q * R + r) * C;
+#pragma unroll
+      for (int c = 0; c < C; ++c) part = fma(__ldg(a + c), __ldg(xr + c), part);
+    }
+  }
+  T tot = part;
+#pragma unroll
+  for (int k = 1; k < NB; ++k) tot += __shfl_sync(0xffffffffu, part, r + k * R);
+  return tot;
+}
+
+// first warp of the grid and warp count, for the warp-per-long-row loops
+__device__ __forceinline__ int grid_warp() {
+  return (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) / kWarp);
+}
+__device__ __forceinline__ int grid_warps() { return (int)(gridDim.x * (size_t)blockDim.x / kWarp); }
+
 // ----------------------------------------------------------------------------------
 // y = A x  or  y = g - A x
 // ----------------------------------------------------------------------------------
@@ -94,7 +130,16 @@ __global__ void __launch_bounds__(kThreads) bsr_spmv_kernel(int nb, const int* _
                                                            const T* __restrict__ x,
                                                            const T* __restrict__ g,
                                                            T* __restrict__ y,
-                                                           const unsigned char* __restrict__ rmask) {
+                                                           const unsigned char* __restrict__ rmask,
+                                                           const int* __restrict__ lrows,
+                                                           int nlong, int lthr) {
+  for (int q = grid_warp(); q < nlong; q += grid_warps()) {  // long rows: a warp each
+    const int i = lrows[q];
+    if (rmask && !rmask[i]) continue;
+    const T sl = warp_row_sum<B, B>(__ldg(rp + i), __ldg(rp + i + 1), -1, ci, v, x, B, 0);
+    const int l = threadIdx.x % kWarp;
+    if (l < B) y[(size_t)i * B + l] = RES ? g[(size_t)i * B + l] - sl : sl;
+  }
   constexpr int GP = Gp<B>::v;
   const int lane = threadIdx.x % GP;
   const int gpb = blockDim.x / GP;
@@ -102,6 +147,7 @@ __global__ void __launch_bounds__(kThreads) bsr_spmv_kernel(int nb, const int* _
   for (int i = blockIdx.x * gpb + threadIdx.x / GP; i < nb; i += stride) {
     if (lane >= B || (rmask && !rmask[i])) continue;
     const int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
+    if (p1 - p0 > lthr) continue;  // taken by a warp above
     T acc = RES ? g[(size_t)i * B + lane] : T(0);
     int p = p0;
     for (; p + 1 < p1; p += 2) {  // two blocks in flight
@@ -132,7 +178,24 @@ template <int B, typename T, bool WR>
 __global__ void __launch_bounds__(kThreads) bsr_restrict_p_kernel(
     int nb, const int* __restrict__ rp, const int* __restrict__ ci, const T* __restrict__ v,
     const T* __restrict__ w, const T* __restrict__ g, const T* __restrict__ omega,
-    T* __restrict__ rP, T* __restrict__ r, const unsigned char* __restrict__ rmask) {
+    T* __restrict__ rP, T* __restrict__ r, const unsigned char* __restrict__ rmask,
+    const int* __restrict__ lrows, int nlong, int lthr) {
+  for (int q = grid_warp(); q < nlong; q += grid_warps()) {  // long rows: a warp each
+    const int i = lrows[q];
+    if (rmask && !rmask[i]) continue;
+    const T sl = warp_row_sum<B, B>(__ldg(rp + i), __ldg(rp + i + 1), -1, ci, v, w, B, 0);
+    const int l = threadIdx.x % kWarp;
+    T term = T(0);
+    if (l < B) {
+      const T al = g[(size_t)i * B + l] - sl;
+      if (WR) r[(size_t)i * B + l] = al;
+      term = omega ? al * omega[(size_t)i * B + l] : (l == 0 ? al : T(0));
+    }
+    T res = term;  // lane 0: the B terms in order
+#pragma unroll
+    for (int k = 1; k < B; ++k) res += __shfl_sync(0xffffffffu, term, k);
+    if (l == 0) rP[i] = res;
+  }
   constexpr int GP = Gp<B>::v;
   const int lane = threadIdx.x % GP;
   const int gpb = blockDim.x / GP;
@@ -140,7 +203,9 @@ __global__ void __launch_bounds__(kThreads) bsr_restrict_p_kernel(
   for (int base = blockIdx.x * gpb; base < nb; base += gridDim.x * gpb) {
     const int i = base + threadIdx.x / GP;
     T res = T(0);
-    const bool live = (i < nb) && (!rmask || rmask[i]);
+    bool live = (i < nb) && (!rmask || rmask[i]);
+    // rows taken by a warp above: every lane of the group reads the same length
+    if (live && __ldg(rp + i + 1) - __ldg(rp + i) > lthr) live = false;
     const bool active = live && (lane < B);
     if (active) {
       const int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
@@ -182,7 +247,16 @@ template <int B, typename T>
 __global__ void __launch_bounds__(kThreads) bsr_col0_update_kernel(
     int nb, const int* __restrict__ rp, const int* __restrict__ ci, const T* __restrict__ c0,
     const T* __restrict__ e, T* __restrict__ r, T* __restrict__ w,
-    const unsigned char* __restrict__ rmask) {
+    const unsigned char* __restrict__ rmask, const int* __restrict__ lrows, int nlong,
+    int lthr) {
+  for (int q = grid_warp(); q < nlong; q += grid_warps()) {  // long rows: a warp each
+    const int i = lrows[q];
+    if (rmask && !rmask[i]) continue;
+    const T sl = warp_row_sum<B, 1>(__ldg(rp + i), __ldg(rp + i + 1), -1, ci, c0, e, 1, 0);
+    const int l = threadIdx.x % kWarp;
+    if (l < B) r[(size_t)i * B + l] -= sl;
+    if (l == 0) w[(size_t)i * B] += __ldg(e + i);
+  }
   constexpr int GP = Gp<B>::v;
   const int lane = threadIdx.x % GP;
   const int gpb = blockDim.x / GP;
@@ -190,6 +264,7 @@ __global__ void __launch_bounds__(kThreads) bsr_col0_update_kernel(
   for (int i = blockIdx.x * gpb + threadIdx.x / GP; i < nb; i += stride) {
     if (lane >= B || (rmask && !rmask[i])) continue;
     const int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
+    if (p1 - p0 > lthr) continue;  // taken by a warp above
     T acc = r[(size_t)i * B + lane];
     int p = p0;
     for (; p + 3 < p1; p += 4) {  // four blocks in flight
@@ -227,58 +302,63 @@ __global__ void __launch_bounds__(kThreads) bgs_colour_kernel(
     int r0, int r1, const int* __restrict__ rp, const int* __restrict__ ci,
     const int* __restrict__ dpos, const T* __restrict__ aN, const T* __restrict__ y,
     T* __restrict__ w, bool lower_only, bool zero_pressure,
-    const unsigned char* __restrict__ rmask) {
+    const unsigned char* __restrict__ rmask, const int* __restrict__ lrows, int nlong,
+    int lthr) {
   constexpr int BN = B - 1;
-  // BN lanes per row, packed 32 / BN rows to a warp (b = 4: 10 rows, 30 lanes busy)
-  constexpr int R = kWarp / BN;
-  const int wl = threadIdx.x % kWarp;
-  const int slot = wl / BN, lane = wl % BN;
-  const int rpb = (blockDim.x / kWarp) * R;
-  const int first = (threadIdx.x / kWarp) * R + slot;
-  for (int base = r0 + blockIdx.x * rpb; base < r1; base += gridDim.x * rpb) {
-    const int i = base + first;
-    T acc = T(0);
-    const bool active = (slot < R) && (i < r1) && (!rmask || rmask[i]);
-    if (active) {
-      acc = y[(size_t)i * BN + lane];
-      const int p0 = __ldg(rp + i), pd = __ldg(dpos + i), p1 = __ldg(rp + i + 1);
-      const int pend = lower_only ? pd : p1;
-      // w rows of other colours: none of them is written by this launch
-      auto load = [&](int p, T (&a)[BN], T (&xx)[BN]) {
-        const T* xr = w + (size_t)__ldg(ci + p) * B + 1;
-        const T* ar = aN + ((size_t)p * BN + lane) * BN;
+  for (int q = grid_warp(); q < nlong; q += grid_warps()) {  // long rows: a warp each
+    const int i = lrows[q];
+    if (rmask && !rmask[i]) continue;
+    const int pd = __ldg(dpos + i);
+    const T sl = warp_row_sum<BN, BN>(__ldg(rp + i), lower_only ? pd : __ldg(rp + i + 1), pd,
+                                      ci, aN, w, B, 1);
+    const int l = threadIdx.x % kWarp;
+    if (l < BN) w[(size_t)i * B + 1 + l] = y[(size_t)i * BN + l] - sl;
+    if (zero_pressure && l == 0) w[(size_t)i * B] = T(0);
+  }
+  // BN consecutive threads per row (thread t: row r0 + t / BN, sub-block row t % BN); a
+  // row may straddle two warps, so every lane is busy whatever b is
+  const size_t total = (size_t)(r1 - r0) * BN;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int i = r0 + (int)(t / BN), lane = (int)(t % BN);
+    if (rmask && !rmask[i]) continue;
+    T acc = y[(size_t)i * BN + lane];
+    const int p0 = __ldg(rp + i), pd = __ldg(dpos + i), p1 = __ldg(rp + i + 1);
+    if (p1 - p0 > lthr) continue;  // taken by a warp above
+    const int pend = lower_only ? pd : p1;
+    // w rows of other colours: none of them is written by this launch
+    auto load = [&](int p, T (&a)[BN], T (&xx)[BN]) {
+      const T* xr = w + (size_t)__ldg(ci + p) * B + 1;
+      const T* ar = aN + ((size_t)p * BN + lane) * BN;
 #pragma unroll
-        for (int c = 0; c < BN; ++c) {
-          a[c] = __ldg(ar + c);
-          xx[c] = __ldg(xr + c);
-        }
-      };
-      int p = p0;
-      for (; p + 1 < pend; p += 2) {  // two blocks in flight, same order as one at a time
-        T a0[BN], x0[BN], a1[BN], x1[BN];
-        load(p, a0, x0);
-        load(p + 1, a1, x1);  // the diagonal block is read but not applied
-        if (p != pd) {
-#pragma unroll
-          for (int c = 0; c < BN; ++c) acc = fma(-a0[c], x0[c], acc);
-        }
-        if (p + 1 != pd) {
-#pragma unroll
-          for (int c = 0; c < BN; ++c) acc = fma(-a1[c], x1[c], acc);
-        }
+      for (int c = 0; c < BN; ++c) {
+        a[c] = __ldg(ar + c);
+        xx[c] = __ldg(xr + c);
       }
-      if (p < pend && p != pd) {
-        T a0[BN], x0[BN];
-        load(p, a0, x0);
+    };
+    int p = p0;
+    for (; p + 1 < pend; p += 2) {  // two blocks in flight, same order as one at a time
+      T a0[BN], x0[BN], a1[BN], x1[BN];
+      load(p, a0, x0);
+      load(p + 1, a1, x1);  // the diagonal block is read but not applied
+      if (p != pd) {
 #pragma unroll
         for (int c = 0; c < BN; ++c) acc = fma(-a0[c], x0[c], acc);
       }
+      if (p + 1 != pd) {
+#pragma unroll
+        for (int c = 0; c < BN; ++c) acc = fma(-a1[c], x1[c], acc);
+      }
+    }
+    if (p < pend && p != pd) {
+      T a0[BN], x0[BN];
+      load(p, a0, x0);
+#pragma unroll
+      for (int c = 0; c < BN; ++c) acc = fma(-a0[c], x0[c], acc);
     }
     // the blocks are D_N,i^-1 A_ij and y_i = D_N,i^-1 g_i: acc is x_i itself
-    if (active) {
-      w[(size_t)i * B + 1 + lane] = acc;
-      if (zero_pressure && lane == 0) w[(size_t)i * B] = T(0);
-    }
+    w[(size_t)i * B + 1 + lane] = acc;
+    if (zero_pressure && lane == 0) w[(size_t)i * B] = T(0);
   }
 }
 
@@ -309,12 +389,21 @@ template <int B, typename T>
 __global__ void __launch_bounds__(kThreads) bilu_fwd_kernel(
     int r0, int r1, const int* __restrict__ rp, const int* __restrict__ ci,
     const int* __restrict__ dpos, const T* __restrict__ lu, const T* __restrict__ r,
-    T* __restrict__ y, const unsigned char* __restrict__ rmask) {
+    T* __restrict__ y, const unsigned char* __restrict__ rmask, const int* __restrict__ lrows,
+    int nlong, int lthr) {
+  for (int q = grid_warp(); q < nlong; q += grid_warps()) {  // long rows: a warp each
+    const int i = lrows[q];
+    if (rmask && !rmask[i]) continue;
+    const T sl = warp_row_sum<B, B>(__ldg(rp + i), __ldg(dpos + i), -1, ci, lu, y, B, 0);
+    const int l = threadIdx.x % kWarp;
+    if (l < B) y[(size_t)i * B + l] = r[(size_t)i * B + l] - sl;
+  }
   constexpr int GP = Gp<B>::v;
   const int lane = threadIdx.x % GP;
   const int gpb = blockDim.x / GP;
   for (int i = r0 + blockIdx.x * gpb + threadIdx.x / GP; i < r1; i += gridDim.x * gpb) {
     if (lane >= B || (rmask && !rmask[i])) continue;
+    if (__ldg(rp + i + 1) - __ldg(rp + i) > lthr) continue;  // taken by a warp above
     T acc = r[(size_t)i * B + lane];
     const int p0 = __ldg(rp + i), pd = __ldg(dpos + i);
     // y rows of earlier colours: none of them is written by this launch
@@ -346,14 +435,35 @@ __global__ void __launch_bounds__(kThreads) bilu_bwd_kernel(
     int r0, int r1, const int* __restrict__ rp, const int* __restrict__ ci,
     const int* __restrict__ dpos, const T* __restrict__ lu, const T* __restrict__ uinv,
     const T* __restrict__ y, T* __restrict__ x, T* __restrict__ w,
-    const unsigned char* __restrict__ rmask) {
+    const unsigned char* __restrict__ rmask, const int* __restrict__ lrows, int nlong,
+    int lthr) {
+  for (int q = grid_warp(); q < nlong; q += grid_warps()) {  // long rows: a warp each
+    const int i = lrows[q];
+    if (rmask && !rmask[i]) continue;
+    const T sl = warp_row_sum<B, B>(__ldg(dpos + i) + 1, __ldg(rp + i + 1), -1, ci, lu, x, B, 0);
+    const int l = threadIdx.x % kWarp;
+    const T t = l < B ? y[(size_t)i * B + l] - sl : T(0);
+    const T* ui = uinv + ((size_t)i * B + (l < B ? l : 0)) * B;
+    T out = T(0);
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+      const T tc = __shfl_sync(0xffffffffu, t, c);
+      if (l < B) out = fma(__ldg(ui + c), tc, out);
+    }
+    if (l < B) {
+      x[(size_t)i * B + l] = out;
+      w[(size_t)i * B + l] += out;
+    }
+  }
   constexpr int GP = Gp<B>::v;
   const int lane = threadIdx.x % GP;
   const int gpb = blockDim.x / GP;
   const int grp = threadIdx.x / GP;
   for (int base = r0 + blockIdx.x * gpb; base < r1; base += gridDim.x * gpb) {
     const int i = base + grp;
-    const bool active = (i < r1) && (lane < B) && (!rmask || rmask[i]);
+    // rows taken by a warp above are left out; every lane of the group reads the same length
+    const bool active = (i < r1) && (lane < B) && (!rmask || rmask[i]) &&
+                        __ldg(rp + i + 1) - __ldg(rp + i) <= lthr;
     T acc = T(0);
     if (active) {
       acc = y[(size_t)i * B + lane];
@@ -875,8 +985,8 @@ __global__ void reduce_partials_strided_kernel(int K, int nblocks, int stride,
 //   g = T_{j+1}^-1 h                                          (w - Q h = w - U g)
 // out[0..j] = h, out[72 + k] = c_j[k], out[144] = nu_j, out[145] = nu_j^2, out[146] = w.w,
 // out[147] = 1 if nu_j^2 <= 0 (u_j lies in span Q: the previous step broke down).
-__global__ void dcgs_coef_kernel(int j, const double* __restrict__ d, double* __restrict__ T,
-                                 int ldt, double* __restrict__ g, double* __restrict__ out) {
+__device__ void dcgs_coef_body(int j, const double* __restrict__ d, double* __restrict__ T, int ldt,
+                               double* __restrict__ g, double* __restrict__ out) {
   // the warp stages the triangle of T and the dot products in shared memory (coalesced),
   // then one thread runs the three substitutions from there
   __shared__ double sT[(kMaxRestart + 2) * (kMaxRestart + 2)];
@@ -930,12 +1040,30 @@ __global__ void dcgs_coef_kernel(int j, const double* __restrict__ d, double* __
   }
 }
 
+__global__ void dcgs_coef_kernel(int j, const double* __restrict__ d, double* __restrict__ T,
+                                 int ldt, double* __restrict__ g, double* __restrict__ out) {
+  dcgs_coef_body(j, d, T, ldt, g, out);
+}
+
+// the same for every active instance of a batch (one block per instance; per-instance
+// dot products, factor, coefficients and results at the given strides)
+__global__ void dcgs_coef_batch_kernel(int j, const int* __restrict__ active,
+                                       const double* __restrict__ d, int dstride,
+                                       double* __restrict__ T, int tstride, int ldt,
+                                       double* __restrict__ g, int gstride,
+                                       double* __restrict__ out, int ostride) {
+  const int i = blockIdx.x;
+  if (!active[i]) return;  // uniform over the block
+  dcgs_coef_body(j, d + (size_t)i * dstride, T + (size_t)i * tstride, ldt, g + (size_t)i * gstride,
+                 out + (size_t)i * ostride);
+}
+
 // Column j + 1 of T from d[k] = u_k . u_{j+1}, k <= j + 1 (the last vector's own
 // correction, computed when the Arnoldi column of step j must be final: at convergence, at
 // MaxIt and at the end of a restart cycle).  out[72 + k] = c_{j+1}[k], out[144] = nu_{j+1},
 // out[145] = nu_{j+1}^2, out[147] = 1 if nu_{j+1}^2 <= 0.
-__global__ void dcgs_finalize_kernel(int j1, const double* __restrict__ d, double* __restrict__ T,
-                                     int ldt, double* __restrict__ out) {
+__device__ void dcgs_finalize_body(int j1, const double* __restrict__ d, double* __restrict__ T,
+                                   int ldt, double* __restrict__ out) {
   if (threadIdx.x != 0) return;
   double c2 = 0.0;
   for (int k = 0; k < j1; ++k) {
@@ -954,6 +1082,21 @@ __global__ void dcgs_finalize_kernel(int j1, const double* __restrict__ d, doubl
     for (int k = 0; k < j1; ++k) T[(size_t)j1 * ldt + k] = out[72 + k];
     T[(size_t)j1 * ldt + j1] = out[144];
   }
+}
+
+__global__ void dcgs_finalize_kernel(int j1, const double* __restrict__ d, double* __restrict__ T,
+                                     int ldt, double* __restrict__ out) {
+  dcgs_finalize_body(j1, d, T, ldt, out);
+}
+
+__global__ void dcgs_finalize_batch_kernel(int j1, const int* __restrict__ active,
+                                           const double* __restrict__ d, int dstride,
+                                           double* __restrict__ T, int tstride, int ldt,
+                                           double* __restrict__ out, int ostride) {
+  const int i = blockIdx.x;
+  if (!active[i]) return;
+  dcgs_finalize_body(j1, d + (size_t)i * dstride, T + (size_t)i * tstride, ldt,
+                     out + (size_t)i * ostride);
 }
 
 // one warp per output k: lanes sum strided partials, then a fixed-order shuffle tree
@@ -1074,6 +1217,72 @@ __global__ void __launch_bounds__(kThreads) seg_multi_dot_kernel(
       }
     }
   }
+}
+
+// Two right-hand vectors per chunk: partial[c][k] = V_k . x0 and partial[c][K + k] = V_k .
+// x1 over chunk c (row stride 2 * kMaxK), the chunks of the active instances only
+__global__ void __launch_bounds__(kThreads) seg_multi_dot2_kernel(
+    int nchunks, const int* __restrict__ cs, const int* __restrict__ ce,
+    const int* __restrict__ cinst, const int* __restrict__ active, const double* __restrict__ V,
+    size_t ldv, int K, const double* __restrict__ x0, const double* __restrict__ x1,
+    double* __restrict__ partial) {
+  __shared__ double sh[2][kThreads / kWarp][kDotChunk];
+  const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp;
+  const int slot = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    if (!active[cinst[c]]) continue;  // uniform over the block
+    const size_t i0 = cs[c], i1 = ce[c];
+    for (int k0 = 0; k0 < K; k0 += kDotChunk) {
+      const int kc = min(kDotChunk, K - k0);
+      double a0[kDotChunk], a1[kDotChunk];
+#pragma unroll
+      for (int k = 0; k < kDotChunk; ++k) a0[k] = a1[k] = 0.0;
+      for (size_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const double u = x0[i], w = x1[i];
+#pragma unroll
+        for (int k = 0; k < kDotChunk; ++k)
+          if (k < kc) {
+            const double vk = __ldg(V + (size_t)(k0 + k) * ldv + i);
+            a0[k] = fma(vk, u, a0[k]);
+            a1[k] = fma(vk, w, a1[k]);
+          }
+      }
+      const double r0 = transpose_sum8(a0, lane);
+      const double r1 = transpose_sum8(a1, lane);
+      __syncthreads();
+      if ((lane & 3) == 0) {
+        sh[0][wid][slot] = r0;
+        sh[1][wid][slot] = r1;
+      }
+      __syncthreads();
+      if (threadIdx.x < 2 * kc) {
+        const int r = threadIdx.x / kc, k = threadIdx.x % kc;
+        double t = 0.0;
+#pragma unroll
+        for (int w2 = 0; w2 < kThreads / kWarp; ++w2) t += sh[r][w2][k];
+        partial[(size_t)c * (2 * kMaxK) + r * K + k0 + k] = t;
+      }
+    }
+  }
+}
+
+// out[i * ostride + k] = sum over instance i's chunks (in order) of partial[c * pstride + k];
+// one warp per (instance, k)
+__global__ void seg_reduce_strided_kernel(int B, int K, const int* __restrict__ iptr,
+                                          const int* __restrict__ ichunks,
+                                          const int* __restrict__ active,
+                                          const double* __restrict__ partial, int pstride,
+                                          double* __restrict__ out, int ostride) {
+  const int q = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
+  const int lane = threadIdx.x % kWarp;
+  if (q >= B * K) return;
+  const int inst = q / K, k = q % K;
+  if (!active[inst]) return;
+  double s = 0.0;
+  for (int t = iptr[inst] + lane; t < iptr[inst + 1]; t += kWarp)
+    s += partial[(size_t)ichunks[t] * pstride + k];
+  s = group_sum<kWarp>(s);
+  if (lane == 0) out[(size_t)inst * ostride + k] = s;
 }
 
 // out[i * kMaxK + koff + k] = sum over instance i's chunks (in order) of partial[c][k];
@@ -1229,14 +1438,16 @@ inline unsigned grid_groups(size_t groups, int gp) {
 template <typename T>
 int launch_bsr_spmv(int b, int nb, const int* rp, const int* ci, const T* v, const T* x,
                     const T* g, T* y, bool residual, cudaStream_t s,
-                    const unsigned char* rmask) {
+                    const unsigned char* rmask, LongRows lr) {
   if (nb <= 0) return MSP_OK;
   MSP_B_SWITCH(b, {
     const unsigned grid = grid_groups(nb, Gp<B_>::v);
     if (residual)
-      bsr_spmv_kernel<B_, T, true><<<grid, kThreads, 0, s>>>(nb, rp, ci, v, x, g, y, rmask);
+      bsr_spmv_kernel<B_, T, true><<<grid, kThreads, 0, s>>>(nb, rp, ci, v, x, g, y, rmask,
+                                                             lr.rows, lr.n, lr.thr);
     else
-      bsr_spmv_kernel<B_, T, false><<<grid, kThreads, 0, s>>>(nb, rp, ci, v, x, g, y, rmask);
+      bsr_spmv_kernel<B_, T, false><<<grid, kThreads, 0, s>>>(nb, rp, ci, v, x, g, y, rmask,
+                                                              lr.rows, lr.n, lr.thr);
   });
   return launch_status();
 }
@@ -1244,27 +1455,29 @@ int launch_bsr_spmv(int b, int nb, const int* rp, const int* ci, const T* v, con
 template <typename T>
 int launch_bsr_restrict_p(int b, int nb, const int* rp, const int* ci, const T* v, const T* w,
                           const T* g, const T* omega, T* rP, T* r, cudaStream_t s,
-                          const unsigned char* rmask) {
+                          const unsigned char* rmask, LongRows lr) {
   if (nb <= 0) return MSP_OK;
   MSP_B_SWITCH(b, {
     const unsigned grid = grid_groups(nb, Gp<B_>::v);
     if (r)
-      bsr_restrict_p_kernel<B_, T, true><<<grid, kThreads, 0, s>>>(nb, rp, ci, v, w, g, omega,
-                                                                   rP, r, rmask);
+      bsr_restrict_p_kernel<B_, T, true><<<grid, kThreads, 0, s>>>(
+          nb, rp, ci, v, w, g, omega, rP, r, rmask, lr.rows, lr.n, lr.thr);
     else
-      bsr_restrict_p_kernel<B_, T, false><<<grid, kThreads, 0, s>>>(nb, rp, ci, v, w, g, omega,
-                                                                    rP, r, rmask);
+      bsr_restrict_p_kernel<B_, T, false><<<grid, kThreads, 0, s>>>(
+          nb, rp, ci, v, w, g, omega, rP, r, rmask, lr.rows, lr.n, lr.thr);
   });
   return launch_status();
 }
 
 template <typename T>
 int launch_bsr_col0_update(int b, int nb, const int* rp, const int* ci, const T* c0, const T* e,
-                           T* r, T* w, cudaStream_t s, const unsigned char* rmask) {
+                           T* r, T* w, cudaStream_t s, const unsigned char* rmask,
+                           LongRows lr) {
   if (nb <= 0) return MSP_OK;
   MSP_B_SWITCH(b, {
     const unsigned grid = grid_groups(nb, Gp<B_>::v);
-    bsr_col0_update_kernel<B_, T><<<grid, kThreads, 0, s>>>(nb, rp, ci, c0, e, r, w, rmask);
+    bsr_col0_update_kernel<B_, T><<<grid, kThreads, 0, s>>>(nb, rp, ci, c0, e, r, w, rmask,
+                                                            lr.rows, lr.n, lr.thr);
   });
   return launch_status();
 }
@@ -1279,14 +1492,15 @@ int launch_extract_col0(size_t nnzb, int b, const T* v, T* c0, cudaStream_t s) {
 template <typename T>
 int launch_bgs_colour(int b, int r0, int r1, const int* rp, const int* ci, const int* dpos,
                       const T* aN, const T* y, T* w, bool lower_only, bool zero_pressure,
-                      cudaStream_t s, const unsigned char* rmask) {
+                      cudaStream_t s, const unsigned char* rmask, LongRows lr) {
   if (r1 <= r0 || b < 2) return MSP_OK;
   switch (b) {
 #define MSP_BGS_CASE(BB)                                                                   \
   case BB: {                                                                               \
-    const unsigned grid = grid_for((size_t)(r1 - r0) * kWarp / (kWarp / (BB - 1)), kThreads); \
-    bgs_colour_kernel<BB, T><<<grid, kThreads, 0, s>>>(r0, r1, rp, ci, dpos, aN, y, w,      \
-                                                       lower_only, zero_pressure, rmask);   \
+    const unsigned grid = grid_for((size_t)(r1 - r0) * (BB - 1), kThreads);                 \
+    bgs_colour_kernel<BB, T><<<grid, kThreads, 0, s>>>(                                    \
+        r0, r1, rp, ci, dpos, aN, y, w, lower_only, zero_pressure, rmask, lr.rows, lr.n,    \
+        lr.thr);                                                                           \
   } break;
     MSP_BGS_CASE(2)
     MSP_BGS_CASE(3)
@@ -1321,11 +1535,13 @@ int launch_nscale(int b, int nb, const T* dNinv, const T* g, T* y, cudaStream_t 
 
 template <typename T>
 int launch_bilu_fwd(int b, int r0, int r1, const int* rp, const int* ci, const int* dpos,
-                    const T* lu, const T* r, T* y, cudaStream_t s, const unsigned char* rmask) {
+                    const T* lu, const T* r, T* y, cudaStream_t s, const unsigned char* rmask,
+                    LongRows lr) {
   if (r1 <= r0) return MSP_OK;
   MSP_B_SWITCH(b, {
     const unsigned grid = grid_groups(r1 - r0, Gp<B_>::v);
-    bilu_fwd_kernel<B_, T><<<grid, kThreads, 0, s>>>(r0, r1, rp, ci, dpos, lu, r, y, rmask);
+    bilu_fwd_kernel<B_, T><<<grid, kThreads, 0, s>>>(r0, r1, rp, ci, dpos, lu, r, y, rmask,
+                                                     lr.rows, lr.n, lr.thr);
   });
   return launch_status();
 }
@@ -1333,12 +1549,12 @@ int launch_bilu_fwd(int b, int r0, int r1, const int* rp, const int* ci, const i
 template <typename T>
 int launch_bilu_bwd(int b, int r0, int r1, const int* rp, const int* ci, const int* dpos,
                     const T* lu, const T* uinv, const T* y, T* x, T* w, cudaStream_t s,
-                    const unsigned char* rmask) {
+                    const unsigned char* rmask, LongRows lr) {
   if (r1 <= r0) return MSP_OK;
   MSP_B_SWITCH(b, {
     const unsigned grid = grid_groups(r1 - r0, Gp<B_>::v);
     bilu_bwd_kernel<B_, T><<<grid, kThreads, 0, s>>>(r0, r1, rp, ci, dpos, lu, uinv, y, x, w,
-                                                     rmask);
+                                                     rmask, lr.rows, lr.n, lr.thr);
   });
   return launch_status();
 }
@@ -1659,6 +1875,48 @@ int launch_seg_reduce(const SegChunks& sc, int B, int K, const int* active,
   return launch_status();
 }
 
+int launch_seg_multi_dot2(const SegChunks& sc, const int* active, const double* V, size_t ldv,
+                          int K, const double* x0, const double* x1, double* partial,
+                          cudaStream_t s) {
+  if (K > kMaxK) return MSP_ERR_ARG;
+  if (K <= 0 || sc.n <= 0) return MSP_OK;
+  seg_multi_dot2_kernel<<<seg_grid(sc.n), kThreads, 0, s>>>(sc.n, sc.start, sc.end, sc.inst,
+                                                            active, V, ldv, K, x0, x1, partial);
+  return launch_status();
+}
+
+int launch_seg_reduce_strided(const SegChunks& sc, int B, int K, const int* active,
+                              const double* partial, int pstride, double* out, int ostride,
+                              cudaStream_t s) {
+  if (K > pstride || K > ostride) return MSP_ERR_ARG;
+  if (K <= 0 || B <= 0) return MSP_OK;
+  const int wpb = 4;
+  const long long q = (long long)B * K;
+  seg_reduce_strided_kernel<<<(unsigned)((q + wpb - 1) / wpb), wpb * kWarp, 0, s>>>(
+      B, K, sc.iptr, sc.ichunks, active, partial, pstride, out, ostride);
+  return launch_status();
+}
+
+int launch_dcgs_coef_batch(int B, int j, const int* active, const double* d, int dstride,
+                           double* T, int tstride, int ldt, double* g, int gstride, double* out,
+                           int ostride, cudaStream_t s) {
+  if (B <= 0) return MSP_OK;
+  if (j < 0 || j + 2 > kMaxK || j + 1 > ldt) return MSP_ERR_ARG;
+  dcgs_coef_batch_kernel<<<B, kWarp, 0, s>>>(j, active, d, dstride, T, tstride, ldt, g, gstride,
+                                             out, ostride);
+  return launch_status();
+}
+
+int launch_dcgs_finalize_batch(int B, int j1, const int* active, const double* d, int dstride,
+                               double* T, int tstride, int ldt, double* out, int ostride,
+                               cudaStream_t s) {
+  if (B <= 0) return MSP_OK;
+  if (j1 < 1 || j1 + 1 > kMaxK || j1 + 1 > ldt) return MSP_ERR_ARG;
+  dcgs_finalize_batch_kernel<<<B, kWarp, 0, s>>>(j1, active, d, dstride, T, tstride, ldt, out,
+                                                 ostride);
+  return launch_status();
+}
+
 int launch_seg_multi_axpy_norm(const SegChunks& sc, const int* active, const double* V,
                                size_t ldv, int K, const double* coef, double* w, double* partial,
                                cudaStream_t s) {
@@ -1721,22 +1979,25 @@ int launch_scatter_blocks(int nb, int b, const int* perm, const double* in, doub
 // explicit instantiations for the two value types of the preconditioner
 #define MSP_INST(T)                                                                         \
   template int launch_bsr_spmv<T>(int, int, const int*, const int*, const T*, const T*,     \
-                                  const T*, T*, bool, cudaStream_t, const unsigned char*);  \
+                                  const T*, T*, bool, cudaStream_t, const unsigned char*,   \
+                                  LongRows);                                                \
   template int launch_bsr_restrict_p<T>(int, int, const int*, const int*, const T*,         \
                                         const T*, const T*, const T*, T*, T*, cudaStream_t, \
-                                        const unsigned char*);                              \
+                                        const unsigned char*, LongRows);                    \
   template int launch_bsr_col0_update<T>(int, int, const int*, const int*, const T*,        \
-                                         const T*, T*, T*, cudaStream_t, const unsigned char*); \
+                                         const T*, T*, T*, cudaStream_t, const unsigned char*, \
+                                         LongRows);                                          \
   template int launch_extract_col0<T>(size_t, int, const T*, T*, cudaStream_t);             \
   template int launch_bgs_colour<T>(int, int, int, const int*, const int*, const int*,      \
                                     const T*, const T*, T*, bool, bool, cudaStream_t,       \
-                                    const unsigned char*);                                  \
+                                    const unsigned char*, LongRows);                        \
   template int launch_nscale<T>(int, int, const T*, const T*, T*, cudaStream_t);            \
   template int launch_bilu_fwd<T>(int, int, int, const int*, const int*, const int*,        \
-                                  const T*, const T*, T*, cudaStream_t, const unsigned char*); \
+                                  const T*, const T*, T*, cudaStream_t, const unsigned char*, \
+                                  LongRows);                                                \
   template int launch_bilu_bwd<T>(int, int, int, const int*, const int*, const int*,        \
                                   const T*, const T*, const T*, T*, T*, cudaStream_t,       \
-                                  const unsigned char*);                                    \
+                                  const unsigned char*, LongRows);                          \
   template int launch_prolong_p<T>(int, int, const T*, T*, cudaStream_t);                   \
   template int launch_csr_gs_colour<T>(int, int, const int*, const int*, const T*,          \
                                        const int*, const T*, const T*, T*, bool, int,       \

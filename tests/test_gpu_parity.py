@@ -180,6 +180,48 @@ def test_long_rows_take_the_csr_path():
     g.close()
 
 
+@pytest.mark.parametrize("b", [2, 4, 6])
+def test_level0_long_rows_walked_by_a_warp(b):
+    """Wells perforating 40 layers give level-0 block rows of 41 blocks, more than the 16
+    that one lane group walks: the SpMV, the stage-N sweeps (b - 1 = 1, 3, 5 lanes per
+    sub-block row), the stage-P restriction and correction and both BILU sweeps give each
+    such row a warp.  SpMV elementwise, every stage alone and the whole application within
+    the FP64 tolerance, the solve within one iteration of the oracle, in FP64 and with the
+    FP32 preconditioner (Section 3.3: same convergence, FP64 residual)."""
+    a = box_jacobian(7, 6, 40, b, 17 + b, layered=True, kz_ratio=0.1, n_wells=3)
+    assert int((np.diff(a.row_ptr) > 16).sum()) == 3
+    x = np.random.default_rng(b).normal(size=a.n)
+    for precond in (msp.MSP_PREC_N_ONLY, msp.MSP_PREC_P_ONLY, msp.MSP_PREC_R_ONLY, None):
+        cfg = dict(coarse_max=80) if precond is None else dict(coarse_max=80, precond=precond)
+        g, o = _pair(a, **cfg)
+        if precond is None:
+            y = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+            g.spmv(_vec(x), y)
+            ref = o.spmv(x)
+            assert np.allclose(y.cpu().numpy(), ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+        w = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+        g.apply_precond(_vec(x), w)
+        ref = o.apply_precond(x)
+        err = np.abs(w.cpu().numpy() - ref).max() / np.abs(ref).max()
+        assert err <= TOL_APPLY, (precond, err)
+        if precond is None:
+            rhs = random_rhs(a, 7)
+            _, io = o.solve(rhs, 1e-6)
+            for prec in ("fp64", "fp32"):
+                gs = g if prec == "fp64" else msp.Solver(
+                    a.nb, a.b, *_dev(a), coarse_max=80, precision=msp.MSP_PRECISION_FP32)
+                xd = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+                info = gs.solve(_vec(rhs), xd, 1e-6)
+                assert info["status"] == 0, (prec, info)
+                assert abs(info["iterations"] - io["iterations"]) <= 1, (prec, info, io)
+                xg = xd.cpu().numpy()
+                assert np.linalg.norm(rhs - a.to_scipy() @ xg) <= 1e-6 * 1.001 * np.linalg.norm(rhs)
+                if gs is not g:
+                    gs.close()
+        g.close()
+        o.close()
+
+
 @pytest.mark.parametrize("name", ["spe10_like_b4", "wells_b2", "b6_ragged"])
 def test_jp_colouring_option_matches_oracle(name):
     """msp_config.colouring = MSP_COLOURING_JP (greedy in Jones-Plassmann priority order,
