@@ -24,6 +24,13 @@ struct Gp {
   static constexpr int v = B <= 1 ? 1 : (B <= 2 ? 2 : (B <= 4 ? 4 : 8));
 };
 
+// The level-0 block-row kernels are bound by chains of dependent loads per row (row
+// pointers, column index, gathered x): launched with one thread (group) per row and as
+// many blocks as that takes, the block scheduler refills SMs as blocks finish, where a
+// grid-stride loop capped at one resident wave left SMs idle behind the threads that drew
+// an extra row (stage-N colour of 561k rows: 81.9 against 94.2 us).
+constexpr unsigned kRowGridPerSm = 1u << 20;
+
 // Load B consecutive values with the widest aligned vector loads (rows start at
 // multiples of B*sizeof(T) bytes from a 256-byte aligned allocation).  Components are
 // assigned one by one: copying a loaded vector into the array as raw bytes would put
@@ -1417,7 +1424,7 @@ inline int launch_status() { return launch_check(__FILE__, __LINE__); }
 
 // grid covering `groups` thread groups of GP lanes, capped at 8 blocks per SM
 inline unsigned grid_groups(size_t groups, int gp) {
-  return grid_for(groups * (size_t)gp, kThreads, 8);
+  return grid_for(groups * (size_t)gp, kThreads, kRowGridPerSm);
 }
 
 }  // namespace
@@ -1497,7 +1504,7 @@ int launch_bgs_colour(int b, int r0, int r1, const int* rp, const int* ci, const
   switch (b) {
 #define MSP_BGS_CASE(BB)                                                                   \
   case BB: {                                                                               \
-    const unsigned grid = grid_for((size_t)(r1 - r0) * (BB - 1), kThreads);                 \
+    const unsigned grid = grid_for((size_t)(r1 - r0) * (BB - 1), kThreads, kRowGridPerSm);  \
     bgs_colour_kernel<BB, T><<<grid, kThreads, 0, s>>>(                                    \
         r0, r1, rp, ci, dpos, aN, y, w, lower_only, zero_pressure, rmask, lr.rows, lr.n,    \
         lr.thr);                                                                           \
