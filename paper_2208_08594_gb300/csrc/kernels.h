@@ -13,11 +13,11 @@ namespace msp {
 //
 // Long rows (a well row couples to every perforated cell: ~nz blocks against <= 8 for a
 // cell) would make one lane group walk a long dependent chain of loads while the rest of
-// the launch waits for it.  Rows with more than `thr` blocks are taken by one warp each,
-// the row's blocks dealt round-robin over the lanes and the partial sums combined by a
-// fixed butterfly (deterministic); `rows` lists exactly the rows of the launch's range
-// with more than `thr` blocks, ascending.  The default (no list, thr = INT_MAX) leaves
-// every row to its lane group.
+// the launch waits for it.  Rows with more than `thr` blocks are taken by one thread
+// block each, the row's blocks dealt round-robin over its threads and the partial sums
+// combined in a fixed order (deterministic); `rows` lists exactly the rows of the
+// launch's range with more than `thr` blocks, ascending.  The default (no list, thr =
+// INT_MAX) leaves every row to its lane group.
 struct LongRows {
   const int* rows = nullptr;
   int n = 0;

@@ -12,7 +12,13 @@
 //     released least recently used first to make room; if it still does not fit, it waits,
 //     and so do the later requests that need a new system (they keep their order), while
 //     later requests of resident systems, replacements included, may still start;
-//   * once a system is set up its measured footprint replaces the estimate.
+//   * once a system is set up its measured footprint replaces the estimate;
+//   * a request of a resident system is charged, while it runs, the difference between the
+//     estimate and the system's measured footprint (a system grows after its setup: the
+//     staging copy of new values, a regenerated hierarchy of another size), admitted like
+//     a new system (idle systems released to make room, else it waits for a running
+//     request to finish; with nothing running it starts anyway), so that the charged
+//     total never exceeds the budget while the estimate bounds every footprint.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -79,6 +85,35 @@ struct Pick {
   std::vector<std::pair<int64_t, msp_handle>> evict;  // key, handle (CUDA executor)
 };
 
+// Idle resident systems (not `key`, no request running or queued), least recently used
+// first, whose release makes `extra` more bytes available than `avail`; false if even all
+// of them are not enough.
+bool room_by_release(msp_server_s* S, int64_t key, int64_t avail, int64_t need,
+                     std::vector<std::pair<uint64_t, int64_t>>& idle) {
+  idle.clear();
+  if (avail >= need) return true;
+  for (auto& kv : S->systems)
+    if (kv.first != key && !kv.second.busy && kv.second.ready && kv.second.queued == 0)
+      idle.push_back({kv.second.last_used, kv.first});
+  std::sort(idle.begin(), idle.end());
+  int64_t extra = 0;
+  size_t k = 0;
+  for (; k < idle.size() && avail + extra < need; ++k) extra += S->systems[idle[k].second].bytes;
+  idle.resize(k);
+  return avail + extra >= need;
+}
+
+void release_idle(msp_server_s* S, const std::vector<std::pair<uint64_t, int64_t>>& idle,
+                  Pick& out) {
+  for (auto& e : idle) {
+    System& v = S->systems[e.second];
+    out.evict.push_back({e.second, v.h});
+    S->charged -= v.bytes;
+    S->systems.erase(e.second);
+    ++S->st.evictions;
+  }
+}
+
 // Choose the next runnable job (server lock held).  Every queued key has an entry in
 // S->systems (its queued count); `ready` marks the ones that are set up.
 bool pick_job(msp_server_s* S, Pick& out) {
@@ -94,7 +129,20 @@ bool pick_job(msp_server_s* S, Pick& out) {
       continue;
     }
     const bool new_pattern = (j->req.flags & MSP_REQ_NEW_PATTERN) != 0;
+    std::vector<std::pair<uint64_t, int64_t>> idle;  // last_used, key
     if (sy.ready && !new_pattern) {
+      const int64_t est = msp_estimate_device_bytes(j->req.nb, j->req.b, j->req.nnzb, &S->cfg.cfg);
+      const int64_t grow = est > sy.bytes ? est - sy.bytes : 0;
+      if (!room_by_release(S, key, S->cfg.hbm_budget - S->charged, grow, idle) &&
+          S->st.running > 0) {
+        memory_blocked = true;  // later new systems wait behind it
+        blocked_keys.insert(key);  // a running request will free or shrink its charge
+        continue;
+      }
+      release_idle(S, idle, out);
+      S->systems[key].bytes += grow;
+      S->charged += grow;
+      S->st.peak_charged_bytes = std::max(S->st.peak_charged_bytes, S->charged);
       out.job = j;
       out.setup = false;
       S->queue.erase(it);
@@ -110,31 +158,14 @@ bool pick_job(msp_server_s* S, Pick& out) {
     }
     const int64_t need = msp_estimate_device_bytes(j->req.nb, j->req.b, j->req.nnzb, &S->cfg.cfg);
     const int64_t avail = S->cfg.hbm_budget - S->charged + (sy.ready ? sy.bytes : 0);
-    std::vector<std::pair<uint64_t, int64_t>> idle;  // last_used, key
-    if (avail < need) {
-      for (auto& kv : S->systems)
-        if (kv.first != key && !kv.second.busy && kv.second.ready && kv.second.queued == 0)
-          idle.push_back({kv.second.last_used, kv.first});
-      std::sort(idle.begin(), idle.end());
-      int64_t extra = 0;
-      size_t k = 0;
-      for (; k < idle.size() && avail + extra < need; ++k) extra += S->systems[idle[k].second].bytes;
-      if (avail + extra < need) {
-        memory_blocked = true;
-        blocked_keys.insert(key);
-        continue;
-      }
-      idle.resize(k);
+    if (!room_by_release(S, key, avail, need, idle)) {
+      memory_blocked = true;
+      blocked_keys.insert(key);
+      continue;
     }
     // admitted.  The worker frees the systems it releases before it allocates anything for
     // the new one, so their bytes are uncharged at once.
-    for (auto& e : idle) {
-      System& v = S->systems[e.second];
-      out.evict.push_back({e.second, v.h});
-      S->charged -= v.bytes;
-      S->systems.erase(e.second);
-      ++S->st.evictions;
-    }
+    release_idle(S, idle, out);
     System& me = S->systems[key];
     if (me.ready) {
       out.evict.push_back({key, me.h});

@@ -91,19 +91,23 @@ __device__ __forceinline__ T group_sum(T v) {
   return v;
 }
 
-// One long row by one warp: S_r = sum over the blocks q in [q0, q1), q != skip, of
-// sum_c A_q[r][c] x_{ci[q]}[c], with A_q the R x C values at vals + q * R * C (row-major)
-// and x_j the C values at x + j * xs + xo.  The warp holds NB = 32 / R blocks at a time,
-// R lanes each (lane l: row l % R of blocks q0 + l / R, q0 + l / R + NB, ...), the same
-// few registers per lane as the lane-group kernels; lane r < R returns S_r, summed over
-// its NB partners in a fixed order.  x rows are never written by the launch.
+// One long row by one thread block (kThreads threads): S_r = sum over the blocks q in
+// [q0, q1), q != skip, of sum_c A_q[r][c] x_{ci[q]}[c], with A_q the R x C values at
+// vals + q * R * C (row-major) and x_j the C values at x + j * xs + xo.  The block holds
+// NB = kThreads / R blocks at a time, R threads each (thread t: row t % R of blocks
+// q0 + t / R, q0 + t / R + NB, ...), the same few registers per thread as the lane-group
+// kernels; thread r < R returns S_r, the partial sums combined through shared memory in
+// a fixed order.  Every thread of the block calls it (it synchronises the block).  x rows
+// are never written by the launch.
 template <int R, int C, typename T>
-__device__ __forceinline__ T warp_row_sum(int q0, int q1, int skip, const int* __restrict__ ci,
-                                          const T* __restrict__ vals, const T* x, int xs,
-                                          int xo) {
-  constexpr int NB = kWarp / R;
-  const int l = threadIdx.x % kWarp;
-  const int r = l % R, k0 = l / R;
+__device__ __forceinline__ T block_row_sum(int q0, int q1, int skip, const int* __restrict__ ci,
+                                           const T* __restrict__ vals, const T* x, int xs,
+                                           int xo) {
+  constexpr int NB = kThreads / R, G = 8;
+  __shared__ T part_s[kThreads];
+  __shared__ T group_s[G * 8];
+  const int t = threadIdx.x;
+  const int r = t % R, k0 = t / R;
   T part = T(0);
   if (k0 < NB) {
 #pragma unroll 1
@@ -115,17 +119,28 @@ __device__ __forceinline__ T warp_row_sum(int q0, int q1, int skip, const int* _
       for (int c = 0; c < C; ++c) part = fma(__ldg(a + c), __ldg(xr + c), part);
     }
   }
-  T tot = part;
+  part_s[t] = part;
+  __syncthreads();
+  if (t < R * G) {  // G partial sums per row r, then their sum in order
+    const int rr = t % R, g = t / R;
+    T sg = T(0);
+    for (int k = g; k < NB; k += G) sg += part_s[rr + k * R];
+    group_s[g * R + rr] = sg;
+  }
+  __syncthreads();
+  T tot = T(0);
+  if (t < R) {
 #pragma unroll
-  for (int k = 1; k < NB; ++k) tot += __shfl_sync(0xffffffffu, part, r + k * R);
+    for (int g = 0; g < G; ++g) tot += group_s[g * R + t];
+  }
+  __syncthreads();  // the shared arrays are reused by the next row
   return tot;
 }
 
-// first warp of the grid and warp count, for the warp-per-long-row loops
-__device__ __forceinline__ int grid_warp() {
-  return (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) / kWarp);
+// blocks of a launch: enough for one thread per work item and one block per long row
+inline unsigned with_long_rows(unsigned grid, int nlong) {
+  return std::max(grid, (unsigned)std::min(nlong, 1 << 16));
 }
-__device__ __forceinline__ int grid_warps() { return (int)(gridDim.x * (size_t)blockDim.x / kWarp); }
 
 // ----------------------------------------------------------------------------------
 // y = A x  or  y = g - A x
@@ -140,11 +155,12 @@ __global__ void __launch_bounds__(kThreads) bsr_spmv_kernel(int nb, const int* _
                                                            const unsigned char* __restrict__ rmask,
                                                            const int* __restrict__ lrows,
                                                            int nlong, int lthr) {
-  for (int q = grid_warp(); q < nlong; q += grid_warps()) {  // long rows: a warp each
+  for (int q = blockIdx.x; q < nlong; q += gridDim.x) {  // long rows: a block each
     const int i = lrows[q];
     if (rmask && !rmask[i]) continue;
-    const T sl = warp_row_sum<B, B>(__ldg(rp + i), __ldg(rp + i + 1), -1, ci, v, x, B, 0);
-    const int l = threadIdx.x % kWarp;
+    const T sl = block_row_sum<B, B>(__ldg(rp + i), __ldg(rp + i + 1), -1, ci, v, x, B, 0);
+    if (threadIdx.x >= kWarp) continue;  // the row's outputs are warp 0's
+    const int l = threadIdx.x;
     if (l < B) y[(size_t)i * B + l] = RES ? g[(size_t)i * B + l] - sl : sl;
   }
   constexpr int GP = Gp<B>::v;
@@ -154,7 +170,7 @@ __global__ void __launch_bounds__(kThreads) bsr_spmv_kernel(int nb, const int* _
   for (int i = blockIdx.x * gpb + threadIdx.x / GP; i < nb; i += stride) {
     if (lane >= B || (rmask && !rmask[i])) continue;
     const int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
-    if (p1 - p0 > lthr) continue;  // taken by a warp above
+    if (p1 - p0 > lthr) continue;  // taken by a block above
     T acc = RES ? g[(size_t)i * B + lane] : T(0);
     int p = p0;
     for (; p + 1 < p1; p += 2) {  // two blocks in flight
@@ -187,11 +203,12 @@ __global__ void __launch_bounds__(kThreads) bsr_restrict_p_kernel(
     const T* __restrict__ w, const T* __restrict__ g, const T* __restrict__ omega,
     T* __restrict__ rP, T* __restrict__ r, const unsigned char* __restrict__ rmask,
     const int* __restrict__ lrows, int nlong, int lthr) {
-  for (int q = grid_warp(); q < nlong; q += grid_warps()) {  // long rows: a warp each
+  for (int q = blockIdx.x; q < nlong; q += gridDim.x) {  // long rows: a block each
     const int i = lrows[q];
     if (rmask && !rmask[i]) continue;
-    const T sl = warp_row_sum<B, B>(__ldg(rp + i), __ldg(rp + i + 1), -1, ci, v, w, B, 0);
-    const int l = threadIdx.x % kWarp;
+    const T sl = block_row_sum<B, B>(__ldg(rp + i), __ldg(rp + i + 1), -1, ci, v, w, B, 0);
+    if (threadIdx.x >= kWarp) continue;  // the row's outputs are warp 0's
+    const int l = threadIdx.x;
     T term = T(0);
     if (l < B) {
       const T al = g[(size_t)i * B + l] - sl;
@@ -211,7 +228,7 @@ __global__ void __launch_bounds__(kThreads) bsr_restrict_p_kernel(
     const int i = base + threadIdx.x / GP;
     T res = T(0);
     bool live = (i < nb) && (!rmask || rmask[i]);
-    // rows taken by a warp above: every lane of the group reads the same length
+    // rows taken by a block above: every lane of the group reads the same length
     if (live && __ldg(rp + i + 1) - __ldg(rp + i) > lthr) live = false;
     const bool active = live && (lane < B);
     if (active) {
@@ -256,11 +273,12 @@ __global__ void __launch_bounds__(kThreads) bsr_col0_update_kernel(
     const T* __restrict__ e, T* __restrict__ r, T* __restrict__ w,
     const unsigned char* __restrict__ rmask, const int* __restrict__ lrows, int nlong,
     int lthr) {
-  for (int q = grid_warp(); q < nlong; q += grid_warps()) {  // long rows: a warp each
+  for (int q = blockIdx.x; q < nlong; q += gridDim.x) {  // long rows: a block each
     const int i = lrows[q];
     if (rmask && !rmask[i]) continue;
-    const T sl = warp_row_sum<B, 1>(__ldg(rp + i), __ldg(rp + i + 1), -1, ci, c0, e, 1, 0);
-    const int l = threadIdx.x % kWarp;
+    const T sl = block_row_sum<B, 1>(__ldg(rp + i), __ldg(rp + i + 1), -1, ci, c0, e, 1, 0);
+    if (threadIdx.x >= kWarp) continue;  // the row's outputs are warp 0's
+    const int l = threadIdx.x;
     if (l < B) r[(size_t)i * B + l] -= sl;
     if (l == 0) w[(size_t)i * B] += __ldg(e + i);
   }
@@ -271,7 +289,7 @@ __global__ void __launch_bounds__(kThreads) bsr_col0_update_kernel(
   for (int i = blockIdx.x * gpb + threadIdx.x / GP; i < nb; i += stride) {
     if (lane >= B || (rmask && !rmask[i])) continue;
     const int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
-    if (p1 - p0 > lthr) continue;  // taken by a warp above
+    if (p1 - p0 > lthr) continue;  // taken by a block above
     T acc = r[(size_t)i * B + lane];
     int p = p0;
     for (; p + 3 < p1; p += 4) {  // four blocks in flight
@@ -312,13 +330,14 @@ __global__ void __launch_bounds__(kThreads) bgs_colour_kernel(
     const unsigned char* __restrict__ rmask, const int* __restrict__ lrows, int nlong,
     int lthr) {
   constexpr int BN = B - 1;
-  for (int q = grid_warp(); q < nlong; q += grid_warps()) {  // long rows: a warp each
+  for (int q = blockIdx.x; q < nlong; q += gridDim.x) {  // long rows: a block each
     const int i = lrows[q];
     if (rmask && !rmask[i]) continue;
     const int pd = __ldg(dpos + i);
-    const T sl = warp_row_sum<BN, BN>(__ldg(rp + i), lower_only ? pd : __ldg(rp + i + 1), pd,
+    const T sl = block_row_sum<BN, BN>(__ldg(rp + i), lower_only ? pd : __ldg(rp + i + 1), pd,
                                       ci, aN, w, B, 1);
-    const int l = threadIdx.x % kWarp;
+    if (threadIdx.x >= kWarp) continue;  // the row's outputs are warp 0's
+    const int l = threadIdx.x;
     if (l < BN) w[(size_t)i * B + 1 + l] = y[(size_t)i * BN + l] - sl;
     if (zero_pressure && l == 0) w[(size_t)i * B] = T(0);
   }
@@ -331,8 +350,12 @@ __global__ void __launch_bounds__(kThreads) bgs_colour_kernel(
     if (rmask && !rmask[i]) continue;
     T acc = y[(size_t)i * BN + lane];
     const int p0 = __ldg(rp + i), pd = __ldg(dpos + i), p1 = __ldg(rp + i + 1);
-    if (p1 - p0 > lthr) continue;  // taken by a warp above
+    if (p1 - p0 > lthr) continue;  // taken by a block above
     const int pend = lower_only ? pd : p1;
+    // the off-diagonal blocks only (the diagonal block is not read): the k-th of them
+    // sits at p0 + k, one further on from the diagonal position
+    const int cnt = (pend - p0) - (pd < pend ? 1 : 0);
+    auto at = [&](int k) { return p0 + k + (p0 + k >= pd ? 1 : 0); };
     // w rows of other colours: none of them is written by this launch
     auto load = [&](int p, T (&a)[BN], T (&xx)[BN]) {
       const T* xr = w + (size_t)__ldg(ci + p) * B + 1;
@@ -343,23 +366,19 @@ __global__ void __launch_bounds__(kThreads) bgs_colour_kernel(
         xx[c] = __ldg(xr + c);
       }
     };
-    int p = p0;
-    for (; p + 1 < pend; p += 2) {  // two blocks in flight, same order as one at a time
+    int k = 0;
+    for (; k + 1 < cnt; k += 2) {  // two blocks in flight, same order as one at a time
       T a0[BN], x0[BN], a1[BN], x1[BN];
-      load(p, a0, x0);
-      load(p + 1, a1, x1);  // the diagonal block is read but not applied
-      if (p != pd) {
+      load(at(k), a0, x0);
+      load(at(k + 1), a1, x1);
 #pragma unroll
-        for (int c = 0; c < BN; ++c) acc = fma(-a0[c], x0[c], acc);
-      }
-      if (p + 1 != pd) {
+      for (int c = 0; c < BN; ++c) acc = fma(-a0[c], x0[c], acc);
 #pragma unroll
-        for (int c = 0; c < BN; ++c) acc = fma(-a1[c], x1[c], acc);
-      }
+      for (int c = 0; c < BN; ++c) acc = fma(-a1[c], x1[c], acc);
     }
-    if (p < pend && p != pd) {
+    if (k < cnt) {
       T a0[BN], x0[BN];
-      load(p, a0, x0);
+      load(at(k), a0, x0);
 #pragma unroll
       for (int c = 0; c < BN; ++c) acc = fma(-a0[c], x0[c], acc);
     }
@@ -398,11 +417,12 @@ __global__ void __launch_bounds__(kThreads) bilu_fwd_kernel(
     const int* __restrict__ dpos, const T* __restrict__ lu, const T* __restrict__ r,
     T* __restrict__ y, const unsigned char* __restrict__ rmask, const int* __restrict__ lrows,
     int nlong, int lthr) {
-  for (int q = grid_warp(); q < nlong; q += grid_warps()) {  // long rows: a warp each
+  for (int q = blockIdx.x; q < nlong; q += gridDim.x) {  // long rows: a block each
     const int i = lrows[q];
     if (rmask && !rmask[i]) continue;
-    const T sl = warp_row_sum<B, B>(__ldg(rp + i), __ldg(dpos + i), -1, ci, lu, y, B, 0);
-    const int l = threadIdx.x % kWarp;
+    const T sl = block_row_sum<B, B>(__ldg(rp + i), __ldg(dpos + i), -1, ci, lu, y, B, 0);
+    if (threadIdx.x >= kWarp) continue;  // the row's outputs are warp 0's
+    const int l = threadIdx.x;
     if (l < B) y[(size_t)i * B + l] = r[(size_t)i * B + l] - sl;
   }
   constexpr int GP = Gp<B>::v;
@@ -410,7 +430,7 @@ __global__ void __launch_bounds__(kThreads) bilu_fwd_kernel(
   const int gpb = blockDim.x / GP;
   for (int i = r0 + blockIdx.x * gpb + threadIdx.x / GP; i < r1; i += gridDim.x * gpb) {
     if (lane >= B || (rmask && !rmask[i])) continue;
-    if (__ldg(rp + i + 1) - __ldg(rp + i) > lthr) continue;  // taken by a warp above
+    if (__ldg(rp + i + 1) - __ldg(rp + i) > lthr) continue;  // taken by a block above
     T acc = r[(size_t)i * B + lane];
     const int p0 = __ldg(rp + i), pd = __ldg(dpos + i);
     // y rows of earlier colours: none of them is written by this launch
@@ -444,11 +464,12 @@ __global__ void __launch_bounds__(kThreads) bilu_bwd_kernel(
     const T* __restrict__ y, T* __restrict__ x, T* __restrict__ w,
     const unsigned char* __restrict__ rmask, const int* __restrict__ lrows, int nlong,
     int lthr) {
-  for (int q = grid_warp(); q < nlong; q += grid_warps()) {  // long rows: a warp each
+  for (int q = blockIdx.x; q < nlong; q += gridDim.x) {  // long rows: a block each
     const int i = lrows[q];
     if (rmask && !rmask[i]) continue;
-    const T sl = warp_row_sum<B, B>(__ldg(dpos + i) + 1, __ldg(rp + i + 1), -1, ci, lu, x, B, 0);
-    const int l = threadIdx.x % kWarp;
+    const T sl = block_row_sum<B, B>(__ldg(dpos + i) + 1, __ldg(rp + i + 1), -1, ci, lu, x, B, 0);
+    if (threadIdx.x >= kWarp) continue;  // the row's outputs are warp 0's
+    const int l = threadIdx.x;
     const T t = l < B ? y[(size_t)i * B + l] - sl : T(0);
     const T* ui = uinv + ((size_t)i * B + (l < B ? l : 0)) * B;
     T out = T(0);
@@ -468,7 +489,7 @@ __global__ void __launch_bounds__(kThreads) bilu_bwd_kernel(
   const int grp = threadIdx.x / GP;
   for (int base = r0 + blockIdx.x * gpb; base < r1; base += gridDim.x * gpb) {
     const int i = base + grp;
-    // rows taken by a warp above are left out; every lane of the group reads the same length
+    // rows taken by a block above are left out; every lane of the group reads the same length
     const bool active = (i < r1) && (lane < B) && (!rmask || rmask[i]) &&
                         __ldg(rp + i + 1) - __ldg(rp + i) <= lthr;
     T acc = T(0);
@@ -1448,7 +1469,7 @@ int launch_bsr_spmv(int b, int nb, const int* rp, const int* ci, const T* v, con
                     const unsigned char* rmask, LongRows lr) {
   if (nb <= 0) return MSP_OK;
   MSP_B_SWITCH(b, {
-    const unsigned grid = grid_groups(nb, Gp<B_>::v);
+    const unsigned grid = with_long_rows(grid_groups(nb, Gp<B_>::v), lr.n);
     if (residual)
       bsr_spmv_kernel<B_, T, true><<<grid, kThreads, 0, s>>>(nb, rp, ci, v, x, g, y, rmask,
                                                              lr.rows, lr.n, lr.thr);
@@ -1465,7 +1486,7 @@ int launch_bsr_restrict_p(int b, int nb, const int* rp, const int* ci, const T* 
                           const unsigned char* rmask, LongRows lr) {
   if (nb <= 0) return MSP_OK;
   MSP_B_SWITCH(b, {
-    const unsigned grid = grid_groups(nb, Gp<B_>::v);
+    const unsigned grid = with_long_rows(grid_groups(nb, Gp<B_>::v), lr.n);
     if (r)
       bsr_restrict_p_kernel<B_, T, true><<<grid, kThreads, 0, s>>>(
           nb, rp, ci, v, w, g, omega, rP, r, rmask, lr.rows, lr.n, lr.thr);
@@ -1482,7 +1503,7 @@ int launch_bsr_col0_update(int b, int nb, const int* rp, const int* ci, const T*
                            LongRows lr) {
   if (nb <= 0) return MSP_OK;
   MSP_B_SWITCH(b, {
-    const unsigned grid = grid_groups(nb, Gp<B_>::v);
+    const unsigned grid = with_long_rows(grid_groups(nb, Gp<B_>::v), lr.n);
     bsr_col0_update_kernel<B_, T><<<grid, kThreads, 0, s>>>(nb, rp, ci, c0, e, r, w, rmask,
                                                             lr.rows, lr.n, lr.thr);
   });
@@ -1504,7 +1525,8 @@ int launch_bgs_colour(int b, int r0, int r1, const int* rp, const int* ci, const
   switch (b) {
 #define MSP_BGS_CASE(BB)                                                                   \
   case BB: {                                                                               \
-    const unsigned grid = grid_for((size_t)(r1 - r0) * (BB - 1), kThreads, kRowGridPerSm);  \
+    const unsigned grid =                                                                  \
+        with_long_rows(grid_for((size_t)(r1 - r0) * (BB - 1), kThreads, kRowGridPerSm), lr.n); \
     bgs_colour_kernel<BB, T><<<grid, kThreads, 0, s>>>(                                    \
         r0, r1, rp, ci, dpos, aN, y, w, lower_only, zero_pressure, rmask, lr.rows, lr.n,    \
         lr.thr);                                                                           \
@@ -1546,7 +1568,7 @@ int launch_bilu_fwd(int b, int r0, int r1, const int* rp, const int* ci, const i
                     LongRows lr) {
   if (r1 <= r0) return MSP_OK;
   MSP_B_SWITCH(b, {
-    const unsigned grid = grid_groups(r1 - r0, Gp<B_>::v);
+    const unsigned grid = with_long_rows(grid_groups(r1 - r0, Gp<B_>::v), lr.n);
     bilu_fwd_kernel<B_, T><<<grid, kThreads, 0, s>>>(r0, r1, rp, ci, dpos, lu, r, y, rmask,
                                                      lr.rows, lr.n, lr.thr);
   });
@@ -1559,7 +1581,7 @@ int launch_bilu_bwd(int b, int r0, int r1, const int* rp, const int* ci, const i
                     const unsigned char* rmask, LongRows lr) {
   if (r1 <= r0) return MSP_OK;
   MSP_B_SWITCH(b, {
-    const unsigned grid = grid_groups(r1 - r0, Gp<B_>::v);
+    const unsigned grid = with_long_rows(grid_groups(r1 - r0, Gp<B_>::v), lr.n);
     bilu_bwd_kernel<B_, T><<<grid, kThreads, 0, s>>>(r0, r1, rp, ci, dpos, lu, uinv, y, x, w,
                                                      rmask, lr.rows, lr.n, lr.thr);
   });

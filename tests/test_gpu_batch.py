@@ -136,6 +136,37 @@ def test_fp32_and_new_values():
     g.close()
 
 
+def test_instances_with_long_well_rows():
+    """Wells perforating 20-24 layers: rows of more than 16 blocks, walked by a thread block
+    each in the level-0 kernels, in several instances at once, with instances leaving the
+    active set at different steps."""
+    ms = [box_jacobian(5, 4, 24, 4, 41, layered=True, kz_ratio=0.1, n_wells=2),
+          box_jacobian(6, 5, 20, 4, 42, n_wells=1),
+          box_jacobian(7, 3, 22, 4, 43, layered=True, kz_ratio=0.1, n_wells=3)]
+    S, off = _stack(ms)
+    assert int((np.diff(S.row_ptr) > 16).sum()) == 6
+    g = msp.BatchSolver(S.nb, S.b, _t(S.row_ptr), _t(S.col_idx), _t(S.values.reshape(-1)), off,
+                        **CFG)
+    o = oracle.Oracle(S, **CFG)
+    rhs = _rhs(ms, off, S.b, 90)
+    x = torch.zeros(S.nb * S.b, dtype=torch.float64, device=DEV)
+    infos = g.solve_batch(_t(rhs), x, 1e-6)
+    xx = x.cpu().numpy()
+    A = S.to_scipy()
+    for k in range(len(ms)):
+        lo, hi = off[k] * S.b, off[k + 1] * S.b
+        gk = np.zeros_like(rhs)
+        gk[lo:hi] = rhs[lo:hi]
+        _, oinfo = o.solve(gk, 1e-6)
+        assert infos[k]["status"] == 0, (k, infos[k])
+        assert abs(infos[k]["iterations"] - oinfo["iterations"]) <= 1, (k, infos[k], oinfo)
+        xk = np.zeros_like(xx)
+        xk[lo:hi] = xx[lo:hi]
+        assert np.linalg.norm(gk - A @ xk) <= 1e-6 * np.linalg.norm(gk) * 1.001, k
+    g.close()
+    o.close()
+
+
 def test_rejected_instances():
     ms = _instances()[:2]
     S, off = _stack(ms)

@@ -159,6 +159,36 @@ def test_replacement_passes_a_memory_waiter():
     assert rec.max_alive <= 2.5 * EST
 
 
+class Growing(Recorder):
+    """A system's footprint grows after its first request (0.5 x the estimate at setup,
+    0.9 x after a later request: the staging copy of new values), as the CUDA executor's
+    do; the executor tracks what it holds."""
+
+    def _exec(self, user, op, req, slot, setup, bytes_out):
+        st = super()._exec(user, op, req, slot, setup, bytes_out)
+        if op != _native.MSP_EXEC_RELEASE:
+            key = req.contents.key
+            with self.mu:
+                self.alive[key] = int((0.5 if setup else 0.9) * EST)
+                self.max_alive = max(self.max_alive, sum(self.alive.values()))
+            bytes_out[0] = self.alive[key]
+        return st
+
+
+def test_growth_of_resident_systems_is_charged_before_it_happens():
+    """Budget 2 x the estimate.  Keys 0, 1, 2 set up (0.5 each), key 0 runs again and grows
+    to 0.9; key 1's second request would take the total to 2.3: it is charged its possible
+    growth first, so the idle key 2 is released before it runs."""
+    rec = Growing(run_s=0.005)
+    budget = 2 * EST
+    results, stats = _run(1, budget, [(0, 0), (1, 0), (2, 0), (0, 0), (1, 0)], rec)
+    assert all(r["status"] == 0 for r in results)
+    assert [r["setup"] for r in results] == [1, 1, 1, 0, 0]
+    assert [k for e, k, *_ in rec.before_free if e == "release"] == [2]
+    assert stats["peak_charged_bytes"] <= budget
+    assert rec.max_alive <= budget
+
+
 def test_oversized_request_rejected_and_bad_arguments():
     rec = Recorder()
     S = _native.msp_server_create(2, EST // 2, None, 0, rec.fn)
