@@ -13,12 +13,12 @@
 //     and so do the later requests that need a new system (they keep their order), while
 //     later requests of resident systems, replacements included, may still start;
 //   * once a system is set up its measured footprint replaces the estimate;
-//   * a request of a resident system is charged, while it runs, the difference between the
-//     estimate and the system's measured footprint (a system grows after its setup: the
-//     staging copy of new values, a regenerated hierarchy of another size), admitted like
-//     a new system (idle systems released to make room, else it waits for a running
-//     request to finish; with nothing running it starts anyway), so that the charged
-//     total never exceeds the budget while the estimate bounds every footprint.
+//   * a system grows once after its setup: its first update of values from the host
+//     allocates the staging copy of the values (nnzb * b * b doubles, part of the
+//     estimate).  That request is charged the copy before it runs and admitted like a new
+//     system (idle systems released to make room, else it waits for a running request to
+//     finish; with nothing running it starts anyway), so that the charged total does not
+//     run past the budget after the fact.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -55,6 +55,7 @@ struct System {
   int64_t bytes = 0;       // charged against the budget (estimate until set up)
   bool busy = false;
   bool ready = false;      // set up (false while its first request runs)
+  bool staged = false;     // holds the staging copy of host values (after its first update)
   int queued = 0;          // requests of this key waiting in the queue
   uint64_t last_used = 0;
 };
@@ -85,9 +86,11 @@ struct Pick {
   std::vector<std::pair<int64_t, msp_handle>> evict;  // key, handle (CUDA executor)
 };
 
+// The staging copy of host values a system allocates at its first value update
+int64_t staging_bytes(const msp_request& r) { return r.nnzb * (int64_t)r.b * r.b * 8; }
+
 // Idle resident systems (not `key`, no request running or queued), least recently used
-// first, whose release makes `extra` more bytes available than `avail`; false if even all
-// of them are not enough.
+// first, whose release raises `avail` to `need`; false if even all of them are not enough.
 bool room_by_release(msp_server_s* S, int64_t key, int64_t avail, int64_t need,
                      std::vector<std::pair<uint64_t, int64_t>>& idle) {
   idle.clear();
@@ -131,8 +134,7 @@ bool pick_job(msp_server_s* S, Pick& out) {
     const bool new_pattern = (j->req.flags & MSP_REQ_NEW_PATTERN) != 0;
     std::vector<std::pair<uint64_t, int64_t>> idle;  // last_used, key
     if (sy.ready && !new_pattern) {
-      const int64_t est = msp_estimate_device_bytes(j->req.nb, j->req.b, j->req.nnzb, &S->cfg.cfg);
-      const int64_t grow = est > sy.bytes ? est - sy.bytes : 0;
+      const int64_t grow = (!sy.staged && j->req.h_values) ? staging_bytes(j->req) : 0;
       if (!room_by_release(S, key, S->cfg.hbm_budget - S->charged, grow, idle) &&
           S->st.running > 0) {
         memory_blocked = true;  // later new systems wait behind it
@@ -140,7 +142,9 @@ bool pick_job(msp_server_s* S, Pick& out) {
         continue;
       }
       release_idle(S, idle, out);
-      S->systems[key].bytes += grow;
+      System& me = S->systems[key];
+      me.bytes += grow;
+      if (j->req.h_values) me.staged = true;
       S->charged += grow;
       S->st.peak_charged_bytes = std::max(S->st.peak_charged_bytes, S->charged);
       out.job = j;

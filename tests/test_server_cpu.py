@@ -63,14 +63,14 @@ def _estimate():
     assert EST > NNZB * B * B * 8
 
 
-def _request(key, flags=0):
-    rp = np.zeros(NB + 1, np.int32)
-    ci = np.zeros(NNZB, np.int32)
-    v = np.zeros(NNZB * B * B)
-    g = np.zeros(NB * B)
-    x = np.zeros(NB * B)
+def _request(key, flags=0, nb=NB, nnzb=NNZB):
+    rp = np.zeros(nb + 1, np.int32)
+    ci = np.zeros(nnzb, np.int32)
+    v = np.zeros(nnzb * B * B)
+    g = np.zeros(nb * B)
+    x = np.zeros(nb * B)
     req = _native.MspRequest()
-    req.key, req.nb, req.b, req.nnzb = key, NB, B, NNZB
+    req.key, req.nb, req.b, req.nnzb = key, nb, B, nnzb
     req.h_row_ptr, req.h_col_idx, req.h_values = rp.ctypes.data, ci.ctypes.data, v.ctypes.data
     req.h_rhs, req.h_x, req.rel_tol, req.flags = g.ctypes.data, x.ctypes.data, 1e-6, flags
     return req, (rp, ci, v, g, x)
@@ -159,32 +159,48 @@ def test_replacement_passes_a_memory_waiter():
     assert rec.max_alive <= 2.5 * EST
 
 
-class Growing(Recorder):
-    """A system's footprint grows after its first request (0.5 x the estimate at setup,
-    0.9 x after a later request: the staging copy of new values), as the CUDA executor's
-    do; the executor tracks what it holds."""
+def test_first_value_update_is_charged_before_it_runs():
+    """A system's footprint grows once after its setup: its first update of values from the
+    host allocates the staging copy (nnzb * b * b doubles).  Budget 2 x the estimate minus
+    half a copy: keys 0 and 1 set up and key 0 updates; key 1's update would take the
+    total past the budget, so it is charged the copy first and the idle key 0 is released
+    before it runs (without that charge the total would exceed the budget afterwards)."""
+    nb, nnzb = 200, 20000
+    est = _native.msp_estimate_device_bytes(nb, B, nnzb)
+    copy = nnzb * B * B * 8
+    assert copy > 0.1 * est
+    grown = set()
 
-    def _exec(self, user, op, req, slot, setup, bytes_out):
-        st = super()._exec(user, op, req, slot, setup, bytes_out)
-        if op != _native.MSP_EXEC_RELEASE:
-            key = req.contents.key
-            with self.mu:
-                self.alive[key] = int((0.5 if setup else 0.9) * EST)
-                self.max_alive = max(self.max_alive, sum(self.alive.values()))
-            bytes_out[0] = self.alive[key]
-        return st
+    class Staging(Recorder):
+        def _exec(self, user, op, req, slot, setup, bytes_out):
+            st = super()._exec(user, op, req, slot, setup, bytes_out)
+            if op != _native.MSP_EXEC_RELEASE:
+                key = req.contents.key
+                if setup:
+                    grown.discard(key)
+                else:
+                    grown.add(key)
+                with self.mu:
+                    self.alive[key] = est - 1000 - (0 if key in grown else copy)
+                    self.max_alive = max(self.max_alive, sum(self.alive.values()))
+                bytes_out[0] = self.alive[key]
+            return st
 
-
-def test_growth_of_resident_systems_is_charged_before_it_happens():
-    """Budget 2 x the estimate.  Keys 0, 1, 2 set up (0.5 each), key 0 runs again and grows
-    to 0.9; key 1's second request would take the total to 2.3: it is charged its possible
-    growth first, so the idle key 2 is released before it runs."""
-    rec = Growing(run_s=0.005)
-    budget = 2 * EST
-    results, stats = _run(1, budget, [(0, 0), (1, 0), (2, 0), (0, 0), (1, 0)], rec)
+    rec = Staging(run_s=0.005, bytes_of=lambda key: est - 1000 - copy)
+    budget = 2 * est - copy // 2
+    S = _native.msp_server_create(1, budget, None, 0, rec.fn)
+    keep, tickets = [], []
+    for key in (0, 1, 0, 1):
+        req, arrays = _request(key, 0, nb=nb, nnzb=nnzb)
+        keep.append(arrays)
+        tickets.append(_native.msp_server_submit(S, req))
+    results = [_native.msp_server_wait(S, t, 30.0) for t in tickets]
+    stats = _native.msp_server_get_stats(S)
+    released = [k for e, k, *_ in rec.log if e == "release"]
+    _native.msp_server_free(S)
     assert all(r["status"] == 0 for r in results)
-    assert [r["setup"] for r in results] == [1, 1, 1, 0, 0]
-    assert [k for e, k, *_ in rec.before_free if e == "release"] == [2]
+    assert [r["setup"] for r in results] == [1, 1, 0, 0]
+    assert released == [0]
     assert stats["peak_charged_bytes"] <= budget
     assert rec.max_alive <= budget
 
