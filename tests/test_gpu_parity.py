@@ -180,12 +180,12 @@ def test_long_rows_take_the_csr_path():
     g.close()
 
 
-@pytest.mark.parametrize("b", [2, 4, 6])
-def test_level0_long_rows_walked_by_a_warp(b):
+@pytest.mark.parametrize("b", [2, 4, 6, 8])
+def test_level0_long_rows_walked_by_a_block(b):
     """Wells perforating 40 layers give level-0 block rows of 41 blocks, more than the 16
-    that one lane group walks: the SpMV, the stage-N sweeps (b - 1 = 1, 3, 5 lanes per
-    sub-block row), the stage-P restriction and correction and both BILU sweeps give each
-    such row a warp.  SpMV elementwise, every stage alone and the whole application within
+    that one lane group walks: the SpMV, the stage-N sweeps (b - 1 = 1, 3, 5, 7 threads per
+    row, rows straddling warps for 3, 5, 7), the stage-P restriction and correction and
+    both BILU sweeps give each such row a thread block.  SpMV elementwise, every stage alone and the whole application within
     the FP64 tolerance, the solve within one iteration of the oracle, in FP64 and with the
     FP32 preconditioner (Section 3.3: same convergence, FP64 residual)."""
     a = box_jacobian(7, 6, 40, b, 17 + b, layered=True, kz_ratio=0.1, n_wells=3)
