@@ -57,6 +57,7 @@ struct System {
   bool ready = false;      // set up (false while its first request runs)
   bool staged = false;     // holds the staging copy of host values (after its first update)
   int queued = 0;          // requests of this key waiting in the queue
+  int queued_bare = 0;     // of those, requests without the pattern (they need it resident)
   uint64_t last_used = 0;
 };
 
@@ -89,14 +90,17 @@ struct Pick {
 // The staging copy of host values a system allocates at its first value update
 int64_t staging_bytes(const msp_request& r) { return r.nnzb * (int64_t)r.b * r.b * 8; }
 
-// Idle resident systems (not `key`, no request running or queued), least recently used
-// first, whose release raises `avail` to `need`; false if even all of them are not enough.
+// Idle resident systems (not `key`, no request running), least recently used first, whose
+// release raises `avail` to `need`; false if even all of them are not enough.  Only systems
+// without queued requests, unless `queued_too`: then also those whose queued requests all
+// carry the pattern (they set the system up again).
 bool room_by_release(msp_server_s* S, int64_t key, int64_t avail, int64_t need,
-                     std::vector<std::pair<uint64_t, int64_t>>& idle) {
+                     std::vector<std::pair<uint64_t, int64_t>>& idle, bool queued_too = false) {
   idle.clear();
   if (avail >= need) return true;
   for (auto& kv : S->systems)
-    if (kv.first != key && !kv.second.busy && kv.second.ready && kv.second.queued == 0)
+    if (kv.first != key && !kv.second.busy && kv.second.ready &&
+        (kv.second.queued == 0 || (queued_too && kv.second.queued_bare == 0)))
       idle.push_back({kv.second.last_used, kv.first});
   std::sort(idle.begin(), idle.end());
   int64_t extra = 0;
@@ -112,8 +116,15 @@ void release_idle(msp_server_s* S, const std::vector<std::pair<uint64_t, int64_t
     System& v = S->systems[e.second];
     out.evict.push_back({e.second, v.h});
     S->charged -= v.bytes;
-    S->systems.erase(e.second);
     ++S->st.evictions;
+    if (v.queued == 0) {
+      S->systems.erase(e.second);
+    } else {  // its queued requests set it up again
+      v.h = nullptr;
+      v.ready = false;
+      v.staged = false;
+      v.bytes = 0;
+    }
   }
 }
 
@@ -135,11 +146,15 @@ bool pick_job(msp_server_s* S, Pick& out) {
     std::vector<std::pair<uint64_t, int64_t>> idle;  // last_used, key
     if (sy.ready && !new_pattern) {
       const int64_t grow = (!sy.staged && j->req.h_values) ? staging_bytes(j->req) : 0;
-      if (!room_by_release(S, key, S->cfg.hbm_budget - S->charged, grow, idle) &&
-          S->st.running > 0) {
-        memory_blocked = true;  // later new systems wait behind it
-        blocked_keys.insert(key);  // a running request will free or shrink its charge
-        continue;
+      if (!room_by_release(S, key, S->cfg.hbm_budget - S->charged, grow, idle)) {
+        if (S->st.running > 0) {
+          memory_blocked = true;  // later new systems wait behind it
+          blocked_keys.insert(key);  // a running request will free or shrink its charge
+          continue;
+        }
+        // nothing runs that could free memory: release idle systems whose queued requests
+        // can set them up again; if even that is not enough, start anyway
+        room_by_release(S, key, S->cfg.hbm_budget - S->charged, grow, idle, true);
       }
       release_idle(S, idle, out);
       System& me = S->systems[key];
@@ -247,6 +262,7 @@ void worker_main(msp_server_s* S, int slot) {
     System& sys0 = S->systems[key];
     sys0.busy = true;
     --sys0.queued;
+    if (!j->req.h_row_ptr || !j->req.h_col_idx) --sys0.queued_bare;
     msp_handle h = sys0.h;
     ++S->st.running;
     --S->st.queued;
@@ -389,7 +405,9 @@ int msp_server_submit(msp_server S, const msp_request* req, int64_t* ticket) {
     S->cv.notify_all();
     return MSP_OK;
   }
-  S->systems[req->key].queued++;
+  System& sy = S->systems[req->key];
+  sy.queued++;
+  if (!req->h_row_ptr || !req->h_col_idx) sy.queued_bare++;
   S->queue.push_back(j);
   ++S->st.queued;
   S->cv.notify_all();

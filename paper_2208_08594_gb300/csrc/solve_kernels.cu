@@ -137,6 +137,130 @@ __device__ __forceinline__ T block_row_sum(int q0, int q1, int skip, const int* 
   return tot;
 }
 
+// A colour made only of long rows (the well rows form one at level 0): one thread block
+// per row, every thread of the block holding two of the row's blocks in the first pass,
+// whose column indices and values it loads before `griddepcontrol.wait` (PDL: launched as
+// a programmatic dependent of the previous colour's sweep, it waits only for the gathered
+// x, which it reads from L2, where the previous kernel's writes are).  Thread r < R
+// returns S_r (as block_row_sum, in a fixed order).
+template <int R, int C, typename T, bool PDL>
+__device__ __forceinline__ T long_colour_row_sum(int q0, int q1, int skip,
+                                                 const int* __restrict__ ci,
+                                                 const T* __restrict__ vals, const T* x, int xs,
+                                                 int xo) {
+  constexpr int NB = kThreads / R, G = 8;
+  __shared__ T part_s[kThreads];
+  __shared__ T group_s[G * 8];
+  const int t = threadIdx.x;
+  const int r = t % R, k0 = t / R;
+  const int qa = q0 + k0, qb = q0 + k0 + NB;
+  const bool ha = k0 < NB && qa < q1 && qa != skip;
+  const bool hb = k0 < NB && qb < q1 && qb != skip;
+  const int ja = ha ? __ldg(ci + qa) : 0, jb = hb ? __ldg(ci + qb) : 0;
+  T aa[C], ab[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    aa[c] = ha ? __ldg(vals + ((size_t)qa * R + r) * C + c) : T(0);
+    ab[c] = hb ? __ldg(vals + ((size_t)qb * R + r) * C + c) : T(0);
+  }
+  if constexpr (PDL) asm volatile("griddepcontrol.wait;" ::: "memory");
+  T part = T(0);
+  if (ha) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) part = fma(aa[c], __ldcg(x + (size_t)ja * xs + xo + c), part);
+  }
+  if (hb) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) part = fma(ab[c], __ldcg(x + (size_t)jb * xs + xo + c), part);
+  }
+  if (k0 < NB) {  // rows longer than 2 NB blocks
+#pragma unroll 1
+    for (int q = q0 + k0 + 2 * NB; q < q1; q += NB) {
+      if (q == skip) continue;
+      const T* xr = x + (size_t)__ldg(ci + q) * xs + xo;
+      const T* a = vals + ((size_t)q * R + r) * C;
+#pragma unroll
+      for (int c = 0; c < C; ++c) part = fma(__ldg(a + c), __ldcg(xr + c), part);
+    }
+  }
+  part_s[t] = part;
+  __syncthreads();
+  if (t < R * G) {
+    const int rr = t % R, g = t / R;
+    T sg = T(0);
+    for (int k = g; k < NB; k += G) sg += part_s[rr + k * R];
+    group_s[g * R + rr] = sg;
+  }
+  __syncthreads();
+  T tot = T(0);
+  if (t < R) {
+#pragma unroll
+    for (int g = 0; g < G; ++g) tot += group_s[g * R + t];
+  }
+  return tot;
+}
+
+// stage-N sweep over a colour of long rows only: block q takes row r0 + q
+template <int B, typename T, bool PDL>
+__global__ void __launch_bounds__(kThreads) bgs_long_colour_kernel(
+    int r0, const int* __restrict__ rp, const int* __restrict__ ci, const int* __restrict__ dpos,
+    const T* __restrict__ aN, const T* __restrict__ y, T* __restrict__ w, bool lower_only,
+    bool zero_pressure, const unsigned char* __restrict__ rmask) {
+  constexpr int BN = B - 1;
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int i = r0 + blockIdx.x;
+  if (rmask && !rmask[i]) return;  // uniform over the block
+  const int pd = __ldg(dpos + i);
+  const int l = threadIdx.x;
+  const T yl = l < BN ? __ldg(y + (size_t)i * BN + l) : T(0);
+  const T sl = long_colour_row_sum<BN, BN, T, PDL>(__ldg(rp + i), lower_only ? pd : __ldg(rp + i + 1),
+                                                   pd, ci, aN, w, B, 1);
+  if (l < BN) w[(size_t)i * B + 1 + l] = yl - sl;
+  if (zero_pressure && l == 0) w[(size_t)i * B] = T(0);
+}
+
+// BILU(0) forward over a colour of long rows only
+template <int B, typename T, bool PDL>
+__global__ void __launch_bounds__(kThreads) bilu_fwd_long_colour_kernel(
+    int r0, const int* __restrict__ rp, const int* __restrict__ ci, const int* __restrict__ dpos,
+    const T* __restrict__ lu, const T* __restrict__ r, T* __restrict__ y,
+    const unsigned char* __restrict__ rmask) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int i = r0 + blockIdx.x;
+  if (rmask && !rmask[i]) return;
+  const int l = threadIdx.x;
+  const T rl = l < B ? __ldg(r + (size_t)i * B + l) : T(0);
+  const T sl = long_colour_row_sum<B, B, T, PDL>(__ldg(rp + i), __ldg(dpos + i), -1, ci, lu, y, B, 0);
+  if (l < B) y[(size_t)i * B + l] = rl - sl;
+}
+
+// BILU(0) backward over a colour of long rows only: x_i = U_ii^-1 (y_i - sum_{j>i} U_ij x_j)
+template <int B, typename T, bool PDL>
+__global__ void __launch_bounds__(kThreads) bilu_bwd_long_colour_kernel(
+    int r0, const int* __restrict__ rp, const int* __restrict__ ci, const int* __restrict__ dpos,
+    const T* __restrict__ lu, const T* __restrict__ uinv, const T* __restrict__ y,
+    T* __restrict__ x, T* __restrict__ w, const unsigned char* __restrict__ rmask) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int i = r0 + blockIdx.x;
+  if (rmask && !rmask[i]) return;
+  const int l = threadIdx.x;
+  const T sl = long_colour_row_sum<B, B, T, PDL>(__ldg(dpos + i) + 1, __ldg(rp + i + 1), -1, ci, lu,
+                                                 x, B, 0);
+  if (l >= kWarp) return;  // the row's outputs are warp 0's
+  const T t = l < B ? __ldcg(y + (size_t)i * B + l) - sl : T(0);
+  const T* ui = uinv + ((size_t)i * B + (l < B ? l : 0)) * B;
+  T out = T(0);
+#pragma unroll
+  for (int c = 0; c < B; ++c) {
+    const T tc = __shfl_sync(0xffffffffu, t, c);
+    if (l < B) out = fma(__ldg(ui + c), tc, out);
+  }
+  if (l < B) {
+    x[(size_t)i * B + l] = out;
+    w[(size_t)i * B + l] += out;
+  }
+}
+
 // blocks of a launch: enough for one thread per work item and one block per long row
 inline unsigned with_long_rows(unsigned grid, int nlong) {
   return std::max(grid, (unsigned)std::min(nlong, 1 << 16));
@@ -330,6 +454,9 @@ __global__ void __launch_bounds__(kThreads) bgs_colour_kernel(
     const unsigned char* __restrict__ rmask, const int* __restrict__ lrows, int nlong,
     int lthr) {
   constexpr int BN = B - 1;
+  // a colour of long rows may follow as a programmatic dependent (it waits for this grid
+  // before it reads w)
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   for (int q = blockIdx.x; q < nlong; q += gridDim.x) {  // long rows: a block each
     const int i = lrows[q];
     if (rmask && !rmask[i]) continue;
@@ -397,8 +524,7 @@ __global__ void nscale_kernel(int nb, const T* __restrict__ dNinv, const T* __re
   const size_t total = (size_t)nb * BN;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
        t += (size_t)gridDim.x * blockDim.x) {
-    const size_t i = t / BN;
-    const int r = (int)(t % BN);
+    const size_t i = t / BN;  // row i, concentration unknown t % BN
     const T* d = dNinv + t * BN;
     const T* gi = g + i * B + 1;
     T acc = T(0);
@@ -417,6 +543,7 @@ __global__ void __launch_bounds__(kThreads) bilu_fwd_kernel(
     const int* __restrict__ dpos, const T* __restrict__ lu, const T* __restrict__ r,
     T* __restrict__ y, const unsigned char* __restrict__ rmask, const int* __restrict__ lrows,
     int nlong, int lthr) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");  // as in the stage-N sweep
   for (int q = blockIdx.x; q < nlong; q += gridDim.x) {  // long rows: a block each
     const int i = lrows[q];
     if (rmask && !rmask[i]) continue;
@@ -1003,7 +1130,7 @@ __global__ void reduce_partials_strided_kernel(int K, int nblocks, int stride,
   if (lane == 0) out[k] = s;
 }
 
-// One-pass Gram-Schmidt of FGMRES step j (one thread: j <= 64, a few microseconds).  The
+// One-pass Gram-Schmidt of FGMRES step j (one warp, j < 64).  The
 // stored basis U = [u_0 .. u_j] is orthogonalised once; the orthonormal basis it stands for
 // is Q = U T^-1 with T upper triangular (column k of T holds c_k = Q_k^T u_k above the
 // diagonal and nu_k = ||u_k - Q_k c_k|| on it), so Q is never formed.  Inputs: d[k] = u_k .
@@ -1015,57 +1142,104 @@ __global__ void reduce_partials_strided_kernel(int K, int nblocks, int stride,
 // out[147] = 1 if nu_j^2 <= 0 (u_j lies in span Q: the previous step broke down).
 __device__ void dcgs_coef_body(int j, const double* __restrict__ d, double* __restrict__ T, int ldt,
                                double* __restrict__ g, double* __restrict__ out) {
-  // the warp stages the triangle of T and the dot products in shared memory (coalesced),
-  // then one thread runs the three substitutions from there
-  __shared__ double sT[(kMaxRestart + 2) * (kMaxRestart + 2)];
-  __shared__ double sd[2 * kMaxK], sc[kMaxK], sh[kMaxK];
-  const int K = j + 2, ld = kMaxRestart + 2;
-  for (int q = threadIdx.x; q < j * j; q += blockDim.x) {
+  // One warp.  The triangle of T, the dot products and the reciprocal diagonal of T are
+  // staged in shared memory; the three triangular solves are column-oriented: lane l owns
+  // rows l and l + 32, and at step k the owner of row k finishes its unknown, which is
+  // broadcast, and every lane removes that unknown's column from its rows — so a step costs
+  // one shuffle and one FMA per lane on the critical path, not a row's dot product.  The
+  // updates of a row come in the order of a row-by-row substitution (increasing column in
+  // the two forward solves); the unknowns are the row's value times the stored reciprocal.
+  constexpr int ld = kMaxRestart + 1;  // odd: the row reads of the forward solves are
+                                       // spread over the banks
+  __shared__ double sT[(kMaxRestart + 2) * ld];
+  __shared__ double sd[2 * kMaxK], rd[kMaxRestart + 2];
+  const int lane = threadIdx.x;
+  const int K = j + 2;
+  for (int q = lane; q < j * j; q += kWarp) {
     const int col = q / j, row = q % j;
     if (row <= col) sT[col * ld + row] = T[(size_t)col * ldt + row];
   }
-  for (int q = threadIdx.x; q < 2 * K; q += blockDim.x) sd[q] = d[q];
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  double c2 = 0.0;
-  for (int k = 0; k < j; ++k) {  // forward substitution with T_j^T
-    double t = sd[k];
-    for (int i = 0; i < k; ++i) t -= sT[k * ld + i] * sc[i];
-    const double ck = t / sT[k * ld + k];
-    sc[k] = ck;
-    out[72 + k] = ck;
-    c2 += ck * ck;
-  }
+  for (int q = lane; q < 2 * K; q += kWarp) sd[q] = d[q];
+  for (int k = lane; k < j; k += kWarp) rd[k] = 1.0 / T[(size_t)k * ldt + k];
+  __syncwarp();
+  const int i0 = lane, i1 = lane + kWarp;  // the rows this lane owns
+  // forward substitution with L = T^T (L[i][k] = T[k][i] = sT[i * ld + k]) over n rows of
+  // the right-hand side rhs: returns the unknowns of rows i0 and i1
+  auto forward = [&](int n, const double* rhs, double& x0, double& x1) {
+    double r0 = i0 < n ? rhs[i0] : 0.0, r1 = i1 < n ? rhs[i1] : 0.0;
+    x0 = 0.0;
+    x1 = 0.0;
+    for (int k = 0; k < n; ++k) {
+      const bool hi = k >= kWarp;
+      const double mine = (hi ? r1 : r0) * rd[k];
+      const double xk = __shfl_sync(0xffffffffu, mine, k & (kWarp - 1));
+      if (lane == (k & (kWarp - 1))) {
+        if (hi) x1 = xk;
+        else x0 = xk;
+      }
+      if (i0 > k && i0 < n) r0 = fma(-sT[i0 * ld + k], xk, r0);
+      if (i1 > k && i1 < n) r1 = fma(-sT[i1 * ld + k], xk, r1);
+    }
+  };
+  // c = T_j^-T (U_j^T u_j): column j of T above the diagonal
+  double c0, c1;
+  forward(j, sd, c0, c1);
+  double c2 = (i0 < j ? c0 * c0 : 0.0) + (i1 < j ? c1 * c1 : 0.0);
+#pragma unroll
+  for (int o = kWarp / 2; o > 0; o >>= 1) c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+  if (i0 < j) out[72 + i0] = c0;
+  if (i1 < j) out[72 + i1] = c1;
   const double nu2 = sd[j] - c2;
-  out[145] = nu2;
-  out[146] = sd[K + j + 1];
+  if (lane == 0) {
+    out[145] = nu2;
+    out[146] = sd[K + j + 1];
+  }
   if (!(nu2 > 0.0)) {
-    out[144] = 0.0;
-    out[147] = 1.0;
-    for (int k = 0; k <= j; ++k) g[k] = 0.0;
+    if (lane == 0) {
+      out[144] = 0.0;
+      out[147] = 1.0;
+    }
+    for (int k = lane; k <= j; k += kWarp) g[k] = 0.0;
     return;
   }
   const double nu = sqrt(nu2);
-  out[144] = nu;
-  out[147] = 0.0;
-  for (int k = 0; k < j; ++k) {  // column j of T, stored by column
-    T[(size_t)j * ldt + k] = sc[k];
-    sT[j * ld + k] = sc[k];
+  // column j of T, stored by column
+  if (i0 < j) {
+    T[(size_t)j * ldt + i0] = c0;
+    sT[j * ld + i0] = c0;
   }
-  T[(size_t)j * ldt + j] = nu;
-  sT[j * ld + j] = nu;
-  for (int k = 0; k <= j; ++k) {  // h = T^-T (U^T w)
-    double t = sd[K + k];
-    for (int i = 0; i < k; ++i) t -= sT[k * ld + i] * sh[i];
-    sh[k] = t / sT[k * ld + k];
-    out[k] = sh[k];
+  if (i1 < j) {
+    T[(size_t)j * ldt + i1] = c1;
+    sT[j * ld + i1] = c1;
   }
-  for (int k = j; k >= 0; --k) {  // g = T^-1 h; the computed g_i are kept in sd[0..j]
-    double t = sh[k];
-    for (int i = k + 1; i <= j; ++i) t -= sT[i * ld + k] * sd[i];
-    sd[k] = t / sT[k * ld + k];
-    g[k] = sd[k];
+  if (lane == 0) {
+    out[144] = nu;
+    out[147] = 0.0;
+    T[(size_t)j * ldt + j] = nu;
+    sT[j * ld + j] = nu;
+    rd[j] = 1.0 / nu;
   }
+  __syncwarp();
+  // h = T^-T (U^T w)
+  double h0, h1;
+  forward(j + 1, sd + K, h0, h1);
+  if (i0 <= j) out[i0] = h0;
+  if (i1 <= j) out[i1] = h1;
+  // g = T^-1 h, back substitution by columns (column k of T: sT[k * ld + i], i <= k)
+  double r0 = h0, r1 = h1, g0 = 0.0, g1 = 0.0;
+  for (int k = j; k >= 0; --k) {
+    const bool hi = k >= kWarp;
+    const double mine = (hi ? r1 : r0) * rd[k];
+    const double gk = __shfl_sync(0xffffffffu, mine, k & (kWarp - 1));
+    if (lane == (k & (kWarp - 1))) {
+      if (hi) g1 = gk;
+      else g0 = gk;
+    }
+    if (i0 < k) r0 = fma(-sT[k * ld + i0], gk, r0);
+    if (i1 < k) r1 = fma(-sT[k * ld + i1], gk, r1);
+  }
+  if (i0 <= j) g[i0] = g0;
+  if (i1 <= j) g[i1] = g1;
 }
 
 __global__ void dcgs_coef_kernel(int j, const double* __restrict__ d, double* __restrict__ T,
@@ -1450,6 +1624,26 @@ inline unsigned grid_groups(size_t groups, int gp) {
 
 }  // namespace
 
+// a launch as a programmatic dependent of the previous kernel in the stream
+template <typename... Args, typename... Act>
+int launch_programmatic(void (*kern)(Args...), unsigned grid, cudaStream_t s, Act&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, std::forward<Act>(args)...);
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, "cudaLaunchKernelEx", __FILE__, __LINE__);
+    return MSP_ERR_CUDA;
+  }
+  return MSP_OK;
+}
+
 #define MSP_B_SWITCH(b, ...)  \
   switch (b) {                 \
     case 1: { constexpr int B_ = 1; __VA_ARGS__; } break; \
@@ -1522,6 +1716,24 @@ int launch_bgs_colour(int b, int r0, int r1, const int* rp, const int* ci, const
                       const T* aN, const T* y, T* w, bool lower_only, bool zero_pressure,
                       cudaStream_t s, const unsigned char* rmask, LongRows lr) {
   if (r1 <= r0 || b < 2) return MSP_OK;
+  if (lr.n > 0 && lr.n == r1 - r0) {  // a colour of long rows only (the well rows)
+    switch (b) {
+#define MSP_BGS_LONG_CASE(BB)                                                                  \
+  case BB:                                                                                     \
+    return launch_programmatic(bgs_long_colour_kernel<BB, T, true>, (unsigned)(r1 - r0), s, r0, \
+                               rp, ci, dpos, aN, y, w, lower_only, zero_pressure, rmask);
+      MSP_BGS_LONG_CASE(2)
+      MSP_BGS_LONG_CASE(3)
+      MSP_BGS_LONG_CASE(4)
+      MSP_BGS_LONG_CASE(5)
+      MSP_BGS_LONG_CASE(6)
+      MSP_BGS_LONG_CASE(7)
+      MSP_BGS_LONG_CASE(8)
+#undef MSP_BGS_LONG_CASE
+      default:
+        return MSP_ERR_ARG;
+    }
+  }
   switch (b) {
 #define MSP_BGS_CASE(BB)                                                                   \
   case BB: {                                                                               \
@@ -1567,6 +1779,13 @@ int launch_bilu_fwd(int b, int r0, int r1, const int* rp, const int* ci, const i
                     const T* lu, const T* r, T* y, cudaStream_t s, const unsigned char* rmask,
                     LongRows lr) {
   if (r1 <= r0) return MSP_OK;
+  if (lr.n > 0 && lr.n == r1 - r0) {  // a colour of long rows only (the well rows)
+    MSP_B_SWITCH(b, {
+      MSP_TRY(launch_programmatic(bilu_fwd_long_colour_kernel<B_, T, true>, (unsigned)(r1 - r0),
+                                  s, r0, rp, ci, dpos, lu, r, y, rmask));
+    });
+    return MSP_OK;
+  }
   MSP_B_SWITCH(b, {
     const unsigned grid = with_long_rows(grid_groups(r1 - r0, Gp<B_>::v), lr.n);
     bilu_fwd_kernel<B_, T><<<grid, kThreads, 0, s>>>(r0, r1, rp, ci, dpos, lu, r, y, rmask,
@@ -1580,6 +1799,13 @@ int launch_bilu_bwd(int b, int r0, int r1, const int* rp, const int* ci, const i
                     const T* lu, const T* uinv, const T* y, T* x, T* w, cudaStream_t s,
                     const unsigned char* rmask, LongRows lr) {
   if (r1 <= r0) return MSP_OK;
+  if (lr.n > 0 && lr.n == r1 - r0) {  // a colour of long rows only (the well rows)
+    MSP_B_SWITCH(b, {
+      MSP_TRY(launch_programmatic(bilu_bwd_long_colour_kernel<B_, T, true>, (unsigned)(r1 - r0),
+                                  s, r0, rp, ci, dpos, lu, uinv, y, x, w, rmask));
+    });
+    return MSP_OK;
+  }
   MSP_B_SWITCH(b, {
     const unsigned grid = with_long_rows(grid_groups(r1 - r0, Gp<B_>::v), lr.n);
     bilu_bwd_kernel<B_, T><<<grid, kThreads, 0, s>>>(r0, r1, rp, ci, dpos, lu, uinv, y, x, w,
@@ -1626,25 +1852,6 @@ int launch_csr_gs_colour(int r0, int r1, const int* rp, const int* ci, const T* 
   return launch_status();
 }
 
-// a launch as a programmatic dependent of the previous kernel in the stream
-template <typename... Args, typename... Act>
-int launch_programmatic(void (*kern)(Args...), unsigned grid, cudaStream_t s, Act&&... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kThreads);
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, std::forward<Act>(args)...);
-  if (e != cudaSuccess) {
-    set_last_cuda_error(e, "cudaLaunchKernelEx", __FILE__, __LINE__);
-    return MSP_ERR_CUDA;
-  }
-  return MSP_OK;
-}
 
 // lanes per row of the ELL kernels by default (measured: one lane per 4 slots, 8 at most)
 int ell_default_tpr(int K) { return K <= 8 ? 2 : (K <= 16 ? 4 : 8); }
@@ -1827,7 +2034,7 @@ int launch_reduce_partials_strided(int K, int nblocks, int stride, const double*
 
 int launch_dcgs_coef(int j, const double* d, double* T, int ldt, double* g, double* out,
                      cudaStream_t s) {
-  if (j < 0 || j + 2 > kMaxK || j + 1 > ldt) return MSP_ERR_ARG;
+  if (j < 0 || j >= kMaxRestart || j + 2 > kMaxK || j + 1 > ldt) return MSP_ERR_ARG;
   dcgs_coef_kernel<<<1, kWarp, 0, s>>>(j, d, T, ldt, g, out);
   return launch_status();
 }
@@ -1930,7 +2137,7 @@ int launch_dcgs_coef_batch(int B, int j, const int* active, const double* d, int
                            double* T, int tstride, int ldt, double* g, int gstride, double* out,
                            int ostride, cudaStream_t s) {
   if (B <= 0) return MSP_OK;
-  if (j < 0 || j + 2 > kMaxK || j + 1 > ldt) return MSP_ERR_ARG;
+  if (j < 0 || j >= kMaxRestart || j + 2 > kMaxK || j + 1 > ldt) return MSP_ERR_ARG;
   dcgs_coef_batch_kernel<<<B, kWarp, 0, s>>>(j, active, d, dstride, T, tstride, ldt, g, gstride,
                                              out, ostride);
   return launch_status();

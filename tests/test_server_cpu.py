@@ -186,23 +186,31 @@ def test_first_value_update_is_charged_before_it_runs():
                 bytes_out[0] = self.alive[key]
             return st
 
-    rec = Staging(run_s=0.005, bytes_of=lambda key: est - 1000 - copy)
     budget = 2 * est - copy // 2
-    S = _native.msp_server_create(1, budget, None, 0, rec.fn)
-    keep, tickets = [], []
-    for key in (0, 1, 0, 1):
-        req, arrays = _request(key, 0, nb=nb, nnzb=nnzb)
-        keep.append(arrays)
-        tickets.append(_native.msp_server_submit(S, req))
-    results = [_native.msp_server_wait(S, t, 30.0) for t in tickets]
-    stats = _native.msp_server_get_stats(S)
-    released = [k for e, k, *_ in rec.log if e == "release"]
-    _native.msp_server_free(S)
-    assert all(r["status"] == 0 for r in results)
-    assert [r["setup"] for r in results] == [1, 1, 0, 0]
-    assert released == [0]
-    assert stats["peak_charged_bytes"] <= budget
-    assert rec.max_alive <= budget
+
+    def run(keys):
+        rec = Staging(run_s=0.005, bytes_of=lambda key: est - 1000 - copy)
+        grown.clear()
+        S = _native.msp_server_create(1, budget, None, 0, rec.fn)
+        keep, tickets = [], []
+        for key in keys:
+            req, arrays = _request(key, 0, nb=nb, nnzb=nnzb)
+            keep.append(arrays)
+            tickets.append(_native.msp_server_submit(S, req))
+        results = [_native.msp_server_wait(S, t, 30.0) for t in tickets]
+        stats = _native.msp_server_get_stats(S)
+        released = [k for e, k, *_ in rec.log if e == "release"]
+        _native.msp_server_free(S)
+        assert all(r["status"] == 0 for r in results)
+        assert stats["peak_charged_bytes"] <= budget
+        assert rec.max_alive <= budget
+        return [r["setup"] for r in results], released
+
+    # key 0 is idle with nothing queued when key 1 updates: it is released
+    assert run((0, 1, 0, 1)) == ([1, 1, 0, 0], [0])
+    # key 0 has a request queued (with its pattern) and nothing runs: it is released all
+    # the same and set up again by that request (which in turn releases the idle key 1)
+    assert run((0, 1, 0, 1, 0)) == ([1, 1, 0, 0, 1], [0, 1])
 
 
 def test_oversized_request_rejected_and_bad_arguments():
