@@ -682,9 +682,9 @@ def run_reference(args):
     value = 1.0 / (setup_frac * setup_s + its_mean * t_it)
     wall = time.perf_counter() - t0
     sample = ("oracle on the full %dx%dx%d matrix: SETUP once (%.1f s), one full solve to "
-              "1e-6 (%d iterations), then %d timed single Arnoldi iterations (median %.3f s, "
-              "solve capped at 2 minus capped at 1); solves/s = 1 / (%.2f * setup + %d "
-              "iterations)" % (args.nx, args.ny, args.nz, setup_s, its_mean, args.steps, t_it,
+              "1e-6 (%d iterations), then %d timed single Arnoldi iterations (each a solve "
+              "capped at 2 iterations minus one capped at 1; median %.3f s); solves/s = "
+              "1 / (%.2f * setup + %d iterations)" % (args.nx, args.ny, args.nz, setup_s, its_mean, args.steps, t_it,
                                setup_frac, its_mean))
     from synthetic import grid_spe10
     a = grid_spe10(seed=2209, nx=args.nx, ny=args.ny, nz=args.nz)
