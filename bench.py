@@ -109,6 +109,9 @@ def parse():
                         "rate divided by the mean Newton steps per reservoir)")
     p.add_argument("--serve-slots", type=int, nargs="+", default=[1, 4])
     p.add_argument("--serve-budget-gb", type=float, default=150.0)
+    p.add_argument("--latency", action="store_true",
+                   help="latency of single solves of the small 16x16x8, b = 3 system (C1: "
+                        "launch- and latency-bound; p50/p99 over --steps solves)")
     p.add_argument("--batch", action="store_true",
                    help="batched instances: many uneven systems stacked block-diagonally and "
                         "solved together, against the same systems one at a time")
@@ -1066,8 +1069,75 @@ def run_batch(args):
     print(json.dumps(out))
 
 
+def run_latency(args):
+    """Latency of one solve of the small system (16x16x8 cells, b = 3, no wells, RHS N(0,1)):
+    SETUP once, then `steps` solves of the same system timed one by one with CUDA events on
+    the solver stream (device-resident inputs) and, through the host-buffer entry points,
+    with the host clock (rhs in, x out)."""
+    import torch
+
+    import paper_2208_08594_gb300 as msp
+    from synthetic import grid_small
+    a = grid_small()
+    rng = np.random.default_rng(2208)
+    rhs = rng.normal(size=a.n)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    prec = msp.MSP_PRECISION_FP32 if args.precision == "fp32" else msp.MSP_PRECISION_FP64
+    t0 = time.perf_counter()
+    s = msp.Solver(a.nb, a.b, torch.from_numpy(a.row_ptr).to(dev),
+                   torch.from_numpy(a.col_idx).to(dev),
+                   torch.from_numpy(a.values.reshape(-1)).to(dev), mu=args.mu, precision=prec)
+    torch.cuda.synchronize()
+    setup_ms = 1000.0 * (time.perf_counter() - t0)
+    g = torch.from_numpy(rhs).to(dev)
+    x = torch.zeros(a.n, dtype=torch.float64, device=dev)
+    for _ in range(max(args.warmup, 3)):
+        s.solve(g, x, TOL)
+    dev_ms, its = [], []
+    msp.msp_stats_reset()
+    msp.msp_stats_enable(1)
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = s.solve(g, x, TOL)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dev_ms.append(e0.elapsed_time(e1))
+        its.append(info["iterations"])
+    launches = msp.msp_stats_launches()
+    msp.msp_stats_enable(0)
+    host_ms = []
+    xh = np.zeros(a.n)
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        s.solve_host(rhs, xh, TOL)
+        host_ms.append(1000.0 * (time.perf_counter() - t))
+    s.close()
+    res = a.to_scipy() @ xh - rhs
+    out = {"metric": "solve latency, 16x16x8 cells x3 (C1)", "unit": "ms",
+           "value": round(float(np.percentile(dev_ms, 50)), 4), "higher_is_better": False,
+           "n_gpus": 1, "steps": args.steps, "dtype": "f64" if prec == msp.MSP_PRECISION_FP64
+           else "f32-precond/f64-krylov", "data": "synthetic",
+           "config": {"workload": "16x16x8 box, b = 3, ln k ~ N(0,1), no wells, RHS ~ N(0,1)",
+                      "block_rows": a.nb, "nnzb": a.nnzb, "tol": TOL, "mu": args.mu},
+           "p50_ms": round(float(np.percentile(dev_ms, 50)), 4),
+           "p99_ms": round(float(np.percentile(dev_ms, 99)), 4),
+           "mean_ms": round(float(np.mean(dev_ms)), 4),
+           "iterations": sorted(set(its)), "launches_per_solve": launches / args.steps,
+           "host_buffers": {"p50_ms": round(float(np.percentile(host_ms, 50)), 4),
+                            "p99_ms": round(float(np.percentile(host_ms, 99)), 4)},
+           "true_rel_residual": float(np.linalg.norm(res) / np.linalg.norm(rhs)),
+           "setup_ms": round(setup_ms, 1)}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
+    if args.latency:
+        run_latency(args)
+        return
     if args.batch:
         run_batch(args)
         return
