@@ -124,23 +124,24 @@ int launch_cast_d2f(size_t n, const double* in, float* out, cudaStream_t s);
 int launch_cast_f2d(size_t n, const float* in, double* out, cudaStream_t s);
 
 // ---------------- Krylov (FP64) ----------------
-// partial[blk * kmax + k] = sum over this block's rows of V[k][i] * w[i], k < K
-// (gate: optional device flag; the kernel does nothing when *gate == 0)
-int launch_multi_dot(size_t n, const double* V, size_t ldv, int K, const double* w,
-                     double* partial, int nblocks, cudaStream_t s, const int* gate = nullptr);
-// out[k] = sum_b partial[b * kmax + k] (fixed order), k < K;  accumulate: out[k] += ...
-// one-pass Gram-Schmidt of FGMRES: dots of V[0..K) with two vectors (partials of block b at
-// b * 2 * kKrylovMaxK: [0, K) against x0, [K, 2K) against x1), strided reduction, and the
-// small triangular solves of one step (kernel comments in solve_kernels.cu)
-int krylov_dot2_blocks();
-int launch_multi_dot2(size_t n, const double* V, size_t ldv, int K, const double* x0,
-                      const double* x1, double* partial, int nblocks, cudaStream_t s);
+// one-pass Gram-Schmidt of FGMRES: dots of V[0..K) with one vector, strided reductions, and
+// the small triangular solves of one step (kernel comments in solve_kernels.cu)
+// out[k] = sum_b partial[b * stride + k], k < K; with jsel (device index j, K ignored):
+// k <= j, then *jsel = j + 1 (unchanged when j < 0)
 int launch_reduce_partials_strided(int K, int nblocks, int stride, const double* partial,
-                                   double* out, cudaStream_t s);
+                                   double* out, cudaStream_t s, int* jsel = nullptr);
+// *p = v in stream order (a kernel, so that it never waits behind host copies)
+int launch_set_int(int* p, int v, cudaStream_t s);
+// partial[b * stride + k] = block b's share of V_k . x, k < K; with jsel (device index j),
+// K = j + 1 and x = V_j at run time (nothing when j < 0); stride <= kKrylovMaxK
+int launch_multi_dot1(size_t n, const double* V, size_t ldv, int K, const double* x,
+                      double* partial, int stride, int nblocks, cudaStream_t s,
+                      const int* jsel = nullptr);
 int launch_dcgs_coef(int j, const double* d, double* T, int ldt, double* g, double* out,
                      cudaStream_t s);
 int launch_dcgs_finalize(int j1, const double* d, double* T, int ldt, double* out,
                          cudaStream_t s);
+// out[k] = sum_b partial[b * kmax + k] (fixed order), k < K;  accumulate: out[k] += ...
 int launch_reduce_partials(int K, int nblocks, const double* partial, double* out,
                            bool accumulate, cudaStream_t s, const int* gate = nullptr);
 // w -= sum_k h[k] V[k]; partial[blk] = sum of w_new^2 over the block

@@ -113,10 +113,12 @@ int site_index(const char* name) {
 }
 
 // algorithmic bytes known only after a launch (device-side decisions) for a timed site
-void stats_add_bytes(const char* site, double bytes) {
+void stats_add_bytes(const char* site, double bytes, double flops = 0.0) {
   if (g_stats_mode < 2) return;
   std::lock_guard<std::mutex> lk(g_stats_mu);
-  g_sites[site_index(site)].bytes += bytes;
+  auto& st = g_sites[site_index(site)];
+  st.bytes += bytes;
+  st.flops += flops;
 }
 
 // fold finished timings into the sites (waits for the recorded events)
@@ -430,6 +432,15 @@ struct msp_handle_s {
   bool graph_timed = false;      // captured with event nodes around every site
   std::vector<msp::GraphProbe> graph_probes;
   msp::DevBuf<double> pg64, pw64;
+  // the single solve's dot products of the basis against its newest vector u_j run inside
+  // the preconditioner's graph, on a branch beside the coarse AMG levels: j is read from
+  // dot_j (-1: none) and the sums land in gs_d[0..j]
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  msp::DevBuf<int> dot_j;
+  msp::DevBuf<double> partial_u;
+  bool dot_launched = false, dot_branch = false;  // during one application
+  int dot_j_dev = -1;  // what dot_j holds once the enqueued work has run (kDotUnknown: not known)
   // autotuned lanes per row of the ELL kernels, per (level, slots per row)
   std::map<std::pair<int, int>, std::pair<int, int>> tuned;
   // adaptive setup
@@ -459,6 +470,8 @@ namespace msp {
 namespace {
 
 void drop_graph(msp_handle h);
+constexpr int kDotUnknown = -2;  // msp_handle_s::dot_j_dev when a write may not have run
+
 int permute_pattern(msp_handle h, int n, const int* rp, const int* ci, int nnz, const int* iperm,
                     DevBuf<int>& brp, DevBuf<int>& bci, DevBuf<int>& src, cudaStream_t s);
 
@@ -1156,6 +1169,45 @@ const char* level_site(const char* prefix, int l) {
   return p->c_str();
 }
 
+// The dot products u_k . u_j, k <= j, of the single solve's step j (j = *dot_j; nothing when
+// -1) into gs_d[0..j]; *dot_j then moves on to j + 1, so consecutive steps need no write.
+// They need only the basis, so they run while the preconditioner is applied to u_j: on a
+// branch of the captured graph that starts at the first coarse AMG level (whose
+// latency-bound sweeps leave most of the GPU idle) — on small systems, whose every launch is
+// latency-bound, at the start of the application — and joins at its end; in order on s
+// when no graph is being captured.
+int basis_dot(msp_handle h, cudaStream_t s, bool branch) {
+  if (h->dot_launched) return MSP_OK;
+  h->dot_launched = true;
+  cudaStream_t d = s;
+  if (branch && t_capturing) {
+    if (!h->side_stream)
+      MSP_CUDA_TRY(cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking));
+    if (!h->ev_fork) MSP_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    if (!h->ev_join) MSP_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    MSP_CUDA_TRY(cudaEventRecord(h->ev_fork, s));
+    MSP_CUDA_TRY(cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0));
+    d = h->side_stream;
+    h->dot_branch = true;
+  }
+  const size_t n = (size_t)h->nb * h->b;
+  // two blocks per SM (half the reduction grid): fast enough to end within the coarse
+  // levels, and leaving most of each SM's registers to the sweeps it runs beside (measured
+  // on the 1.12M-row system: 166.5 ms per solve, against 178.7 with one block per SM and
+  // 171.3 with four)
+  const int nbk = std::min(krylov_blocks(), sm_count() * 2);
+  {
+    Probe pr("krylov_basis_dot", 0.0, d);  // bytes are counted by the caller (j is known there)
+    MSP_TRY(launch_multi_dot1(n, h->V.p, n, 0, nullptr, h->partial_u.p, kKrylovMaxK, nbk, d,
+                              h->dot_j.p));
+    // also moves dot_j on to the next step's index
+    MSP_TRY(launch_reduce_partials_strided(0, nbk, kKrylovMaxK, h->partial_u.p, h->gs_d.p, d,
+                                           h->dot_j.p));
+  }
+  if (d != s) MSP_CUDA_TRY(cudaEventRecord(h->ev_join, d));
+  return MSP_OK;
+}
+
 template <typename T>
 int vcycle(msp_handle h, const PView<T>& P, int l, cudaStream_t s) {
   Level& L = h->levels[l];
@@ -1228,6 +1280,7 @@ int vcycle(msp_handle h, const PView<T>& P, int l, cudaStream_t s) {
     return launch_pgs_no_sweep<T>(n, L.A.rp.p, L.A.ci.p, P.lv[l], L.dpos.p, P.lrd[l], P.lb[l],
                                   P.lt[l], P.lx[l], forward, s);
   };
+  if (l == 1) MSP_TRY(basis_dot(h, s, true));
   if (h->cfg.pre_sweeps <= 0) MSP_CUDA_TRY(cudaMemsetAsync(P.lx[l], 0, n * sizeof(T), s));
   if (natural) {
     for (int sw = 0; sw < h->cfg.pre_sweeps; ++sw) MSP_TRY(natural_sweep(true, sw == 0));
@@ -1375,9 +1428,37 @@ int stage_R(msp_handle h, const PView<T>& P, const T* r, T* w, cudaStream_t s) {
   return MSP_OK;
 }
 
-// w = B g (colour-ordered vectors of nb*b values of type T)
+template <typename T>
+int apply_precond_body(msp_handle h, const PView<T>& P, const T* g, T* w, cudaStream_t s);
+
+// systems of at most this many unknowns start the basis dot products with the application
+constexpr size_t kBasisDotEarly = size_t(1) << 18;
+
+// w = B g (colour-ordered vectors of nb*b values of type T), with the single solve's basis
+// dot products for the step in dot_j on a branch: from the start of the application on
+// small systems, beside the coarse levels on larger ones, at the end (in order) when the
+// preconditioner has no coarse levels
 template <typename T>
 int apply_precond_t(msp_handle h, const PView<T>& P, const T* g, T* w, cudaStream_t s) {
+  h->dot_launched = false;
+  h->dot_branch = false;
+  int st = MSP_OK;
+  if ((size_t)h->nb * h->b <= kBasisDotEarly) st = basis_dot(h, s, true);
+  if (st == MSP_OK) st = apply_precond_body<T>(h, P, g, w, s);
+  if (st == MSP_OK) st = basis_dot(h, s, false);
+  if (h->dot_branch) {
+    h->dot_branch = false;
+    const cudaError_t e = cudaStreamWaitEvent(s, h->ev_join, 0);
+    if (st == MSP_OK && e != cudaSuccess) {
+      set_last_cuda_error(e, "cudaStreamWaitEvent", __FILE__, __LINE__);
+      st = MSP_ERR_CUDA;
+    }
+  }
+  return st;
+}
+
+template <typename T>
+int apply_precond_body(msp_handle h, const PView<T>& P, const T* g, T* w, cudaStream_t s) {
   const size_t n = (size_t)h->nb * h->b;
   switch (h->cfg.precond) {
     case MSP_PREC_NONE:
@@ -1471,7 +1552,24 @@ int capture_graph(msp_handle h) {
 
 // w = B g on FP64 colour-ordered vectors, in the configured precision.  Replays the
 // captured graph, except while every launch is timed (stats mode 2).
-int apply_precond(msp_handle h, const double* g, double* w, cudaStream_t s) {
+int apply_precond_run(msp_handle h, const double* g, double* w, cudaStream_t s);
+
+// dot_j >= 0 (the single solve's step j, g = u_j): the application also leaves the dot
+// products u_k . u_j, k <= j, in gs_d[0..j].  The device index is written only when it does
+// not already hold dot_j (in a cycle, only at its first step).
+int apply_precond(msp_handle h, const double* g, double* w, cudaStream_t s, int dot_j = -1) {
+  if (dot_j < -1 || dot_j + 1 > kKrylovMaxK) return MSP_ERR_ARG;
+  if (h->dot_j_dev != dot_j) {
+    h->dot_j_dev = kDotUnknown;
+    MSP_TRY(launch_set_int(h->dot_j.p, dot_j, s));
+  }
+  h->dot_j_dev = kDotUnknown;
+  MSP_TRY(apply_precond_run(h, g, w, s));
+  h->dot_j_dev = dot_j >= 0 ? dot_j + 1 : -1;
+  return MSP_OK;
+}
+
+int apply_precond_run(msp_handle h, const double* g, double* w, cudaStream_t s) {
   NvtxRange nvtx("msp:precond");
   const size_t n = (size_t)h->nb * h->b;
   const bool fp32 = h->cfg.precision == MSP_PRECISION_FP32;
@@ -1542,6 +1640,10 @@ int alloc_work(msp_handle h) {
   MSP_TRY(h->xperm.alloc(n));
   MSP_TRY(h->rvec.alloc(n));
   MSP_TRY(h->partial.alloc((size_t)krylov_blocks() * 2 * kKrylovMaxK));
+  MSP_TRY(h->partial_u.alloc((size_t)krylov_blocks() * kKrylovMaxK));
+  MSP_TRY(h->dot_j.alloc(1));
+  MSP_CUDA_TRY(cudaMemset(h->dot_j.p, 0xff, sizeof(int)));  // -1
+  h->dot_j_dev = -1;
   MSP_TRY(h->gs_T.alloc((size_t)(m + 2) * (m + 2)));
   MSP_TRY(h->gs_d.alloc(2 * kKrylovMaxK));
   MSP_TRY(h->gs_g.alloc(kKrylovMaxK));
@@ -1583,7 +1685,6 @@ int fgmres(msp_handle h, double tol, int* iters, double* relres, double* relres_
   const size_t n = (size_t)h->nb * h->b;
   const int m = h->cfg.restart;
   const int nbk = krylov_blocks();
-  const int nbk2 = krylov_dot2_blocks();
   const double* bvec = h->bperm.p;
   double* x = h->xperm.p;
   double* V = h->V.p;
@@ -1685,7 +1786,8 @@ int fgmres(msp_handle h, double tol, int* iters, double* relres, double* relres_
       double* vj = V + (size_t)j * n;
       double* zj = Z + (size_t)j * n;
       double* w = V + (size_t)(j + 1) * n;
-      MSP_TRY(apply_precond(h, vj, zj, s));
+      MSP_TRY(apply_precond(h, vj, zj, s, j));  // also gs_d[0..j] = u_k . u_j
+      stats_add_bytes("krylov_basis_dot", (j + 2.0) * n * 8.0, 2.0 * (j + 1) * n);
       {
         Probe pr("krylov_spmv", bsr_bytes(h, 8.0, 1), s, 1, 2.0 * bsr_fmas(h));
         MSP_TRY(launch_bsr_spmv<double>(h->b, h->nb, h->rp.p, h->ci.p, h->vals.p, zj, nullptr, w,
@@ -1695,11 +1797,11 @@ int fgmres(msp_handle h, double tol, int* iters, double* relres, double* relres_
       ++it;
       const int K = j + 2;  // u_0 .. u_j and w
       {
-        Probe pr("krylov_multi_dot", (double)K * n * 8.0, s, 1, 4.0 * K * n);
-        MSP_TRY(launch_multi_dot2(n, V, n, K, vj, w, h->partial.p, nbk2, s));
+        Probe pr("krylov_multi_dot", (double)(K + 1) * n * 8.0, s, 1, 2.0 * K * n);
+        MSP_TRY(launch_multi_dot1(n, V, n, K, w, h->partial.p, kKrylovMaxK, nbk, s));
       }
-      MSP_TRY(launch_reduce_partials_strided(2 * K, nbk2, 2 * kKrylovMaxK, h->partial.p,
-                                             h->gs_d.p, s));
+      MSP_TRY(launch_reduce_partials_strided(K, nbk, kKrylovMaxK, h->partial.p, h->gs_d.p + K,
+                                             s));
       MSP_TRY(launch_dcgs_coef(j, h->gs_d.p, T, ldt, h->gs_g.p, out, s));
       {
         Probe pr("krylov_multi_axpy", (double)(K + 1) * n * 8.0, s, 1, 2.0 * K * n);
@@ -1747,7 +1849,7 @@ int fgmres(msp_handle h, double tol, int* iters, double* relres, double* relres_
         // column j final now: column j + 1 of T from the dot products of u_{j+1}
         {
           Probe pr("krylov_finalize_dot", (double)(j + 2) * n * 8.0, s, 1, 2.0 * (j + 2) * n);
-          MSP_TRY(launch_multi_dot(n, V, n, j + 2, w, h->partial.p, nbk, s));
+          MSP_TRY(launch_multi_dot1(n, V, n, j + 2, w, h->partial.p, kKrylovMaxK, nbk, s));
         }
         MSP_TRY(launch_reduce_partials(j + 2, nbk, h->partial.p, h->gs_d.p, false, s));
         MSP_TRY(launch_dcgs_finalize(j + 1, h->gs_d.p, T, ldt, out, s));
@@ -2225,6 +2327,9 @@ void destroy(msp_handle h) {
   if (!h) return;
   drop_graph(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->side_stream) cudaStreamDestroy(h->side_stream);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->h_flags) cudaFreeHost(h->h_flags);
   if (h->h_pin) cudaFreeHost(h->h_pin);
   if (h->h_bpin) cudaFreeHost(h->h_bpin);

@@ -1013,121 +1013,91 @@ __device__ __forceinline__ double transpose_sum8(double (&a)[8], int lane) {
   return r;
 }
 
-__global__ void __launch_bounds__(kThreads) multi_dot_kernel(size_t n, const double* __restrict__ V,
-                                                            size_t ldv, int K,
-                                                            const double* __restrict__ w,
-                                                            double* __restrict__ partial,
-                                                            const int* __restrict__ gate) {
+__global__ void set_int_kernel(int* __restrict__ p, int v) { *p = v; }
+
+// One right-hand vector, four elements in flight per thread: partial[b * stride + k] =
+// V_k . x over block b's share, k < K.  With `jsel` (a device index j, read at run time) the
+// kernel takes K = j + 1 and x = V_j, the basis against its newest vector, so that one
+// captured launch serves every step; j < 0 makes it return at once.  The basis is read
+// with evict-first loads: it is streamed once, and the kernel may run beside other work
+// whose data should stay in L2.
+__global__ void __launch_bounds__(kThreads) multi_dot1_kernel(size_t n, const double* __restrict__ V,
+                                                             size_t ldv, int K,
+                                                             const double* __restrict__ x,
+                                                             double* __restrict__ partial,
+                                                             int stride,
+                                                             const int* __restrict__ jsel) {
   static_assert(kDotChunk == 8 && kThreads == 256, "the reduction below is for 8 x 8 warps");
   __shared__ double sh[kThreads / kWarp][kDotChunk];
-  if (gate && *gate == 0) return;
-  const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp;
-  for (int k0 = 0; k0 < K; k0 += kDotChunk) {
-    const int kc = min(kDotChunk, K - k0);
-    double acc[kDotChunk];
-#pragma unroll
-    for (int k = 0; k < kDotChunk; ++k) acc[k] = 0.0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x) {
-      const double wi = w[i];
-#pragma unroll
-      for (int k = 0; k < kDotChunk; ++k)
-        if (k < kc) acc[k] = fma(__ldg(V + (size_t)(k0 + k) * ldv + i), wi, acc[k]);
-    }
-    const double r = transpose_sum8(acc, lane);
-    __syncthreads();  // the previous chunk's reads of sh are done
-    if ((lane & 3) == 0) sh[wid][((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)] = r;
-    __syncthreads();
-    if (threadIdx.x < kc) {  // fixed order over the warps
-      double t = 0.0;
-#pragma unroll
-      for (int w2 = 0; w2 < kThreads / kWarp; ++w2) t += sh[w2][threadIdx.x];
-      partial[(size_t)blockIdx.x * kMaxK + k0 + threadIdx.x] = t;
-    }
+  if (jsel) {
+    const int j = *jsel;
+    if (j < 0 || j + 1 > stride) return;  // uniform over the grid
+    K = j + 1;
+    x = V + (size_t)j * ldv;
   }
-}
-
-// Two right-hand vectors at once: partial[b][k] = V_k . x0 and partial[b][K + k] = V_k . x1
-// for k < K (block b's share; row stride 2 * kMaxK).  The one-pass Gram-Schmidt of FGMRES
-// needs the basis against the newest basis vector and against the new Krylov vector: one
-// read of the basis serves both (two FMAs per element of V read).
-__global__ void __launch_bounds__(kThreads) multi_dot2_kernel(size_t n, const double* __restrict__ V,
-                                                             size_t ldv, int K,
-                                                             const double* __restrict__ x0,
-                                                             const double* __restrict__ x1,
-                                                             double* __restrict__ partial) {
-  static_assert(kDotChunk == 8 && kThreads == 256, "the reduction below is for 8 x 8 warps");
-  __shared__ double sh[2][kThreads / kWarp][kDotChunk];
   const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp;
   const int slot = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
   for (int k0 = 0; k0 < K; k0 += kDotChunk) {
     const int kc = min(kDotChunk, K - k0);
-    double a0[kDotChunk], a1[kDotChunk];
+    double a[kDotChunk];
 #pragma unroll
-    for (int k = 0; k < kDotChunk; ++k) a0[k] = a1[k] = 0.0;
-    // four elements per thread per trip (a grid-stride apart): four times the loads in
-    // flight of one element at a time, measured 1.3-2x faster (the FP64 pipe stays fed)
+    for (int k = 0; k < kDotChunk; ++k) a[k] = 0.0;
     const size_t G = (size_t)gridDim.x * blockDim.x;
     size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     for (; i + 3 * G < n; i += 4 * G) {
-      double u[4], w[4];
+      double u[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        u[q] = x0[i + q * G];
-        w[q] = x1[i + q * G];
-      }
+      for (int q = 0; q < 4; ++q) u[q] = x[i + q * G];
 #pragma unroll
       for (int k = 0; k < kDotChunk; ++k)
         if (k < kc) {
           double vk[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) vk[q] = __ldg(V + (size_t)(k0 + k) * ldv + i + q * G);
+          for (int q = 0; q < 4; ++q) vk[q] = __ldcs(V + (size_t)(k0 + k) * ldv + i + q * G);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            a0[k] = fma(vk[q], u[q], a0[k]);
-            a1[k] = fma(vk[q], w[q], a1[k]);
-          }
+          for (int q = 0; q < 4; ++q) a[k] = fma(vk[q], u[q], a[k]);
         }
     }
     for (; i < n; i += G) {
-      const double u = x0[i], w = x1[i];
+      const double u = x[i];
 #pragma unroll
       for (int k = 0; k < kDotChunk; ++k)
-        if (k < kc) {
-          const double vk = __ldg(V + (size_t)(k0 + k) * ldv + i);
-          a0[k] = fma(vk, u, a0[k]);
-          a1[k] = fma(vk, w, a1[k]);
-        }
+        if (k < kc) a[k] = fma(__ldcs(V + (size_t)(k0 + k) * ldv + i), u, a[k]);
     }
-    const double r0 = transpose_sum8(a0, lane);
-    const double r1 = transpose_sum8(a1, lane);
+    const double r = transpose_sum8(a, lane);
     __syncthreads();  // the previous chunk's reads of sh are done
-    if ((lane & 3) == 0) {
-      sh[0][wid][slot] = r0;
-      sh[1][wid][slot] = r1;
-    }
+    if ((lane & 3) == 0) sh[wid][slot] = r;
     __syncthreads();
-    if (threadIdx.x < 2 * kc) {  // fixed order over the warps
-      const int r = threadIdx.x / kc, k = threadIdx.x % kc;
+    if (threadIdx.x < kc) {  // fixed order over the warps
       double t = 0.0;
 #pragma unroll
-      for (int w2 = 0; w2 < kThreads / kWarp; ++w2) t += sh[r][w2][k];
-      partial[(size_t)blockIdx.x * (2 * kMaxK) + r * K + k0 + k] = t;
+      for (int w2 = 0; w2 < kThreads / kWarp; ++w2) t += sh[w2][threadIdx.x];
+      partial[(size_t)blockIdx.x * stride + k0 + threadIdx.x] = t;
     }
   }
 }
 
-// out[k] = sum over blocks of partial[b * stride + k], k < K (one warp per output)
+// out[k] = sum over blocks of partial[b * stride + k], k < K (one warp per output, the
+// warps of the grid striding over the outputs); with `jsel` (launched as one block),
+// K = *jsel + 1 (nothing when *jsel < 0) and, once every thread has read it, the index
+// moves on to the next step: *jsel = j + 1
 __global__ void reduce_partials_strided_kernel(int K, int nblocks, int stride,
                                                const double* __restrict__ partial,
-                                               double* __restrict__ out) {
-  const int k = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
-  const int lane = threadIdx.x % kWarp;
-  if (k >= K) return;
-  double s = 0.0;
-  for (int b = lane; b < nblocks; b += kWarp) s += partial[(size_t)b * stride + k];
-  s = group_sum<kWarp>(s);
-  if (lane == 0) out[k] = s;
+                                               double* __restrict__ out,
+                                               int* __restrict__ jsel) {
+  const int j = jsel ? *jsel : 0;
+  if (jsel) K = j < 0 ? 0 : min(j + 1, stride);
+  const int wpb = blockDim.x / kWarp, lane = threadIdx.x % kWarp;
+  for (int k = blockIdx.x * wpb + threadIdx.x / kWarp; k < K; k += gridDim.x * wpb) {
+    double s = 0.0;
+    for (int b = lane; b < nblocks; b += kWarp) s += partial[(size_t)b * stride + k];
+    s = group_sum<kWarp>(s);
+    if (lane == 0) out[k] = s;
+  }
+  if (jsel) {
+    __syncthreads();  // every thread has read *jsel
+    if (threadIdx.x == 0 && j >= 0) *jsel = j + 1;
+  }
 }
 
 // One-pass Gram-Schmidt of FGMRES step j (one warp, j < 64).  The
@@ -1993,42 +1963,32 @@ int launch_cast_f2d(size_t n, const float* in, double* out, cudaStream_t s) {
 
 int krylov_blocks() { return sm_count() * 4; }
 
-// Blocks of the two-vector multi-dot: as many as fit on the SMs at once (its 16
-// accumulators and four elements in flight per thread take more registers than four
-// blocks of 256 threads per SM leave; a fourth block per SM would run as a second wave).
-int krylov_dot2_blocks() {
-  static const int cached = [] {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, multi_dot2_kernel, kThreads, 0) !=
-            cudaSuccess ||
-        per_sm < 1)
-      per_sm = 2;
-    return sm_count() * std::min(per_sm, 4);
-  }();
-  return cached;
-}
-
-int launch_multi_dot(size_t n, const double* V, size_t ldv, int K, const double* w,
-                     double* partial, int nblocks, cudaStream_t s, const int* gate) {
-  if (K > kMaxK) return MSP_ERR_ARG;
-  multi_dot_kernel<<<nblocks, kThreads, 0, s>>>(n, V, ldv, K, w, partial, gate);
-  return launch_status();
-}
-
-int launch_multi_dot2(size_t n, const double* V, size_t ldv, int K, const double* x0,
-                      const double* x1, double* partial, int nblocks, cudaStream_t s) {
-  if (K > kMaxK) return MSP_ERR_ARG;
-  multi_dot2_kernel<<<nblocks, kThreads, 0, s>>>(n, V, ldv, K, x0, x1, partial);
-  return launch_status();
-}
-
 int launch_reduce_partials_strided(int K, int nblocks, int stride, const double* partial,
-                                   double* out, cudaStream_t s) {
+                                   double* out, cudaStream_t s, int* jsel) {
+  if (jsel) {  // one block: its threads all read the index before it moves on
+    if (stride > kMaxK) return MSP_ERR_ARG;
+    reduce_partials_strided_kernel<<<1, 32 * kWarp, 0, s>>>(0, nblocks, stride, partial, out,
+                                                            jsel);
+    return launch_status();
+  }
   if (K <= 0) return MSP_OK;
   if (K > stride) return MSP_ERR_ARG;
   const int wpb = 4;
   reduce_partials_strided_kernel<<<(K + wpb - 1) / wpb, wpb * kWarp, 0, s>>>(K, nblocks, stride,
-                                                                             partial, out);
+                                                                             partial, out, jsel);
+  return launch_status();
+}
+
+int launch_set_int(int* p, int v, cudaStream_t s) {
+  set_int_kernel<<<1, 1, 0, s>>>(p, v);
+  return launch_status();
+}
+
+int launch_multi_dot1(size_t n, const double* V, size_t ldv, int K, const double* x,
+                      double* partial, int stride, int nblocks, cudaStream_t s, const int* jsel) {
+  if (stride > kMaxK || (!jsel && (K > stride || !x))) return MSP_ERR_ARG;
+  if (!jsel && K <= 0) return MSP_OK;
+  multi_dot1_kernel<<<nblocks, kThreads, 0, s>>>(n, V, ldv, K, x, partial, stride, jsel);
   return launch_status();
 }
 

@@ -45,13 +45,13 @@ def test_every_timed_site_maps_to_a_defined_kernel():
 
 def test_kernels_from_sites_groups_by_kernel():
     sites = {"krylov_multi_dot": (139, 20.0, 1e9, 4e9), "krylov_finalize_dot": (5, 1.0, 1e8, 2e8),
+             "krylov_basis_dot": (139, 30.0, 1e9, 2e9),
              "amg_gs_pre_l1": (417, 2.0, 1e8, 0.0), "amg_gs_post_l3": (1390, 5.0, 2e8, 0.0),
              "precond_graph": (139, 200.0, 5e9, 0.0), "setup:galerkin": (1, 30.0, 0.0, 0.0)}
     out = bench.kernels_from_sites(sites)
-    assert out["multi_dot2_kernel"] == [139, 20.0, 1e9, 4e9]
-    assert out["multi_dot_kernel"] == [5, 1.0, 1e8, 2e8]
+    assert out["multi_dot1_kernel"] == [144, 21.0, 1.1e9, 4.2e9]
     assert out["ell_gs_colour_kernel"] == [1807, 7.0, 3e8, 0.0]
-    assert "precond_graph" not in out and len(out) == 3
+    assert "precond_graph" not in out and len(out) == 2
 
 
 def test_roofline_picks_the_binding_roof():

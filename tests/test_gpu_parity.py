@@ -500,3 +500,42 @@ def test_autotuned_tiles_match_oracle_and_persist():
     assert [msp.msp_level_tiles(g.h, l) for l in range(g.num_levels)] == tiles
     assert i2["iterations"] == i1["iterations"] and torch.equal(x1, x2)
     g.close()
+
+
+@pytest.mark.parametrize("where", ["start", "coarse_levels", "end"])
+def test_basis_dots_beside_the_preconditioner_equal_in_order_dots(where):
+    """The single solve's dot products u_k . u_j run on a branch of the preconditioner's
+    graph: from the start of the application on small systems (at most 2^18 unknowns),
+    beside the coarse AMG levels on larger ones, and at the end of the application when
+    there are no coarse levels (stage N alone here).  Without a graph (stats mode 2) the
+    same kernels run in order on the solver's stream.  The reductions are deterministic, so
+    all give the same iterates bit for bit, and with event nodes in the graph (stats mode 3)
+    too; the device's step index, which the kernels move on themselves, stays in step."""
+    if where == "start":
+        a, cfg = grid_spe10(nx=23, ny=17, nz=9), dict(coarse_max=120)
+    else:
+        a = grid_spe10(nx=50, ny=40, nz=35)  # 70,004 block rows, 280,016 unknowns
+        cfg = dict(max_it=45) if where == "coarse_levels" else dict(
+            precond=msp.MSP_PREC_N_ONLY, max_it=45)
+    assert (a.n <= 1 << 18) == (where == "start")
+    rhs = _vec(random_rhs(a, 5))
+    out = []
+    for mode in (0, 2, 3):
+        rp, ci, v = _dev(a)
+        g = msp.Solver(a.nb, a.b, rp, ci, v, **cfg)
+        msp.msp_stats_reset()
+        msp.msp_stats_enable(mode)
+        try:
+            res = []
+            for _ in range(2):  # a second solve starts again from step 0
+                x = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+                info = g.solve(rhs, x, 1e-6)
+                res.append((info["iterations"], x.cpu().numpy()))
+        finally:
+            msp.msp_stats_enable(0)
+            msp.msp_stats_reset()
+            g.close()
+        assert res[0][0] == res[1][0] and np.array_equal(res[0][1], res[1][1])
+        out.append(res[0])
+    assert out[0][0] == out[1][0] == out[2][0]
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][1], out[2][1])
