@@ -363,13 +363,14 @@ __device__ void bm_clear_atomic(const Bitmap3& bm, int r) {
   }
 }
 
+// set bit r where several lanes may set bits concurrently (and nobody clears): the summary
+// bits one and two levels up are set unconditionally (each stands for a non-empty word, which
+// the word now is), so no lane waits for an old value before its next entry
 __device__ void bm_set(const Bitmap3& bm, int r) {
   const int i0 = r >> 5, i1 = r >> 10, i2 = r >> 15;
-  const unsigned o0 = atomicOr(bm.l0 + i0, 1u << (r & 31));
-  if (o0 == 0u) {
-    const unsigned o1 = atomicOr(bm.l1 + i1, 1u << (i0 & 31));
-    if (o1 == 0u) atomicOr(bm.l2 + i2, 1u << (i1 & 31));
-  }
+  atomicOr(bm.l0 + i0, 1u << (r & 31));
+  atomicOr(bm.l1 + i1, 1u << (i0 & 31));
+  atomicOr(bm.l2 + i2, 1u << (i1 & 31));
 }
 
 __device__ __forceinline__ bool in_v(const unsigned* inV, int v) {
@@ -567,10 +568,13 @@ __global__ void __launch_bounds__(64) colouring_kernel(int n, const int* __restr
             kl0 = __ldg(srp + j + 1) - kb0;
           }
           const unsigned bit = 1u << (j & 31);
-          take = (atomicAnd(inV + (j >> 5), ~bit) & bit) != 0u;
+          const unsigned was = atomicAnd(inV + (j >> 5), ~bit);
           // a vertex leaving V also leaves the frontier now, rather than being popped and
-          // dropped later (same picks: the frontier's first vertex still in V)
-          if (take) bm_clear_atomic(bm, j);
+          // dropped later (same picks: the frontier's first vertex still in V).  The frontier
+          // holds vertices of V only, so j's frontier bit is cleared without waiting for the
+          // test above (nothing changes when j was not in V)
+          bm_clear_atomic(bm, j);
+          take = (was & bit) != 0u;
         }
         const unsigned m = __ballot_sync(0xffffffffu, take);
         if (take) wbar[nwbar + __popc(m & ((1u << lane) - 1u))] = j;
