@@ -75,3 +75,35 @@ def test_static_config_is_shared_by_both_arms():
     c = bench.static_config(args, a)
     assert c["cells"] == 120 and c["block_rows"] == 124 and c["nnzb"] == a.nnzb
     assert "R_ij + 3 I" in c["workload"] and "rebalanced" in c["workload"]
+
+
+def _bench(args, env=None):
+    import json
+    import os
+    import subprocess
+    import sys
+    e = dict(os.environ, **(env or {}))
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, cwd=ROOT,
+                       env=e, capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [l for l in p.stdout.splitlines() if l.startswith("{")]
+    return [json.loads(l) for l in lines]
+
+
+def test_reference_arm_prints_the_contract_line_on_rank_0_only():
+    """The reference arm times the oracle on the host cores: one JSON line on rank 0 with the
+    base contract's keys, a cpu_baseline of kind oracle and an e2e without host copies; the
+    other ranks print nothing and exit 0."""
+    args = ["--impl", "reference", "--nx", "6", "--ny", "5", "--nz", "4", "--steps", "2",
+            "--warmup", "1"]
+    (line,) = _bench(args)
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "solves/s"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["config"]["cells"] == 120
+    assert _bench(args, env={"RANK": "1", "WORLD_SIZE": "2"}) == []
